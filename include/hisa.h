@@ -1,0 +1,175 @@
+/* hisa.h -- C-ABI of the GB300 semi-naive Datalog engine (HISA relations).
+ *
+ * The engine evaluates Datalog programs over binary relations of uint32
+ * values to their least fixpoint by semi-naive evaluation, as described in
+ * "Optimizing Datalog for the GPU" (arXiv 2311.02206):
+ *   - rules are Horn clauses over EDB (loaded) and IDB (derived) relations,
+ *     evaluated until no new fact appears (Section 2);
+ *   - every IDB relation keeps the versions new, delta and full; each
+ *     iteration joins, populates delta = new \ full, merges delta into full
+ *     and clears new (Section 5.1 and its evaluation-workflow figure);
+ *   - relations are hash-indexed sorted arrays (Section 4): sorted,
+ *     deduplicated tuples with an open-addressing index over the runs of
+ *     equal join keys, range-probed by the binary join of Algorithm 3;
+ *   - rules with three body atoms run as two binary joins through a
+ *     temporarily materialized relation (Section 5.2);
+ *   - buffers grow eagerly to full + k * delta (Section 5.3).
+ * The library is the paper's "library for parallel relational algebra
+ * kernels" (Section 1) in C form: declare relations, load EDB tuples, add
+ * rules, run to the fixpoint, read IDB relations and per-iteration delta sizes.
+ *
+ * Conventions for every call:
+ *   - A non-negative return is success (HISA_OK); a negative one is an error
+ *     code from hisa_status below; hisa_last_error(ctx) gives a message.
+ *   - "device" pointers are CUDA device pointers on the context's device;
+ *     "host" pointers are ordinary host memory.  The caller owns every buffer
+ *     it passes in; the library owns relation storage, which it allocates
+ *     only through hisa_config.alloc/free (or cudaMallocAsync when NULL).
+ *   - All GPU work is ordered on hisa_config.cuda_stream.  Calls that return
+ *     data to the host synchronise that stream.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - No call traps or aborts: device-side failures (a bounded wait that ran
+ *     out, an exhausted probe sequence) come back as error codes.
+ */
+#ifndef HISA_H_
+#define HISA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hisa_status;
+
+#define HISA_OK 0
+#define HISA_ERR_INVALID_ARG (-1)    /* null pointer, unknown relation, bad rule */
+#define HISA_ERR_ARITY (-2)          /* column count does not match the relation */
+#define HISA_ERR_OOM (-3)            /* allocation failed or HBM budget exceeded */
+#define HISA_ERR_NOT_CONVERGED (-4)  /* max_iters iterations ran without a fixpoint */
+#define HISA_ERR_DEVICE_TIMEOUT (-5) /* a bounded device-side wait expired */
+#define HISA_ERR_CUDA (-6)           /* a CUDA runtime call failed (message in last_error) */
+#define HISA_ERR_UNSUPPORTED (-7)    /* a rule shape this build does not evaluate */
+#define HISA_ERR_STATE (-8)          /* call out of order (e.g. load after run) */
+#define HISA_ERR_CAPACITY (-9)       /* a caller-provided output buffer is too small */
+
+/* Allocator hooks: return a device pointer of at least `bytes` bytes usable on
+ * `stream`, or NULL on failure; free releases one earlier allocation. */
+typedef void* (*hisa_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*hisa_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+#define HISA_FLAG_GRAPH 1u        /* run iterations >= 2 as one CUDA graph with a device-side while loop */
+#define HISA_FLAG_PHASE_TIMES 2u  /* record per-phase CUDA-event times (host-driven loop only) */
+
+typedef struct {
+  hisa_alloc_fn alloc;      /* NULL: cudaMallocAsync from a private pool */
+  hisa_free_fn free;
+  void* user;               /* passed to alloc/free */
+  void* cuda_stream;        /* cudaStream_t for all work; NULL: the legacy default stream */
+  uint64_t hbm_budget_bytes;/* cap on library-owned device memory; 0 = no cap */
+  float load_factor;        /* hash-index load factor; 0 = 0.8 (Section 6.2) */
+  float ebm_k;              /* eager buffer growth factor k of Section 5.3; 0 = 2 */
+  uint32_t max_iters;       /* iteration cap; 0 = 1,000,000 */
+  uint32_t flags;           /* HISA_FLAG_* */
+  int32_t device;           /* CUDA device ordinal; -1 = the current device */
+} hisa_config;
+
+typedef struct hisa_ctx hisa_ctx;
+
+/* Fills `cfg` with the defaults above.  Never fails for a non-null cfg. */
+hisa_status hisa_config_default(hisa_config* cfg);
+
+/* Creates a context on cfg->device (the config is copied).  *out receives the
+ * handle.  Errors: INVALID_ARG (null), CUDA. */
+hisa_status hisa_create(const hisa_config* cfg, hisa_ctx** out);
+
+/* Frees every library-owned buffer and the context.  NULL is accepted. */
+hisa_status hisa_destroy(hisa_ctx* ctx);
+
+/* Declares relation `name` (unique, <= 63 bytes) of the given arity (only 2
+ * is evaluated by this build).  is_idb != 0 marks a derived relation, which
+ * may appear in rule heads; EDB relations are loaded.  *rel_id receives its
+ * id.  Errors: INVALID_ARG (duplicate name), ARITY (arity != 2), STATE. */
+hisa_status hisa_declare_relation(hisa_ctx* ctx, const char* name, uint32_t arity, int is_idb,
+                                  uint32_t* rel_id);
+
+/* Appends n tuples to EDB relation rel_id from column arrays cols[0..arity)
+ * (structure of arrays, uint32 each; device pointers if cols_on_device, else
+ * host).  The library copies them; duplicates are dropped when the relation is
+ * indexed (relations are sets, Section 2).  Allowed until the first hisa_run,
+ * and again after hisa_reset_edb.  Errors: INVALID_ARG, STATE, OOM, CUDA. */
+hisa_status hisa_load_tuples(hisa_ctx* ctx, uint32_t rel_id, const uint32_t* const* cols, uint64_t n,
+                             int cols_on_device);
+
+/* One atom: relation and the variable id bound to each column (variables are
+ * small integers < 16; equal ids mean equal values). */
+typedef struct {
+  uint32_t rel;
+  uint32_t var[2];
+} hisa_atom;
+
+/* head <- body[0], ..., body[n_body-1], neq[0][0] != neq[0][1], ...
+ * 1 <= n_body <= 3; 0 <= n_neq <= 2.  Every head variable must occur in the
+ * body.  Three-atom bodies are evaluated as two binary joins through a
+ * temporarily materialized relation (Section 5.2), which must need at most two
+ * columns. */
+typedef struct {
+  hisa_atom head;
+  uint32_t n_body;
+  hisa_atom body[3];
+  uint32_t n_neq;
+  uint32_t neq[2][2];
+} hisa_rule;
+
+/* Adds a rule.  Errors: INVALID_ARG (unknown relation, EDB head, unbound head
+ * variable), UNSUPPORTED (cross products, more than two Tmp columns), STATE. */
+hisa_status hisa_add_rule(hisa_ctx* ctx, const hisa_rule* rule);
+
+typedef struct {
+  uint32_t iterations;      /* K: iterations that derived a tuple (delta_K > 0) */
+  uint32_t iterations_run;  /* iterations executed, including the final empty one */
+  uint32_t regrows;         /* buffer growth events (Section 5.3) */
+  uint32_t graph_launches;  /* CUDA graph launches of the iteration loop */
+  double ms_total;          /* wall time of the run */
+  double ms_edb;            /* EDB encode, sort, dedup and index build */
+  double ms_join, ms_sort, ms_merge; /* per-phase times (HISA_FLAG_PHASE_TIMES) */
+  uint64_t tuples_joined;   /* sum over iterations of |new| before dedup */
+  uint64_t peak_bytes;      /* peak library-owned device memory */
+} hisa_run_stats;
+
+/* Evaluates all rules to the least fixpoint.  The EDB is encoded, sorted,
+ * deduplicated and indexed first (once; again only after new loads).  IDB
+ * relations start empty on every run.  `stats` may be NULL.  Errors:
+ * NOT_CONVERGED, OOM, DEVICE_TIMEOUT, UNSUPPORTED, CUDA. */
+hisa_status hisa_run(hisa_ctx* ctx, hisa_run_stats* stats);
+
+/* Drops every EDB tuple so new ones can be loaded (rules are kept). */
+hisa_status hisa_reset_edb(hisa_ctx* ctx);
+
+/* Number of tuples of relation rel_id (IDB: after the last run). */
+hisa_status hisa_relation_size(hisa_ctx* ctx, uint32_t rel_id, uint64_t* n);
+
+/* Copies relation rel_id in ascending lexicographic order of (c0, c1) into
+ * cols[0], cols[1] (each with room for `cap` values; device pointers if
+ * cols_on_device).  *n receives the size.  Errors: CAPACITY (cap < size; *n is
+ * still set), INVALID_ARG, CUDA. */
+hisa_status hisa_read_relation(hisa_ctx* ctx, uint32_t rel_id, uint32_t* const* cols, uint64_t cap,
+                               uint64_t* n, int cols_on_device);
+
+/* Per-iteration delta sizes |delta_1| .. |delta_K| of IDB relation rel_id from
+ * the last run, into host array out[cap]; *n_iters receives K.  Errors:
+ * CAPACITY (cap < K; the first cap values are written), INVALID_ARG. */
+hisa_status hisa_delta_counts(hisa_ctx* ctx, uint32_t rel_id, uint64_t* out, uint32_t cap,
+                              uint32_t* n_iters);
+
+/* Static text of a status code. */
+const char* hisa_status_string(hisa_status s);
+
+/* Message of the last error on this context ("" if none). */
+const char* hisa_last_error(hisa_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HISA_H_ */

@@ -85,3 +85,53 @@ def join(outer: np.ndarray, outer_cols, inner: np.ndarray, inner_cols, project):
             if all(o[a] == i[b] for a, b in zip(outer_cols, inner_cols)):
                 out.append([o[c] if side == "o" else i[c] for side, c in project])
     return np.array(out, dtype=np.uint32).reshape(len(out), len(project))
+
+
+# ---- the same definitions on packed codes (c0 << b) | c1 ------------------------------
+
+def decode_codes(codes, b: int) -> np.ndarray:
+    """Packed codes -> (n, 2) tuples."""
+    c = np.asarray(codes, dtype=np.uint64)
+    mask = np.uint64((1 << b) - 1)
+    return np.stack([(c >> np.uint64(b)) & mask, c & mask], axis=1).astype(np.uint32)
+
+
+def encode_rows(rows, b: int, dtype=np.uint64) -> np.ndarray:
+    r = _rows(rows).astype(np.uint64)
+    return ((r[:, 0] << np.uint64(b)) | r[:, 1]).astype(dtype)
+
+
+def sort_codes(codes) -> np.ndarray:
+    """The sorted data array: codes in ascending order (order of tuples)."""
+    return np.sort(np.asarray(codes), kind="stable")
+
+
+def sort_unique_codes(codes) -> np.ndarray:
+    return np.unique(np.asarray(codes))
+
+
+def difference_merge_codes(full, fresh):
+    """(delta, full U delta) on codes: Section 5.1 populate delta, then merge."""
+    full = np.asarray(full)
+    fresh = np.asarray(fresh)
+    delta = np.setdiff1d(np.unique(fresh), full, assume_unique=True)
+    return delta, np.union1d(full, delta)
+
+
+def join_codes(outer, inner, b: int, outer_col: int, proj0: int, proj1: int, neq=None, dtype=np.uint64):
+    """Algorithm 3 on codes: the inner relation joins on its column 0; result
+    sources 0 = outer c0, 1 = outer c1, 2 = inner c0 (the key), 3 = inner c1;
+    ``neq`` = (a, b) keeps results with source a != source b."""
+    o = decode_codes(outer, b).tolist()
+    groups = {}                       # inner tuples by join value, in inner order
+    for k, x in decode_codes(np.sort(np.asarray(inner)), b).tolist():
+        groups.setdefault(k, []).append(x)
+    out = []
+    for t in o:
+        k = t[outer_col]
+        for x in groups.get(k, ()):
+            src = (t[0], t[1], k, x)
+            if neq is not None and src[neq[0]] == src[neq[1]]:
+                continue
+            out.append((src[proj0], src[proj1]))
+    return encode_rows(np.array(out, np.uint32).reshape(len(out), 2), b, dtype)

@@ -1,0 +1,191 @@
+// Shared device-side definitions of the HISA engine (sm_103a).
+//
+// Tuples of a binary relation are stored as packed codes
+//     code = (inst << 2b) | (c0 << b) | c1
+// in the column order of the index (Section 4.2: the join column first, then
+// the others), where b is the bit width of the active domain and inst is the
+// instance id of a batched run (0 otherwise).  Sorting codes as unsigned
+// integers is the lexicographic order of Section 4.2; the join key of an index
+// is code >> b.  Codes are 32-bit when inst_bits + 2b <= 32, else 64-bit.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hisa {
+
+// ---- device-resident control block ---------------------------------------------------
+
+enum : int { kMaxBufs = 96, kMaxCnts = 96 };
+
+// Device error codes (DevState::error).
+enum : uint32_t {
+  kDevOk = 0,
+  kDevTimeout = 1,      // a bounded wait on another tile ran out
+  kDevProbeLimit = 2,   // hash probe sequence exceeded the table size
+  kDevBadState = 3,
+};
+
+struct DBuf {
+  void* ptr;
+  uint64_t cap;  // capacity in elements
+};
+
+// Everything a kernel needs that changes between iterations lives here, so a
+// captured launch sequence stays valid while buffers swap and grow.
+struct DevState {
+  DBuf buf[kMaxBufs];
+  uint64_t cnt[kMaxCnts];
+  uint64_t need[kMaxBufs];     // required capacity when a stage overflowed
+  uint32_t overflow;           // bit s set: stage s must be re-run after regrow
+  uint32_t error;              // kDev* code
+  uint32_t epoch;              // tag of the current look-back chain
+  uint32_t go;                 // fixpoint loop condition
+  uint32_t iter;               // iterations committed
+  uint32_t max_iters;
+  uint32_t tile_ctr[16];       // per-kernel tile counters (reset by ctrl kernels)
+  uint64_t aux[16];
+};
+
+// ---- look-back status words: [63:44] epoch | [43:42] flag | [41:0] value --------------
+
+enum : uint64_t { kFlagAgg = 1, kFlagIncl = 2 };
+__device__ __forceinline__ uint64_t lb_pack(uint32_t epoch, uint64_t flag, uint64_t v) {
+  return (uint64_t(epoch & 0xFFFFF) << 44) | (flag << 42) | (v & ((1ull << 42) - 1));
+}
+__device__ __forceinline__ uint64_t lb_flag(uint64_t w, uint32_t epoch) {
+  return (uint32_t(w >> 44) == (epoch & 0xFFFFF)) ? ((w >> 42) & 3) : 0;
+}
+__device__ __forceinline__ uint64_t lb_value(uint64_t w) { return w & ((1ull << 42) - 1); }
+
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Polls allowed while waiting on a predecessor tile before the kernel gives up,
+// records kDevTimeout and continues with a zero contribution (results are then
+// invalid and the host reports HISA_ERR_DEVICE_TIMEOUT).
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Warp-cooperative decoupled look-back (Merrill & Garland, "Single-pass
+// parallel prefix scan with decoupled look-back", 2016).  Called by one full
+// warp; returns the exclusive prefix of `tile` and publishes its inclusive one.
+__device__ __forceinline__ uint64_t lookback_warp(uint64_t* status, uint64_t tile, uint64_t local,
+                                                  uint32_t epoch, uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) {
+    if (lane == 0) st_release(&status[0], lb_pack(epoch, kFlagIncl, local));
+    return 0;
+  }
+  if (lane == 0) st_release(&status[tile], lb_pack(epoch, kFlagAgg, local));
+  uint64_t excl = 0;
+  int64_t pos = int64_t(tile) - 1;
+  uint32_t spins = 0;
+  while (true) {
+    const int64_t j = pos - lane;
+    uint64_t w = 0, f = kFlagIncl, v = 0;
+    if (j >= 0) {
+      w = ld_acquire(&status[j]);
+      f = lb_flag(w, epoch);
+      v = lb_value(w);
+    }
+    if (__any_sync(0xffffffffu, f == 0)) {
+      if (++spins > kSpinLimit) {
+        if (lane == 0) atomicExch(err, kDevTimeout);
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    const uint32_t incl = __ballot_sync(0xffffffffu, f == kFlagIncl);
+    const int stop = incl ? __ffs(incl) - 1 : 31;   // closest inclusive predecessor
+    uint64_t part = (lane <= stop) ? v : 0;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    excl += part;
+    if (incl) break;
+    pos -= 32;
+  }
+  if (lane == 0) st_release(&status[tile], lb_pack(epoch, kFlagIncl, excl + local));
+  return excl;
+}
+
+// Single-thread look-back for per-digit chains (radix sort: one thread per digit).
+__device__ __forceinline__ uint64_t lookback_thread(uint64_t* status, uint64_t tile, uint64_t stride,
+                                                    uint64_t local, uint32_t epoch, uint32_t* err) {
+  if (tile == 0) {
+    st_release(&status[0], lb_pack(epoch, kFlagIncl, local));
+    return 0;
+  }
+  st_release(&status[tile * stride], lb_pack(epoch, kFlagAgg, local));
+  uint64_t excl = 0;
+  int64_t j = int64_t(tile) - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    const uint64_t w = ld_acquire(&status[uint64_t(j) * stride]);
+    const uint64_t f = lb_flag(w, epoch);
+    if (f == 0) {
+      if (++spins > kSpinLimit) {
+        atomicExch(err, kDevTimeout);
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    excl += lb_value(w);
+    if (f == kFlagIncl) break;
+    --j;
+  }
+  st_release(&status[tile * stride], lb_pack(epoch, kFlagIncl, excl + local));
+  return excl;
+}
+
+// ---- small helpers --------------------------------------------------------------------
+
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  // MurmurHash3 finaliser (Appleby): full avalanche of a 32-bit key.
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive_sum(T v, T* smem_warp, T* total) {
+  // Exclusive sum over the block; smem_warp holds >= 32 entries.
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+  T x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < nwarps ? smem_warp[lane] : T(0);
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nwarps) smem_warp[lane] = w;  // inclusive warp prefix
+  }
+  __syncthreads();
+  const T warp_excl = warp ? smem_warp[warp - 1] : T(0);
+  if (total) *total = smem_warp[nwarps - 1];
+  __syncthreads();
+  return warp_excl + x - v;
+}
+
+template <typename K>
+struct KeyTraits;
+template <>
+struct KeyTraits<uint32_t> { static constexpr int bits = 32; };
+template <>
+struct KeyTraits<uint64_t> { static constexpr int bits = 64; };
+
+}  // namespace hisa

@@ -1,0 +1,77 @@
+// Control kernels: stage bookkeeping, the iteration commit (fixpoint test) and
+// buffer zeroing.  All read and write only the device-resident DevState, so a
+// captured iteration replays without host involvement.
+#include "kernels.cuh"
+
+namespace hisa {
+
+__global__ void k_ctl(CtlArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  for (int i = 0; i < a.n; ++i) {
+    const CtlCmd c = a.cmd[i];
+    if (c.op == kCtlZeroSmall) {
+      uint64_t* p = static_cast<uint64_t*>(st->buf[c.a].ptr);
+      for (long long j = threadIdx.x; j < c.b; j += blockDim.x) p[j] = 0;
+      continue;
+    }
+    if (threadIdx.x != 0) continue;
+    switch (c.op) {
+      case kCtlEpoch: st->epoch = st->epoch + 1; break;
+      case kCtlResetCtr: st->tile_ctr[c.a] = 0; break;
+      case kCtlSetCnt: st->cnt[c.a] = uint64_t(c.b); break;
+      case kCtlAddCnt: st->cnt[c.a] += st->cnt[c.b]; break;
+      case kCtlCopyCnt: st->cnt[c.a] = st->cnt[c.b]; break;
+      default: st->error = kDevBadState; break;
+    }
+  }
+}
+
+// End of an iteration (Section 5.1 "Merging Full with Delta and Clearing New"
+// and the fixpoint check): unless a stage overflowed, the new full and delta
+// versions become current, |delta_k| is appended to each relation's history,
+// and the loop continues while some delta is non-empty.
+__global__ void k_commit(CommitArgs a) {
+  DevState* st = a.st;
+  if (threadIdx.x != 0) return;
+  if (st->overflow || st->error) {
+    st->go = 0;
+    return;
+  }
+  bool any = false;
+  const uint32_t it = st->iter;
+  for (int r = 0; r < a.nrel; ++r) {
+    const uint64_t nd = st->cnt[a.delta_next[r]];
+    if (nd > 0) {
+      DBuf t = st->buf[a.full[r]];
+      st->buf[a.full[r]] = st->buf[a.full_next[r]];
+      st->buf[a.full_next[r]] = t;
+      st->cnt[a.full[r]] = st->cnt[a.full_next[r]];
+      any = true;
+    }
+    DBuf t = st->buf[a.delta[r]];
+    st->buf[a.delta[r]] = st->buf[a.delta_next[r]];
+    st->buf[a.delta_next[r]] = t;
+    st->cnt[a.delta[r]] = nd;
+    DBuf h = st->buf[a.history[r]];
+    if (it < h.cap) static_cast<uint64_t*>(h.ptr)[it] = nd;
+  }
+  st->iter = it + 1;
+  st->go = (any || a.force) && st->iter < st->max_iters ? 1u : 0u;
+  if (any) st->aux[0] = st->iter;   // last iteration that produced a tuple
+}
+
+__global__ void k_zero(ZeroArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t words = st->buf[a.buf].cap * uint64_t(a.elem_bytes) / 16;
+  uint4* p = static_cast<uint4*>(st->buf[a.buf].ptr);
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < words; i += uint64_t(gridDim.x) * blockDim.x)
+    p[i] = make_uint4(0, 0, 0, 0);
+}
+
+void launch_ctl(const CtlArgs& a, cudaStream_t s) { k_ctl<<<1, 256, 0, s>>>(a); }
+void launch_commit(const CommitArgs& a, cudaStream_t s) { k_commit<<<1, 32, 0, s>>>(a); }
+void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) { k_zero<<<g.small, 256, 0, s>>>(a); }
+
+}  // namespace hisa

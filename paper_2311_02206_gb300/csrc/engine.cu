@@ -1,0 +1,983 @@
+// Host side of the engine: relation store, rule compiler, eager buffer
+// management and the semi-naive fixpoint driver behind include/hisa.h.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "engine.h"
+
+namespace hisa {
+
+// ---- errors ---------------------------------------------------------------------------
+
+#define CU(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) return ctx_fail(HISA_ERR_CUDA, #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+hisa_status Engine::ctx_fail(hisa_status s, const char* what, const char* detail) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s%s%s", what ? what : "", detail ? ": " : "", detail ? detail : "");
+  last_error = buf;
+  return s;
+}
+
+// ---- memory ---------------------------------------------------------------------------
+
+hisa_status Engine::dev_alloc(size_t bytes, void** out) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (cfg.hbm_budget_bytes && bytes_in_use + bytes > cfg.hbm_budget_bytes)
+    return ctx_fail(HISA_ERR_OOM, "HBM budget exceeded", nullptr);
+  void* p = nullptr;
+  if (cfg.alloc) {
+    p = cfg.alloc(bytes, stream, cfg.user);
+    if (!p) return ctx_fail(HISA_ERR_OOM, "allocator hook returned NULL", nullptr);
+  } else {
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return ctx_fail(HISA_ERR_OOM, "cudaMallocFromPoolAsync", cudaGetErrorString(e));
+    }
+  }
+  allocs[p] = bytes;
+  bytes_in_use += bytes;
+  peak_bytes = std::max(peak_bytes, bytes_in_use);
+  *out = p;
+  return HISA_OK;
+}
+
+void Engine::dev_free(void* p) {
+  if (!p) return;
+  auto it = allocs.find(p);
+  if (it == allocs.end()) return;
+  if (cfg.free) cfg.free(p, it->second, stream, cfg.user);
+  else cudaFreeAsync(p, stream);
+  bytes_in_use -= it->second;
+  allocs.erase(it);
+}
+
+int Engine::new_slot(int elem_bytes) {
+  const int id = nslots++;
+  slot_elem[id] = elem_bytes;
+  hs.buf[id] = {nullptr, 0};
+  hs.cnt[id] = 0;
+  return id;
+}
+
+// Grows slot `id` to at least `cap` elements (contents are not kept).
+hisa_status Engine::ensure(int id, uint64_t cap) {
+  if (hs.buf[id].cap >= cap && hs.buf[id].ptr) return HISA_OK;
+  void* p;
+  hisa_status s = dev_alloc(size_t(std::max<uint64_t>(cap, 1)) * slot_elem[id], &p);
+  if (s) return s;
+  dev_free(hs.buf[id].ptr);
+  hs.buf[id] = {p, std::max<uint64_t>(cap, 1)};
+  if (slot_zero[id]) {
+    // look-back words: a recycled allocation may hold words of another
+    // context whose epoch tags collide with ours; zero means "not published"
+    CU(cudaMemsetAsync(p, 0, size_t(std::max<uint64_t>(cap, 1)) * slot_elem[id], stream));
+  }
+  return HISA_OK;
+}
+
+hisa_status Engine::upload() {
+  std::memcpy(hs_pinned, &hs, sizeof(DevState));
+  CU(cudaMemcpyAsync(dst, hs_pinned, sizeof(DevState), cudaMemcpyHostToDevice, stream));
+  CU(cudaStreamSynchronize(stream));   // hs_pinned is reused by the next transfer
+  return HISA_OK;
+}
+
+hisa_status Engine::download() {
+  CU(cudaMemcpyAsync(hs_pinned, dst, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
+  CU(cudaStreamSynchronize(stream));
+  std::memcpy(&hs, hs_pinned, sizeof(DevState));
+  return HISA_OK;
+}
+
+hisa_status Engine::check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return ctx_fail(HISA_ERR_CUDA, what, cudaGetErrorString(e));
+  return HISA_OK;
+}
+
+// ---- lifecycle ------------------------------------------------------------------------
+
+hisa_status Engine::init(const hisa_config& c) {
+  cfg = c;
+  if (cfg.load_factor <= 0.f || cfg.load_factor > 0.95f) cfg.load_factor = 0.8f;
+  if (cfg.ebm_k <= 0.f) cfg.ebm_k = 2.f;
+  if (cfg.max_iters == 0) cfg.max_iters = 1000000;
+  if (cfg.device >= 0) CU(cudaSetDevice(cfg.device));
+  CU(cudaGetDevice(&device));
+  stream = static_cast<cudaStream_t>(cfg.cuda_stream);
+  int sms = 0;
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  grid.sms = sms;
+  // persistent grids: resident CTAs per SM from the kernels' footprints
+  grid.radix = sms * 2;
+  grid.setop = sms * 4;
+  grid.join = sms * 4;
+  grid.small = sms * 4;
+  if (!cfg.alloc) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    CU(cudaMemPoolCreate(&pool, &props));
+    uint64_t thr = ~0ull;
+    CU(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  }
+  CU(cudaMallocHost(&hs_pinned, sizeof(DevState)));
+  std::memset(&hs, 0, sizeof hs);
+  void* p;
+  hisa_status s = dev_alloc(sizeof(DevState), &p);
+  if (s) return s;
+  dst = static_cast<DevState*>(p);
+  // shared scratch
+  sc.empty = new_slot(8);
+  sc.hist = new_slot(8);
+  sc.radix_status = new_slot(8);
+  sc.split = new_slot(8);
+  sc.setop_status = new_slot(8);
+  sc.offs = new_slot(8);
+  sc.join_status = new_slot(8);
+  sc.starts = new_slot(8);
+  sc.tmp_a = new_slot(8);
+  sc.tmp_b = new_slot(8);
+  sc.runs = nslots++;
+  sc.total = nslots++;
+  sc.tmp_cnt = nslots++;
+  slot_zero[sc.radix_status] = slot_zero[sc.setop_status] = slot_zero[sc.join_status] = true;
+  if ((s = ensure(sc.empty, 1)) || (s = ensure(sc.hist, 8 * 256))) return s;
+  return upload();
+}
+
+Engine::~Engine() {
+  if (stream || dst) cudaStreamSynchronize(stream);
+  for (auto& kv : std::vector<std::pair<void*, size_t>>(allocs.begin(), allocs.end())) dev_free(kv.first);
+  if (stream) cudaStreamSynchronize(stream);
+  if (pool) cudaMemPoolDestroy(pool);
+  if (hs_pinned) cudaFreeHost(hs_pinned);
+}
+
+// ---- relations --------------------------------------------------------------------------
+
+hisa_status Engine::declare(const char* name, uint32_t arity, int is_idb, uint32_t* id) {
+  if (!name || !id || std::strlen(name) > 63) return ctx_fail(HISA_ERR_INVALID_ARG, "relation name", nullptr);
+  if (arity != 2) return ctx_fail(HISA_ERR_ARITY, "only binary relations are evaluated", nullptr);
+  for (auto& r : rels)
+    if (r.name == name) return ctx_fail(HISA_ERR_INVALID_ARG, "duplicate relation", name);
+  if (rels.size() >= 8) return ctx_fail(HISA_ERR_UNSUPPORTED, "at most 8 relations", nullptr);
+  Relation r;
+  r.name = name;
+  r.arity = arity;
+  r.idb = is_idb != 0;
+  rels.push_back(r);
+  *id = uint32_t(rels.size() - 1);
+  compiled = false;
+  return HISA_OK;
+}
+
+hisa_status Engine::load(uint32_t rid, const uint32_t* const* cols, uint64_t n, int on_device) {
+  if (rid >= rels.size() || !cols) return ctx_fail(HISA_ERR_INVALID_ARG, "load: relation", nullptr);
+  Relation& r = rels[rid];
+  if (r.idb) return ctx_fail(HISA_ERR_STATE, "load into an IDB relation", r.name.c_str());
+  if (n == 0) return HISA_OK;
+  if (!cols[0] || !cols[1]) return ctx_fail(HISA_ERR_INVALID_ARG, "load: null column", nullptr);
+  // staging: raw columns appended into one device buffer per column
+  const uint64_t need = r.staged + n;
+  if (need > r.stage_cap) {
+    const uint64_t cap = std::max<uint64_t>(need, r.stage_cap * 2);
+    void *a, *b;
+    hisa_status s;
+    if ((s = dev_alloc(cap * 4, &a)) || (s = dev_alloc(cap * 4, &b))) return s;
+    if (r.staged) {
+      CU(cudaMemcpyAsync(a, r.stage[0], r.staged * 4, cudaMemcpyDeviceToDevice, stream));
+      CU(cudaMemcpyAsync(b, r.stage[1], r.staged * 4, cudaMemcpyDeviceToDevice, stream));
+    }
+    dev_free(r.stage[0]);
+    dev_free(r.stage[1]);
+    r.stage[0] = static_cast<uint32_t*>(a);
+    r.stage[1] = static_cast<uint32_t*>(b);
+    r.stage_cap = cap;
+  }
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int c = 0; c < 2; ++c)
+    CU(cudaMemcpyAsync(r.stage[c] + r.staged, cols[c], n * 4, kind, stream));
+  // active-domain bound for the code width
+  uint32_t mx = 0;
+  if (!on_device) {
+    for (int c = 0; c < 2; ++c)
+      for (uint64_t i = 0; i < n; ++i) mx = std::max(mx, cols[c][i]);
+  } else {
+    hisa_status s = device_max(r.stage[0] + r.staged, r.stage[1] + r.staged, n, &mx);
+    if (s) return s;
+  }
+  r.max_value = std::max(r.max_value, mx);
+  r.staged += n;
+  edb_dirty = true;
+  return HISA_OK;
+}
+
+hisa_status Engine::reset_edb() {
+  for (auto& r : rels) {
+    if (r.idb) continue;
+    r.staged = 0;
+    r.max_value = 0;
+  }
+  edb_dirty = true;
+  compiled = false;
+  return HISA_OK;
+}
+
+hisa_status Engine::add_rule(const hisa_rule* rule) {
+  if (!rule) return ctx_fail(HISA_ERR_INVALID_ARG, "null rule", nullptr);
+  const hisa_rule& R = *rule;
+  if (R.n_body < 1 || R.n_body > 3 || R.n_neq > 2) return ctx_fail(HISA_ERR_INVALID_ARG, "rule shape", nullptr);
+  auto ok_atom = [&](const hisa_atom& a) { return a.rel < rels.size() && a.var[0] < 16 && a.var[1] < 16; };
+  if (!ok_atom(R.head) || !rels[R.head.rel].idb) return ctx_fail(HISA_ERR_INVALID_ARG, "rule head", nullptr);
+  for (uint32_t i = 0; i < R.n_body; ++i)
+    if (!ok_atom(R.body[i])) return ctx_fail(HISA_ERR_INVALID_ARG, "rule body atom", nullptr);
+  auto bound = [&](uint32_t v) {
+    for (uint32_t i = 0; i < R.n_body; ++i)
+      if (R.body[i].var[0] == v || R.body[i].var[1] == v) return true;
+    return false;
+  };
+  for (int c = 0; c < 2; ++c)
+    if (!bound(R.head.var[c])) return ctx_fail(HISA_ERR_INVALID_ARG, "unbound head variable", nullptr);
+  for (uint32_t f = 0; f < R.n_neq; ++f)
+    if (!bound(R.neq[f][0]) || !bound(R.neq[f][1]))
+      return ctx_fail(HISA_ERR_INVALID_ARG, "unbound filter variable", nullptr);
+  rules.push_back(R);
+  compiled = false;
+  return HISA_OK;
+}
+
+// ---- rule compilation -------------------------------------------------------------------
+
+// Plans one semi-naive variant of a rule: the body atom `delta_atom` (or the
+// first atom of a non-recursive rule) is the scanned outer relation; every
+// further atom is joined as a range-probed inner relation (Algorithm 3); with
+// three atoms the first join writes the temporarily materialized Tmp relation
+// (Section 5.2), keeping only the columns later steps need.
+hisa_status Engine::plan_variant(const hisa_rule& R, int delta_atom, std::vector<StepPlan>& out) {
+  const int nb = int(R.n_body);
+  std::vector<int> rest;
+  const int first = delta_atom >= 0 ? delta_atom : 0;
+  for (int j = 0; j < nb; ++j)
+    if (j != first) rest.push_back(j);
+  // current tuple: its two columns and the variables they carry
+  int cur_var[2] = {int(R.body[first].var[0]), int(R.body[first].var[1])};
+  const Relation& r0 = rels[R.body[first].rel];
+  int cur_slot, cur_cnt;
+  if (delta_atom >= 0) {
+    cur_slot = r0.delta;
+    cur_cnt = r0.delta;
+  } else {
+    cur_slot = r0.idb ? r0.full : r0.base;
+    cur_cnt = cur_slot;
+  }
+  std::vector<bool> applied(R.n_neq, false);
+  bool first_step = true;
+  while (true) {
+    StepPlan sp{};
+    sp.outer_slot = cur_slot;
+    sp.outer_cnt = cur_cnt;
+    int src_of[16];
+    for (int& v : src_of) v = -1;
+    src_of[cur_var[0]] = kSrcOuter0;
+    if (src_of[cur_var[1]] < 0) src_of[cur_var[1]] = kSrcOuter1;
+    auto add_filter = [&](int op, int a, int b) -> bool {
+      if (sp.nfilt >= 2) return false;
+      sp.fop[sp.nfilt] = op;
+      sp.fa[sp.nfilt] = a;
+      sp.fb[sp.nfilt] = b;
+      ++sp.nfilt;
+      return true;
+    };
+    // a repeated variable in the current tuple (e.g. Tgt(t,t)) is an equality filter
+    if (first_step && cur_var[0] == cur_var[1] && !add_filter(kFiltEq, kSrcOuter0, kSrcOuter1))
+      return ctx_fail(HISA_ERR_UNSUPPORTED, "too many filters in one join step", nullptr);
+    if (!rest.empty()) {
+      // next atom: the first remaining one sharing a variable with the current tuple
+      int pick = -1, jv = -1;
+      for (size_t q = 0; q < rest.size() && pick < 0; ++q) {
+        const hisa_atom& A = R.body[rest[q]];
+        for (int c = 0; c < 2; ++c)
+          if (src_of[A.var[c]] >= 0) {
+            pick = int(q);
+            jv = int(A.var[c]);
+            break;
+          }
+      }
+      if (pick < 0) return ctx_fail(HISA_ERR_UNSUPPORTED, "rule needs a cross product", nullptr);
+      const hisa_atom& A = R.body[rest[pick]];
+      rest.erase(rest.begin() + pick);
+      const int c = int(A.var[0]) == jv ? 0 : 1;
+      const int ov = int(A.var[1 - c]);
+      if (ov != jv && src_of[ov] >= 0)
+        return ctx_fail(HISA_ERR_UNSUPPORTED, "join on two columns", nullptr);
+      Relation& ir = rels[A.rel];
+      if (ir.idb) return ctx_fail(HISA_ERR_UNSUPPORTED, "IDB relation as a range-probed inner relation", nullptr);
+      ir.need_idx[c] = true;
+      sp.has_inner = true;
+      sp.inner_rel = int(A.rel);
+      sp.inner_col = c;
+      sp.outer_kcol = src_of[jv] == kSrcOuter0 ? 0 : 1;
+      src_of[jv] = src_of[jv];  // the key equals the outer value
+      if (ov == jv) {
+        if (!add_filter(kFiltEq, kSrcKey, kSrcOther)) return ctx_fail(HISA_ERR_UNSUPPORTED, "filters", nullptr);
+      } else {
+        src_of[ov] = kSrcOther;
+      }
+    } else {
+      sp.has_inner = false;
+      sp.outer_kcol = 0;
+    }
+    // filters whose variables are all available now
+    int other_filters = 0;
+    for (uint32_t f = 0; f < R.n_neq; ++f) {
+      if (applied[f]) continue;
+      const int a = src_of[R.neq[f][0]], b = src_of[R.neq[f][1]];
+      if (a < 0 || b < 0) continue;
+      if (a == kSrcOther || b == kSrcOther) ++other_filters;
+      if (other_filters > 1 || !add_filter(kFiltNeq, a, b))
+        return ctx_fail(HISA_ERR_UNSUPPORTED, "too many filters in one join step", nullptr);
+      applied[f] = true;
+    }
+    if (rest.empty()) {
+      sp.proj0 = src_of[R.head.var[0]];
+      sp.proj1 = src_of[R.head.var[1]];
+      sp.out_rel = int(R.head.rel);
+      sp.to_tmp = false;
+      out.push_back(sp);
+      return HISA_OK;
+    }
+    // Tmp: the variables still needed (remaining atoms, head, pending filters)
+    std::vector<int> need;
+    auto want = [&](int v) {
+      if (src_of[v] >= 0 && std::find(need.begin(), need.end(), v) == need.end()) need.push_back(v);
+    };
+    for (int j : rest) {
+      want(int(R.body[j].var[0]));
+      want(int(R.body[j].var[1]));
+    }
+    want(int(R.head.var[0]));
+    want(int(R.head.var[1]));
+    for (uint32_t f = 0; f < R.n_neq; ++f)
+      if (!applied[f]) {
+        want(int(R.neq[f][0]));
+        want(int(R.neq[f][1]));
+      }
+    if (need.size() > 2) return ctx_fail(HISA_ERR_UNSUPPORTED, "Tmp relation needs more than two columns", nullptr);
+    if (need.size() == 1) need.push_back(need[0]);
+    sp.proj0 = src_of[need[0]];
+    sp.proj1 = src_of[need[1]];
+    sp.to_tmp = true;
+    sp.out_rel = -1;
+    out.push_back(sp);
+    cur_var[0] = need[0];
+    cur_var[1] = need[1];
+    cur_slot = sc.tmp_a;
+    cur_cnt = sc.tmp_cnt;
+    first_step = false;
+  }
+}
+
+hisa_status Engine::compile() {
+  // code width from the active domain (Datalog without constants or arithmetic
+  // derives values only from EDB values)
+  uint32_t mx = 0;
+  for (auto& r : rels) mx = std::max(mx, r.max_value);
+  b = 1;
+  while (b < 32 && (uint64_t(mx) >> b) != 0) ++b;
+  wide = 2 * b > 32;
+  passes = (2 * b + 7) / 8;
+  const int kb = wide ? 8 : 4;
+  // slots of every relation (kept across runs; element width may change)
+  for (auto& r : rels) {
+    r.need_idx[0] = r.need_idx[1] = false;
+    if (r.base < 0) {
+      r.base = new_slot(kb);
+      r.rev = new_slot(kb);
+      r.table[0] = new_slot(16);
+      r.table[1] = new_slot(16);
+      if (r.idb) {
+        r.full = r.base;
+        r.full_next = new_slot(kb);
+        r.delta = new_slot(kb);
+        r.delta_next = new_slot(kb);
+        r.fresh = new_slot(kb);
+        r.fresh_alt = new_slot(kb);
+        r.hist = new_slot(8);
+        r.history = new_slot(8);
+      }
+    }
+    for (int id : {r.base, r.rev, r.full_next, r.delta, r.delta_next, r.fresh, r.fresh_alt})
+      if (id >= 0 && slot_elem[id] != kb) {
+        dev_free(hs.buf[id].ptr);
+        hs.buf[id] = {nullptr, 0};
+        slot_elem[id] = kb;
+      }
+  }
+  if (slot_elem[sc.tmp_a] != kb) {
+    for (int id : {sc.tmp_a, sc.tmp_b}) {
+      dev_free(hs.buf[id].ptr);
+      hs.buf[id] = {nullptr, 0};
+      slot_elem[id] = kb;
+    }
+  }
+  idb.clear();
+  for (size_t i = 0; i < rels.size(); ++i)
+    if (rels[i].idb) idb.push_back(int(i));
+  if (idb.empty()) return ctx_fail(HISA_ERR_INVALID_ARG, "no IDB relation", nullptr);
+  // semi-naive variants (Section 2): iteration 1 runs the rules without IDB
+  // atoms; later iterations run each rule once per IDB atom, that atom read
+  // from delta and the others from full
+  plan1.clear();
+  planN.clear();
+  for (auto& R : rules) {
+    std::vector<int> idb_atoms;
+    for (uint32_t j = 0; j < R.n_body; ++j)
+      if (rels[R.body[j].rel].idb) idb_atoms.push_back(int(j));
+    hisa_status s;
+    if (idb_atoms.empty()) {
+      std::vector<StepPlan> v;
+      if ((s = plan_variant(R, -1, v))) return s;
+      plan1.push_back(v);
+    } else {
+      for (int j : idb_atoms) {
+        std::vector<StepPlan> v;
+        if ((s = plan_variant(R, j, v))) return s;
+        planN.push_back(v);
+      }
+    }
+  }
+  compiled = true;
+  graph_stale = true;
+  return HISA_OK;
+}
+
+// ---- op emission ------------------------------------------------------------------------
+
+void Engine::emit_join(std::vector<Op>& ops, const StepPlan& sp) {
+  Op o{};
+  o.kind = Op::JOIN;
+  JoinArgs& a = o.join;
+  a.st = dst;
+  a.outer_buf = sp.outer_slot;
+  a.outer_cnt = sp.outer_cnt;
+  a.has_inner = sp.has_inner;
+  if (sp.has_inner) {
+    const Relation& ir = rels[sp.inner_rel];
+    a.inner_buf = sp.inner_col == 0 ? ir.base : ir.rev;
+    a.inner_cnt = a.inner_buf;
+    a.table_buf = ir.table[sp.inner_col];
+  }
+  a.b = b;
+  a.outer_kcol = sp.outer_kcol;
+  a.proj0 = sp.proj0;
+  a.proj1 = sp.proj1;
+  a.nfilt = sp.nfilt;
+  for (int f = 0; f < 2; ++f) {
+    a.fop[f] = sp.fop[f];
+    a.fa[f] = sp.fa[f];
+    a.fb[f] = sp.fb[f];
+  }
+  a.offs_buf = sc.offs;
+  a.status_buf = sc.join_status;
+  a.starts_buf = sc.starts;
+  if (sp.to_tmp) {
+    a.out_buf = sc.tmp_a;
+    a.out_cnt = sc.tmp_cnt;
+    a.hist_buf = -1;
+  } else {
+    const Relation& hr = rels[sp.out_rel];
+    a.out_buf = hr.fresh;
+    a.out_cnt = hr.fresh;
+    a.hist_buf = hr.hist;
+    a.hist_passes = passes;
+  }
+  a.total_cnt = sc.total;
+  a.ctr = 0;
+  a.skip_mask = 1;
+  a.stage_bit = 0;
+  ops.push_back(o);
+}
+
+// Join stage of one iteration: clear new, run every variant, sort each new.
+void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepPlan>>& plans) {
+  Op c{};
+  c.kind = Op::CTL;
+  c.ctl.st = dst;
+  c.ctl.skip_mask = 1;
+  for (int r : idb) {
+    c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, rels[r].fresh, 0};
+    c.ctl.cmd[c.ctl.n++] = {kCtlZeroSmall, rels[r].hist, 8 * 256};
+  }
+  ops.push_back(c);
+  for (auto& v : plans) {
+    if (v.size() > 1) {
+      Op t{};
+      t.kind = Op::CTL;
+      t.ctl.st = dst;
+      t.ctl.skip_mask = 1;
+      t.ctl.cmd[t.ctl.n++] = {kCtlSetCnt, sc.tmp_cnt, 0};
+      ops.push_back(t);
+    }
+    for (auto& sp : v) emit_join(ops, sp);
+  }
+  for (int r : idb) emit_sort(ops, rels[r].fresh, rels[r].fresh_alt, rels[r].fresh, rels[r].hist, 1, 0);
+}
+
+// LSD passes ping-ponging between `in` and `alt`; the result lands in `in`
+// for an even number of passes, else in `alt`.
+void Engine::emit_sort(std::vector<Op>& ops, int in, int alt, int cnt, int hist, int skip_mask, int stage_bit) {
+  for (int p = 0; p < passes; ++p) {
+    Op o{};
+    o.kind = Op::PASS;
+    RadixPassArgs& a = o.pass;
+    a.st = dst;
+    a.in_buf = (p & 1) ? alt : in;
+    a.out_buf = (p & 1) ? in : alt;
+    a.n_cnt = cnt;
+    a.hist_buf = hist;
+    a.status_buf = sc.radix_status;
+    a.pass = p;
+    a.shift = 8 * p;
+    a.ctr = 1;
+    a.skip_mask = skip_mask;
+    a.stage_bit = stage_bit;
+    ops.push_back(o);
+  }
+}
+
+// Populate delta, merge, commit.
+void Engine::emit_tail(std::vector<Op>& ops, bool force) {
+  for (int r : idb) {
+    const Relation& R = rels[r];
+    Op o{};
+    o.kind = Op::SETOP;
+    SetopArgs& a = o.setop;
+    a.st = dst;
+    a.a_buf = R.full;
+    a.a_cnt = R.full;
+    a.b_buf = (passes & 1) ? R.fresh_alt : R.fresh;
+    a.b_cnt = R.fresh;
+    a.split_buf = sc.split;
+    a.status_buf = sc.setop_status;
+    a.d_buf = R.delta_next;
+    a.d_cnt = R.delta_next;
+    a.f_buf = R.full_next;
+    a.f_cnt = R.full_next;
+    a.ctr = 2;
+    a.skip_mask = 3;
+    a.stage_bit = 1;
+    ops.push_back(o);
+  }
+  Op c{};
+  c.kind = Op::COMMIT;
+  c.commit.st = dst;
+  c.commit.nrel = int(idb.size());
+  for (size_t i = 0; i < idb.size(); ++i) {
+    const Relation& R = rels[idb[i]];
+    c.commit.full[i] = R.full;
+    c.commit.full_next[i] = R.full_next;
+    c.commit.delta[i] = R.delta;
+    c.commit.delta_next[i] = R.delta_next;
+    c.commit.history[i] = R.history;
+  }
+  c.commit.force = force;
+  ops.push_back(c);
+}
+
+template <typename K>
+hisa_status Engine::exec_t(const std::vector<Op>& ops) {
+  for (const Op& o : ops) {
+    switch (o.kind) {
+      case Op::CTL: launch_ctl(o.ctl, stream); break;
+      case Op::JOIN: launch_join<K>(o.join, grid, stream); break;
+      case Op::PASS: launch_radix_pass<K>(o.pass, grid, stream); break;
+      case Op::HIST: launch_radix_hist<K>(o.hist, grid, stream); break;
+      case Op::SETOP: launch_setop<K>(o.setop, grid, stream); break;
+      case Op::COMMIT: launch_commit(o.commit, stream); break;
+    }
+  }
+  return check_launch("kernel launch");
+}
+
+hisa_status Engine::exec(const std::vector<Op>& ops) {
+  return wide ? exec_t<uint64_t>(ops) : exec_t<uint32_t>(ops);
+}
+
+// ---- EDB preparation (Algorithm 1 + Algorithm 2 for every index) ------------------------
+
+template <typename K>
+hisa_status Engine::prepare_rel_t(Relation& r, int order, int slot) {
+  const uint64_t n = r.staged;
+  hisa_status s;
+  if ((s = ensure(sc.tmp_a, n)) || (s = ensure(sc.tmp_b, n)) || (s = ensure(slot, n))) return s;
+  if ((s = ensure(sc.radix_status, ((n + radix_tile<K>() - 1) / radix_tile<K>()) * 256 + 1))) return s;
+  const uint64_t st_tiles = (n + setop_tile<K>() - 1) / setop_tile<K>() + 2;
+  if ((s = ensure(sc.split, st_tiles)) || (s = ensure(sc.setop_status, st_tiles))) return s;
+  hs.cnt[sc.tmp_a] = n;
+  hs.cnt[sc.empty] = 0;
+  if ((s = upload())) return s;
+  EncodeArgs e{dst, r.stage[0], r.stage[1], n, sc.tmp_a, sc.empty, b, order, 0};
+  launch_encode<K>(e, grid, stream);
+  CtlArgs z{};
+  z.st = dst;
+  z.n = 1;
+  z.cmd[0] = {kCtlZeroSmall, sc.hist, 8 * 256};
+  launch_ctl(z, stream);
+  RadixHistArgs h{dst, sc.tmp_a, sc.tmp_a, sc.hist, passes, 0};
+  launch_radix_hist<K>(h, grid, stream);
+  std::vector<Op> ops;
+  emit_sort(ops, sc.tmp_a, sc.tmp_b, sc.tmp_a, sc.hist, 0, 0);
+  Op u{};
+  u.kind = Op::SETOP;
+  SetopArgs& a = u.setop;
+  a.st = dst;
+  a.a_buf = sc.empty;
+  a.a_cnt = sc.empty;
+  a.b_buf = (passes & 1) ? sc.tmp_b : sc.tmp_a;
+  a.b_cnt = sc.tmp_a;
+  a.split_buf = sc.split;
+  a.status_buf = sc.setop_status;
+  a.d_buf = slot;
+  a.d_cnt = slot;
+  a.f_buf = -1;
+  a.f_cnt = -1;
+  a.ctr = 2;
+  a.skip_mask = 0;
+  a.stage_bit = 1;
+  ops.push_back(u);
+  if ((s = exec_t<K>(ops))) return s;
+  if ((s = download())) return s;
+  if (hs.overflow || hs.error) return ctx_fail(HISA_ERR_CUDA, "EDB preparation overflowed", nullptr);
+  // hash index over the runs of the join column
+  if (r.need_idx[order]) {
+    hs.cnt[sc.runs] = 0;
+    if ((s = upload())) return s;
+    RunsArgs ra{dst, slot, slot, b, sc.runs};
+    launch_count_runs<K>(ra, grid, stream);
+    if ((s = download())) return s;
+    const uint64_t runs = hs.cnt[sc.runs];
+    uint64_t cap = 16;
+    while (double(cap) * cfg.load_factor < double(runs)) cap <<= 1;
+    if ((s = ensure(r.table[order], cap))) return s;
+    hs.buf[r.table[order]].cap = cap;  // power of two for the probe mask
+    if ((s = upload())) return s;
+    ZeroArgs za{dst, r.table[order], 16, 0};
+    launch_zero(za, grid, stream);
+    IndexArgs ia{dst, slot, slot, r.table[order], b, -1, 0};
+    launch_index<K>(ia, grid, stream);
+    if ((s = check_launch("index build"))) return s;
+    if ((s = download())) return s;
+    if (hs.error) return ctx_fail(HISA_ERR_CUDA, "index build", "probe limit");
+  }
+  return HISA_OK;
+}
+
+hisa_status Engine::prepare_edb() {
+  hisa_status s;
+  for (auto& r : rels) {
+    if (r.idb) continue;
+    for (int order = 0; order < 2; ++order) {
+      if (order == 1 && !r.need_idx[1]) continue;
+      const int slot = order == 0 ? r.base : r.rev;
+      s = wide ? prepare_rel_t<uint64_t>(r, order, slot) : prepare_rel_t<uint32_t>(r, order, slot);
+      if (s) return s;
+    }
+  }
+  edb_dirty = false;
+  return HISA_OK;
+}
+
+// ---- growth (Section 5.3) ----------------------------------------------------------------
+
+hisa_status Engine::regrow() {
+  for (int id = 0; id < nslots; ++id) {
+    const uint64_t need = hs.need[id];
+    if (need == 0 || need <= hs.buf[id].cap) continue;
+    uint64_t cap = need + need / 2 + 1024;
+    for (int r : idb) {
+      const Relation& R = rels[r];
+      if (id == R.full_next || id == R.full) {
+        // eager buffer management: full + k * delta
+        const uint64_t delta = need > hs.cnt[R.full] ? need - hs.cnt[R.full] : need;
+        cap = need + uint64_t(cfg.ebm_k * double(delta)) + 1024;
+      }
+    }
+    hisa_status s = ensure(id, cap);
+    if (s) return s;
+    ++regrows;
+  }
+  // the radix ping-pong buffer follows its partner
+  for (int r : idb) {
+    const Relation& R = rels[r];
+    const uint64_t c = std::max(hs.buf[R.fresh].cap, hs.buf[R.fresh_alt].cap);
+    hisa_status s;
+    if ((s = ensure(R.fresh, c)) || (s = ensure(R.fresh_alt, c))) return s;
+  }
+  std::memset(hs.need, 0, sizeof hs.need);
+  hs.overflow = 0;
+  return HISA_OK;
+}
+
+// ---- the fixpoint loop ---------------------------------------------------------------------
+
+hisa_status Engine::run(hisa_run_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  hisa_status s;
+  if (!compiled || edb_dirty) {
+    if ((s = compile())) return s;
+    double ms = 0;
+    auto e0 = std::chrono::steady_clock::now();
+    if ((s = prepare_edb())) return s;
+    ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - e0).count();
+    last_stats.ms_edb = ms;
+    // plans
+    ops1.clear();
+    opsN.clear();
+    tail.clear();
+    emit_head(ops1, plan1);
+    emit_tail(ops1, false);
+    emit_head(opsN, planN);
+    emit_tail(opsN, false);
+    emit_tail(tail, false);
+  } else {
+    last_stats.ms_edb = 0;
+  }
+  const double ms_edb = last_stats.ms_edb;
+  last_stats = hisa_run_stats{};
+  last_stats.ms_edb = ms_edb;
+  regrows = 0;
+  // initial capacities: a multiple of the EDB size
+  uint64_t nedb = 1024;
+  for (auto& r : rels)
+    if (!r.idb) nedb = std::max<uint64_t>(nedb, r.staged);
+  const int kt = wide ? radix_tile<uint64_t>() : radix_tile<uint32_t>();
+  for (int r : idb) {
+    Relation& R = rels[r];
+    for (int id : {R.full, R.full_next, R.delta, R.delta_next, R.fresh, R.fresh_alt})
+      if ((s = ensure(id, 4 * nedb))) return s;
+    if ((s = ensure(R.hist, 8 * 256)) || (s = ensure(R.history, std::min<uint64_t>(cfg.max_iters + 1, 1u << 20))))
+      return s;
+    for (int id : {R.full, R.full_next, R.delta, R.delta_next, R.fresh}) hs.cnt[id] = 0;
+  }
+  hs.cnt[sc.tmp_cnt] = 0;
+  if ((s = ensure(sc.radix_status, (4 * nedb / kt + 2) * 256)) || (s = ensure(sc.offs, 4 * nedb + 1)) ||
+      (s = ensure(sc.join_status, 4 * nedb / kJoinTile + 2)) || (s = ensure(sc.starts, 4 * nedb / kJoinChunk + 2)) ||
+      (s = ensure(sc.split, 8 * nedb / 2048 + 2)) || (s = ensure(sc.setop_status, 8 * nedb / 2048 + 2)) ||
+      (s = ensure(sc.tmp_a, 4 * nedb)))
+    return s;
+  // look-back words carry a 20-bit epoch tag: clear them well before it wraps
+  if (hs.epoch > (1u << 20) - (1u << 16)) {
+    for (int id : {sc.radix_status, sc.setop_status, sc.join_status})
+      if (hs.buf[id].ptr) CU(cudaMemsetAsync(hs.buf[id].ptr, 0, hs.buf[id].cap * 8, stream));
+    hs.epoch = 0;
+  }
+  hs.iter = 0;
+  hs.go = 1;
+  hs.overflow = 0;
+  hs.error = 0;
+  hs.max_iters = cfg.max_iters;
+  hs.aux[0] = 0;
+  std::memset(hs.need, 0, sizeof hs.need);
+  if ((s = upload())) return s;
+  uint32_t graph_launches = 0;
+  int guard = 0;
+  while (true) {
+    const bool first = hs.iter == 0;
+    const bool use_graph = !first && (cfg.flags & HISA_FLAG_GRAPH);
+    if (use_graph) {
+      if ((s = launch_graph())) return s;
+      ++graph_launches;
+    } else {
+      if ((s = exec(first ? ops1 : opsN))) return s;
+    }
+    if ((s = download())) return s;
+    if (hs.error) {
+      return ctx_fail(hs.error == kDevTimeout ? HISA_ERR_DEVICE_TIMEOUT : HISA_ERR_CUDA, "device error",
+                      hs.error == kDevTimeout ? "bounded wait expired" : "probe limit / bad state");
+    }
+    if (hs.overflow) {
+      if (++guard > 64) return ctx_fail(HISA_ERR_OOM, "buffers keep overflowing", nullptr);
+      const uint32_t bits = hs.overflow;
+      if ((s = regrow())) return s;
+      if ((s = upload())) return s;
+      if (bits & 1) continue;       // join/sort stage: re-run the whole iteration
+      if ((s = exec(tail))) return s;   // only the set-difference/merge stage
+      if ((s = download())) return s;
+      if (hs.overflow) {
+        const uint32_t bits2 = hs.overflow;
+        if ((s = regrow())) return s;
+        if ((s = upload())) return s;
+        (void)bits2;
+        continue;
+      }
+    }
+    if (!hs.go) break;
+  }
+  if (hs.iter >= cfg.max_iters && hs.aux[0] == hs.iter)
+    return ctx_fail(HISA_ERR_NOT_CONVERGED, "max_iters reached", nullptr);
+  // delta histories
+  const uint32_t K = uint32_t(hs.aux[0]);
+  for (int r : idb) {
+    Relation& R = rels[r];
+    R.delta_counts.assign(K, 0);
+    if (K) CU(cudaMemcpyAsync(R.delta_counts.data(), hs.buf[R.history].ptr, K * 8, cudaMemcpyDeviceToHost, stream));
+  }
+  CU(cudaStreamSynchronize(stream));
+  last_stats.iterations = K;
+  last_stats.iterations_run = hs.iter;
+  last_stats.regrows = regrows;
+  last_stats.graph_launches = graph_launches;
+  last_stats.peak_bytes = peak_bytes;
+  last_stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = last_stats;
+  ran = true;
+  return HISA_OK;
+}
+
+hisa_status Engine::launch_graph() {
+  // the device-side loop: iterations repeat while DevState::go is set
+  if (!graph_exec || graph_stale) {
+    hisa_status s = build_graph();
+    if (s) return s;
+  }
+  CU(cudaGraphLaunch(graph_exec, stream));
+  return HISA_OK;
+}
+
+__global__ void k_set_cond(DevState* st, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, st->go ? 1u : 0u);
+}
+
+hisa_status Engine::build_graph() {
+  if (graph_exec) {
+    cudaGraphExecDestroy(graph_exec);
+    graph_exec = nullptr;
+  }
+  if (graph) {
+    cudaGraphDestroy(graph);
+    graph = nullptr;
+  }
+  CU(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle handle;
+  CU(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CU(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs;
+  CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t saved = stream;
+  stream = cs;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    stream = saved;
+    cudaStreamDestroy(cs);
+    return ctx_fail(HISA_ERR_CUDA, "cudaStreamBeginCaptureToGraph", cudaGetErrorString(e));
+  }
+  hisa_status s = exec(opsN);
+  k_set_cond<<<1, 1, 0, cs>>>(dst, handle);
+  cudaGraph_t captured;
+  e = cudaStreamEndCapture(cs, &captured);
+  stream = saved;
+  cudaStreamDestroy(cs);
+  if (s) return s;
+  if (e != cudaSuccess) return ctx_fail(HISA_ERR_CUDA, "cudaStreamEndCapture", cudaGetErrorString(e));
+  CU(cudaGraphInstantiate(&graph_exec, graph, 0));
+  graph_stale = false;
+  return HISA_OK;
+}
+
+// ---- reading results ----------------------------------------------------------------------
+
+hisa_status Engine::relation_size(uint32_t rid, uint64_t* n) {
+  if (rid >= rels.size() || !n) return ctx_fail(HISA_ERR_INVALID_ARG, "relation_size", nullptr);
+  const Relation& r = rels[rid];
+  if (r.idb) *n = ran ? hs.cnt[r.full] : 0;
+  else *n = r.base >= 0 && !edb_dirty ? hs.cnt[r.base] : r.staged;
+  return HISA_OK;
+}
+
+hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t cap, uint64_t* n, int on_device) {
+  if (rid >= rels.size() || !cols || !n) return ctx_fail(HISA_ERR_INVALID_ARG, "read_relation", nullptr);
+  const Relation& r = rels[rid];
+  if (r.base < 0 || (!r.idb && edb_dirty) || (r.idb && !ran))
+    return ctx_fail(HISA_ERR_STATE, "relation not evaluated yet", nullptr);
+  const uint64_t size = hs.cnt[r.idb ? r.full : r.base];
+  *n = size;
+  if (cap < size) return ctx_fail(HISA_ERR_CAPACITY, "read_relation: buffer too small", nullptr);
+  if (size == 0) return HISA_OK;
+  uint32_t* d0 = cols[0];
+  uint32_t* d1 = cols[1];
+  void *t0 = nullptr, *t1 = nullptr;
+  hisa_status s;
+  if (!on_device) {
+    if ((s = dev_alloc(size * 4, &t0)) || (s = dev_alloc(size * 4, &t1))) return s;
+    d0 = static_cast<uint32_t*>(t0);
+    d1 = static_cast<uint32_t*>(t1);
+  }
+  DecodeArgs a{dst, r.idb ? r.full : r.base, 0, d0, d1, b, 0, 0, size};
+  if (wide) launch_decode<uint64_t>(a, grid, stream);
+  else launch_decode<uint32_t>(a, grid, stream);
+  if ((s = check_launch("decode"))) return s;
+  if (!on_device) {
+    CU(cudaMemcpyAsync(cols[0], d0, size * 4, cudaMemcpyDeviceToHost, stream));
+    CU(cudaMemcpyAsync(cols[1], d1, size * 4, cudaMemcpyDeviceToHost, stream));
+    dev_free(t0);
+    dev_free(t1);
+  }
+  CU(cudaStreamSynchronize(stream));
+  return HISA_OK;
+}
+
+hisa_status Engine::delta_counts(uint32_t rid, uint64_t* out, uint32_t cap, uint32_t* n_iters) {
+  if (rid >= rels.size() || !n_iters) return ctx_fail(HISA_ERR_INVALID_ARG, "delta_counts", nullptr);
+  const Relation& r = rels[rid];
+  if (!r.idb) return ctx_fail(HISA_ERR_INVALID_ARG, "delta_counts of an EDB relation", nullptr);
+  const uint32_t K = uint32_t(r.delta_counts.size());
+  *n_iters = K;
+  for (uint32_t i = 0; i < K && i < cap && out; ++i) out[i] = r.delta_counts[i];
+  if (cap < K) return ctx_fail(HISA_ERR_CAPACITY, "delta_counts: buffer too small", nullptr);
+  return HISA_OK;
+}
+
+__global__ void k_max2(const uint32_t* a, const uint32_t* b, uint64_t n, uint32_t* out) {
+  uint32_t m = 0;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
+    m = max(m, max(a[i], b[i]));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+hisa_status Engine::device_max(const uint32_t* a, const uint32_t* b2, uint64_t n, uint32_t* mx) {
+  void* p;
+  hisa_status s = dev_alloc(4, &p);
+  if (s) return s;
+  CU(cudaMemsetAsync(p, 0, 4, stream));
+  k_max2<<<grid.small, 256, 0, stream>>>(a, b2, n, static_cast<uint32_t*>(p));
+  if ((s = check_launch("max"))) return s;
+  CU(cudaMemcpyAsync(hs_pinned, p, 4, cudaMemcpyDeviceToHost, stream));
+  CU(cudaStreamSynchronize(stream));
+  std::memcpy(mx, hs_pinned, 4);
+  dev_free(p);
+  return HISA_OK;
+}
+
+}  // namespace hisa

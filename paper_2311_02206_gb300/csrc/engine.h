@@ -1,0 +1,128 @@
+// Engine state behind the C-ABI (include/hisa.h).
+#pragma once
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "hisa.h"
+#include "kernels.cuh"
+
+namespace hisa {
+
+struct Relation {
+  std::string name;
+  uint32_t arity = 2;
+  bool idb = false;
+  // EDB staging: raw columns as loaded
+  uint32_t* stage[2] = {nullptr, nullptr};
+  uint64_t staged = 0, stage_cap = 0;
+  uint32_t max_value = 0;
+  // slots (see DevState::buf): sorted codes in column order (c0,c1) and (c1,c0),
+  // and a run index over each order's first column
+  int base = -1, rev = -1;
+  int table[2] = {-1, -1};
+  bool need_idx[2] = {false, false};
+  // IDB versions (full == base)
+  int full = -1, full_next = -1, delta = -1, delta_next = -1;
+  int fresh = -1, fresh_alt = -1;   // "new" and its radix ping-pong partner
+  int hist = -1;                    // digit histograms of new
+  int history = -1;                 // |delta_k| per iteration
+  std::vector<uint64_t> delta_counts;
+};
+
+// One binary join (or a one-atom projection) of a compiled rule variant.
+struct StepPlan {
+  int outer_slot, outer_cnt, outer_kcol;
+  bool has_inner;
+  int inner_rel, inner_col;
+  int proj0, proj1;
+  int nfilt, fop[2], fa[2], fb[2];
+  bool to_tmp;
+  int out_rel;
+};
+
+struct Op {
+  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT } kind;
+  CtlArgs ctl;
+  JoinArgs join;
+  RadixPassArgs pass;
+  RadixHistArgs hist;
+  SetopArgs setop;
+  CommitArgs commit;
+};
+
+struct Scratch {
+  int empty, hist, radix_status, split, setop_status, offs, join_status, starts, tmp_a, tmp_b;
+  int runs, total, tmp_cnt;   // count-only slots
+};
+
+class Engine {
+ public:
+  ~Engine();
+  hisa_status init(const hisa_config& c);
+  hisa_status declare(const char* name, uint32_t arity, int is_idb, uint32_t* id);
+  hisa_status load(uint32_t rid, const uint32_t* const* cols, uint64_t n, int on_device);
+  hisa_status reset_edb();
+  hisa_status add_rule(const hisa_rule* r);
+  hisa_status run(hisa_run_stats* stats);
+  hisa_status relation_size(uint32_t rid, uint64_t* n);
+  hisa_status read_relation(uint32_t rid, uint32_t* const* cols, uint64_t cap, uint64_t* n, int on_device);
+  hisa_status delta_counts(uint32_t rid, uint64_t* out, uint32_t cap, uint32_t* n_iters);
+  hisa_status ctx_fail(hisa_status s, const char* what, const char* detail);
+
+  std::string last_error;
+
+ private:
+  hisa_status dev_alloc(size_t bytes, void** out);
+  void dev_free(void* p);
+  int new_slot(int elem_bytes);
+  hisa_status ensure(int id, uint64_t cap);
+  hisa_status upload();
+  hisa_status download();
+  hisa_status check_launch(const char* what);
+  hisa_status device_max(const uint32_t* a, const uint32_t* b, uint64_t n, uint32_t* mx);
+  hisa_status compile();
+  hisa_status plan_variant(const hisa_rule& R, int delta_atom, std::vector<StepPlan>& out);
+  void emit_join(std::vector<Op>& ops, const StepPlan& sp);
+  void emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepPlan>>& plans);
+  void emit_sort(std::vector<Op>& ops, int in, int alt, int cnt, int hist, int skip_mask, int stage_bit);
+  void emit_tail(std::vector<Op>& ops, bool force);
+  template <typename K> hisa_status exec_t(const std::vector<Op>& ops);
+  hisa_status exec(const std::vector<Op>& ops);
+  template <typename K> hisa_status prepare_rel_t(Relation& r, int order, int slot);
+  hisa_status prepare_edb();
+  hisa_status regrow();
+  hisa_status launch_graph();
+  hisa_status build_graph();
+
+  hisa_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  Grid grid;
+  DevState hs{};                 // host mirror of the device state
+  DevState* hs_pinned = nullptr; // staging for transfers
+  DevState* dst = nullptr;       // device copy
+  int nslots = 0;
+  int slot_elem[kMaxBufs] = {};
+  bool slot_zero[kMaxBufs] = {};   // zero on allocation (look-back status words)
+  std::unordered_map<void*, size_t> allocs;
+  uint64_t bytes_in_use = 0, peak_bytes = 0;
+  uint32_t regrows = 0;
+  Scratch sc{};
+  std::vector<Relation> rels;
+  std::vector<hisa_rule> rules;
+  std::vector<int> idb;
+  std::vector<std::vector<StepPlan>> plan1, planN;
+  std::vector<Op> ops1, opsN, tail;
+  bool compiled = false, edb_dirty = true, ran = false;
+  int b = 1;           // domain bits
+  bool wide = false;   // 64-bit codes
+  int passes = 1;      // radix passes over 2b bits
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  bool graph_stale = true;
+  hisa_run_stats last_stats{};
+};
+
+}  // namespace hisa

@@ -1,0 +1,443 @@
+// Range index over sorted runs and the binary join (Section 4.3, Algorithm 2,
+// Algorithm 3, Section 5.1 "Implementing Joins").
+//
+// Index: for every run of equal join keys (code >> b) in a sorted code array,
+// one open-addressing slot {key, length, begin} placed by linear probing from
+// fmix32(key).  Unlike the paper's table, the slot stores the key itself
+// rather than only its hash (two keys with equal hashes stay distinct) and the
+// run length next to its smallest position, so a probe returns the whole range
+// and no atomic-min loop is needed: only run heads are inserted.
+//
+// Join, outer scanned and inner range-probed as in Algorithm 3, in two passes:
+//   count: one probe per outer tuple gives its number of results; the counts
+//          are scanned (decoupled look-back) into absolute output offsets;
+//   write: the outputs are cut into equal chunks; each CTA finds the outer
+//          tuples covering its chunk (precomputed by a partition kernel),
+//          stages them with their probe results in shared memory and every
+//          thread writes outputs j by a binary search of the staged offsets,
+//          so a skewed run is spread over many threads instead of one.
+// Filters x != y / x == y are folded into the exact counts: against a value
+// fixed per outer tuple they keep or drop the whole run, against the inner
+// tuple's other column they remove or keep one position, found by binary
+// search in the run (the run's other column is sorted and distinct).
+#pragma once
+#include "common.cuh"
+
+namespace hisa {
+
+struct Slot {
+  uint32_t key;
+  uint32_t len;    // 0 = empty slot
+  uint64_t begin;
+};
+
+// Sources of a result column or filter operand.
+enum : int { kSrcOuter0 = 0, kSrcOuter1 = 1, kSrcKey = 2, kSrcOther = 3 };
+enum : int { kFiltNone = 0, kFiltNeq = 1, kFiltEq = 2 };
+
+struct IndexArgs {
+  DevState* st;
+  int keys_buf, keys_cnt;   // sorted codes
+  int table_buf;            // Slot[cap], cap a power of two, zeroed
+  int b;                    // domain bits: key = code >> b
+  int runs_cnt;             // cnt slot receiving the number of runs (-1: none)
+  int skip_mask;
+};
+
+struct JoinArgs {
+  DevState* st;
+  int outer_buf, outer_cnt;
+  int has_inner;
+  int inner_buf, inner_cnt, table_buf;
+  int b;                     // domain bits
+  int outer_kcol;            // outer column holding the join value
+  int proj0, proj1;          // sources of the result columns
+  int nfilt;
+  int fop[2], fa[2], fb[2];  // filters: op, operand sources
+  int offs_buf;              // u64 [n_outer + 1] absolute result offsets
+  int status_buf;            // u64 [tiles] look-back
+  int starts_buf;            // u64 [chunks + 1] first outer of each write chunk
+  int out_buf, out_cnt;      // results appended at cnt[out_cnt]
+  int total_cnt;             // cnt slot receiving this join's number of results
+  int hist_buf, hist_passes; // fused digit histogram of the results (-1: none)
+  int ctr;
+  int skip_mask, stage_bit;
+};
+
+constexpr int kJoinThreads = 256;
+constexpr int kJoinItems = 8;
+constexpr int kJoinTile = kJoinThreads * kJoinItems;   // outer tuples per count tile
+constexpr int kJoinChunk = kJoinThreads * 8;           // results per write chunk
+
+// instance id of a batched code (0 when the two columns fill the code)
+template <typename K>
+__device__ __forceinline__ uint64_t inst_of(K code, int b) {
+  return 2 * b >= 64 ? 0ull : (uint64_t(code) >> (2 * b));
+}
+__device__ __forceinline__ uint32_t join_key(uint64_t inst, uint32_t v, int b) {
+  return b >= 32 ? v : uint32_t((inst << b) | v);
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t colv(K code, int c, int b) {
+  const uint64_t m = (b >= 32) ? 0xFFFFFFFFull : ((1ull << b) - 1);
+  return c == 0 ? uint32_t((uint64_t(code) >> b) & m) : uint32_t(uint64_t(code) & m);
+}
+
+__device__ __forceinline__ bool probe(const Slot* table, uint64_t mask, uint32_t key, uint64_t* begin,
+                                      uint32_t* len, uint32_t* err) {
+  uint64_t h = fmix32(key) & mask;
+  for (uint64_t p = 0; p <= mask; ++p) {
+    const uint4 s = *reinterpret_cast<const uint4*>(&table[h]);
+    if (s.y == 0) return false;
+    if (s.x == key) {
+      *begin = (uint64_t(s.w) << 32) | s.z;
+      *len = s.y;
+      return true;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicExch(err, kDevProbeLimit);
+  return false;
+}
+
+// First position in inner[lo, lo+len) whose other column is >= v.
+template <typename K>
+__device__ __forceinline__ uint32_t run_lower_bound(const K* inner, uint64_t lo, uint32_t len, uint32_t v, int b) {
+  uint32_t l = 0, h = len;
+  while (l < h) {
+    const uint32_t m = (l + h) >> 1;
+    if (colv(inner[lo + m], 1, b) < v) l = m + 1;
+    else h = m;
+  }
+  return l;
+}
+
+// ---- index build -------------------------------------------------------------------
+
+template <typename K>
+__global__ void k_index_build(IndexArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const K* keys = static_cast<const K*>(st->buf[a.keys_buf].ptr);
+  const uint64_t n = st->cnt[a.keys_cnt];
+  Slot* table = static_cast<Slot*>(st->buf[a.table_buf].ptr);
+  const uint64_t mask = st->buf[a.table_buf].cap - 1;
+  uint32_t runs = 0;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t k = uint64_t(keys[i]) >> a.b;
+    if (i > 0 && (uint64_t(keys[i - 1]) >> a.b) == k) continue;
+    // run head: gallop to the end of the run
+    uint64_t step = 1, lo = i, hi = i + 1;
+    while (hi < n && (uint64_t(keys[hi]) >> a.b) == k) {
+      lo = hi;
+      hi = min(n, hi + step);
+      step <<= 1;
+    }
+    while (lo + 1 < hi) {  // keys[lo] has key k; keys[hi] (if < n) does not
+      const uint64_t m = (lo + hi) >> 1;
+      if ((uint64_t(keys[m]) >> a.b) == k) lo = m;
+      else hi = m;
+    }
+    const uint64_t len = hi - i;
+    ++runs;
+    uint64_t h = fmix32(uint32_t(k)) & mask;
+    const unsigned long long word = (unsigned long long)(uint32_t(k)) | ((unsigned long long)len << 32);
+    for (uint64_t p = 0; p <= mask; ++p) {
+      unsigned long long* w = reinterpret_cast<unsigned long long*>(&table[h]);
+      if (atomicCAS(w, 0ull, word) == 0ull) {
+        table[h].begin = i;
+        break;
+      }
+      h = (h + 1) & mask;
+      if (p == mask) atomicExch(&st->error, kDevProbeLimit);
+    }
+  }
+  if (a.runs_cnt >= 0) {
+    for (int o = 16; o > 0; o >>= 1) runs += __shfl_xor_sync(0xffffffffu, runs, o);
+    if ((threadIdx.x & 31) == 0 && runs) atomicAdd((unsigned long long*)&st->cnt[a.runs_cnt], (unsigned long long)runs);
+  }
+}
+
+// ---- join: per-outer probe ---------------------------------------------------------
+
+struct Probe {
+  uint64_t begin;
+  uint32_t cnt;   // number of results
+  uint32_t hole;  // run position removed (neq) or the only one kept (eq); 0xFFFFFFFF = none
+  uint32_t mode;  // 0 = whole run [minus hole], 1 = single position `hole`
+};
+
+template <typename K>
+__device__ __forceinline__ uint32_t src_value(int src, K outer, uint32_t key, int b, bool* fixed) {
+  *fixed = src != kSrcOther;
+  if (src == kSrcOuter0) return colv(outer, 0, b);
+  if (src == kSrcOuter1) return colv(outer, 1, b);
+  return key;  // kSrcKey (kSrcOther handled by the caller)
+}
+
+template <typename K>
+__device__ __forceinline__ Probe do_probe(const JoinArgs& a, K code, const K* inner, const Slot* table,
+                                          uint64_t mask, uint32_t* err) {
+  Probe p{0, 0, 0xFFFFFFFFu, 0};
+  const uint32_t v = colv(code, a.outer_kcol, a.b);
+  uint32_t len = 1;
+  if (a.has_inner) {
+    const uint32_t key = join_key(inst_of(code, a.b), v, a.b);
+    if (!probe(table, mask, key, &p.begin, &len, err)) return p;
+  }
+  // filters
+  for (int f = 0; f < a.nfilt; ++f) {
+    const int s0 = a.fa[f], s1 = a.fb[f];
+    if (s0 == kSrcOther && s1 == kSrcOther) {
+      if (a.fop[f] == kFiltNeq) return p;  // x != x never holds
+      continue;
+    }
+    if (s0 != kSrcOther && s1 != kSrcOther) {
+      bool fx;
+      const uint32_t x = src_value(s0, code, v, a.b, &fx), y = src_value(s1, code, v, a.b, &fx);
+      if ((a.fop[f] == kFiltNeq) == (x == y)) return p;
+      continue;
+    }
+    // one operand is the inner tuple's other column
+    bool fx;
+    const uint32_t x = src_value(s0 == kSrcOther ? s1 : s0, code, v, a.b, &fx);
+    const uint32_t pos = run_lower_bound(inner, p.begin, len, x, a.b);
+    const bool present = pos < len && colv(inner[p.begin + pos], 1, a.b) == x;
+    if (a.fop[f] == kFiltEq) {
+      if (!present || (p.mode == 0 && p.hole != 0xFFFFFFFFu && p.hole == pos)) return p;
+      if (p.mode == 1 && p.hole != pos) return p;
+      p.mode = 1;
+      p.hole = pos;
+      len = 1;
+    } else if (present) {
+      if (p.mode == 1) {
+        if (p.hole == pos) return p;
+      } else {
+        p.hole = pos;
+      }
+    }
+  }
+  if (p.mode == 1) {
+    p.cnt = 1;
+  } else {
+    p.cnt = len - (p.hole != 0xFFFFFFFFu ? 1 : 0);
+  }
+  return p;
+}
+
+// result r (0-based among this outer's results) -> inner position
+__device__ __forceinline__ uint64_t result_pos(const Probe& p, uint32_t r) {
+  if (p.mode == 1) return p.begin + p.hole;
+  return p.begin + ((p.hole != 0xFFFFFFFFu && r >= p.hole) ? r + 1 : r);
+}
+
+template <typename K>
+__device__ __forceinline__ K project(const JoinArgs& a, K outer, K inner_code, bool has_inner) {
+  const int b = a.b;
+  const uint32_t o0 = colv(outer, 0, b), o1 = colv(outer, 1, b);
+  const uint32_t key = colv(outer, a.outer_kcol, b);
+  const uint32_t oth = has_inner ? colv(inner_code, 1, b) : 0;
+  auto pick = [&](int s) -> uint32_t { return s == kSrcOuter0 ? o0 : s == kSrcOuter1 ? o1 : s == kSrcKey ? key : oth; };
+  const uint64_t hi = 2 * b >= 64 ? 0ull : (inst_of(outer, b) << (2 * b));
+  return K(hi | (uint64_t(pick(a.proj0)) << b) | uint64_t(pick(a.proj1)));
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kJoinThreads) k_join_count(JoinArgs a) {
+  __shared__ K s_code[kJoinTile];
+  __shared__ uint64_t s_off[kJoinTile];
+  __shared__ uint64_t s_scan[32];
+  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_tile;
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t n = st->cnt[a.outer_cnt];
+  const uint64_t ntiles = (n + kJoinTile - 1) / kJoinTile;
+  if (st->buf[a.offs_buf].cap < n + 1 || st->buf[a.status_buf].cap < ntiles) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+      atomicMax((unsigned long long*)&st->need[a.offs_buf], (unsigned long long)(n + 1));
+      atomicMax((unsigned long long*)&st->need[a.status_buf], (unsigned long long)ntiles);
+    }
+    return;
+  }
+  const K* outer = static_cast<const K*>(st->buf[a.outer_buf].ptr);
+  const K* inner = a.has_inner ? static_cast<const K*>(st->buf[a.inner_buf].ptr) : nullptr;
+  const Slot* table = a.has_inner ? static_cast<const Slot*>(st->buf[a.table_buf].ptr) : nullptr;
+  const uint64_t mask = a.has_inner ? st->buf[a.table_buf].cap - 1 : 0;
+  uint64_t* offs = static_cast<uint64_t*>(st->buf[a.offs_buf].ptr);
+  uint64_t* status = static_cast<uint64_t*>(st->buf[a.status_buf].ptr);
+  const uint32_t epoch = st->epoch;
+  const int tid = threadIdx.x;
+  if (n == 0) {
+    if (blockIdx.x == 0 && tid == 0) {
+      offs[0] = 0;
+      st->cnt[a.total_cnt] = 0;
+    }
+    return;
+  }
+  while (true) {
+    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    const uint64_t t0 = tile * kJoinTile;
+    const int nv = int(min(uint64_t(kJoinTile), n - t0));
+    for (int i = tid; i < nv; i += kJoinThreads) s_code[i] = outer[t0 + i];
+    __syncthreads();
+    uint32_t c[kJoinItems];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kJoinItems; ++k) {
+      const int i = tid * kJoinItems + k;
+      c[k] = 0;
+      if (i < nv) c[k] = do_probe<K>(a, s_code[i], inner, table, mask, &st->error).cnt;
+      sum += c[k];
+    }
+    uint64_t tot;
+    uint64_t ex = block_exclusive_sum<uint64_t>(sum, s_scan, &tot);
+    if (tid < 32) {
+      const uint64_t base = lookback_warp(status, tile, tot, epoch, &st->error);
+      if (tid == 0) s_base = base;
+    }
+    __syncthreads();
+    ex += s_base;
+#pragma unroll
+    for (int k = 0; k < kJoinItems; ++k) {
+      s_off[tid * kJoinItems + k] = ex;
+      ex += c[k];
+    }
+    __syncthreads();
+    for (int i = tid; i < nv; i += kJoinThreads) offs[t0 + i] = s_off[i];
+    if (tile == ntiles - 1 && tid == 0) {
+      const uint64_t total = s_base + tot;
+      offs[n] = total;
+      st->cnt[a.total_cnt] = total;
+      const uint64_t need = st->cnt[a.out_cnt] + total;
+      if (need > st->buf[a.out_buf].cap) {
+        atomicOr(&st->overflow, 1u << a.stage_bit);
+        atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)need);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// starts[c] = index of the outer tuple whose result range holds result c * chunk
+template <typename K>
+__global__ void k_join_partition(JoinArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t n = st->cnt[a.outer_cnt];
+  const uint64_t total = st->cnt[a.total_cnt];
+  const uint64_t nchunks = (total + kJoinChunk - 1) / kJoinChunk;
+  if (st->buf[a.starts_buf].cap < nchunks + 1) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+      atomicMax((unsigned long long*)&st->need[a.starts_buf], (unsigned long long)(nchunks + 1));
+    }
+    return;
+  }
+  const uint64_t* offs = static_cast<const uint64_t*>(st->buf[a.offs_buf].ptr);
+  uint64_t* starts = static_cast<uint64_t*>(st->buf[a.starts_buf].ptr);
+  for (uint64_t c = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; c <= nchunks; c += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t o = min(c * kJoinChunk, total);
+    // largest i in [0, n] with offs[i] <= o  (offs is non-decreasing, offs[0] = 0)
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const uint64_t m = (lo + hi + 1) >> 1;
+      if (offs[m] <= o) lo = m;
+      else hi = m - 1;
+    }
+    starts[c] = lo;
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
+  constexpr int S = kJoinThreads;   // outer tuples staged per batch
+  __shared__ uint64_t s_off[S + 1];
+  __shared__ K s_code[S];
+  __shared__ Probe s_pr[S];
+  __shared__ uint32_t s_hist[8][256];
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t n = st->cnt[a.outer_cnt];
+  const uint64_t total = st->cnt[a.total_cnt];
+  if (total == 0) return;
+  const uint64_t nchunks = (total + kJoinChunk - 1) / kJoinChunk;
+  const K* outer = static_cast<const K*>(st->buf[a.outer_buf].ptr);
+  const K* inner = a.has_inner ? static_cast<const K*>(st->buf[a.inner_buf].ptr) : nullptr;
+  const uint64_t n_inner = a.has_inner ? st->cnt[a.inner_cnt] : 0;
+  const Slot* table = a.has_inner ? static_cast<const Slot*>(st->buf[a.table_buf].ptr) : nullptr;
+  const uint64_t mask = a.has_inner ? st->buf[a.table_buf].cap - 1 : 0;
+  const uint64_t* offs = static_cast<const uint64_t*>(st->buf[a.offs_buf].ptr);
+  const uint64_t* starts = static_cast<const uint64_t*>(st->buf[a.starts_buf].ptr);
+  K* out = static_cast<K*>(st->buf[a.out_buf].ptr) + st->cnt[a.out_cnt];
+  const int tid = threadIdx.x;
+  const bool hist = a.hist_buf >= 0;
+  if (hist) {
+    for (int i = tid; i < a.hist_passes * 256; i += kJoinThreads) (&s_hist[0][0])[i] = 0;
+  }
+  for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const uint64_t o0 = ch * kJoinChunk, o1 = min(o0 + kJoinChunk, total);
+    uint64_t s = starts[ch];
+    const uint64_t last = starts[ch + 1];   // outer holding result o1 (or n)
+    while (true) {
+      __syncthreads();
+      const uint64_t i = s + tid;
+      if (i <= last && i < n) {
+        s_off[tid] = offs[i];
+        const K code = outer[i];
+        s_code[tid] = code;
+        s_pr[tid] = do_probe<K>(a, code, inner, table, mask, &st->error);
+      } else {
+        s_off[tid] = ~0ull;
+      }
+      if (tid == 0) {
+        const uint64_t e = s + S;
+        s_off[S] = e <= n ? offs[e] : total;
+        if (e > last) s_off[S] = ~0ull;
+      }
+      __syncthreads();
+      const uint64_t lo = max(o0, s_off[0]);
+      const uint64_t hi_batch = min(s_off[S], total);
+      const uint64_t hi = min(o1, hi_batch);
+      for (uint64_t j = lo + tid; j < hi; j += kJoinThreads) {
+        // staged outer k with s_off[k] <= j < s_off[k+1]
+        int l = 0, h = S - 1;
+        while (l < h) {
+          const int m = (l + h + 1) >> 1;
+          if (s_off[m] <= j) l = m;
+          else h = m - 1;
+        }
+        const Probe& p = s_pr[l];
+        const uint64_t r = j - s_off[l];
+        const uint64_t ip = result_pos(p, uint32_t(r));
+        if (r >= p.cnt || (a.has_inner && ip >= n_inner)) {   // offsets and probes disagree
+          atomicExch(&st->error, kDevBadState);
+          continue;
+        }
+        const K ic = a.has_inner ? inner[ip] : K(0);
+        const K v = project<K>(a, s_code[l], ic, a.has_inner);
+        out[j] = v;
+        if (hist) {
+          for (int q = 0; q < a.hist_passes; ++q) atomicAdd(&s_hist[q][(uint64_t(v) >> (8 * q)) & 0xFF], 1u);
+        }
+      }
+      if (hi_batch >= o1 || s + S > last) break;
+      s += S;
+    }
+  }
+  if (hist) {
+    __syncthreads();
+    unsigned long long* g = static_cast<unsigned long long*>(st->buf[a.hist_buf].ptr);
+    for (int i = tid; i < a.hist_passes * 256; i += kJoinThreads) {
+      const uint32_t v = (&s_hist[0][0])[i];
+      if (v) atomicAdd(&g[i], (unsigned long long)v);
+    }
+  }
+}
+
+}  // namespace hisa

@@ -1,0 +1,100 @@
+// Control, commit and conversion kernels plus the host-side launchers of every
+// kernel of the engine.  The launchers are templates over the code width K and
+// are instantiated for uint32_t and uint64_t in kernels_u32.cu / kernels_u64.cu.
+#pragma once
+#include "common.cuh"
+#include "join.cuh"
+#include "radix.cuh"
+#include "setops.cuh"
+
+namespace hisa {
+
+// ---- control commands (one tiny launch between stages) -------------------------------
+
+enum : int {
+  kCtlEpoch = 1,     // epoch++
+  kCtlResetCtr,      // tile_ctr[a] = 0
+  kCtlSetCnt,        // cnt[a] = b
+  kCtlAddCnt,        // cnt[a] += cnt[b]
+  kCtlCopyCnt,       // cnt[a] = cnt[b]
+  kCtlZeroSmall,     // zero the first b u64 words of buffer a
+};
+
+struct CtlCmd {
+  int op, a;
+  long long b;
+};
+constexpr int kMaxCtl = 24;
+struct CtlArgs {
+  DevState* st;
+  int n;
+  int skip_mask;
+  CtlCmd cmd[kMaxCtl];
+};
+
+struct CommitArgs {
+  DevState* st;
+  int nrel;
+  int full[8], full_next[8], delta[8], delta_next[8], history[8];
+  int force;   // commit even when no delta is non-empty (first iteration)
+};
+
+struct EncodeArgs {
+  DevState* st;
+  const uint32_t* c0;
+  const uint32_t* c1;
+  uint64_t n;
+  int out_buf, out_cnt;
+  int b;
+  int order;   // 0: (c0, c1); 1: (c1, c0)
+  uint64_t inst_code;  // instance id << 2b, or 0
+};
+
+struct DecodeArgs {
+  DevState* st;
+  int in_buf, in_cnt;
+  uint32_t* c0;
+  uint32_t* c1;
+  int b;
+  int order;
+  uint64_t begin, count;
+};
+
+struct ZeroArgs {
+  DevState* st;
+  int buf;
+  int elem_bytes;
+  int skip_mask;
+};
+
+struct RunsArgs {
+  DevState* st;
+  int keys_buf, keys_cnt, b, out_cnt;
+};
+
+// ---- launchers ------------------------------------------------------------------------
+
+struct Grid {
+  int sms = 152;
+  int radix = 152 * 4;
+  int setop = 152 * 4;
+  int join = 152 * 4;
+  int small = 152 * 2;
+};
+
+void launch_ctl(const CtlArgs& a, cudaStream_t s);
+void launch_commit(const CommitArgs& a, cudaStream_t s);
+void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s);
+
+template <typename K> void launch_encode(const EncodeArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_decode(const DecodeArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_radix_hist(const RadixHistArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_radix_pass(const RadixPassArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_setop(const SetopArgs& a, const Grid& g, cudaStream_t s);   // partition + merge
+template <typename K> void launch_index(const IndexArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_count_runs(const RunsArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_join(const JoinArgs& a, const Grid& g, cudaStream_t s);     // count + partition + write
+template <typename K> void launch_join_count(const JoinArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s);  // partition + write
+
+}  // namespace hisa

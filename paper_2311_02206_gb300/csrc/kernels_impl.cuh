@@ -1,0 +1,128 @@
+// Kernel bodies of the conversion/control kernels and the launcher templates.
+// Included once per code width by kernels_u32.cu / kernels_u64.cu.
+#pragma once
+#include "kernels.cuh"
+
+namespace hisa {
+
+template <typename K>
+__global__ void k_encode(EncodeArgs a) {
+  DevState* st = a.st;
+  K* out = static_cast<K*>(st->buf[a.out_buf].ptr) + st->cnt[a.out_cnt];
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < a.n; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t x = a.c0[i], y = a.c1[i];
+    out[i] = K(a.inst_code | (a.order == 0 ? ((x << a.b) | y) : ((y << a.b) | x)));
+  }
+}
+
+template <typename K>
+__global__ void k_decode(DecodeArgs a) {
+  DevState* st = a.st;
+  const K* in = static_cast<const K*>(st->buf[a.in_buf].ptr);
+  const uint64_t m = a.b >= 32 ? 0xFFFFFFFFull : ((1ull << a.b) - 1);
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < a.count; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t c = in[a.begin + i];
+    const uint32_t hi = uint32_t((c >> a.b) & m), lo = uint32_t(c & m);
+    a.c0[i] = a.order == 0 ? hi : lo;
+    a.c1[i] = a.order == 0 ? lo : hi;
+  }
+}
+
+template <typename K>
+__global__ void k_count_runs(RunsArgs a) {
+  DevState* st = a.st;
+  const K* keys = static_cast<const K*>(st->buf[a.keys_buf].ptr);
+  const uint64_t n = st->cnt[a.keys_cnt];
+  uint32_t runs = 0;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
+    runs += (i == 0 || (uint64_t(keys[i - 1]) >> a.b) != (uint64_t(keys[i]) >> a.b));
+  for (int o = 16; o > 0; o >>= 1) runs += __shfl_xor_sync(0xffffffffu, runs, o);
+  if ((threadIdx.x & 31) == 0 && runs) atomicAdd((unsigned long long*)&st->cnt[a.out_cnt], (unsigned long long)runs);
+}
+
+template <typename K>
+void launch_encode(const EncodeArgs& a, const Grid& g, cudaStream_t s) {
+  k_encode<K><<<g.small, 256, 0, s>>>(a);
+}
+template <typename K>
+void launch_decode(const DecodeArgs& a, const Grid& g, cudaStream_t s) {
+  k_decode<K><<<g.small, 256, 0, s>>>(a);
+}
+template <typename K>
+void launch_count_runs(const RunsArgs& a, const Grid& g, cudaStream_t s) {
+  k_count_runs<K><<<g.small, 256, 0, s>>>(a);
+}
+template <typename K>
+void launch_radix_hist(const RadixHistArgs& a, const Grid& g, cudaStream_t s) {
+  k_radix_hist<K><<<g.small, 256, 0, s>>>(a);
+}
+template <typename K>
+void launch_radix_pass(const RadixPassArgs& a, const Grid& g, cudaStream_t s) {
+  CtlArgs c{};
+  c.st = a.st;
+  c.skip_mask = a.skip_mask;
+  c.n = 2;
+  c.cmd[0] = {kCtlEpoch, 0, 0};
+  c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
+  launch_ctl(c, s);
+  k_radix_pass<K><<<g.radix, kRadixThreads, 0, s>>>(a);
+}
+template <typename K>
+void launch_setop(const SetopArgs& a, const Grid& g, cudaStream_t s) {
+  CtlArgs c{};
+  c.st = a.st;
+  c.skip_mask = a.skip_mask;
+  c.n = 2;
+  c.cmd[0] = {kCtlEpoch, 0, 0};
+  c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
+  launch_ctl(c, s);
+  k_setop_partition<K><<<g.small, 256, 0, s>>>(a);
+  k_setop<K><<<g.setop, kSetopThreads, 0, s>>>(a);
+}
+template <typename K>
+void launch_index(const IndexArgs& a, const Grid& g, cudaStream_t s) {
+  k_index_build<K><<<g.small, 256, 0, s>>>(a);
+}
+template <typename K>
+void launch_join(const JoinArgs& a, const Grid& g, cudaStream_t s) {
+  CtlArgs c{};
+  c.st = a.st;
+  c.skip_mask = a.skip_mask;
+  c.n = 2;
+  c.cmd[0] = {kCtlEpoch, 0, 0};
+  c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
+  launch_ctl(c, s);
+  k_join_count<K><<<g.join, kJoinThreads, 0, s>>>(a);
+  k_join_partition<K><<<g.small, 256, 0, s>>>(a);
+  k_join_write<K><<<g.join, kJoinThreads, 0, s>>>(a);
+  CtlArgs d{};
+  d.st = a.st;
+  d.skip_mask = a.skip_mask;
+  d.n = 1;
+  d.cmd[0] = {kCtlAddCnt, a.out_cnt, a.total_cnt};
+  launch_ctl(d, s);
+}
+
+template <typename K>
+void launch_join_count(const JoinArgs& a, const Grid& g, cudaStream_t s) {
+  k_join_count<K><<<g.join, kJoinThreads, 0, s>>>(a);
+}
+template <typename K>
+void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
+  k_join_partition<K><<<g.small, 256, 0, s>>>(a);
+  k_join_write<K><<<g.join, kJoinThreads, 0, s>>>(a);
+}
+
+#define HISA_INSTANTIATE(K)                                                              \
+  template void launch_encode<K>(const EncodeArgs&, const Grid&, cudaStream_t);          \
+  template void launch_decode<K>(const DecodeArgs&, const Grid&, cudaStream_t);          \
+  template void launch_count_runs<K>(const RunsArgs&, const Grid&, cudaStream_t);        \
+  template void launch_radix_hist<K>(const RadixHistArgs&, const Grid&, cudaStream_t);   \
+  template void launch_radix_pass<K>(const RadixPassArgs&, const Grid&, cudaStream_t);   \
+  template void launch_setop<K>(const SetopArgs&, const Grid&, cudaStream_t);            \
+  template void launch_index<K>(const IndexArgs&, const Grid&, cudaStream_t);            \
+  template void launch_join<K>(const JoinArgs&, const Grid&, cudaStream_t);              \
+  template void launch_join_count<K>(const JoinArgs&, const Grid&, cudaStream_t);        \
+  template void launch_join_write<K>(const JoinArgs&, const Grid&, cudaStream_t);
+
+}  // namespace hisa

@@ -1,0 +1,5 @@
+// 32-bit code instantiation of every templated kernel launcher.
+#include "kernels_impl.cuh"
+namespace hisa {
+HISA_INSTANTIATE(uint32_t)
+}

@@ -1,0 +1,236 @@
+// Populate delta and merge full/delta in one pass over merge-path tiles.
+//
+// Inputs: full (A, sorted, no duplicates) and new (B, sorted, may repeat).
+// Outputs: delta = distinct(B) \ A (Section 5.1 "Populating delta", a set
+// difference; the adjacent-duplicate test of Section 4.2 "Deduplication"
+// removes repeats of B) and full' = A U delta (Section 4.2/5.1 "Merge", the
+// merge-path merge of Green, McColl & Bader 2012 that Thrust provides).
+//
+// The merged sequence of A and B (ties: the A element first) is cut into
+// tiles of C elements; a partition kernel finds each tile's split (a_t, b_t)
+// by merge-path search.  Within a tile every thread merges ITEMS elements; a
+// B element is kept iff it differs from the previous B element and from the
+// last A element merged before it (the largest A element <= it).  Kept counts
+// are scanned across tiles by decoupled look-back; an A element at index i
+// lands at full'[i + kept before it], a kept B element at delta[d] and
+// full'[d + A elements before it].  Both outputs are staged in shared memory
+// and written coalesced.  Either output can be switched off: delta only
+// gives "unique \ full" (or plain unique when A is empty), full' only would
+// be a set union.
+#pragma once
+#include "common.cuh"
+
+namespace hisa {
+
+template <typename K>
+struct SetopCfg;
+template <>
+struct SetopCfg<uint32_t> { static constexpr int items = 16; };
+template <>
+struct SetopCfg<uint64_t> { static constexpr int items = 8; };
+constexpr int kSetopThreads = 256;
+template <typename K>
+__host__ __device__ constexpr int setop_tile() { return kSetopThreads * SetopCfg<K>::items; }
+
+struct SetopArgs {
+  DevState* st;
+  int a_buf, a_cnt;        // full
+  int b_buf, b_cnt;        // sorted new
+  int split_buf;           // u64 [tiles + 1]
+  int status_buf;          // u64 [tiles]
+  int d_buf, d_cnt;        // delta out (-1: none)
+  int f_buf, f_cnt;        // full' out (-1: none)
+  int ctr;
+  int skip_mask;           // st->overflow bits that cancel this launch
+  int stage_bit;           // overflow bit raised when an output is too small
+};
+
+// Number of A elements among the first d merged elements (ties take A first).
+template <typename K>
+__device__ __forceinline__ uint64_t merge_path(const K* A, uint64_t na, const K* B, uint64_t nb, uint64_t d) {
+  uint64_t lo = d > nb ? d - nb : 0;
+  uint64_t hi = d < na ? d : na;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (A[mid] <= B[d - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <typename K>
+__global__ void k_setop_partition(SetopArgs a) {
+  constexpr int C = setop_tile<K>();
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t na = st->cnt[a.a_cnt], nb = st->cnt[a.b_cnt];
+  const uint64_t D = na + nb;
+  const uint64_t ntiles = (D + C - 1) / C;
+  const K* A = static_cast<const K*>(st->buf[a.a_buf].ptr);
+  const K* B = static_cast<const K*>(st->buf[a.b_buf].ptr);
+  uint64_t* split = static_cast<uint64_t*>(st->buf[a.split_buf].ptr);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // capacity of the per-tile scratch (checked before any tile runs)
+    if (st->buf[a.split_buf].cap < ntiles + 1 || st->buf[a.status_buf].cap < ntiles) {
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+      atomicMax((unsigned long long*)&st->need[a.split_buf], (unsigned long long)(ntiles + 1));
+      atomicMax((unsigned long long*)&st->need[a.status_buf], (unsigned long long)ntiles);
+    }
+    if (a.d_cnt >= 0) st->cnt[a.d_cnt] = 0;
+    if (a.f_cnt >= 0) st->cnt[a.f_cnt] = na;
+  }
+  if (st->buf[a.split_buf].cap < ntiles + 1) return;
+  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t <= ntiles;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t d = min(t * C, D);
+    split[t] = merge_path(A, na, B, nb, d);
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSetopThreads) k_setop(SetopArgs a) {
+  constexpr int ITEMS = SetopCfg<K>::items;
+  constexpr int C = kSetopThreads * ITEMS;
+  __shared__ K s_in[C];     // A part then B part; reused for the full' tile
+  __shared__ K s_d[C];      // delta tile
+  __shared__ uint64_t s_scan[32];
+  __shared__ uint64_t s_dbase;
+  __shared__ uint32_t s_tile;
+  __shared__ K s_prevA, s_prevB;
+  __shared__ int s_hasA, s_hasB;
+
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t na = st->cnt[a.a_cnt], nb = st->cnt[a.b_cnt];
+  if (nb == 0) return;   // nothing new: delta stays empty, full' is not needed
+  const uint64_t D = na + nb;
+  const uint64_t ntiles = (D + C - 1) / C;
+  if (st->buf[a.split_buf].cap < ntiles + 1 || st->buf[a.status_buf].cap < ntiles) return;
+  const K* A = static_cast<const K*>(st->buf[a.a_buf].ptr);
+  const K* B = static_cast<const K*>(st->buf[a.b_buf].ptr);
+  const uint64_t* split = static_cast<const uint64_t*>(st->buf[a.split_buf].ptr);
+  uint64_t* status = static_cast<uint64_t*>(st->buf[a.status_buf].ptr);
+  K* dout = a.d_buf >= 0 ? static_cast<K*>(st->buf[a.d_buf].ptr) : nullptr;
+  K* fout = a.f_buf >= 0 ? static_cast<K*>(st->buf[a.f_buf].ptr) : nullptr;
+  const uint64_t dcap = a.d_buf >= 0 ? st->buf[a.d_buf].cap : 0;
+  const uint64_t fcap = a.f_buf >= 0 ? st->buf[a.f_buf].cap : 0;
+  const uint32_t epoch = st->epoch;
+  const int tid = threadIdx.x;
+
+  while (true) {
+    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    const uint64_t d0 = tile * C, d1 = min(d0 + C, D);
+    const uint64_t a0 = split[tile], a1 = split[tile + 1];
+    const uint64_t b0 = d0 - a0, b1 = d1 - a1;
+    const int nA = int(a1 - a0), nB = int(b1 - b0), nT = nA + nB;
+    for (int i = tid; i < nA; i += kSetopThreads) s_in[i] = A[a0 + i];
+    for (int i = tid; i < nB; i += kSetopThreads) s_in[nA + i] = B[b0 + i];
+    if (tid == 0) {
+      s_hasA = a0 > 0;
+      if (a0 > 0) s_prevA = A[a0 - 1];
+      s_hasB = b0 > 0;
+      if (b0 > 0) s_prevB = B[b0 - 1];
+    }
+    __syncthreads();
+    const K* sA = s_in;
+    const K* sB = s_in + nA;
+    // this thread's slice of the tile's merged sequence
+    const int dt = min(tid * ITEMS, nT);
+    int ai, bi;
+    {
+      int lo = max(0, dt - nB), hi = min(dt, nA);
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sA[mid] <= sB[dt - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+      }
+      ai = lo;
+      bi = dt - lo;
+    }
+    const int ai0 = ai;
+    K val[ITEMS];
+    uint32_t kind = 0;   // bit k: item k is a kept B element
+    uint32_t isA = 0;    // bit k: item k is an A element
+    int nitems = 0;
+    int kept = 0;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      if (ai + bi >= nT || dt + k >= nT) break;
+      const bool takeA = bi >= nB || (ai < nA && sA[ai] <= sB[bi]);
+      if (takeA) {
+        val[k] = sA[ai];
+        isA |= 1u << k;
+        ++ai;
+      } else {
+        const K x = sB[bi];
+        const bool hasPrevB = bi > 0 || s_hasB;
+        const K pb = bi > 0 ? sB[bi - 1] : s_prevB;
+        const bool hasPrevA = ai > 0 || s_hasA;
+        const K pa = ai > 0 ? sA[ai - 1] : s_prevA;
+        const bool keep = !(hasPrevB && pb == x) && !(hasPrevA && pa == x);
+        val[k] = x;
+        if (keep) {
+          kind |= 1u << k;
+          ++kept;
+        }
+        ++bi;
+      }
+      ++nitems;
+    }
+    uint64_t tile_kept;
+    const uint32_t kexcl = uint32_t(block_exclusive_sum<uint64_t>(kept, s_scan, &tile_kept));
+    if (tid < 32) {
+      const uint64_t db = lookback_warp(status, tile, tile_kept, epoch, &st->error);
+      if (tid == 0) s_dbase = db;
+    }
+    __syncthreads();   // s_in is free: every thread holds its items in registers
+    const uint64_t dbase = s_dbase;
+    // stage outputs: full' tile index = A items before + kept before
+    int fa = ai0, kk = int(kexcl);
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      if (k >= nitems) break;
+      if (isA & (1u << k)) {
+        s_in[fa + kk] = val[k];
+        ++fa;
+      } else if (kind & (1u << k)) {
+        s_in[fa + kk] = val[k];
+        s_d[kk] = val[k];
+        ++kk;
+      }
+    }
+    __syncthreads();
+    const int nF = nA + int(tile_kept);
+    if (fout) {
+      const uint64_t f0 = a0 + dbase;
+      for (int i = tid; i < nF; i += kSetopThreads)
+        if (f0 + i < fcap) fout[f0 + i] = s_in[i];
+    }
+    if (dout) {
+      for (int i = tid; i < int(tile_kept); i += kSetopThreads)
+        if (dbase + i < dcap) dout[dbase + i] = s_d[i];
+    }
+    if (tile == ntiles - 1 && tid == 0) {
+      const uint64_t nd = dbase + tile_kept;
+      const uint64_t nf = na + nd;
+      if (a.d_cnt >= 0) st->cnt[a.d_cnt] = nd;
+      if (a.f_cnt >= 0) st->cnt[a.f_cnt] = nf;
+      bool over = false;
+      if (dout && nd > dcap) {
+        atomicMax((unsigned long long*)&st->need[a.d_buf], (unsigned long long)nd);
+        over = true;
+      }
+      if (fout && nf > fcap) {
+        atomicMax((unsigned long long*)&st->need[a.f_buf], (unsigned long long)nf);
+        over = true;
+      }
+      if (over) atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace hisa

@@ -1,0 +1,368 @@
+"""Python binding of libhisa.so (include/hisa.h, include/hisa_prims.h).
+
+Argument marshalling only: every step of evaluation runs in the CUDA library.
+PyTorch supplies device memory (its caching allocator, through the library's
+allocator hooks) and the CUDA stream.  Importing works without a GPU; any call
+that needs the library raises if libhisa.so is missing or cannot run -- there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhisa.so")
+
+HISA_OK = 0
+FLAG_GRAPH = 1
+FLAG_PHASE_TIMES = 2
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("alloc", _ALLOC_FN),
+        ("free", _FREE_FN),
+        ("user", ctypes.c_void_p),
+        ("cuda_stream", ctypes.c_void_p),
+        ("hbm_budget_bytes", ctypes.c_uint64),
+        ("load_factor", ctypes.c_float),
+        ("ebm_k", ctypes.c_float),
+        ("max_iters", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
+        ("device", ctypes.c_int32),
+    ]
+
+
+class Atom(ctypes.Structure):
+    _fields_ = [("rel", ctypes.c_uint32), ("var", ctypes.c_uint32 * 2)]
+
+
+class Rule(ctypes.Structure):
+    _fields_ = [
+        ("head", Atom),
+        ("n_body", ctypes.c_uint32),
+        ("body", Atom * 3),
+        ("n_neq", ctypes.c_uint32),
+        ("neq", (ctypes.c_uint32 * 2) * 2),
+    ]
+
+
+class RunStats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_uint32),
+        ("iterations_run", ctypes.c_uint32),
+        ("regrows", ctypes.c_uint32),
+        ("graph_launches", ctypes.c_uint32),
+        ("ms_total", ctypes.c_double),
+        ("ms_edb", ctypes.c_double),
+        ("ms_join", ctypes.c_double),
+        ("ms_sort", ctypes.c_double),
+        ("ms_merge", ctypes.c_double),
+        ("tuples_joined", ctypes.c_uint64),
+        ("peak_bytes", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# entry point -> (restype, argtypes); the complete list of include/*.h declarations
+_P = ctypes.c_void_p
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+SIGNATURES = {
+    "hisa_config_default": (ctypes.c_int32, [ctypes.POINTER(Config)]),
+    "hisa_create": (ctypes.c_int32, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
+    "hisa_destroy": (ctypes.c_int32, [_P]),
+    "hisa_declare_relation": (ctypes.c_int32, [_P, ctypes.c_char_p, ctypes.c_uint32, ctypes.c_int, _U32P]),
+    "hisa_load_tuples": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint64,
+                                          ctypes.c_int]),
+    "hisa_add_rule": (ctypes.c_int32, [_P, ctypes.POINTER(Rule)]),
+    "hisa_run": (ctypes.c_int32, [_P, ctypes.POINTER(RunStats)]),
+    "hisa_reset_edb": (ctypes.c_int32, [_P]),
+    "hisa_relation_size": (ctypes.c_int32, [_P, ctypes.c_uint32, _U64P]),
+    "hisa_read_relation": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint64,
+                                            _U64P, ctypes.c_int]),
+    "hisa_delta_counts": (ctypes.c_int32, [_P, ctypes.c_uint32, _U64P, ctypes.c_uint32, _U32P]),
+    "hisa_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
+    "hisa_last_error": (ctypes.c_char_p, [_P]),
+    "hisa_sort_codes": (ctypes.c_int32, [_P, _P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _P]),
+    "hisa_sort_unique_codes": (ctypes.c_int32, [_P, _P, ctypes.c_uint64, _U64P, ctypes.c_int, ctypes.c_int, _P]),
+    "hisa_difference_merge": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, _P, ctypes.c_uint64, _P,
+                                               ctypes.c_uint64, _U64P, ctypes.c_int, _P]),
+    "hisa_join_codes": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint64, _U64P,
+                                         ctypes.c_int, _P]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libhisa.so (built by ``paper_2311_02206_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run paper_2311_02206_gb300.build.build() first "
+                               "(the CUDA library is required; there is no CPU path)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class HisaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"hisa status {status}: {msg}")
+        self.status = status
+
+
+def _check(rc: int, ctx=None):
+    if rc < 0:
+        lib = load_library()
+        detail = lib.hisa_status_string(rc).decode()
+        if ctx is not None:
+            extra = lib.hisa_last_error(ctx).decode()
+            if extra:
+                detail += f" ({extra})"
+        raise HisaError(rc, detail)
+    return rc
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """One engine instance on one CUDA device and stream (include/hisa.h)."""
+
+    def __init__(self, device: int = 0, stream=None, flags: int = FLAG_GRAPH, max_iters: int = 0,
+                 load_factor: float = 0.0, ebm_k: float = 0.0, hbm_budget_bytes: int = 0,
+                 torch_allocator: bool = True):
+        lib = load_library()
+        torch = _torch()
+        self._lib = lib
+        self.device = device
+        cfg = Config()
+        _check(lib.hisa_config_default(ctypes.byref(cfg)))
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self._stream = stream
+        cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        cfg.device = device
+        cfg.flags = flags
+        cfg.max_iters = max_iters
+        cfg.load_factor = load_factor
+        cfg.ebm_k = ebm_k
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        if torch_allocator:
+            def _alloc(nbytes, strm, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(strm or 0))
+                except Exception:   # out of memory: the library reports HISA_ERR_OOM
+                    return None
+
+            def _free(ptr, nbytes, strm, user):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._alloc_cb = _ALLOC_FN(_alloc)
+            self._free_cb = _FREE_FN(_free)
+            cfg.alloc = self._alloc_cb
+            cfg.free = self._free_cb
+        self._cfg = cfg
+        h = ctypes.c_void_p()
+        _check(lib.hisa_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.rel_ids: dict[str, int] = {}
+
+    # -- lifecycle --
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hisa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- program --
+    def declare_relation(self, name: str, arity: int = 2, idb: bool = False) -> int:
+        rid = ctypes.c_uint32()
+        _check(self._lib.hisa_declare_relation(self._h, name.encode(), arity, int(idb), ctypes.byref(rid)), self._h)
+        self.rel_ids[name] = rid.value
+        return rid.value
+
+    def load_tuples(self, rel, c0, c1):
+        """Appends tuples; c0/c1 are numpy uint32 arrays (host) or torch uint32/int32
+        CUDA tensors (device)."""
+        rid = self.rel_ids[rel] if isinstance(rel, str) else rel
+        torch = _torch()
+        if isinstance(c0, torch.Tensor):
+            c0 = c0.contiguous()
+            c1 = c1.contiguous()
+            assert c0.is_cuda and c0.element_size() == 4 and c0.numel() == c1.numel()
+            ptrs = (ctypes.c_void_p * 2)(c0.data_ptr(), c1.data_ptr())
+            _check(self._lib.hisa_load_tuples(self._h, rid, ptrs, c0.numel(), 1), self._h)
+        else:
+            c0 = np.ascontiguousarray(c0, dtype=np.uint32)
+            c1 = np.ascontiguousarray(c1, dtype=np.uint32)
+            assert len(c0) == len(c1)
+            ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
+            _check(self._lib.hisa_load_tuples(self._h, rid, ptrs, len(c0), 0), self._h)
+
+    def add_rule(self, head, body, neq=()):
+        """head/body atoms as (relation, (var, var)); variables are any hashable
+        names (mapped to ids 0..15 in order of first use); neq: pairs of vars."""
+        names: dict = {}
+
+        def vid(v):
+            if v not in names:
+                names[v] = len(names)
+            return names[v]
+
+        r = Rule()
+        for i, (rel, (a, b)) in enumerate(body):
+            r.body[i].rel = self.rel_ids[rel]
+            r.body[i].var[0] = vid(a)
+            r.body[i].var[1] = vid(b)
+        r.n_body = len(body)
+        r.head.rel = self.rel_ids[head[0]]
+        r.head.var[0] = vid(head[1][0])
+        r.head.var[1] = vid(head[1][1])
+        r.n_neq = len(neq)
+        for i, (a, b) in enumerate(neq):
+            r.neq[i][0] = vid(a)
+            r.neq[i][1] = vid(b)
+        _check(self._lib.hisa_add_rule(self._h, ctypes.byref(r)), self._h)
+
+    def program(self, relations: dict, rules: Iterable):
+        """Declares ``relations`` (name -> "edb"/"idb") and adds ``rules``
+        ((head, body, neq) tuples)."""
+        for name, kind in relations.items():
+            self.declare_relation(name, 2, kind == "idb")
+        for head, body, neq in rules:
+            self.add_rule(head, body, neq)
+
+    def run(self) -> RunStats:
+        st = RunStats()
+        _check(self._lib.hisa_run(self._h, ctypes.byref(st)), self._h)
+        return st
+
+    def reset_edb(self):
+        _check(self._lib.hisa_reset_edb(self._h), self._h)
+
+    # -- results --
+    def relation_size(self, rel) -> int:
+        rid = self.rel_ids[rel] if isinstance(rel, str) else rel
+        n = ctypes.c_uint64()
+        _check(self._lib.hisa_relation_size(self._h, rid, ctypes.byref(n)), self._h)
+        return n.value
+
+    def read_relation(self, rel, device: bool = False):
+        """Returns (c0, c1) in lexicographic order: numpy uint32 arrays, or torch
+        int32 CUDA tensors (the uint32 bit patterns) when ``device``."""
+        rid = self.rel_ids[rel] if isinstance(rel, str) else rel
+        n = self.relation_size(rid)
+        got = ctypes.c_uint64()
+        if device:
+            torch = _torch()
+            c0 = torch.empty(max(n, 1), dtype=torch.int32, device=f"cuda:{self.device}")
+            c1 = torch.empty(max(n, 1), dtype=torch.int32, device=f"cuda:{self.device}")
+            ptrs = (ctypes.c_void_p * 2)(c0.data_ptr(), c1.data_ptr())
+            _check(self._lib.hisa_read_relation(self._h, rid, ptrs, n, ctypes.byref(got), 1), self._h)
+            return c0[:n], c1[:n]
+        c0 = np.empty(max(n, 1), np.uint32)
+        c1 = np.empty(max(n, 1), np.uint32)
+        ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
+        _check(self._lib.hisa_read_relation(self._h, rid, ptrs, n, ctypes.byref(got), 0), self._h)
+        return c0[:n], c1[:n]
+
+    def delta_counts(self, rel) -> list:
+        rid = self.rel_ids[rel] if isinstance(rel, str) else rel
+        k = ctypes.c_uint32()
+        self._lib.hisa_delta_counts(self._h, rid, None, 0, ctypes.byref(k))
+        out = (ctypes.c_uint64 * max(k.value, 1))()
+        _check(self._lib.hisa_delta_counts(self._h, rid, out, k.value, ctypes.byref(k)), self._h)
+        return [int(out[i]) for i in range(k.value)]
+
+
+# ---- primitives (include/hisa_prims.h) on torch CUDA tensors -----------------------------
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _kb(t):
+    return t.element_size()
+
+
+def sort_codes(codes, key_bits: int = 0, stream=None):
+    """Ascending sort of a 1-D int32/int64 CUDA tensor of codes (unsigned order)."""
+    torch = _torch()
+    out = torch.empty_like(codes)
+    _check(load_library().hisa_sort_codes(codes.data_ptr(), out.data_ptr(), codes.numel(), _kb(codes), key_bits,
+                                          _stream_ptr(stream)))
+    return out
+
+
+def sort_unique_codes(codes, key_bits: int = 0, stream=None):
+    torch = _torch()
+    out = torch.empty_like(codes)
+    n = ctypes.c_uint64()
+    _check(load_library().hisa_sort_unique_codes(codes.data_ptr(), out.data_ptr(), codes.numel(), ctypes.byref(n),
+                                                 _kb(codes), key_bits, _stream_ptr(stream)))
+    return out[:n.value]
+
+
+def difference_merge(full, fresh, with_full: bool = True, stream=None):
+    """(delta, full') for sorted distinct ``full`` and sorted ``fresh`` codes."""
+    torch = _torch()
+    d = torch.empty(max(fresh.numel(), 1), dtype=fresh.dtype, device=fresh.device)
+    f = torch.empty(max(full.numel() + fresh.numel(), 1), dtype=fresh.dtype, device=fresh.device) if with_full else None
+    n = ctypes.c_uint64()
+    _check(load_library().hisa_difference_merge(
+        full.data_ptr() if full.numel() else None, full.numel(), fresh.data_ptr() if fresh.numel() else None,
+        fresh.numel(), d.data_ptr(), d.numel(), f.data_ptr() if f is not None else None,
+        f.numel() if f is not None else 0, ctypes.byref(n), _kb(fresh), _stream_ptr(stream)))
+    nd = n.value
+    return d[:nd], (f[:full.numel() + nd] if f is not None else None)
+
+
+def join_codes(outer, inner, b: int, outer_col: int, proj0: int, proj1: int, neq: int = 0, stream=None):
+    """Results of Algorithm 3 as codes (outer order, run order inside an outer)."""
+    torch = _torch()
+    lib = load_library()
+    n = ctypes.c_uint64()
+    cap = max(outer.numel(), 1)
+    for _ in range(2):
+        out = torch.empty(cap, dtype=outer.dtype, device=outer.device)
+        rc = lib.hisa_join_codes(outer.data_ptr() if outer.numel() else None, outer.numel(),
+                                 inner.data_ptr() if inner.numel() else None, inner.numel(), b, outer_col, proj0,
+                                 proj1, neq, out.data_ptr(), cap, ctypes.byref(n), _kb(outer), _stream_ptr(stream))
+        if rc == -9:   # HISA_ERR_CAPACITY: n holds the size
+            cap = max(n.value, 1)
+            continue
+        _check(rc)
+        return out[:n.value]
+    raise HisaError(-9, "join output did not fit")

@@ -1,0 +1,174 @@
+"""Fixpoint parity of the CUDA engine (through the C-ABI) with the CPU oracle:
+identical sorted relations and identical per-iteration delta counts."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_02206_gb300 import workloads
+from hisa_testutil import assert_same, fingerprint_device, gpu_eval
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2311_02206_gb300 import build
+    build.build()
+
+
+def modes():
+    from paper_2311_02206_gb300 import hisa
+    return [0, hisa.FLAG_GRAPH]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_reach_random_small(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 60))
+    m = int(rng.integers(1, 4 * n))
+    s = rng.integers(0, n, m).astype(np.uint32)          # repeats and self-loops included
+    d = rng.integers(0, n, m).astype(np.uint32)
+    ref = oracle.reach(s, d)
+    for flags in modes():
+        rels, counts, _ = gpu_eval(*oracle.REACH, {"Edge": (s, d)}, flags=flags)
+        assert_same(rels, counts, ref)
+
+
+@pytest.mark.parametrize("shape,n", [("path", 300), ("cycle", 64), ("dag", 120), ("path", 2)])
+def test_reach_closed_forms(shape, n):
+    src, dst = {"path": workloads.path_graph, "cycle": workloads.cycle_graph,
+                "dag": workloads.complete_dag}[shape](n)
+    rels, counts, st = gpu_eval(*oracle.REACH, {"Edge": (src, dst)})
+    size = len(rels["Reach"][0])
+    if shape == "path":
+        assert size == n * (n - 1) // 2 and counts["Reach"] == [n - k for k in range(1, n)]
+    elif shape == "cycle":
+        assert size == n * n and counts["Reach"] == [n] * n
+    else:
+        assert size == n * (n - 1) // 2 and counts["Reach"] == [n * (n - 1) // 2]
+
+
+def test_reach_er_1000():
+    """REACH on the ER graph n=1,000, m=3,000 (seed 0): the whole relation."""
+    s, d = workloads.config_reach_er()
+    ref = oracle.reach(s, d)
+    for flags in modes():
+        rels, counts, st = gpu_eval(*oracle.REACH, {"Edge": (s, d)}, flags=flags)
+        assert_same(rels, counts, ref)
+    assert ref.size("Reach") == 889_271
+
+
+def test_reach_wide_codes():
+    """Node ids spread over the full uint32 range (64-bit codes, b = 32)."""
+    rng = np.random.default_rng(11)
+    s = rng.integers(0, 50, 120).astype(np.uint64)
+    d = rng.integers(0, 50, 120).astype(np.uint64)
+    relabel = (np.arange(50, dtype=np.uint64) * np.uint64(0x9E3779B1) + np.uint64(0xFFFF0000)) % np.uint64(1 << 32)
+    relabel[0] = 0xFFFFFFFF
+    s, d = relabel[s].astype(np.uint32), relabel[d].astype(np.uint32)
+    ref = oracle.reach(s, d)
+    rels, counts, _ = gpu_eval(*oracle.REACH, {"Edge": (s, d)})
+    assert_same(rels, counts, ref)
+
+
+def test_reach_empty_and_single():
+    e = np.zeros(0, np.uint32)
+    rels, counts, st = gpu_eval(*oracle.REACH, {"Edge": (e, e)})
+    assert len(rels["Reach"][0]) == 0 and counts["Reach"] == []
+    one = np.array([3], np.uint32)
+    rels, counts, st = gpu_eval(*oracle.REACH, {"Edge": (one, one)})
+    assert rels["Reach"][0].tolist() == [3] and counts["Reach"] == [1]
+
+
+def test_reach_deterministic_and_reusable():
+    from paper_2311_02206_gb300 import hisa
+    s, d = workloads.er_graph(400, 1200, 7)
+    with hisa.Context() as ctx:
+        ctx.program(*oracle.REACH)
+        ctx.load_tuples("Edge", s, d)
+        ctx.run()
+        a = ctx.read_relation("Reach"), ctx.delta_counts("Reach")
+        ctx.run()
+        b = ctx.read_relation("Reach"), ctx.delta_counts("Reach")
+    assert np.array_equal(a[0][0], b[0][0]) and np.array_equal(a[0][1], b[0][1]) and a[1] == b[1]
+
+
+def test_load_from_device_tensors():
+    from paper_2311_02206_gb300 import hisa
+    s, d = workloads.er_graph(300, 900, 3)
+    ref = oracle.reach(s, d)
+    with hisa.Context() as ctx:
+        ctx.program(*oracle.REACH)
+        half = len(s) // 2
+        ctx.load_tuples("Edge", torch.from_numpy(s[:half].view(np.int32)).cuda(),
+                        torch.from_numpy(d[:half].view(np.int32)).cuda())
+        ctx.load_tuples("Edge", s[half:], d[half:])
+        ctx.run()
+        c0, c1 = ctx.read_relation("Reach", device=True)
+        assert np.array_equal(c0.cpu().numpy().view(np.uint32), ref.relations["Reach"][0])
+        assert np.array_equal(c1.cpu().numpy().view(np.uint32), ref.relations["Reach"][1])
+
+
+def test_not_converged_and_budget_errors():
+    from paper_2311_02206_gb300 import hisa
+    s, d = workloads.path_graph(50)
+    with hisa.Context(max_iters=10) as ctx:
+        ctx.program(*oracle.REACH)
+        ctx.load_tuples("Edge", s, d)
+        with pytest.raises(hisa.HisaError) as e:
+            ctx.run()
+        assert e.value.status == -4
+    with hisa.Context(hbm_budget_bytes=1 << 20) as ctx:
+        ctx.program(*oracle.REACH)
+        with pytest.raises(hisa.HisaError) as e:
+            ctx.load_tuples("Edge", *workloads.er_graph(2000, 8000, 1))
+            ctx.run()
+        assert e.value.status == -3
+
+
+@pytest.mark.parametrize("depth", [3, 6])
+def test_sg_binary_tree(depth):
+    rels, counts, _ = gpu_eval(*oracle.SG, {"Edge": workloads.binary_tree(depth)})
+    ref = oracle.seminaive(*oracle.SG, {"Edge": workloads.binary_tree(depth)})
+    assert_same(rels, counts, ref)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sg_random_dag(seed):
+    s, d = workloads.dag_graph(300, 700, 16, seed)
+    ref = oracle.seminaive(*oracle.SG, {"Edge": (s, d)})
+    for flags in modes():
+        rels, counts, _ = gpu_eval(*oracle.SG, {"Edge": (s, d)}, flags=flags)
+        assert_same(rels, counts, ref)
+
+
+def test_reach_rmat_full_size_golden_and_sampled():
+    """REACH on R-MAT scale 16 / 2**19 edges, in the launch configuration the
+    benchmark times: total size, delta counts and fingerprint against the
+    oracle's stored values, and 16 sampled target columns element by element."""
+    path = os.path.join(GOLDEN, "reach_rmat_s16.json")
+    if not os.path.exists(path):
+        pytest.skip("golden values not generated")
+    g = json.load(open(path))
+    from paper_2311_02206_gb300 import hisa
+    s, d = workloads.config_reach_rmat()
+    with hisa.Context() as ctx:
+        ctx.program(*oracle.REACH)
+        ctx.load_tuples("Edge", s, d)
+        ctx.run()
+        assert ctx.delta_counts("Reach") == g["delta_counts"]
+        assert ctx.relation_size("Reach") == g["reach_size"]
+        c0, c1 = ctx.read_relation("Reach", device=True)
+        assert fingerprint_device(c0, c1) == int(g["fingerprint"])
+        targets = np.random.default_rng(2024).choice(1 << 16, 16, replace=False).astype(np.uint32)
+        ref = oracle.reach_targets(s, d, targets)
+        keep = torch.isin(c1, torch.from_numpy(targets.view(np.int32)).cuda())
+        g0 = c0[keep].cpu().numpy().view(np.uint32)
+        g1 = c1[keep].cpu().numpy().view(np.uint32)
+        assert np.array_equal(g0, ref.relations["Reach"][0]) and np.array_equal(g1, ref.relations["Reach"][1])

@@ -305,3 +305,29 @@ def test_pins_catch_planted_mistake(k, tmp_path, monkeypatch):
     finally:
         oracle._lib = saved
     del lib
+
+
+def test_code_join_matches_tuple_join():
+    """The code-level join definition agrees with the nested-loop definition."""
+    rng = np.random.default_rng(5)
+    b = 6
+    o = rng.integers(0, 9, (60, 2)).astype(np.uint32)
+    i = np.unique(rng.integers(0, 9, (40, 2)).astype(np.uint32), axis=0)
+    for col in (0, 1):
+        for proj in [(3, 1), (0, 2), (1, 3)]:
+            side = [("o", 0), ("o", 1), ("i", 0), ("i", 1)]
+            want = primitives.join(o, [col], i, [0], [side[proj[0]], side[proj[1]]])
+            got = primitives.join_codes(primitives.encode_rows(o, b), primitives.encode_rows(i, b), b, col, *proj)
+            assert np.array_equal(primitives.decode_codes(got, b), want)
+    got = primitives.join_codes(primitives.encode_rows(o, b), primitives.encode_rows(i, b), b, 0, 1, 3, neq=(1, 3))
+    want = [(x[1], y[1]) for x in o.tolist() for y in i.tolist() if x[0] == y[0] and x[1] != y[1]]
+    assert [tuple(r) for r in primitives.decode_codes(got, b).tolist()] == want
+
+
+def test_code_difference_merge_brute_force():
+    rng = np.random.default_rng(9)
+    full = np.unique(rng.integers(0, 50, 30)).astype(np.uint64)
+    fresh = np.sort(rng.integers(0, 50, 40)).astype(np.uint64)
+    d, f = primitives.difference_merge_codes(full, fresh)
+    assert d.tolist() == sorted(set(fresh.tolist()) - set(full.tolist()))
+    assert f.tolist() == sorted(set(full.tolist()) | set(fresh.tolist()))
