@@ -136,6 +136,7 @@ typedef struct {
   double ms_join, ms_sort, ms_merge; /* per-phase times (HISA_FLAG_PHASE_TIMES) */
   uint64_t tuples_joined;   /* sum over iterations of |new| before dedup */
   uint64_t peak_bytes;      /* peak library-owned device memory */
+  uint64_t kernel_launches; /* kernels launched by the run (graph-launched ones included) */
 } hisa_run_stats;
 
 /* Evaluates all rules to the least fixpoint.  The EDB is encoded, sorted,
@@ -162,6 +163,21 @@ hisa_status hisa_read_relation(hisa_ctx* ctx, uint32_t rel_id, uint32_t* const* 
  * CAPACITY (cap < K; the first cap values are written), INVALID_ARG. */
 hisa_status hisa_delta_counts(hisa_ctx* ctx, uint32_t rel_id, uint64_t* out, uint32_t cap,
                               uint32_t* n_iters);
+
+/* Per-kernel accounting of the last run made with HISA_FLAG_PHASE_TIMES (the
+ * loop is then host-driven and every launch is bracketed by CUDA events on the
+ * context's stream).  One entry per kernel kind that ran: launches, summed
+ * device time, and the algorithmic bytes those launches had to move (what the
+ * step reads and writes at minimum, from the sizes of each iteration).
+ * Iterations that were re-run after a buffer grew are not counted.  Up to cap
+ * entries go to `out`; *n receives the number of kinds.  Errors: CAPACITY. */
+typedef struct {
+  char name[24];
+  uint64_t launches;
+  double ms;
+  double bytes;
+} hisa_kernel_stat;
+hisa_status hisa_kernel_stats(hisa_ctx* ctx, hisa_kernel_stat* out, uint32_t cap, uint32_t* n);
 
 /* Static text of a status code. */
 const char* hisa_status_string(hisa_status s);

@@ -82,6 +82,11 @@ hisa_status hisa_delta_counts(hisa_ctx* ctx, uint32_t rel_id, uint64_t* out, uin
   return ctx->eng.delta_counts(rel_id, out, cap, n_iters);
 }
 
+hisa_status hisa_kernel_stats(hisa_ctx* ctx, hisa_kernel_stat* out, uint32_t cap, uint32_t* n) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.kernel_stats(out, cap, n);
+}
+
 const char* hisa_status_string(hisa_status s) {
   switch (s) {
     case HISA_OK: return "ok";

@@ -55,6 +55,7 @@ __global__ void k_commit(CommitArgs a) {
     st->cnt[a.delta[r]] = nd;
     DBuf h = st->buf[a.history[r]];
     if (it < h.cap) static_cast<uint64_t*>(h.ptr)[it] = nd;
+    st->aux[1] += st->cnt[a.fresh[r]];   // tuples joined (|new| before dedup)
   }
   st->iter = it + 1;
   st->go = (any || a.force) && st->iter < st->max_iters ? 1u : 0u;
@@ -70,8 +71,45 @@ __global__ void k_zero(ZeroArgs a) {
     p[i] = make_uint4(0, 0, 0, 0);
 }
 
-void launch_ctl(const CtlArgs& a, cudaStream_t s) { k_ctl<<<1, 256, 0, s>>>(a); }
-void launch_commit(const CommitArgs& a, cudaStream_t s) { k_commit<<<1, 32, 0, s>>>(a); }
-void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) { k_zero<<<g.small, 256, 0, s>>>(a); }
+void launch_ctl(const CtlArgs& a, cudaStream_t s) { HISA_LAUNCH(kKCtl, s, (k_ctl<<<1, 256, 0, s>>>(a))); }
+void launch_commit(const CommitArgs& a, cudaStream_t s) { HISA_LAUNCH(kKCommit, s, (k_commit<<<1, 32, 0, s>>>(a))); }
+void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKZero, s, (k_zero<<<g.small, 256, 0, s>>>(a)));
+}
+
+const char* const kKernelNames[kKindCount] = {
+    "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero"};
+
+thread_local KernelTimer* g_timer = nullptr;
+thread_local uint64_t g_launches = 0;
+
+cudaEvent_t KernelTimer::get() {
+  if (used == pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    pool.push_back(e);
+  }
+  return pool[used++];
+}
+void KernelTimer::begin(int kind, cudaStream_t s) {
+  Rec r{kind, get(), get()};
+  cudaEventRecord(r.a, s);
+  recs.push_back(r);
+}
+void KernelTimer::end(cudaStream_t s) { cudaEventRecord(recs.back().b, s); }
+void KernelTimer::truncate(size_t n) {
+  if (n < recs.size()) {
+    recs.resize(n);
+    used = 2 * n;
+  }
+}
+void KernelTimer::reset() {
+  recs.clear();
+  used = 0;
+}
+KernelTimer::~KernelTimer() {
+  for (auto e : pool) cudaEventDestroy(e);
+}
 
 }  // namespace hisa

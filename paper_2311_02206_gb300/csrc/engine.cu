@@ -593,6 +593,7 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
     c.commit.delta[i] = R.delta;
     c.commit.delta_next[i] = R.delta_next;
     c.commit.history[i] = R.history;
+    c.commit.fresh[i] = R.fresh;
   }
   c.commit.force = force;
   ops.push_back(c);
@@ -707,7 +708,7 @@ hisa_status Engine::regrow() {
   for (int id = 0; id < nslots; ++id) {
     const uint64_t need = hs.need[id];
     if (need == 0 || need <= hs.buf[id].cap) continue;
-    uint64_t cap = need + need / 2 + 1024;
+    uint64_t cap = need + need / 8 + 1024;
     for (int r : idb) {
       const Relation& R = rels[r];
       if (id == R.full_next || id == R.full) {
@@ -791,13 +792,31 @@ hisa_status Engine::run(hisa_run_stats* stats) {
   hs.error = 0;
   hs.max_iters = cfg.max_iters;
   hs.aux[0] = 0;
+  hs.aux[1] = 0;
   std::memset(hs.need, 0, sizeof hs.need);
   if ((s = upload())) return s;
   uint32_t graph_launches = 0;
   int guard = 0;
+  const bool timing = cfg.flags & HISA_FLAG_PHASE_TIMES;
+  const double kb = wide ? 8.0 : 4.0;
+  std::memset(kstat, 0, sizeof kstat);
+  timer.reset();
+  struct TimerGuard {
+    explicit TimerGuard(KernelTimer* t) { g_timer = t; }
+    ~TimerGuard() { g_timer = nullptr; }
+  } tg(timing ? &timer : nullptr);
+  const uint64_t launches0 = g_launches;
+  uint64_t graph_kernels = 0;
   while (true) {
     const bool first = hs.iter == 0;
-    const bool use_graph = !first && (cfg.flags & HISA_FLAG_GRAPH);
+    const bool use_graph = !first && (cfg.flags & HISA_FLAG_GRAPH) && !timing;
+    const size_t rec0 = timer.recs.size();
+    std::vector<uint64_t> m_prev, d_prev;
+    for (int r : idb) {
+      m_prev.push_back(hs.cnt[rels[r].full]);
+      d_prev.push_back(hs.cnt[rels[r].delta]);
+    }
+    const uint32_t iter0 = hs.iter;
     if (use_graph) {
       if ((s = launch_graph())) return s;
       ++graph_launches;
@@ -805,6 +824,23 @@ hisa_status Engine::run(hisa_run_stats* stats) {
       if ((s = exec(first ? ops1 : opsN))) return s;
     }
     if ((s = download())) return s;
+    if (use_graph) graph_kernels += body_kernels * (hs.iter - iter0 + (hs.overflow ? 1 : 0));
+    if (timing) {
+      if (hs.overflow) {
+        timer.truncate(rec0);   // the iteration re-runs: keep only clean ones
+      } else {
+        // algorithmic bytes of this iteration's kernels (counts read back above)
+        for (size_t i = 0; i < idb.size(); ++i) {
+          const Relation& R = rels[idb[i]];
+          const double nn = double(hs.cnt[R.fresh]), nd = double(hs.cnt[R.delta]);
+          const double m = double(m_prev[i]), dp = double(d_prev[i]);
+          kstat[kKRadixPass].bytes += passes * 2.0 * nn * kb;
+          if (nn > 0) kstat[kKSetop].bytes += (m + nn) * kb + (m + 2.0 * nd) * kb;
+          kstat[kKJoinWrite].bytes += 2.0 * nn * kb + dp * (kb + 8.0);
+          kstat[kKJoinCount].bytes += dp * (kb + 8.0 + 16.0);
+        }
+      }
+    }
     if (hs.error) {
       return ctx_fail(hs.error == kDevTimeout ? HISA_ERR_DEVICE_TIMEOUT : HISA_ERR_CUDA, "device error",
                       hs.error == kDevTimeout ? "bounded wait expired" : "probe limit / bad state");
@@ -815,8 +851,10 @@ hisa_status Engine::run(hisa_run_stats* stats) {
       if ((s = regrow())) return s;
       if ((s = upload())) return s;
       if (bits & 1) continue;       // join/sort stage: re-run the whole iteration
+      const size_t rec1 = timer.recs.size();
       if ((s = exec(tail))) return s;   // only the set-difference/merge stage
       if ((s = download())) return s;
+      if (timing) timer.truncate(rec1);
       if (hs.overflow) {
         const uint32_t bits2 = hs.overflow;
         if ((s = regrow())) return s;
@@ -837,6 +875,17 @@ hisa_status Engine::run(hisa_run_stats* stats) {
     if (K) CU(cudaMemcpyAsync(R.delta_counts.data(), hs.buf[R.history].ptr, K * 8, cudaMemcpyDeviceToHost, stream));
   }
   CU(cudaStreamSynchronize(stream));
+  if (timing) {
+    for (auto& rc : timer.recs) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, rc.a, rc.b);
+      kstat[rc.kind].ms += ms;
+      kstat[rc.kind].launches += 1;
+    }
+    timer.reset();
+  }
+  last_stats.kernel_launches = (g_launches - launches0) + graph_kernels;
+  last_stats.tuples_joined = hs.aux[1];
   last_stats.iterations = K;
   last_stats.iterations_run = hs.iter;
   last_stats.regrows = regrows;
@@ -892,8 +941,11 @@ hisa_status Engine::build_graph() {
     cudaStreamDestroy(cs);
     return ctx_fail(HISA_ERR_CUDA, "cudaStreamBeginCaptureToGraph", cudaGetErrorString(e));
   }
+  const uint64_t l0 = g_launches;
   hisa_status s = exec(opsN);
   k_set_cond<<<1, 1, 0, cs>>>(dst, handle);
+  body_kernels = g_launches - l0 + 1;
+  g_launches = l0;
   cudaGraph_t captured;
   e = cudaStreamEndCapture(cs, &captured);
   stream = saved;
@@ -977,6 +1029,30 @@ hisa_status Engine::device_max(const uint32_t* a, const uint32_t* b2, uint64_t n
   CU(cudaStreamSynchronize(stream));
   std::memcpy(mx, hs_pinned, 4);
   dev_free(p);
+  return HISA_OK;
+}
+
+}  // namespace hisa
+
+namespace hisa {
+
+hisa_status Engine::kernel_stats(hisa_kernel_stat* out, uint32_t cap, uint32_t* n) {
+  if (!n) return ctx_fail(HISA_ERR_INVALID_ARG, "kernel_stats", nullptr);
+  uint32_t k = 0;
+  for (int i = 0; i < kKindCount; ++i) {
+    if (!kstat[i].launches) continue;
+    if (out && k < cap) {
+      hisa_kernel_stat& o = out[k];
+      std::memset(&o, 0, sizeof o);
+      std::snprintf(o.name, sizeof o.name, "%s", kKernelNames[i]);
+      o.launches = kstat[i].launches;
+      o.ms = kstat[i].ms;
+      o.bytes = kstat[i].bytes;
+    }
+    ++k;
+  }
+  *n = k;
+  if (out && cap < k) return ctx_fail(HISA_ERR_CAPACITY, "kernel_stats: buffer too small", nullptr);
   return HISA_OK;
 }
 

@@ -123,6 +123,13 @@ class Engine {
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_stale = true;
   hisa_run_stats last_stats{};
+  KernelTimer timer;
+  struct KStat { uint64_t launches; double ms, bytes; };
+  KStat kstat[kKindCount] = {};
+  uint64_t body_kernels = 0;   // kernels in one captured iteration
+
+ public:
+  hisa_status kernel_stats(hisa_kernel_stat* out, uint32_t cap, uint32_t* n);
 };
 
 }  // namespace hisa

@@ -6,6 +6,7 @@
 #include "join.cuh"
 #include "radix.cuh"
 #include "setops.cuh"
+#include <vector>
 
 namespace hisa {
 
@@ -35,7 +36,7 @@ struct CtlArgs {
 struct CommitArgs {
   DevState* st;
   int nrel;
-  int full[8], full_next[8], delta[8], delta_next[8], history[8];
+  int full[8], full_next[8], delta[8], delta_next[8], history[8], fresh[8];
   int force;   // commit even when no delta is non-empty (first iteration)
 };
 
@@ -71,6 +72,38 @@ struct RunsArgs {
   DevState* st;
   int keys_buf, keys_cnt, b, out_cnt;
 };
+
+// ---- launch accounting -----------------------------------------------------------------
+
+enum KernelKind : int {
+  kKEncode, kKDecode, kKRuns, kKHist, kKRadixPass, kKSetopPartition, kKSetop, kKIndex,
+  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKindCount
+};
+extern const char* const kKernelNames[kKindCount];
+
+// CUDA-event timer around every kernel launch (host-driven loop only).
+struct KernelTimer {
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t get();
+  void begin(int kind, cudaStream_t s);
+  void end(cudaStream_t s);
+  void truncate(size_t n);   // drop records from n on (an iteration that was re-run)
+  void reset();
+  ~KernelTimer();
+};
+extern thread_local KernelTimer* g_timer;
+extern thread_local uint64_t g_launches;
+
+#define HISA_LAUNCH(kind, s, stmt)            \
+  do {                                        \
+    if (g_timer) g_timer->begin((kind), (s)); \
+    stmt;                                     \
+    ++g_launches;                             \
+    if (g_timer) g_timer->end((s));           \
+  } while (0)
 
 // ---- launchers ------------------------------------------------------------------------
 

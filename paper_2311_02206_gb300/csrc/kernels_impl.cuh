@@ -42,19 +42,19 @@ __global__ void k_count_runs(RunsArgs a) {
 
 template <typename K>
 void launch_encode(const EncodeArgs& a, const Grid& g, cudaStream_t s) {
-  k_encode<K><<<g.small, 256, 0, s>>>(a);
+  HISA_LAUNCH(kKEncode, s, (k_encode<K><<<g.small, 256, 0, s>>>(a)));
 }
 template <typename K>
 void launch_decode(const DecodeArgs& a, const Grid& g, cudaStream_t s) {
-  k_decode<K><<<g.small, 256, 0, s>>>(a);
+  HISA_LAUNCH(kKDecode, s, (k_decode<K><<<g.small, 256, 0, s>>>(a)));
 }
 template <typename K>
 void launch_count_runs(const RunsArgs& a, const Grid& g, cudaStream_t s) {
-  k_count_runs<K><<<g.small, 256, 0, s>>>(a);
+  HISA_LAUNCH(kKRuns, s, (k_count_runs<K><<<g.small, 256, 0, s>>>(a)));
 }
 template <typename K>
 void launch_radix_hist(const RadixHistArgs& a, const Grid& g, cudaStream_t s) {
-  k_radix_hist<K><<<g.small, 256, 0, s>>>(a);
+  HISA_LAUNCH(kKHist, s, (k_radix_hist<K><<<g.small, 256, 0, s>>>(a)));
 }
 template <typename K>
 void launch_radix_pass(const RadixPassArgs& a, const Grid& g, cudaStream_t s) {
@@ -65,7 +65,7 @@ void launch_radix_pass(const RadixPassArgs& a, const Grid& g, cudaStream_t s) {
   c.cmd[0] = {kCtlEpoch, 0, 0};
   c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
   launch_ctl(c, s);
-  k_radix_pass<K><<<g.radix, kRadixThreads, 0, s>>>(a);
+  HISA_LAUNCH(kKRadixPass, s, (k_radix_pass<K><<<g.radix, kRadixThreads, 0, s>>>(a)));
 }
 template <typename K>
 void launch_setop(const SetopArgs& a, const Grid& g, cudaStream_t s) {
@@ -76,12 +76,12 @@ void launch_setop(const SetopArgs& a, const Grid& g, cudaStream_t s) {
   c.cmd[0] = {kCtlEpoch, 0, 0};
   c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
   launch_ctl(c, s);
-  k_setop_partition<K><<<g.small, 256, 0, s>>>(a);
-  k_setop<K><<<g.setop, kSetopThreads, 0, s>>>(a);
+  HISA_LAUNCH(kKSetopPartition, s, (k_setop_partition<K><<<g.small, 256, 0, s>>>(a)));
+  HISA_LAUNCH(kKSetop, s, (k_setop<K><<<g.setop, kSetopThreads, 0, s>>>(a)));
 }
 template <typename K>
 void launch_index(const IndexArgs& a, const Grid& g, cudaStream_t s) {
-  k_index_build<K><<<g.small, 256, 0, s>>>(a);
+  HISA_LAUNCH(kKIndex, s, (k_index_build<K><<<g.small, 256, 0, s>>>(a)));
 }
 template <typename K>
 void launch_join(const JoinArgs& a, const Grid& g, cudaStream_t s) {
@@ -92,9 +92,9 @@ void launch_join(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   c.cmd[0] = {kCtlEpoch, 0, 0};
   c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
   launch_ctl(c, s);
-  k_join_count<K><<<g.join, kJoinThreads, 0, s>>>(a);
-  k_join_partition<K><<<g.small, 256, 0, s>>>(a);
-  k_join_write<K><<<g.join, kJoinThreads, 0, s>>>(a);
+  HISA_LAUNCH(kKJoinCount, s, (k_join_count<K><<<g.join, kJoinThreads, 0, s>>>(a)));
+  HISA_LAUNCH(kKJoinPartition, s, (k_join_partition<K><<<g.small, 256, 0, s>>>(a)));
+  HISA_LAUNCH(kKJoinWrite, s, (k_join_write<K><<<g.join, kJoinThreads, 0, s>>>(a)));
   CtlArgs d{};
   d.st = a.st;
   d.skip_mask = a.skip_mask;
@@ -105,12 +105,12 @@ void launch_join(const JoinArgs& a, const Grid& g, cudaStream_t s) {
 
 template <typename K>
 void launch_join_count(const JoinArgs& a, const Grid& g, cudaStream_t s) {
-  k_join_count<K><<<g.join, kJoinThreads, 0, s>>>(a);
+  HISA_LAUNCH(kKJoinCount, s, (k_join_count<K><<<g.join, kJoinThreads, 0, s>>>(a)));
 }
 template <typename K>
 void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
-  k_join_partition<K><<<g.small, 256, 0, s>>>(a);
-  k_join_write<K><<<g.join, kJoinThreads, 0, s>>>(a);
+  HISA_LAUNCH(kKJoinPartition, s, (k_join_partition<K><<<g.small, 256, 0, s>>>(a)));
+  HISA_LAUNCH(kKJoinWrite, s, (k_join_write<K><<<g.join, kJoinThreads, 0, s>>>(a)));
 }
 
 #define HISA_INSTANTIATE(K)                                                              \

@@ -67,10 +67,16 @@ class RunStats(ctypes.Structure):
         ("ms_merge", ctypes.c_double),
         ("tuples_joined", ctypes.c_uint64),
         ("peak_bytes", ctypes.c_uint64),
+        ("kernel_launches", ctypes.c_uint64),
     ]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 # entry point -> (restype, argtypes); the complete list of include/*.h declarations
@@ -91,6 +97,7 @@ SIGNATURES = {
     "hisa_read_relation": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint64,
                                             _U64P, ctypes.c_int]),
     "hisa_delta_counts": (ctypes.c_int32, [_P, ctypes.c_uint32, _U64P, ctypes.c_uint32, _U32P]),
+    "hisa_kernel_stats": (ctypes.c_int32, [_P, ctypes.POINTER(KernelStat), ctypes.c_uint32, _U32P]),
     "hisa_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "hisa_last_error": (ctypes.c_char_p, [_P]),
     "hisa_sort_codes": (ctypes.c_int32, [_P, _P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _P]),
@@ -277,12 +284,20 @@ class Context:
         _check(self._lib.hisa_relation_size(self._h, rid, ctypes.byref(n)), self._h)
         return n.value
 
-    def read_relation(self, rel, device: bool = False):
+    def read_relation(self, rel, device: bool = False, out=None):
         """Returns (c0, c1) in lexicographic order: numpy uint32 arrays, or torch
-        int32 CUDA tensors (the uint32 bit patterns) when ``device``."""
+        int32 CUDA tensors (the uint32 bit patterns) when ``device``.  ``out``
+        may give two preallocated host arrays (e.g. pinned) to fill."""
         rid = self.rel_ids[rel] if isinstance(rel, str) else rel
         n = self.relation_size(rid)
         got = ctypes.c_uint64()
+        if out is not None:
+            c0, c1 = out
+            assert len(c0) >= n and len(c1) >= n and c0.dtype.itemsize == 4
+            ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
+            _check(self._lib.hisa_read_relation(self._h, rid, ptrs, min(len(c0), len(c1)), ctypes.byref(got), 0),
+                   self._h)
+            return c0[:n], c1[:n]
         if device:
             torch = _torch()
             c0 = torch.empty(max(n, 1), dtype=torch.int32, device=f"cuda:{self.device}")
@@ -295,6 +310,16 @@ class Context:
         ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
         _check(self._lib.hisa_read_relation(self._h, rid, ptrs, n, ctypes.byref(got), 0), self._h)
         return c0[:n], c1[:n]
+
+    def kernel_stats(self) -> list:
+        """Per-kernel launches, device ms and algorithmic bytes of the last run
+        made with FLAG_PHASE_TIMES."""
+        n = ctypes.c_uint32()
+        _check(self._lib.hisa_kernel_stats(self._h, None, 0, ctypes.byref(n)), self._h)
+        arr = (KernelStat * max(n.value, 1))()
+        _check(self._lib.hisa_kernel_stats(self._h, arr, n.value, ctypes.byref(n)), self._h)
+        return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms,
+                 "bytes": arr[i].bytes} for i in range(n.value)]
 
     def delta_counts(self, rel) -> list:
         rid = self.rel_ids[rel] if isinstance(rel, str) else rel
