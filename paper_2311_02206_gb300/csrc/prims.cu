@@ -144,6 +144,16 @@ template <typename K>
 hisa_status diff_merge_t(const void* full, uint64_t nf, const void* fresh, uint64_t nn, void* dout, uint64_t dcap,
                          void* fout, uint64_t fcap, uint64_t* n_delta, void* stream) {
   *n_delta = 0;
+  if (nn == 0) {   // nothing new: delta is empty and full' is a copy of full
+    if (fout && nf) {
+      if (fcap < nf) return HISA_ERR_CAPACITY;
+      if (cudaMemcpyAsync(fout, full, nf * sizeof(K), cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return HISA_ERR_CUDA;
+    }
+    return HISA_OK;
+  }
   Prim P(stream);
   const int A = P.wrap(full, nf, nf);
   const int B = P.wrap(fresh, nn, nn);

@@ -90,6 +90,17 @@ def test_difference_merge(nf, nn, width):
     assert np.array_equal(host(f, dt), wf)
 
 
+def test_difference_merge_nothing_new_copies_full():
+    from paper_2311_02206_gb300 import hisa
+    full = np.arange(0, 30_000, 3, dtype=np.uint32)
+    empty = np.zeros(0, np.uint32)
+    for _ in range(2):
+        junk = torch.full((full.size,), -1, dtype=torch.int32, device="cuda")   # dirty the allocator's cache
+        del junk
+        d, f = hisa.difference_merge(dev(full, np.int32), dev(empty, np.int32))
+        assert d.numel() == 0 and np.array_equal(host(f, np.uint32), full)
+
+
 def test_difference_merge_max_keys():
     from paper_2311_02206_gb300 import hisa
     full = np.array([0, 5, 0xFFFFFFFE, 0xFFFFFFFF], np.uint32)
