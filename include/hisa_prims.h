@@ -70,6 +70,35 @@ hisa_status hisa_join_codes(const void* outer, uint64_t n_outer, const void* inn
                             int outer_col, int proj0, int proj1, int neq, void* out, uint64_t out_cap,
                             uint64_t* n_out, int key_bytes, void* stream);
 
+/* ---- variant that allocates nothing ---------------------------------------------
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory while they run this step (for instance inside a
+ * stream capture whose mode forbids allocation calls, on a real-time or
+ * signal-safe path that must not enter an allocator, or under a device-memory
+ * budget fixed in advance).
+ *
+ * hisa_difference_merge_noalloc computes exactly what hisa_difference_merge
+ * computes, with the same arguments, outputs and errors, but calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its scratch (tile splits,
+ * look-back words, control block) lives in one 1 MiB array that the library
+ * reserves on every GPU that loads it and holds until the process exits.
+ *   - Size limit: n_full + n_new <= HISA_NOALLOC_MAX_CODES (2^26 codes);
+ *     larger inputs return HISA_ERR_TOO_LARGE before any GPU work.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current (cudaGetSymbolAddress); make that first call before any
+ *     stream capture that includes this step.
+ *   - All calls share the array, which keeps the last call's contents; each
+ *     call clears what must start at zero.  Calls whose GPU work overlaps
+ *     (other streams or host threads without ordering) race on the array and
+ *     give wrong results: order them on one stream.
+ *   - Synchronises `stream` to return *n_delta. */
+#define HISA_NOALLOC_MAX_CODES (1ull << 26)
+#define HISA_ERR_TOO_LARGE (-10) /* input larger than a fixed maximum size */
+hisa_status hisa_difference_merge_noalloc(const void* full, uint64_t n_full, const void* fresh, uint64_t n_new,
+                                          void* delta_out, uint64_t delta_cap, void* full_out, uint64_t full_cap,
+                                          uint64_t* n_delta, int key_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,7 @@ const char* hisa_status_string(hisa_status s) {
     case HISA_ERR_UNSUPPORTED: return "unsupported rule shape";
     case HISA_ERR_STATE: return "call out of order";
     case HISA_ERR_CAPACITY: return "output buffer too small";
+    case -10: return "input larger than the fixed maximum size";
     default: return "unknown status";
   }
 }

@@ -104,6 +104,9 @@ SIGNATURES = {
     "hisa_sort_unique_codes": (ctypes.c_int32, [_P, _P, ctypes.c_uint64, _U64P, ctypes.c_int, ctypes.c_int, _P]),
     "hisa_difference_merge": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, _P, ctypes.c_uint64, _P,
                                                ctypes.c_uint64, _U64P, ctypes.c_int, _P]),
+    "hisa_difference_merge_noalloc": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, _P,
+                                                       ctypes.c_uint64, _P, ctypes.c_uint64, _U64P, ctypes.c_int,
+                                                       _P]),
     "hisa_join_codes": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint64, _U64P,
                                          ctypes.c_int, _P]),
@@ -372,6 +375,23 @@ def difference_merge(full, fresh, with_full: bool = True, stream=None):
         f.numel() if f is not None else 0, ctypes.byref(n), _kb(fresh), _stream_ptr(stream)))
     nd = n.value
     return d[:nd], (f[:full.numel() + nd] if f is not None else None)
+
+
+NOALLOC_MAX_CODES = 1 << 26
+HISA_ERR_TOO_LARGE = -10
+
+
+def difference_merge_noalloc(full, fresh, delta_out, full_out=None, stream=None):
+    """hisa_difference_merge_noalloc on caller-provided outputs (the library
+    allocates nothing); returns (delta, full') views of the outputs."""
+    n = ctypes.c_uint64()
+    _check(load_library().hisa_difference_merge_noalloc(
+        full.data_ptr() if full.numel() else None, full.numel(), fresh.data_ptr() if fresh.numel() else None,
+        fresh.numel(), delta_out.data_ptr(), delta_out.numel(),
+        full_out.data_ptr() if full_out is not None else None, full_out.numel() if full_out is not None else 0,
+        ctypes.byref(n), _kb(fresh), _stream_ptr(stream)))
+    nd = n.value
+    return delta_out[:nd], (full_out[:full.numel() + nd] if full_out is not None else None)
 
 
 def join_codes(outer, inner, b: int, outer_col: int, proj0: int, proj1: int, neq: int = 0, stream=None):
