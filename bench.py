@@ -45,7 +45,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hisa", "reference"], default="hisa")
-    ap.add_argument("--workload", choices=["rmat16", "er1000"], default="rmat16")
+    ap.add_argument("--workload", choices=["rmat16", "rmat13", "er1000"], default="rmat16",
+                    help="rmat16: the benchmark workload; rmat13: a smaller R-MAT graph for profiler captures")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -63,6 +64,9 @@ def _workload(name):
         desc = ("REACH (2 rules) on R-MAT scale 16: 65,536 nodes, 2^19 distinct edges, "
                 "(a,b,c,d)=(.57,.19,.19,.05), no self-loops, seed 3")
         return s, d, desc, 65536
+    if name == "rmat13":
+        s, d = workloads.rmat_graph(13, 1 << 16, 3)
+        return s, d, "REACH (2 rules) on R-MAT scale 13: 8,192 nodes, 2^16 distinct edges, seed 3", 1 << 13
     s, d = workloads.config_reach_er()
     return s, d, "REACH (2 rules) on Erdos-Renyi n=1,000, m=3,000, seed 0", 1000
 

@@ -57,12 +57,15 @@ __device__ __forceinline__ uint64_t lb_flag(uint64_t w, uint32_t epoch) {
 }
 __device__ __forceinline__ uint64_t lb_value(uint64_t w) { return w & ((1ull << 42) - 1); }
 
+// A look-back word carries its value, flag and epoch in one 64-bit word and no
+// other data depends on it, so single-copy-atomic relaxed accesses suffice (no
+// fence per publish).
 __device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
   uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -113,7 +116,19 @@ __device__ __forceinline__ uint64_t lookback_warp(uint64_t* status, uint64_t til
   return excl;
 }
 
-// Single-thread look-back for per-digit chains (radix sort: one thread per digit).
+// Split form of the per-digit look-back: publish the tile's aggregate as soon
+// as it is known, resolve the prefix later.
+__device__ __forceinline__ void lookback_publish(uint64_t* status, uint64_t tile, uint64_t stride, uint64_t local,
+                                                 uint32_t epoch) {
+  st_release(&status[tile * stride], lb_pack(epoch, tile == 0 ? kFlagIncl : kFlagAgg, local));
+}
+__device__ __forceinline__ uint64_t lookback_resolve(uint64_t* status, uint64_t tile, uint64_t stride, uint64_t local,
+                                                     uint32_t epoch, uint32_t* err);
+
+// Single-thread look-back for per-digit chains (radix sort: one thread per
+// digit).  Eight predecessor words are read per round trip, so a walk over
+// tiles that only published their aggregate costs 1/8 of the latency.
+constexpr int kLookbackBatch = 8;
 __device__ __forceinline__ uint64_t lookback_thread(uint64_t* status, uint64_t tile, uint64_t stride,
                                                     uint64_t local, uint32_t epoch, uint32_t* err) {
   if (tile == 0) {
@@ -124,20 +139,67 @@ __device__ __forceinline__ uint64_t lookback_thread(uint64_t* status, uint64_t t
   uint64_t excl = 0;
   int64_t j = int64_t(tile) - 1;
   uint32_t spins = 0;
-  while (j >= 0) {
-    const uint64_t w = ld_acquire(&status[uint64_t(j) * stride]);
-    const uint64_t f = lb_flag(w, epoch);
-    if (f == 0) {
+  while (true) {
+    uint64_t w[kLookbackBatch];
+#pragma unroll
+    for (int b = 0; b < kLookbackBatch; ++b)
+      w[b] = (j - b >= 0) ? ld_acquire(&status[uint64_t(j - b) * stride]) : lb_pack(epoch, kFlagIncl, 0);
+    int used = 0;
+    bool done = false;
+#pragma unroll
+    for (int b = 0; b < kLookbackBatch; ++b) {
+      if (done || used < b) break;           // stopped earlier in this batch
+      const uint64_t f = lb_flag(w[b], epoch);
+      if (f == 0) break;                     // not published yet: re-read from here
+      excl += lb_value(w[b]);
+      ++used;
+      if (f == kFlagIncl) done = true;
+    }
+    if (done) break;
+    j -= used;
+    if (used == 0) {
       if (++spins > kSpinLimit) {
         atomicExch(err, kDevTimeout);
         break;
       }
       __nanosleep(32);
-      continue;
     }
-    excl += lb_value(w);
-    if (f == kFlagIncl) break;
-    --j;
+  }
+  st_release(&status[tile * stride], lb_pack(epoch, kFlagIncl, excl + local));
+  return excl;
+}
+
+__device__ __forceinline__ uint64_t lookback_resolve(uint64_t* status, uint64_t tile, uint64_t stride, uint64_t local,
+                                                     uint32_t epoch, uint32_t* err) {
+  if (tile == 0) return 0;
+  uint64_t excl = 0;
+  int64_t j = int64_t(tile) - 1;
+  uint32_t spins = 0;
+  while (true) {
+    uint64_t w[kLookbackBatch];
+#pragma unroll
+    for (int b = 0; b < kLookbackBatch; ++b)
+      w[b] = (j - b >= 0) ? ld_acquire(&status[uint64_t(j - b) * stride]) : lb_pack(epoch, kFlagIncl, 0);
+    int used = 0;
+    bool done = false;
+#pragma unroll
+    for (int b = 0; b < kLookbackBatch; ++b) {
+      if (done || used < b) break;
+      const uint64_t f = lb_flag(w[b], epoch);
+      if (f == 0) break;
+      excl += lb_value(w[b]);
+      ++used;
+      if (f == kFlagIncl) done = true;
+    }
+    if (done) break;
+    j -= used;
+    if (used == 0) {
+      if (++spins > kSpinLimit) {
+        atomicExch(err, kDevTimeout);
+        break;
+      }
+      __nanosleep(32);
+    }
   }
   st_release(&status[tile * stride], lb_pack(epoch, kFlagIncl, excl + local));
   return excl;

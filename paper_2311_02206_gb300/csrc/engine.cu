@@ -121,7 +121,7 @@ hisa_status Engine::init(const hisa_config& c) {
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   grid.sms = sms;
   // persistent grids: resident CTAs per SM from the kernels' footprints
-  grid.radix = sms * 2;
+  grid.radix = sms * 3;
   grid.setop = sms * 4;
   grid.join = sms * 4;
   grid.small = sms * 4;

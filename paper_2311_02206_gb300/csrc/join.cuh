@@ -186,8 +186,10 @@ __device__ __forceinline__ Probe do_probe(const JoinArgs& a, K code, const K* in
     const uint32_t key = join_key(inst_of(code, a.b), v, a.b);
     if (!probe(table, mask, key, &p.begin, &len, err)) return p;
   }
-  // filters
-  for (int f = 0; f < a.nfilt; ++f) {
+  // filters (at most two; unrolled so the argument arrays stay in registers)
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    if (f >= a.nfilt) break;
     const int s0 = a.fa[f], s1 = a.fb[f];
     if (s0 == kSrcOther && s1 == kSrcOther) {
       if (a.fop[f] == kFiltNeq) return p;  // x != x never holds
@@ -356,11 +358,15 @@ __global__ void k_join_partition(JoinArgs a) {
 
 template <typename K>
 __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
-  constexpr int S = kJoinThreads;   // outer tuples staged per batch
-  __shared__ uint64_t s_off[S + 1];
+  constexpr int S = kJoinThreads;          // outer tuples staged per batch
+  constexpr int IPT = kJoinChunk / kJoinThreads;   // consecutive results per thread
+  __shared__ uint64_t s_off[S + 1];        // result offset of each staged outer tuple
+  __shared__ uint64_t s_begin[S];          // first inner position of its range
+  __shared__ uint32_t s_hole[S];           // see Probe::hole
+  __shared__ uint32_t s_mode[S];
   __shared__ K s_code[S];
-  __shared__ Probe s_pr[S];
-  __shared__ uint32_t s_hist[8][256];
+  __shared__ K s_out[kJoinChunk];          // the chunk's results, for coalesced stores
+  __shared__ uint32_t s_hist[kJoinThreads / 32][256];   // per-warp digit counts of one pass
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
   const uint64_t n = st->cnt[a.outer_cnt];
@@ -375,11 +381,11 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
   const uint64_t* offs = static_cast<const uint64_t*>(st->buf[a.offs_buf].ptr);
   const uint64_t* starts = static_cast<const uint64_t*>(st->buf[a.starts_buf].ptr);
   K* out = static_cast<K*>(st->buf[a.out_buf].ptr) + st->cnt[a.out_cnt];
-  const int tid = threadIdx.x;
-  const bool hist = a.hist_buf >= 0;
-  if (hist) {
-    for (int i = tid; i < a.hist_passes * 256; i += kJoinThreads) (&s_hist[0][0])[i] = 0;
-  }
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int passes = a.hist_buf >= 0 ? a.hist_passes : 0;
+  // the histogram of up to 8 digit passes is accumulated one pass at a time
+  // over the staged results of each chunk; counts are flushed per chunk
+  unsigned long long* ghist = passes ? static_cast<unsigned long long*>(st->buf[a.hist_buf].ptr) : nullptr;
   for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const uint64_t o0 = ch * kJoinChunk, o1 = min(o0 + kJoinChunk, total);
     uint64_t s = starts[ch];
@@ -391,7 +397,10 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
         s_off[tid] = offs[i];
         const K code = outer[i];
         s_code[tid] = code;
-        s_pr[tid] = do_probe<K>(a, code, inner, table, mask, &st->error);
+        const Probe p = do_probe<K>(a, code, inner, table, mask, &st->error);
+        s_begin[tid] = p.begin;
+        s_hole[tid] = p.hole;
+        s_mode[tid] = p.mode;
       } else {
         s_off[tid] = ~0ull;
       }
@@ -404,38 +413,56 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
       const uint64_t lo = max(o0, s_off[0]);
       const uint64_t hi_batch = min(s_off[S], total);
       const uint64_t hi = min(o1, hi_batch);
-      for (uint64_t j = lo + tid; j < hi; j += kJoinThreads) {
-        // staged outer k with s_off[k] <= j < s_off[k+1]
-        int l = 0, h = S - 1;
+      // this thread's results: IPT consecutive ones of the chunk
+      const uint64_t j0 = o0 + uint64_t(tid) * IPT;
+      uint64_t j = max(j0, lo);
+      const uint64_t jend = min(j0 + IPT, hi);
+      if (j < jend) {
+        int l = 0, h = S - 1;   // staged outer with s_off[l] <= j < s_off[l+1]
         while (l < h) {
           const int m = (l + h + 1) >> 1;
           if (s_off[m] <= j) l = m;
           else h = m - 1;
         }
-        const Probe& p = s_pr[l];
-        const uint64_t r = j - s_off[l];
-        const uint64_t ip = result_pos(p, uint32_t(r));
-        if (r >= p.cnt || (a.has_inner && ip >= n_inner)) {   // offsets and probes disagree
-          atomicExch(&st->error, kDevBadState);
-          continue;
-        }
-        const K ic = a.has_inner ? inner[ip] : K(0);
-        const K v = project<K>(a, s_code[l], ic, a.has_inner);
-        out[j] = v;
-        if (hist) {
-          for (int q = 0; q < a.hist_passes; ++q) atomicAdd(&s_hist[q][(uint64_t(v) >> (8 * q)) & 0xFF], 1u);
+        uint64_t next = s_off[l + 1];
+        for (; j < jend; ++j) {
+          while (j >= next) {   // skip to the outer tuple owning result j
+            ++l;
+            next = s_off[l + 1];
+          }
+          const uint64_t r = j - s_off[l];
+          K ic = K(0);
+          if (a.has_inner) {
+            Probe p;
+            p.begin = s_begin[l];
+            p.hole = s_hole[l];
+            p.mode = s_mode[l];
+            const uint64_t ip = result_pos(p, uint32_t(r));
+            if (ip >= n_inner) {   // offsets and probes disagree
+              atomicExch(&st->error, kDevBadState);
+              continue;
+            }
+            ic = inner[ip];
+          }
+          s_out[j - o0] = project<K>(a, s_code[l], ic, a.has_inner);
         }
       }
       if (hi_batch >= o1 || s + S > last) break;
       s += S;
     }
-  }
-  if (hist) {
     __syncthreads();
-    unsigned long long* g = static_cast<unsigned long long*>(st->buf[a.hist_buf].ptr);
-    for (int i = tid; i < a.hist_passes * 256; i += kJoinThreads) {
-      const uint32_t v = (&s_hist[0][0])[i];
-      if (v) atomicAdd(&g[i], (unsigned long long)v);
+    const uint32_t cn = uint32_t(o1 - o0);
+    for (uint32_t t = tid; t < cn; t += kJoinThreads) out[o0 + t] = s_out[t];
+    for (int q = 0; q < passes; ++q) {
+      for (int w = 0; w < kJoinThreads / 32; ++w) s_hist[w][tid] = 0;
+      __syncthreads();
+      for (uint32_t t = tid; t < cn; t += kJoinThreads)
+        atomicAdd(&s_hist[warp][uint32_t(uint64_t(s_out[t]) >> (8 * q)) & 0xFF], 1u);
+      __syncthreads();
+      uint32_t c = 0;
+      for (int w = 0; w < kJoinThreads / 32; ++w) c += s_hist[w][tid];
+      if (c) atomicAdd(&ghist[q * 256 + tid], (unsigned long long)c);
+      __syncthreads();
     }
   }
 }

@@ -65,7 +65,12 @@ void launch_radix_pass(const RadixPassArgs& a, const Grid& g, cudaStream_t s) {
   c.cmd[0] = {kCtlEpoch, 0, 0};
   c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
   launch_ctl(c, s);
-  HISA_LAUNCH(kKRadixPass, s, (k_radix_pass<K><<<g.radix, kRadixThreads, 0, s>>>(a)));
+  static bool attr_set = false;   // opt in to the pass's dynamic shared memory once per process
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_radix_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, radix_dyn_smem<K>());
+    attr_set = true;
+  }
+  HISA_LAUNCH(kKRadixPass, s, (k_radix_pass<K><<<g.radix, kRadixThreads, radix_dyn_smem<K>(), s>>>(a)));
 }
 template <typename K>
 void launch_setop(const SetopArgs& a, const Grid& g, cudaStream_t s) {

@@ -24,7 +24,7 @@ struct Prim {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
     g.sms = sms;
-    g.radix = sms * 2;
+    g.radix = sms * 3;
     g.setop = sms * 4;
     g.join = sms * 4;
     g.small = sms * 4;

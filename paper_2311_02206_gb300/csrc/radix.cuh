@@ -23,12 +23,17 @@ constexpr int kRadixWarps = kRadixThreads / 32;
 template <typename K>
 struct RadixCfg;
 template <>
-struct RadixCfg<uint32_t> { static constexpr int items = 16; };
+struct RadixCfg<uint32_t> { static constexpr int items = 24; };
 template <>
 struct RadixCfg<uint64_t> { static constexpr int items = 12; };
 
 template <typename K>
 __host__ __device__ constexpr int radix_tile() { return kRadixThreads * RadixCfg<K>::items; }
+
+// Dynamic shared memory of one pass: two tile buffers (the one being ranked,
+// which then holds the tile in digit order, and the next tile's TMA target).
+template <typename K>
+__host__ __device__ constexpr int radix_dyn_smem() { return 2 * radix_tile<K>() * int(sizeof(K)); }
 
 struct RadixPassArgs {
   DevState* st;
@@ -72,17 +77,61 @@ __global__ void __launch_bounds__(256) k_radix_hist(RadixHistArgs a) {
   }
 }
 
+// ---- mbarrier / bulk-copy helpers (sm_90+ PTX) --------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 1-D bulk copy global -> shared (TMA engine); both addresses 16-byte aligned,
+// size a multiple of 16; completion is signalled on the mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(m))
+               : "memory");
+}
+// Bounded wait for the mbarrier phase `parity`; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 26); ++i)
+    if (mbar_try_wait(m, parity)) return true;
+  return false;
+}
+
+// One LSD pass.  Per tile: (1) the keys arrive in shared memory (bulk copy
+// issued one tile ahead, so a CTA's next tile loads while it ranks the
+// current one); (2) per-warp digit counts by shared atomics; (3) the tile's
+// per-digit counts are published for the look-back at once, before ranking,
+// so successors rarely wait; (4) stable ranks: the lanes holding the same
+// digit are found with eight warp ballots (one per digit bit), the lowest of
+// them advances the warp's running offset of that digit, and every key goes
+// straight to its position in the tile's digit order (written over the
+// consumed input buffer); (5) look-back gives each digit run's global start;
+// (6) the tile is written out digit run by digit run.
 template <typename K>
-__global__ void __launch_bounds__(kRadixThreads) k_radix_pass(RadixPassArgs a) {
+__global__ void __launch_bounds__(kRadixThreads, 3) k_radix_pass(RadixPassArgs a) {
   constexpr int ITEMS = RadixCfg<K>::items;
   constexpr int TILE = kRadixThreads * ITEMS;
-  __shared__ K s_keys[TILE];
-  __shared__ uint32_t s_wh[kRadixWarps][kRadixDigits];  // per-warp counts, then offsets
-  __shared__ uint32_t s_excl[kRadixDigits];             // tile-local digit start
-  __shared__ uint64_t s_gbase[kRadixDigits];            // global start of the tile's digit run
+  extern __shared__ __align__(128) unsigned char radix_dyn[];
+  K* s_buf[2] = {reinterpret_cast<K*>(radix_dyn), reinterpret_cast<K*>(radix_dyn) + TILE};
+  __shared__ uint32_t s_wh[kRadixWarps][kRadixDigits];  // per-warp counts, then tile positions
+  __shared__ uint64_t s_gdelta[kRadixDigits];           // global position - tile position, per digit
   __shared__ uint64_t s_bucket[kRadixDigits];           // global start of each digit bucket
   __shared__ uint64_t s_scan[32];
-  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_tile[2];
+  __shared__ __align__(8) uint64_t s_mbar[2];
 
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
@@ -104,48 +153,66 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_pass(RadixPassArgs a) {
   const uint32_t epoch = st->epoch;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1;
+  const uint32_t shift = uint32_t(a.shift);
+  const bool aligned = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
 
   {  // bucket starts of this pass: exclusive scan of the digit histogram
     uint64_t tot;
-    const uint64_t e = block_exclusive_sum<uint64_t>(hist[tid], s_scan, &tot);
-    s_bucket[tid] = e;
+    s_bucket[tid] = block_exclusive_sum<uint64_t>(hist[tid], s_scan, &tot);
   }
-
+  if (tid == 0) {
+    mbar_init(&s_mbar[0], 1);
+    mbar_init(&s_mbar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // thread 0: bulk-load tile t into buffer b when it is a whole, aligned tile
+  auto prefetch = [&](uint64_t t, int b) {
+    if (t < ntiles && aligned && n - t * TILE >= uint64_t(TILE)) {
+      mbar_expect_tx(&s_mbar[b], TILE * sizeof(K));
+      bulk_load(s_buf[b], in + t * TILE, TILE * sizeof(K), &s_mbar[b]);
+    }
+  };
+  if (tid == 0) {
+    const uint32_t t = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+    s_tile[0] = t;
+    prefetch(t, 0);
+  }
+  uint32_t parity0 = 0, parity1 = 0;
+  int b = 0;
   while (true) {
-    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+    __syncthreads();   // s_tile[b] visible; the other buffer is no longer read
+    const uint64_t tile = s_tile[b];
+    if (tile >= ntiles) break;
+    if (tid == 0) {
+      const uint32_t t = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+      s_tile[b ^ 1] = t;
+      prefetch(t, b ^ 1);
+    }
+    const uint64_t t0 = tile * TILE;
+    const uint32_t tile_n = uint32_t(min(uint64_t(TILE), n - t0));
+    K* sk = s_buf[b];
+    if (aligned && tile_n == TILE) {
+      const uint32_t par = b ? parity1 : parity0;
+      if (!mbar_wait(&s_mbar[b], par)) atomicExch(&st->error, kDevTimeout);
+      if (b) parity1 ^= 1; else parity0 ^= 1;
+    } else {
+      for (uint32_t i = tid; i < tile_n; i += kRadixThreads) sk[i] = in[t0 + i];
+    }
+#pragma unroll
     for (int w = 0; w < kRadixWarps; ++w) s_wh[w][tid] = 0;
     __syncthreads();
-    const uint64_t tile = s_tile;
-    if (tile >= ntiles) break;
-    const uint64_t t0 = tile * TILE;
-
-    K key[ITEMS];
-    uint32_t rank[ITEMS];
-    uint32_t dig[ITEMS];
-    // warp-striped arrangement: item k of lane l is key t0 + warp*32*ITEMS + k*32 + l,
+    // warp-striped arrangement: item k of lane l is tile key warp*32*ITEMS + k*32 + l,
     // so processing items in order keeps the tile's key order (stable ranks)
-    const uint64_t wbase = t0 + uint64_t(warp) * 32 * ITEMS + lane;
+    K key[ITEMS];
+    const uint32_t wofs = uint32_t(warp) * 32 * ITEMS + lane;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-      const uint64_t i = wbase + k * 32;
-      const bool valid = i < n;
-      key[k] = valid ? in[i] : K(0);
-      dig[k] = valid ? uint32_t((key[k] >> a.shift) & 0xFF) : 256u;
-    }
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      const uint32_t d = dig[k];
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      const uint32_t before = __popc(peers & lt_mask);
-      uint32_t base = 0;
-      if (d < 256) base = s_wh[warp][d];
-      __syncwarp();
-      if (d < 256 && before == 0) s_wh[warp][d] = base + __popc(peers);
-      __syncwarp();
-      rank[k] = base + before;
+      const uint32_t i = wofs + k * 32;
+      key[k] = i < tile_n ? sk[i] : K(0);
+      if (i < tile_n) atomicAdd(&s_wh[warp][uint32_t(key[k] >> shift) & 0xFF], 1u);
     }
     __syncthreads();
-    // per digit: offsets of each warp inside the tile's digit run
     uint32_t cnt = 0;
 #pragma unroll
     for (int w = 0; w < kRadixWarps; ++w) {
@@ -153,30 +220,42 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_pass(RadixPassArgs a) {
       s_wh[w][tid] = cnt;
       cnt += c;
     }
-    {
-      uint64_t tot;
-      const uint64_t e = block_exclusive_sum<uint64_t>(cnt, s_scan, &tot);
-      s_excl[tid] = uint32_t(e);
-    }
-    // global offset of this tile's run of digit `tid`
-    const uint64_t prev = lookback_thread(status + tid, tile, kRadixDigits, cnt, epoch, &st->error);
-    s_gbase[tid] = s_bucket[tid] + prev;
-    __syncthreads();
+    lookback_publish(status + tid, tile, kRadixDigits, cnt, epoch);
+    uint64_t tot;
+    const uint32_t excl = uint32_t(block_exclusive_sum<uint64_t>(cnt, s_scan, &tot));
+#pragma unroll
+    for (int w = 0; w < kRadixWarps; ++w) s_wh[w][tid] += excl;
+    __syncthreads();   // every key is in registers: the buffer takes the ranked tile
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-      const uint32_t d = dig[k];
-      if (d < 256) s_keys[s_excl[d] + s_wh[warp][d] + rank[k]] = key[k];
+      const bool valid = wofs + k * 32 < tile_n;
+      const uint32_t d = valid ? uint32_t(key[k] >> shift) & 0xFF : 256u;
+      uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (int bit = 0; bit < 8; ++bit) {
+        const bool on = (d >> bit) & 1;
+        const uint32_t bal = __ballot_sync(0xffffffffu, on);
+        peers &= on ? bal : ~bal;
+      }
+      const uint32_t before = __popc(peers & lt_mask);
+      uint32_t base = 0;
+      if (valid) base = s_wh[warp][d];
+      __syncwarp();
+      if (valid && before == 0) s_wh[warp][d] = base + __popc(peers);
+      __syncwarp();
+      if (valid) sk[base + before] = key[k];
     }
+    // global offset of this tile's run of digit `tid`
+    const uint64_t prev = lookback_resolve(status + tid, tile, kRadixDigits, cnt, epoch, &st->error);
+    s_gdelta[tid] = s_bucket[tid] + prev - excl;
     __syncthreads();
-    const uint32_t valid_n = uint32_t(min(uint64_t(TILE), n - t0));
-    for (uint32_t i = tid; i < valid_n; i += kRadixThreads) {
-      const K k = s_keys[i];
-      const uint32_t d = uint32_t((k >> a.shift) & 0xFF);
-      const uint64_t pos = s_gbase[d] + (i - s_excl[d]);
+    for (uint32_t i = tid; i < tile_n; i += kRadixThreads) {
+      const K k = sk[i];
+      const uint64_t pos = s_gdelta[uint32_t(k >> shift) & 0xFF] + i;
       if (pos < n) out[pos] = k;
       else atomicExch(&st->error, kDevBadState);   // histogram and keys disagree
     }
-    __syncthreads();
+    b ^= 1;
   }
 }
 

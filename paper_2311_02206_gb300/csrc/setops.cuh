@@ -156,27 +156,37 @@ __global__ void __launch_bounds__(kSetopThreads) k_setop(SetopArgs a) {
     uint32_t isA = 0;    // bit k: item k is an A element
     int nitems = 0;
     int kept = 0;
+    // heads of A and B and the last element merged from each, kept in registers
+    bool hasA = ai < nA, hasB = bi < nB;
+    K va = hasA ? sA[ai] : K(0), vb = hasB ? sB[bi] : K(0);
+    bool hasPrevA = ai > 0 || s_hasA, hasPrevB = bi > 0 || s_hasB;
+    K pa = ai > 0 ? sA[ai - 1] : s_prevA;
+    K pb = bi > 0 ? sB[bi - 1] : s_prevB;
+    const int nmine = min(ITEMS, nT - dt);
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-      if (ai + bi >= nT || dt + k >= nT) break;
-      const bool takeA = bi >= nB || (ai < nA && sA[ai] <= sB[bi]);
+      if (k >= nmine) break;
+      const bool takeA = !hasB || (hasA && va <= vb);
       if (takeA) {
-        val[k] = sA[ai];
+        val[k] = va;
         isA |= 1u << k;
+        pa = va;
+        hasPrevA = true;
         ++ai;
+        hasA = ai < nA;
+        if (hasA) va = sA[ai];
       } else {
-        const K x = sB[bi];
-        const bool hasPrevB = bi > 0 || s_hasB;
-        const K pb = bi > 0 ? sB[bi - 1] : s_prevB;
-        const bool hasPrevA = ai > 0 || s_hasA;
-        const K pa = ai > 0 ? sA[ai - 1] : s_prevA;
-        const bool keep = !(hasPrevB && pb == x) && !(hasPrevA && pa == x);
-        val[k] = x;
+        const bool keep = !(hasPrevB && pb == vb) && !(hasPrevA && pa == vb);
+        val[k] = vb;
         if (keep) {
           kind |= 1u << k;
           ++kept;
         }
+        pb = vb;
+        hasPrevB = true;
         ++bi;
+        hasB = bi < nB;
+        if (hasB) vb = sB[bi];
       }
       ++nitems;
     }
