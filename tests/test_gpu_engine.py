@@ -172,3 +172,23 @@ def test_reach_rmat_full_size_golden_and_sampled():
         g0 = c0[keep].cpu().numpy().view(np.uint32)
         g1 = c1[keep].cpu().numpy().view(np.uint32)
         assert np.array_equal(g0, ref.relations["Reach"][0]) and np.array_equal(g1, ref.relations["Reach"][1])
+
+
+def test_sg_dag_full_size_golden():
+    """SG (x != y on both rules) on the 20,000-node DAG: size, all 104 delta
+    counts and the fingerprint of the whole relation against the oracle's
+    stored values."""
+    path = os.path.join(GOLDEN, "sg_dag_20k.json")
+    if not os.path.exists(path):
+        pytest.skip("golden values not generated")
+    g = json.load(open(path))
+    from paper_2311_02206_gb300 import hisa
+    s, d = workloads.config_sg_dag()
+    with hisa.Context() as ctx:
+        ctx.program(*oracle.SG)
+        ctx.load_tuples("Edge", s, d)
+        ctx.run()
+        assert ctx.delta_counts("SG") == g["delta_counts"]
+        assert ctx.relation_size("SG") == g["sg_size"]
+        c0, c1 = ctx.read_relation("SG", device=True)
+        assert fingerprint_device(c0, c1) == int(g["fingerprint"])
