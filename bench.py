@@ -50,7 +50,7 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--micro", choices=["sort", "merge"], default=None,
+    ap.add_argument("--micro", choices=["sort", "merge", "join"], default=None,
                     help="sort/merge microbenchmark on random tuples (the shapes of the paper's Table 6)")
     ap.add_argument("--tuples", type=int, default=100_000_000)
     ap.add_argument("--key-bits", type=int, default=64, help="64: 2-arity tuples of uint32; 32: packed 16+16")
@@ -428,7 +428,24 @@ def run_micro(a):
         keys = (keys * 2 + torch.randint(0, 2, (n,), generator=g, device="cuda", dtype=torch.int64)).to(torch.int32)
     flush = torch.empty(512 << 18, dtype=torch.int32, device="cuda")
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if a.micro == "sort":
+    if a.micro == "join":
+        # Algorithm 3 as in REACH: outer (m, t) codes probe the R-MAT 16 edge index
+        # on m (codes (m, f)); results (f, t).  About 8 results per outer tuple.
+        import numpy as np
+        from paper_2311_02206_gb300 import workloads
+        es, ed = workloads.config_reach_rmat()
+        inner_np = np.unique((ed.astype(np.uint64) << np.uint64(16)) | es.astype(np.uint64)).astype(np.uint32)
+        inner = torch.from_numpy(inner_np.view(np.int32)).cuda()
+        m = ed[torch.randint(0, len(ed), (n,), generator=torch.Generator().manual_seed(3)).numpy()]
+        t = torch.randint(0, 1 << 16, (n,), generator=torch.Generator().manual_seed(4)).numpy().astype(np.uint32)
+        outer_np = np.sort((m.astype(np.uint32) << np.uint32(16)) | t)
+        outer = torch.from_numpy(outer_np.view(np.int32)).cuda()
+
+        def op():
+            return hisa.join_codes(outer, inner, 16, 0, 3, 1)
+        res = op()
+        alg = 2 * 4 * res.numel() + 12 * n
+    elif a.micro == "sort":
         def op():
             return hisa.sort_codes(keys, a.key_bits)
         passes = (a.key_bits + 7) // 8

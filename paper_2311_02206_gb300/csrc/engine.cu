@@ -71,13 +71,15 @@ int Engine::new_slot(int elem_bytes) {
   return id;
 }
 
-// Grows slot `id` to at least `cap` elements (contents are not kept).
+// Grows slot `id` to at least `cap` elements (contents are not kept: the old
+// buffer is released first, so growth never holds both).
 hisa_status Engine::ensure(int id, uint64_t cap) {
   if (hs.buf[id].cap >= cap && hs.buf[id].ptr) return HISA_OK;
+  dev_free(hs.buf[id].ptr);
+  hs.buf[id] = {nullptr, 0};
   void* p;
   hisa_status s = dev_alloc(size_t(std::max<uint64_t>(cap, 1)) * slot_elem[id], &p);
   if (s) return s;
-  dev_free(hs.buf[id].ptr);
   hs.buf[id] = {p, std::max<uint64_t>(cap, 1)};
   if (slot_zero[id]) {
     // look-back words: a recycled allocation may hold words of another
@@ -122,7 +124,7 @@ hisa_status Engine::init(const hisa_config& c) {
   grid.sms = sms;
   // persistent grids: resident CTAs per SM from the kernels' footprints
   grid.radix = sms * 3;
-  grid.setop = sms * 4;
+  grid.setop = sms * 5;
   grid.join = sms * 4;
   grid.small = sms * 4;
   if (!cfg.alloc) {
@@ -704,25 +706,50 @@ hisa_status Engine::prepare_edb() {
 
 // ---- growth (Section 5.3) ----------------------------------------------------------------
 
+// Grows slot `id` to `cap` elements keeping its first `keep` elements.
+hisa_status Engine::grow_keep(int id, uint64_t cap, uint64_t keep) {
+  if (hs.buf[id].cap >= cap && hs.buf[id].ptr) return HISA_OK;
+  void* p;
+  hisa_status s = dev_alloc(size_t(cap) * slot_elem[id], &p);
+  if (s) return s;
+  if (keep && hs.buf[id].ptr)
+    CU(cudaMemcpyAsync(p, hs.buf[id].ptr, size_t(keep) * slot_elem[id], cudaMemcpyDeviceToDevice, stream));
+  dev_free(hs.buf[id].ptr);
+  hs.buf[id] = {p, cap};
+  return HISA_OK;
+}
+
 hisa_status Engine::regrow() {
   for (int id = 0; id < nslots; ++id) {
     const uint64_t need = hs.need[id];
     if (need == 0 || need <= hs.buf[id].cap) continue;
     uint64_t cap = need + need / 8 + 1024;
+    int partner = -1, live = -1;
     for (int r : idb) {
       const Relation& R = rels[r];
       if (id == R.full_next || id == R.full) {
-        // eager buffer management: full + k * delta
+        // eager buffer management: full + k * delta, and at least a quarter more
         const uint64_t delta = need > hs.cnt[R.full] ? need - hs.cnt[R.full] : need;
-        cap = need + uint64_t(cfg.ebm_k * double(delta)) + 1024;
+        cap = need + std::max(uint64_t(cfg.ebm_k * double(delta)), need / 4) + 1024;
+        partner = id == R.full_next ? R.full : R.full_next;
+        live = R.full;
+      } else if (id == R.delta_next || id == R.delta) {
+        cap = need + need / 4 + 1024;
+        partner = id == R.delta_next ? R.delta : R.delta_next;
+        live = R.delta;
       }
     }
     hisa_status s = ensure(id, cap);
     if (s) return s;
+    // the two versions swap every iteration: grow the partner too (keeping the
+    // live version's tuples), or the next iteration overflows again
+    if (partner >= 0 && (s = grow_keep(partner, cap, partner == live ? hs.cnt[live] : 0))) return s;
     ++regrows;
   }
-  // the radix ping-pong buffer follows its partner
+  // the radix ping-pong buffer follows its partner (only when the join stage
+  // re-runs: after a merge-stage overflow they hold the sorted new tuples)
   for (int r : idb) {
+    if (!(hs.overflow & 1)) break;
     const Relation& R = rels[r];
     const uint64_t c = std::max(hs.buf[R.fresh].cap, hs.buf[R.fresh_alt].cap);
     hisa_status s;
@@ -845,8 +872,9 @@ hisa_status Engine::run(hisa_run_stats* stats) {
       return ctx_fail(hs.error == kDevTimeout ? HISA_ERR_DEVICE_TIMEOUT : HISA_ERR_CUDA, "device error",
                       hs.error == kDevTimeout ? "bounded wait expired" : "probe limit / bad state");
     }
+    if (hs.iter != iter0) guard = 0;   // progress: an iteration committed
     if (hs.overflow) {
-      if (++guard > 64) return ctx_fail(HISA_ERR_OOM, "buffers keep overflowing", nullptr);
+      if (++guard > 16) return ctx_fail(HISA_ERR_OOM, "buffers keep overflowing", nullptr);
       const uint32_t bits = hs.overflow;
       if ((s = regrow())) return s;
       if ((s = upload())) return s;

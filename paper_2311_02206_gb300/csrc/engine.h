@@ -92,6 +92,7 @@ class Engine {
   template <typename K> hisa_status prepare_rel_t(Relation& r, int order, int slot);
   hisa_status prepare_edb();
   hisa_status regrow();
+  hisa_status grow_keep(int id, uint64_t cap, uint64_t keep);
   hisa_status launch_graph();
   hisa_status build_graph();
 

@@ -365,7 +365,9 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
   __shared__ uint32_t s_hole[S];           // see Probe::hole
   __shared__ uint32_t s_mode[S];
   __shared__ K s_code[S];
-  __shared__ K s_out[kJoinChunk];          // the chunk's results, for coalesced stores
+  // the chunk's results, for coalesced stores; one pad word per 32 keeps the
+  // per-thread runs of IPT consecutive results on distinct banks
+  __shared__ K s_out[kJoinChunk + kJoinChunk / 32];
   __shared__ uint32_t s_hist[kJoinThreads / 32][256];   // per-warp digit counts of one pass
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
@@ -444,7 +446,8 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
             }
             ic = inner[ip];
           }
-          s_out[j - o0] = project<K>(a, s_code[l], ic, a.has_inner);
+          const uint32_t q = uint32_t(j - o0);
+          s_out[q + (q >> 5)] = project<K>(a, s_code[l], ic, a.has_inner);
         }
       }
       if (hi_batch >= o1 || s + S > last) break;
@@ -452,12 +455,12 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
     }
     __syncthreads();
     const uint32_t cn = uint32_t(o1 - o0);
-    for (uint32_t t = tid; t < cn; t += kJoinThreads) out[o0 + t] = s_out[t];
+    for (uint32_t t = tid; t < cn; t += kJoinThreads) out[o0 + t] = s_out[t + (t >> 5)];
     for (int q = 0; q < passes; ++q) {
       for (int w = 0; w < kJoinThreads / 32; ++w) s_hist[w][tid] = 0;
       __syncthreads();
       for (uint32_t t = tid; t < cn; t += kJoinThreads)
-        atomicAdd(&s_hist[warp][uint32_t(uint64_t(s_out[t]) >> (8 * q)) & 0xFF], 1u);
+        atomicAdd(&s_hist[warp][uint32_t(uint64_t(s_out[t + (t >> 5)]) >> (8 * q)) & 0xFF], 1u);
       __syncthreads();
       uint32_t c = 0;
       for (int w = 0; w < kJoinThreads / 32; ++w) c += s_hist[w][tid];

@@ -25,7 +25,7 @@ struct Prim {
     if (sms <= 0) sms = 1;
     g.sms = sms;
     g.radix = sms * 3;
-    g.setop = sms * 4;
+    g.setop = sms * 5;
     g.join = sms * 4;
     g.small = sms * 4;
     void* p = nullptr;

@@ -88,7 +88,7 @@ __global__ void k_setop_partition(SetopArgs a) {
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kSetopThreads) k_setop(SetopArgs a) {
+__global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
   constexpr int ITEMS = SetopCfg<K>::items;
   constexpr int C = kSetopThreads * ITEMS;
   __shared__ K s_in[C];     // A part then B part; reused for the full' tile
