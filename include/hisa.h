@@ -164,6 +164,62 @@ hisa_status hisa_read_relation(hisa_ctx* ctx, uint32_t rel_id, uint32_t* const* 
 hisa_status hisa_delta_counts(hisa_ctx* ctx, uint32_t rel_id, uint64_t* out, uint32_t cap,
                               uint32_t* n_iters);
 
+/* ---- batched instances (many independent fixpoints in one run) ----------------------
+ *
+ * Tuples loaded with hisa_load_instance carry an instance id (0 .. 2^k - 1):
+ * every relation then holds the union of independent instances, each with its
+ * own EDB, and one run evaluates all of them at once (codes carry the instance
+ * id above the two columns, so joins never cross instances).  Plain
+ * hisa_load_tuples loads into instance 0.  Requires instance bits + domain
+ * bits <= 32; the run is host-driven so that per-instance delta sizes can be
+ * read back after every iteration. */
+hisa_status hisa_load_instance(hisa_ctx* ctx, uint32_t rel_id, uint32_t instance, const uint32_t* const* cols,
+                               uint64_t n, int cols_on_device);
+/* Tuples of one instance of relation rel_id after the last run. */
+hisa_status hisa_instance_size(hisa_ctx* ctx, uint32_t rel_id, uint32_t instance, uint64_t* n);
+/* Copies one instance's tuples (ascending (c0, c1)) like hisa_read_relation. */
+hisa_status hisa_read_instance(hisa_ctx* ctx, uint32_t rel_id, uint32_t instance, uint32_t* const* cols,
+                               uint64_t cap, uint64_t* n, int cols_on_device);
+/* |delta_1| .. |delta_K| of one instance (K = its last productive iteration). */
+hisa_status hisa_instance_delta_counts(hisa_ctx* ctx, uint32_t rel_id, uint32_t instance, uint64_t* out,
+                                       uint32_t cap, uint32_t* n_iters);
+
+/* ---- serving: continuous batching of independent requests ---------------------------
+ *
+ * A request is one instance's EDB tuples for relation rel_id (host columns,
+ * copied at submit).  hisa_serve_step admits pending requests at iteration
+ * boundaries while instance slots are free and the estimated device memory of
+ * the admitted instances stays within the budget, runs up to max_iterations
+ * iterations of the shared fixpoint (admitted instances join it with their
+ * non-recursive rules at the next iteration), and retires every instance whose
+ * delta became empty: its tuples and delta sizes are copied to host memory and
+ * its slot and tuples are released.  Results stay available until
+ * hisa_serve_release.  The rules must be added before hisa_serve_open;
+ * hisa_load_tuples / hisa_run are not used in a serving session. */
+typedef struct {
+  uint32_t admitted;    /* requests admitted in this call */
+  uint32_t retired;     /* requests completed in this call */
+  uint32_t active;      /* instances on the device after the call */
+  uint32_t pending;     /* submitted, not yet admitted */
+  uint32_t iterations;  /* iterations run by this call */
+} hisa_serve_stats;
+/* Fixes the session's limits: up to max_instances concurrent instances (a
+ * power of two is best), EDB values <= max_value, estimated bytes of admitted
+ * instances <= budget_bytes (0: no limit).  Errors: INVALID_ARG, STATE. */
+hisa_status hisa_serve_open(hisa_ctx* ctx, uint32_t max_instances, uint32_t max_value, uint64_t budget_bytes);
+hisa_status hisa_serve_submit(hisa_ctx* ctx, uint32_t rel_id, const uint32_t* const* cols, uint64_t n,
+                              uint64_t* ticket);
+hisa_status hisa_serve_step(hisa_ctx* ctx, uint32_t max_iterations, hisa_serve_stats* stats);
+/* *done = 1 once the request's fixpoint is complete. */
+hisa_status hisa_serve_poll(hisa_ctx* ctx, uint64_t ticket, int* done);
+/* A completed request's tuples of IDB relation rel_id (host arrays with room
+ * for cap tuples; *n receives the size) and its delta sizes (host array of
+ * dcap; *n_iters receives K).  Errors: STATE (not complete), CAPACITY. */
+hisa_status hisa_serve_result(hisa_ctx* ctx, uint64_t ticket, uint32_t rel_id, uint32_t* const* cols, uint64_t cap,
+                              uint64_t* n, uint64_t* deltas, uint32_t dcap, uint32_t* n_iters);
+/* Forgets a completed request. */
+hisa_status hisa_serve_release(hisa_ctx* ctx, uint64_t ticket);
+
 /* Per-kernel accounting of the last run made with HISA_FLAG_PHASE_TIMES (the
  * loop is then host-driven and every launch is bracketed by CUDA events on the
  * context's stream).  One entry per kernel kind that ran: launches, summed

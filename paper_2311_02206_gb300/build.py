@@ -17,7 +17,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
-SOURCES = ["ctl.cu", "kernels_u32.cu", "kernels_u64.cu", "engine.cu", "capi.cu", "prims.cu", "noalloc.cu"]
+SOURCES = ["ctl.cu", "kernels_u32.cu", "kernels_u64.cu", "engine.cu", "capi.cu", "prims.cu", "noalloc.cu", "serve.cu"]
 
 
 def _newer(out: str, deps) -> bool:

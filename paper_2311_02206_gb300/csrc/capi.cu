@@ -82,6 +82,61 @@ hisa_status hisa_delta_counts(hisa_ctx* ctx, uint32_t rel_id, uint64_t* out, uin
   return ctx->eng.delta_counts(rel_id, out, cap, n_iters);
 }
 
+hisa_status hisa_load_instance(hisa_ctx* ctx, uint32_t rel_id, uint32_t instance, const uint32_t* const* cols,
+                               uint64_t n, int cols_on_device) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.load_instance(rel_id, instance, cols, n, cols_on_device);
+}
+
+hisa_status hisa_instance_size(hisa_ctx* ctx, uint32_t rel_id, uint32_t instance, uint64_t* n) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.instance_size(rel_id, instance, n);
+}
+
+hisa_status hisa_read_instance(hisa_ctx* ctx, uint32_t rel_id, uint32_t instance, uint32_t* const* cols,
+                               uint64_t cap, uint64_t* n, int cols_on_device) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.read_instance(rel_id, instance, cols, cap, n, cols_on_device);
+}
+
+hisa_status hisa_instance_delta_counts(hisa_ctx* ctx, uint32_t rel_id, uint32_t instance, uint64_t* out,
+                                       uint32_t cap, uint32_t* n_iters) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.instance_delta_counts(rel_id, instance, out, cap, n_iters);
+}
+
+hisa_status hisa_serve_open(hisa_ctx* ctx, uint32_t max_instances, uint32_t max_value, uint64_t budget_bytes) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.serve_open(max_instances, max_value, budget_bytes);
+}
+
+hisa_status hisa_serve_submit(hisa_ctx* ctx, uint32_t rel_id, const uint32_t* const* cols, uint64_t n,
+                              uint64_t* ticket) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.serve_submit(rel_id, cols, n, ticket);
+}
+
+hisa_status hisa_serve_step(hisa_ctx* ctx, uint32_t max_iterations, hisa_serve_stats* stats) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.serve_step(max_iterations, stats);
+}
+
+hisa_status hisa_serve_poll(hisa_ctx* ctx, uint64_t ticket, int* done) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.serve_poll(ticket, done);
+}
+
+hisa_status hisa_serve_result(hisa_ctx* ctx, uint64_t ticket, uint32_t rel_id, uint32_t* const* cols, uint64_t cap,
+                              uint64_t* n, uint64_t* deltas, uint32_t dcap, uint32_t* n_iters) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.serve_result(ticket, rel_id, cols, cap, n, deltas, dcap, n_iters);
+}
+
+hisa_status hisa_serve_release(hisa_ctx* ctx, uint64_t ticket) {
+  if (!ctx) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.serve_release(ticket);
+}
+
 hisa_status hisa_kernel_stats(hisa_ctx* ctx, hisa_kernel_stat* out, uint32_t cap, uint32_t* n) {
   if (!ctx) return HISA_ERR_INVALID_ARG;
   return ctx->eng.kernel_stats(out, cap, n);

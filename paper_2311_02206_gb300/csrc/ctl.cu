@@ -71,6 +71,14 @@ __global__ void k_zero(ZeroArgs a) {
     p[i] = make_uint4(0, 0, 0, 0);
 }
 
+__global__ void k_fill_u32(uint32_t* p, uint64_t n, uint32_t v) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
+    p[i] = v;
+}
+void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKZero, s, (k_fill_u32<<<g.small, 256, 0, s>>>(p, n, v)));
+}
+
 void launch_ctl(const CtlArgs& a, cudaStream_t s) { HISA_LAUNCH(kKCtl, s, (k_ctl<<<1, 256, 0, s>>>(a))); }
 void launch_commit(const CommitArgs& a, cudaStream_t s) { HISA_LAUNCH(kKCommit, s, (k_commit<<<1, 32, 0, s>>>(a))); }
 void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {

@@ -197,19 +197,23 @@ hisa_status Engine::load(uint32_t rid, const uint32_t* const* cols, uint64_t n, 
   const uint64_t need = r.staged + n;
   if (need > r.stage_cap) {
     const uint64_t cap = std::max<uint64_t>(need, r.stage_cap * 2);
-    void *a, *b;
+    void *a, *b, *c;
     hisa_status s;
-    if ((s = dev_alloc(cap * 4, &a)) || (s = dev_alloc(cap * 4, &b))) return s;
+    if ((s = dev_alloc(cap * 4, &a)) || (s = dev_alloc(cap * 4, &b)) || (s = dev_alloc(cap * 4, &c))) return s;
     if (r.staged) {
       CU(cudaMemcpyAsync(a, r.stage[0], r.staged * 4, cudaMemcpyDeviceToDevice, stream));
       CU(cudaMemcpyAsync(b, r.stage[1], r.staged * 4, cudaMemcpyDeviceToDevice, stream));
+      CU(cudaMemcpyAsync(c, r.stage_inst, r.staged * 4, cudaMemcpyDeviceToDevice, stream));
     }
     dev_free(r.stage[0]);
     dev_free(r.stage[1]);
+    dev_free(r.stage_inst);
     r.stage[0] = static_cast<uint32_t*>(a);
     r.stage[1] = static_cast<uint32_t*>(b);
+    r.stage_inst = static_cast<uint32_t*>(c);
     r.stage_cap = cap;
   }
+  launch_fill_u32(r.stage_inst + r.staged, n, load_inst, grid, stream);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   for (int c = 0; c < 2; ++c)
     CU(cudaMemcpyAsync(r.stage[c] + r.staged, cols[c], n * 4, kind, stream));
@@ -400,9 +404,24 @@ hisa_status Engine::compile() {
   for (auto& r : rels) mx = std::max(mx, r.max_value);
   b = 1;
   while (b < 32 && (uint64_t(mx) >> b) != 0) ++b;
-  wide = 2 * b > 32;
-  passes = (2 * b + 7) / 8;
+  inst_bits = 0;
+  if (batched) {
+    inst_bits = 1;
+    while (inst_bits < 32 && (uint64_t(max_inst) >> inst_bits) != 0) ++inst_bits;
+  }
+  if (serving) {   // a serving session fixes the widths up front
+    b = fixed_b;
+    inst_bits = fixed_inst_bits;
+  }
+  if (inst_bits + b > 32)
+    return ctx_fail(HISA_ERR_UNSUPPORTED, "instance bits + domain bits exceed the 32-bit join key", nullptr);
+  wide = 2 * b + inst_bits > 32;
+  passes = (2 * b + inst_bits + 7) / 8;
   const int kb = wide ? 8 : 4;
+  if (inst_row < 0) {
+    inst_row = new_slot(8);
+    inst_bnd = new_slot(8);
+  }
   // slots of every relation (kept across runs; element width may change)
   for (auto& r : rels) {
     r.need_idx[0] = r.need_idx[1] = false;
@@ -633,7 +652,7 @@ hisa_status Engine::prepare_rel_t(Relation& r, int order, int slot) {
   hs.cnt[sc.tmp_a] = n;
   hs.cnt[sc.empty] = 0;
   if ((s = upload())) return s;
-  EncodeArgs e{dst, r.stage[0], r.stage[1], n, sc.tmp_a, sc.empty, b, order, 0};
+  EncodeArgs e{dst, r.stage[0], r.stage[1], n, sc.tmp_a, sc.empty, b, order, 0, batched ? r.stage_inst : nullptr};
   launch_encode<K>(e, grid, stream);
   CtlArgs z{};
   z.st = dst;
@@ -788,6 +807,13 @@ hisa_status Engine::run(hisa_run_stats* stats) {
   last_stats = hisa_run_stats{};
   last_stats.ms_edb = ms_edb;
   regrows = 0;
+  if ((s = init_run_state())) return s;
+  return run_loop(stats, t0);
+}
+
+// Fresh IDB state: empty versions with initial capacities, counters reset.
+hisa_status Engine::init_run_state() {
+  hisa_status s;
   // initial capacities: a multiple of the EDB size
   uint64_t nedb = 1024;
   for (auto& r : rels)
@@ -821,7 +847,12 @@ hisa_status Engine::run(hisa_run_stats* stats) {
   hs.aux[0] = 0;
   hs.aux[1] = 0;
   std::memset(hs.need, 0, sizeof hs.need);
-  if ((s = upload())) return s;
+  inst_hist.assign(idb.size(), {});
+  return upload();
+}
+
+hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::time_point t0) {
+  hisa_status s;
   uint32_t graph_launches = 0;
   int guard = 0;
   const bool timing = cfg.flags & HISA_FLAG_PHASE_TIMES;
@@ -836,7 +867,7 @@ hisa_status Engine::run(hisa_run_stats* stats) {
   uint64_t graph_kernels = 0;
   while (true) {
     const bool first = hs.iter == 0;
-    const bool use_graph = !first && (cfg.flags & HISA_FLAG_GRAPH) && !timing;
+    const bool use_graph = !first && (cfg.flags & HISA_FLAG_GRAPH) && !timing && !batched;
     const size_t rec0 = timer.recs.size();
     std::vector<uint64_t> m_prev, d_prev;
     for (int r : idb) {
@@ -891,6 +922,16 @@ hisa_status Engine::run(hisa_run_stats* stats) {
         continue;
       }
     }
+    if (batched && !hs.overflow && hs.iter != iter0) {
+      // per-instance |delta| of the iteration just committed
+      std::vector<std::vector<uint64_t>> rows;
+      if ((s = collect_inst_rows(rows))) return s;
+      for (size_t i = 0; i < idb.size(); ++i) {
+        auto& h = inst_hist[i];
+        if (h.size() < rows[i].size()) h.resize(rows[i].size());
+        for (size_t q = 0; q < rows[i].size(); ++q) h[q].push_back(rows[i][q]);
+      }
+    }
     if (!hs.go) break;
   }
   if (hs.iter >= cfg.max_iters && hs.aux[0] == hs.iter)
@@ -923,6 +964,24 @@ hisa_status Engine::run(hisa_run_stats* stats) {
   if (stats) *stats = last_stats;
   ran = true;
   return HISA_OK;
+}
+
+// Runs one iteration with `ops` (host-driven) until it commits, growing
+// buffers and re-running the overflowed stage as needed.
+hisa_status Engine::iterate_once(const std::vector<Op>& ops) {
+  hisa_status s;
+  bool rerun_all = true;
+  for (int guard = 0; guard < 16; ++guard) {
+    if ((s = exec(rerun_all ? ops : tail))) return s;
+    if ((s = download())) return s;
+    if (hs.error)
+      return ctx_fail(hs.error == kDevTimeout ? HISA_ERR_DEVICE_TIMEOUT : HISA_ERR_CUDA, "device error",
+                      hs.error == kDevTimeout ? "bounded wait expired" : "probe limit / bad state");
+    if (!hs.overflow) return HISA_OK;
+    rerun_all = (hs.overflow & 1) != 0;
+    if ((s = regrow()) || (s = upload())) return s;
+  }
+  return ctx_fail(HISA_ERR_OOM, "buffers keep overflowing", nullptr);
 }
 
 hisa_status Engine::launch_graph() {

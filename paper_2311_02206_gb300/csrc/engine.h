@@ -1,5 +1,8 @@
 // Engine state behind the C-ABI (include/hisa.h).
 #pragma once
+#include <chrono>
+#include <deque>
+#include <map>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -15,6 +18,7 @@ struct Relation {
   bool idb = false;
   // EDB staging: raw columns as loaded
   uint32_t* stage[2] = {nullptr, nullptr};
+  uint32_t* stage_inst = nullptr;   // instance id of each staged tuple
   uint64_t staged = 0, stage_cap = 0;
   uint32_t max_value = 0;
   // slots (see DevState::buf): sorted codes in column order (c0,c1) and (c1,c0),
@@ -56,6 +60,18 @@ struct Scratch {
   int runs, total, tmp_cnt;   // count-only slots
 };
 
+// One request of the serving loop: the EDB tuples of an independent instance.
+struct Request {
+  uint64_t ticket = 0;
+  uint32_t rel = 0;
+  std::vector<uint32_t> c0, c1;
+  uint64_t est_bytes = 0;
+  int slot = -1;
+  bool done = false;
+  std::map<int, std::vector<uint64_t>> deltas;                          // IDB rel -> |delta_k|
+  std::map<int, std::pair<std::vector<uint32_t>, std::vector<uint32_t>>> result;
+};
+
 class Engine {
  public:
   ~Engine();
@@ -68,7 +84,21 @@ class Engine {
   hisa_status relation_size(uint32_t rid, uint64_t* n);
   hisa_status read_relation(uint32_t rid, uint32_t* const* cols, uint64_t cap, uint64_t* n, int on_device);
   hisa_status delta_counts(uint32_t rid, uint64_t* out, uint32_t cap, uint32_t* n_iters);
+  // batched instances (serve.cu)
+  hisa_status load_instance(uint32_t rid, uint32_t inst, const uint32_t* const* cols, uint64_t n, int on_device);
+  hisa_status instance_size(uint32_t rid, uint32_t inst, uint64_t* n);
+  hisa_status read_instance(uint32_t rid, uint32_t inst, uint32_t* const* cols, uint64_t cap, uint64_t* n,
+                            int on_device);
+  hisa_status instance_delta_counts(uint32_t rid, uint32_t inst, uint64_t* out, uint32_t cap, uint32_t* n_iters);
+  hisa_status serve_open(uint32_t max_instances, uint32_t max_value, uint64_t budget);
+  hisa_status serve_submit(uint32_t rid, const uint32_t* const* cols, uint64_t n, uint64_t* ticket);
+  hisa_status serve_step(uint32_t max_iters, hisa_serve_stats* st);
+  hisa_status serve_poll(uint64_t ticket, int* done);
+  hisa_status serve_result(uint64_t ticket, uint32_t rid, uint32_t* const* cols, uint64_t cap, uint64_t* n,
+                           uint64_t* deltas, uint32_t dcap, uint32_t* n_iters);
+  hisa_status serve_release(uint64_t ticket);
   hisa_status ctx_fail(hisa_status s, const char* what, const char* detail);
+  uint32_t load_inst = 0;   // instance id given to tuples by the next load
 
   std::string last_error;
 
@@ -93,6 +123,15 @@ class Engine {
   hisa_status prepare_edb();
   hisa_status regrow();
   hisa_status grow_keep(int id, uint64_t cap, uint64_t keep);
+  hisa_status init_run_state();
+  hisa_status run_loop(hisa_run_stats* stats, std::chrono::steady_clock::time_point t0);
+  hisa_status iterate_once(const std::vector<Op>& ops);
+  hisa_status collect_inst_rows(std::vector<std::vector<uint64_t>>& rows);
+  hisa_status inst_bounds(int slot, std::vector<uint64_t>& bounds);
+  hisa_status decode_range(int slot, uint64_t begin, uint64_t count, std::vector<uint32_t>& c0,
+                           std::vector<uint32_t>& c1);
+  hisa_status rebuild_serving_edb();
+  hisa_status retire(const std::vector<uint64_t>& tickets);
   hisa_status launch_graph();
   hisa_status build_graph();
 
@@ -125,6 +164,22 @@ class Engine {
   bool graph_stale = true;
   hisa_run_stats last_stats{};
   KernelTimer timer;
+  // batched instances: codes carry an instance id above the two columns
+  bool batched = false;
+  uint32_t max_inst = 0;
+  int inst_bits = 0;
+  int inst_row = -1;          // slot: per-instance counts of one iteration
+  int inst_bnd = -1;          // slot: per-instance bounds of a sorted array
+  std::vector<std::vector<std::vector<uint64_t>>> inst_hist;   // [idb][inst] -> |delta_k| per iteration
+  // serving session
+  bool serving = false;
+  int fixed_b = 0, fixed_inst_bits = 0;
+  uint32_t serve_slots = 0;
+  uint64_t serve_budget = 0, active_bytes = 0, next_ticket = 1;
+  std::vector<uint64_t> slot_owner;                  // ticket per slot, 0 = free
+  std::unordered_map<uint64_t, Request> reqs;
+  std::deque<uint64_t> pending;
+  std::vector<Op> ops_admit;
   struct KStat { uint64_t launches; double ms, bytes; };
   KStat kstat[kKindCount] = {};
   uint64_t body_kernels = 0;   // kernels in one captured iteration

@@ -49,6 +49,16 @@ struct EncodeArgs {
   int b;
   int order;   // 0: (c0, c1); 1: (c1, c0)
   uint64_t inst_code;  // instance id << 2b, or 0
+  const uint32_t* inst;  // per-tuple instance ids (batched runs), or null
+};
+
+// Per-instance counts of a sorted code array (instance id = code >> 2b).
+struct InstArgs {
+  DevState* st;
+  int buf, cnt;
+  int shift;              // 2b
+  uint32_t ninst;         // instance slots
+  unsigned long long* out;   // [ninst] counts (added to) or [ninst + 1] bounds
 };
 
 struct DecodeArgs {
@@ -126,6 +136,9 @@ template <typename K> void launch_radix_pass(const RadixPassArgs& a, const Grid&
 template <typename K> void launch_setop(const SetopArgs& a, const Grid& g, cudaStream_t s);   // partition + merge
 template <typename K> void launch_index(const IndexArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_count_runs(const RunsArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_inst_hist(const InstArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_inst_bounds(const InstArgs& a, const Grid& g, cudaStream_t s);
+void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStream_t s);
 template <typename K> void launch_join(const JoinArgs& a, const Grid& g, cudaStream_t s);     // count + partition + write
 template <typename K> void launch_join_count(const JoinArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s);  // partition + write

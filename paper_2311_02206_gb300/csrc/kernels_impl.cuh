@@ -11,7 +11,8 @@ __global__ void k_encode(EncodeArgs a) {
   K* out = static_cast<K*>(st->buf[a.out_buf].ptr) + st->cnt[a.out_cnt];
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < a.n; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t x = a.c0[i], y = a.c1[i];
-    out[i] = K(a.inst_code | (a.order == 0 ? ((x << a.b) | y) : ((y << a.b) | x)));
+    const uint64_t inst = a.inst ? (uint64_t(a.inst[i]) << (2 * a.b)) : a.inst_code;
+    out[i] = K(inst | (a.order == 0 ? ((x << a.b) | y) : ((y << a.b) | x)));
   }
 }
 
@@ -38,6 +39,57 @@ __global__ void k_count_runs(RunsArgs a) {
     runs += (i == 0 || (uint64_t(keys[i - 1]) >> a.b) != (uint64_t(keys[i]) >> a.b));
   for (int o = 16; o > 0; o >>= 1) runs += __shfl_xor_sync(0xffffffffu, runs, o);
   if ((threadIdx.x & 31) == 0 && runs) atomicAdd((unsigned long long*)&st->cnt[a.out_cnt], (unsigned long long)runs);
+}
+
+// Counts of each instance id in a sorted code array: every thread walks a
+// contiguous stretch and adds one count per run of equal ids.
+template <typename K>
+__global__ void k_inst_hist(InstArgs a) {
+  DevState* st = a.st;
+  const K* c = static_cast<const K*>(st->buf[a.buf].ptr);
+  const uint64_t n = st->cnt[a.cnt];
+  const uint64_t nth = uint64_t(gridDim.x) * blockDim.x;
+  const uint64_t per = (n + nth - 1) / nth;
+  const uint64_t lo = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) * per;
+  const uint64_t hi = min(n, lo + per);
+  if (lo >= hi) return;
+  uint64_t cur = uint64_t(c[lo]) >> a.shift, run = 0;
+  for (uint64_t i = lo; i < hi; ++i) {
+    const uint64_t id = uint64_t(c[i]) >> a.shift;
+    if (id != cur) {
+      if (cur < a.ninst) atomicAdd(&a.out[cur], (unsigned long long)run);
+      cur = id;
+      run = 0;
+    }
+    ++run;
+  }
+  if (cur < a.ninst) atomicAdd(&a.out[cur], (unsigned long long)run);
+}
+
+// out[i] = first position whose instance id is >= i, for i in [0, ninst].
+template <typename K>
+__global__ void k_inst_bounds(InstArgs a) {
+  DevState* st = a.st;
+  const K* c = static_cast<const K*>(st->buf[a.buf].ptr);
+  const uint64_t n = st->cnt[a.cnt];
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i <= a.ninst; i += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const uint64_t m = (lo + hi) >> 1;
+      if ((uint64_t(c[m]) >> a.shift) < i) lo = m + 1;
+      else hi = m;
+    }
+    a.out[i] = lo;
+  }
+}
+
+template <typename K>
+void launch_inst_hist(const InstArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKCtl, s, (k_inst_hist<K><<<g.small, 256, 0, s>>>(a)));
+}
+template <typename K>
+void launch_inst_bounds(const InstArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKCtl, s, (k_inst_bounds<K><<<g.small, 256, 0, s>>>(a)));
 }
 
 template <typename K>
@@ -126,6 +178,8 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_radix_pass<K>(const RadixPassArgs&, const Grid&, cudaStream_t);   \
   template void launch_setop<K>(const SetopArgs&, const Grid&, cudaStream_t);            \
   template void launch_index<K>(const IndexArgs&, const Grid&, cudaStream_t);            \
+  template void launch_inst_hist<K>(const InstArgs&, const Grid&, cudaStream_t);          \
+  template void launch_inst_bounds<K>(const InstArgs&, const Grid&, cudaStream_t);        \
   template void launch_join<K>(const JoinArgs&, const Grid&, cudaStream_t);              \
   template void launch_join_count<K>(const JoinArgs&, const Grid&, cudaStream_t);        \
   template void launch_join_write<K>(const JoinArgs&, const Grid&, cudaStream_t);

@@ -1,0 +1,387 @@
+// Batched instances and the serving loop (continuous batching) of the engine.
+//
+// Many independent fixpoint instances share one run: every code carries its
+// instance id above the two columns, so the packed relations are the union of
+// the instances and every kernel of the iteration works on all of them at
+// once (one launch per stage for the whole instance table).  Joins probe keys
+// (instance, value), so instances never meet.  A serving session admits new
+// instances at iteration boundaries (their non-recursive rules run in that
+// iteration next to everyone else's recursive ones), and retires each
+// instance whose delta becomes empty: its tuples are copied out and its range
+// of the sorted relations is cut out.
+#include <algorithm>
+#include <cstring>
+
+#include "engine.h"
+
+namespace hisa {
+
+#define CU(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return ctx_fail(HISA_ERR_CUDA, #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static uint32_t instance_slots(uint32_t max_inst) { return max_inst + 1; }
+
+hisa_status Engine::load_instance(uint32_t rid, uint32_t inst, const uint32_t* const* cols, uint64_t n,
+                                  int on_device) {
+  if (serving) return ctx_fail(HISA_ERR_STATE, "load during a serving session", nullptr);
+  if (inst >= (1u << 24)) return ctx_fail(HISA_ERR_INVALID_ARG, "instance id too large", nullptr);
+  load_inst = inst;
+  hisa_status s = load(rid, cols, n, on_device);
+  load_inst = 0;
+  if (s) return s;
+  batched = true;
+  max_inst = std::max(max_inst, inst);
+  return HISA_OK;
+}
+
+// Per-instance counts of delta (after the commit) of every IDB relation.
+hisa_status Engine::collect_inst_rows(std::vector<std::vector<uint64_t>>& rows) {
+  const uint32_t ninst = serving ? serve_slots : instance_slots(max_inst);
+  hisa_status s;
+  if ((s = ensure(inst_row, ninst)) || (s = upload())) return s;
+  rows.assign(idb.size(), std::vector<uint64_t>(ninst, 0));
+  for (size_t i = 0; i < idb.size(); ++i) {
+    const Relation& R = rels[idb[i]];
+    CU(cudaMemsetAsync(hs.buf[inst_row].ptr, 0, ninst * 8, stream));
+    InstArgs a{dst, R.delta, R.delta, 2 * b, ninst, static_cast<unsigned long long*>(hs.buf[inst_row].ptr)};
+    if (wide) launch_inst_hist<uint64_t>(a, grid, stream);
+    else launch_inst_hist<uint32_t>(a, grid, stream);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(rows[i].data(), hs.buf[inst_row].ptr, ninst * 8, cudaMemcpyDeviceToHost, stream));
+  }
+  CU(cudaStreamSynchronize(stream));
+  return HISA_OK;
+}
+
+// bounds[i] = first position of instance i in the sorted array of `slot`.
+hisa_status Engine::inst_bounds(int slot, std::vector<uint64_t>& bounds) {
+  const uint32_t ninst = serving ? serve_slots : instance_slots(max_inst);
+  hisa_status s;
+  if ((s = ensure(inst_bnd, ninst + 1)) || (s = upload())) return s;
+  InstArgs a{dst, slot, slot, 2 * b, ninst, static_cast<unsigned long long*>(hs.buf[inst_bnd].ptr)};
+  if (wide) launch_inst_bounds<uint64_t>(a, grid, stream);
+  else launch_inst_bounds<uint32_t>(a, grid, stream);
+  CU(cudaGetLastError());
+  bounds.assign(ninst + 1, 0);
+  CU(cudaMemcpyAsync(bounds.data(), hs.buf[inst_bnd].ptr, (ninst + 1) * 8, cudaMemcpyDeviceToHost, stream));
+  CU(cudaStreamSynchronize(stream));
+  return HISA_OK;
+}
+
+hisa_status Engine::decode_range(int slot, uint64_t begin, uint64_t count, std::vector<uint32_t>& c0,
+                                 std::vector<uint32_t>& c1) {
+  c0.assign(count, 0);
+  c1.assign(count, 0);
+  if (count == 0) return HISA_OK;
+  void *t0, *t1;
+  hisa_status s;
+  if ((s = dev_alloc(count * 4, &t0)) || (s = dev_alloc(count * 4, &t1))) return s;
+  DecodeArgs a{dst, slot, slot, static_cast<uint32_t*>(t0), static_cast<uint32_t*>(t1), b, 0, begin, count};
+  if (wide) launch_decode<uint64_t>(a, grid, stream);
+  else launch_decode<uint32_t>(a, grid, stream);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(c0.data(), t0, count * 4, cudaMemcpyDeviceToHost, stream));
+  CU(cudaMemcpyAsync(c1.data(), t1, count * 4, cudaMemcpyDeviceToHost, stream));
+  dev_free(t0);
+  dev_free(t1);
+  CU(cudaStreamSynchronize(stream));
+  return HISA_OK;
+}
+
+static int find_idb(const std::vector<int>& idb, uint32_t rid) {
+  for (size_t i = 0; i < idb.size(); ++i)
+    if (uint32_t(idb[i]) == rid) return int(i);
+  return -1;
+}
+
+hisa_status Engine::instance_size(uint32_t rid, uint32_t inst, uint64_t* n) {
+  if (!n || rid >= rels.size()) return ctx_fail(HISA_ERR_INVALID_ARG, "instance_size", nullptr);
+  if (!batched || inst > max_inst) return ctx_fail(HISA_ERR_INVALID_ARG, "no such instance", nullptr);
+  const Relation& r = rels[rid];
+  if ((r.idb && !ran) || (!r.idb && edb_dirty)) return ctx_fail(HISA_ERR_STATE, "relation not evaluated yet", nullptr);
+  std::vector<uint64_t> bnd;
+  hisa_status s = inst_bounds(r.idb ? r.full : r.base, bnd);
+  if (s) return s;
+  *n = bnd[inst + 1] - bnd[inst];
+  return HISA_OK;
+}
+
+hisa_status Engine::read_instance(uint32_t rid, uint32_t inst, uint32_t* const* cols, uint64_t cap, uint64_t* n,
+                                  int on_device) {
+  if (!cols || !n || rid >= rels.size()) return ctx_fail(HISA_ERR_INVALID_ARG, "read_instance", nullptr);
+  if (!batched || inst > max_inst) return ctx_fail(HISA_ERR_INVALID_ARG, "no such instance", nullptr);
+  const Relation& r = rels[rid];
+  if ((r.idb && !ran) || (!r.idb && edb_dirty)) return ctx_fail(HISA_ERR_STATE, "relation not evaluated yet", nullptr);
+  const int slot = r.idb ? r.full : r.base;
+  std::vector<uint64_t> bnd;
+  hisa_status s = inst_bounds(slot, bnd);
+  if (s) return s;
+  const uint64_t lo = bnd[inst], cnt = bnd[inst + 1] - bnd[inst];
+  *n = cnt;
+  if (cap < cnt) return ctx_fail(HISA_ERR_CAPACITY, "read_instance: buffer too small", nullptr);
+  if (cnt == 0) return HISA_OK;
+  if (on_device) {
+    DecodeArgs a{dst, slot, slot, cols[0], cols[1], b, 0, lo, cnt};
+    if (wide) launch_decode<uint64_t>(a, grid, stream);
+    else launch_decode<uint32_t>(a, grid, stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(stream));
+    return HISA_OK;
+  }
+  std::vector<uint32_t> c0, c1;
+  if ((s = decode_range(slot, lo, cnt, c0, c1))) return s;
+  std::memcpy(cols[0], c0.data(), cnt * 4);
+  std::memcpy(cols[1], c1.data(), cnt * 4);
+  return HISA_OK;
+}
+
+hisa_status Engine::instance_delta_counts(uint32_t rid, uint32_t inst, uint64_t* out, uint32_t cap,
+                                          uint32_t* n_iters) {
+  if (!n_iters || rid >= rels.size()) return ctx_fail(HISA_ERR_INVALID_ARG, "instance_delta_counts", nullptr);
+  const int i = find_idb(idb, rid);
+  if (i < 0 || !batched || !ran) return ctx_fail(HISA_ERR_INVALID_ARG, "not an evaluated IDB relation", nullptr);
+  if (size_t(i) >= inst_hist.size() || inst >= inst_hist[i].size()) {
+    *n_iters = 0;
+    return HISA_OK;
+  }
+  const auto& h = inst_hist[i][inst];
+  uint32_t K = uint32_t(h.size());
+  while (K > 0 && h[K - 1] == 0) --K;
+  *n_iters = K;
+  for (uint32_t k = 0; k < K && k < cap && out; ++k) out[k] = h[k];
+  if (cap < K) return ctx_fail(HISA_ERR_CAPACITY, "instance_delta_counts: buffer too small", nullptr);
+  return HISA_OK;
+}
+
+// ---- serving --------------------------------------------------------------------------
+
+hisa_status Engine::serve_open(uint32_t max_instances, uint32_t max_value, uint64_t budget) {
+  if (serving) return ctx_fail(HISA_ERR_STATE, "serving session already open", nullptr);
+  if (max_instances == 0 || rules.empty()) return ctx_fail(HISA_ERR_INVALID_ARG, "serve_open", nullptr);
+  for (auto& r : rels)
+    if (!r.idb && r.staged) return ctx_fail(HISA_ERR_STATE, "EDB tuples loaded before serve_open", nullptr);
+  int bb = 1;
+  while (bb < 32 && (uint64_t(max_value) >> bb) != 0) ++bb;
+  int ib = 1;
+  while (ib < 32 && (uint64_t(max_instances - 1) >> ib) != 0) ++ib;
+  if (ib + bb > 32) return ctx_fail(HISA_ERR_UNSUPPORTED, "instance bits + domain bits exceed 32", nullptr);
+  serving = true;
+  batched = true;
+  fixed_b = bb;
+  fixed_inst_bits = ib;
+  serve_slots = max_instances;
+  max_inst = max_instances - 1;
+  serve_budget = budget ? budget : cfg.hbm_budget_bytes;
+  active_bytes = 0;
+  slot_owner.assign(max_instances, 0);
+  hisa_status s;
+  if ((s = compile())) return s;
+  // plans: ordinary iterations, and admission iterations that also run the
+  // non-recursive rules (for the instances admitted at that boundary)
+  ops1.clear();
+  opsN.clear();
+  tail.clear();
+  ops_admit.clear();
+  std::vector<std::vector<StepPlan>> both = plan1;
+  both.insert(both.end(), planN.begin(), planN.end());
+  emit_head(ops_admit, both);
+  emit_tail(ops_admit, false);
+  emit_head(opsN, planN);
+  emit_tail(opsN, false);
+  emit_tail(tail, false);
+  if ((s = init_run_state())) return s;
+  for (int r : idb) rels[r].delta_counts.clear();
+  ran = true;
+  return HISA_OK;
+}
+
+hisa_status Engine::serve_submit(uint32_t rid, const uint32_t* const* cols, uint64_t n, uint64_t* ticket) {
+  if (!serving) return ctx_fail(HISA_ERR_STATE, "no serving session", nullptr);
+  if (rid >= rels.size() || rels[rid].idb || !ticket || (n && (!cols || !cols[0] || !cols[1])))
+    return ctx_fail(HISA_ERR_INVALID_ARG, "serve_submit", nullptr);
+  Request q;
+  q.ticket = next_ticket++;
+  q.rel = rid;
+  q.c0.assign(cols ? cols[0] : nullptr, cols ? cols[0] + n : nullptr);
+  q.c1.assign(cols ? cols[1] : nullptr, cols ? cols[1] + n : nullptr);
+  uint32_t mx = 0;
+  std::vector<uint32_t> nodes(q.c0);
+  nodes.insert(nodes.end(), q.c1.begin(), q.c1.end());
+  for (uint32_t v : nodes) mx = std::max(mx, v);
+  if (n && (uint64_t(mx) >> fixed_b) != 0) return ctx_fail(HISA_ERR_INVALID_ARG, "value above max_value", nullptr);
+  std::sort(nodes.begin(), nodes.end());
+  const uint64_t distinct = uint64_t(std::unique(nodes.begin(), nodes.end()) - nodes.begin());
+  // worst case of a binary IDB relation over these values, in both versions
+  q.est_bytes = distinct * distinct * (wide ? 8 : 4) * 2 + n * 64;
+  *ticket = q.ticket;
+  pending.push_back(q.ticket);
+  reqs.emplace(q.ticket, std::move(q));
+  return HISA_OK;
+}
+
+// The EDB of a serving session: the tuples of every active request, tagged
+// with its slot, staged and indexed again (after admissions).
+hisa_status Engine::rebuild_serving_edb() {
+  for (auto& r : rels)
+    if (!r.idb) r.staged = 0;
+  for (uint32_t slot = 0; slot < serve_slots; ++slot) {
+    const uint64_t t = slot_owner[slot];
+    if (!t) continue;
+    Request& q = reqs[t];
+    if (q.c0.empty()) continue;
+    const uint32_t* cols[2] = {q.c0.data(), q.c1.data()};
+    load_inst = slot;
+    hisa_status s = load(q.rel, cols, q.c0.size(), 0);
+    load_inst = 0;
+    if (s) return s;
+  }
+  return prepare_edb();
+}
+
+// Copies out and removes the tuples of finished requests.
+hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
+  if (tickets.empty()) return HISA_OK;
+  hisa_status s;
+  for (int r : idb) {
+    Relation& R = rels[r];
+    std::vector<uint64_t> bnd;
+    if ((s = inst_bounds(R.full, bnd))) return s;
+    std::vector<bool> drop(serve_slots, false);
+    for (uint64_t t : tickets) {
+      Request& q = reqs[t];
+      auto& out = q.result[r];
+      if ((s = decode_range(R.full, bnd[q.slot], bnd[q.slot + 1] - bnd[q.slot], out.first, out.second))) return s;
+      drop[q.slot] = true;
+    }
+    // keep every other instance's range: copy the kept runs into full_next, swap
+    const uint64_t kb = wide ? 8 : 4;
+    const uint64_t n = hs.cnt[R.full];
+    if ((s = ensure(R.full_next, std::max<uint64_t>(n, 1)))) return s;
+    uint64_t w = 0;
+    uint32_t i = 0;
+    while (i < serve_slots) {
+      if (drop[i]) {
+        ++i;
+        continue;
+      }
+      uint32_t j = i;
+      while (j < serve_slots && !drop[j]) ++j;
+      const uint64_t lo = bnd[i], hi = bnd[j];
+      if (hi > lo)
+        CU(cudaMemcpyAsync(static_cast<char*>(hs.buf[R.full_next].ptr) + w * kb,
+                           static_cast<char*>(hs.buf[R.full].ptr) + lo * kb, (hi - lo) * kb,
+                           cudaMemcpyDeviceToDevice, stream));
+      w += hi - lo;
+      i = j;
+    }
+    std::swap(hs.buf[R.full], hs.buf[R.full_next]);
+    hs.cnt[R.full] = w;
+    hs.cnt[R.full_next] = 0;
+  }
+  for (uint64_t t : tickets) {
+    Request& q = reqs[t];
+    slot_owner[q.slot] = 0;
+    active_bytes -= std::min(active_bytes, q.est_bytes);
+    q.done = true;
+    q.c0.clear();
+    q.c0.shrink_to_fit();
+    q.c1.clear();
+    q.c1.shrink_to_fit();
+  }
+  return upload();
+}
+
+hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
+  if (!serving) return ctx_fail(HISA_ERR_STATE, "no serving session", nullptr);
+  hisa_serve_stats out{};
+  hisa_status s;
+  for (uint32_t it = 0; it < std::max(max_iters, 1u); ++it) {
+    // admission at the iteration boundary: free slot and budget
+    std::vector<uint64_t> admitted;
+    while (!pending.empty()) {
+      const uint64_t t = pending.front();
+      Request& q = reqs[t];
+      auto free_slot = std::find(slot_owner.begin(), slot_owner.end(), 0ull);
+      if (free_slot == slot_owner.end()) break;
+      if (serve_budget && active_bytes + q.est_bytes > serve_budget && active_bytes > 0) break;
+      q.slot = int(free_slot - slot_owner.begin());
+      *free_slot = t;
+      active_bytes += q.est_bytes;
+      admitted.push_back(t);
+      pending.pop_front();
+    }
+    out.admitted += uint32_t(admitted.size());
+    if (!admitted.empty() && (s = rebuild_serving_edb())) return s;
+    const bool any_active = std::any_of(slot_owner.begin(), slot_owner.end(), [](uint64_t t) { return t != 0; });
+    if (!any_active) break;
+    // one iteration of the shared fixpoint
+    if ((s = iterate_once(admitted.empty() ? opsN : ops_admit))) return s;
+    ++out.iterations;
+    std::vector<std::vector<uint64_t>> rows;
+    if ((s = collect_inst_rows(rows))) return s;
+    std::vector<uint64_t> finished;
+    for (uint32_t slot = 0; slot < serve_slots; ++slot) {
+      const uint64_t t = slot_owner[slot];
+      if (!t) continue;
+      Request& q = reqs[t];
+      bool empty = true;
+      for (size_t i = 0; i < idb.size(); ++i) {
+        q.deltas[idb[i]].push_back(rows[i][slot]);
+        if (rows[i][slot]) empty = false;
+      }
+      if (empty) finished.push_back(t);
+    }
+    for (uint64_t t : finished)
+      for (auto& kv : reqs[t].deltas) {
+        auto& v = kv.second;
+        while (!v.empty() && v.back() == 0) v.pop_back();
+      }
+    if ((s = retire(finished))) return s;
+    out.retired += uint32_t(finished.size());
+  }
+  out.pending = uint32_t(pending.size());
+  out.active = uint32_t(std::count_if(slot_owner.begin(), slot_owner.end(), [](uint64_t t) { return t != 0; }));
+  if (st) *st = out;
+  return HISA_OK;
+}
+
+hisa_status Engine::serve_poll(uint64_t ticket, int* done) {
+  auto it = reqs.find(ticket);
+  if (it == reqs.end() || !done) return ctx_fail(HISA_ERR_INVALID_ARG, "unknown ticket", nullptr);
+  *done = it->second.done ? 1 : 0;
+  return HISA_OK;
+}
+
+hisa_status Engine::serve_result(uint64_t ticket, uint32_t rid, uint32_t* const* cols, uint64_t cap, uint64_t* n,
+                                 uint64_t* deltas, uint32_t dcap, uint32_t* n_iters) {
+  auto it = reqs.find(ticket);
+  if (it == reqs.end() || !n) return ctx_fail(HISA_ERR_INVALID_ARG, "unknown ticket", nullptr);
+  Request& q = it->second;
+  if (!q.done) return ctx_fail(HISA_ERR_STATE, "request not complete", nullptr);
+  auto r = q.result.find(int(rid));
+  const uint64_t size = r == q.result.end() ? 0 : r->second.first.size();
+  *n = size;
+  const auto& dv = q.deltas[int(rid)];
+  if (n_iters) *n_iters = uint32_t(dv.size());
+  for (uint32_t k = 0; deltas && k < dv.size() && k < dcap; ++k) deltas[k] = dv[k];
+  if (cap < size || (deltas && dcap < dv.size()))
+    return ctx_fail(HISA_ERR_CAPACITY, "serve_result: buffer too small", nullptr);
+  if (size && cols) {
+    std::memcpy(cols[0], r->second.first.data(), size * 4);
+    std::memcpy(cols[1], r->second.second.data(), size * 4);
+  }
+  return HISA_OK;
+}
+
+hisa_status Engine::serve_release(uint64_t ticket) {
+  auto it = reqs.find(ticket);
+  if (it == reqs.end()) return ctx_fail(HISA_ERR_INVALID_ARG, "unknown ticket", nullptr);
+  if (!it->second.done) return ctx_fail(HISA_ERR_STATE, "request not complete", nullptr);
+  reqs.erase(it);
+  return HISA_OK;
+}
+
+}  // namespace hisa

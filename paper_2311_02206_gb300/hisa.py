@@ -74,6 +74,14 @@ class RunStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServeStats(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_uint32), ("retired", ctypes.c_uint32), ("active", ctypes.c_uint32),
+                ("pending", ctypes.c_uint32), ("iterations", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -97,6 +105,21 @@ SIGNATURES = {
     "hisa_read_relation": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint64,
                                             _U64P, ctypes.c_int]),
     "hisa_delta_counts": (ctypes.c_int32, [_P, ctypes.c_uint32, _U64P, ctypes.c_uint32, _U32P]),
+    "hisa_load_instance": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.c_uint64, ctypes.c_int]),
+    "hisa_instance_size": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.c_uint32, _U64P]),
+    "hisa_read_instance": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.c_uint64, _U64P, ctypes.c_int]),
+    "hisa_instance_delta_counts": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.c_uint32, _U64P, ctypes.c_uint32,
+                                                    _U32P]),
+    "hisa_serve_open": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64]),
+    "hisa_serve_submit": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint64,
+                                           _U64P]),
+    "hisa_serve_step": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.POINTER(ServeStats)]),
+    "hisa_serve_poll": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+    "hisa_serve_result": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.c_uint64, _U64P, _U64P, ctypes.c_uint32, _U32P]),
+    "hisa_serve_release": (ctypes.c_int32, [_P, ctypes.c_uint64]),
     "hisa_kernel_stats": (ctypes.c_int32, [_P, ctypes.POINTER(KernelStat), ctypes.c_uint32, _U32P]),
     "hisa_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "hisa_last_error": (ctypes.c_char_p, [_P]),
@@ -313,6 +336,78 @@ class Context:
         ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
         _check(self._lib.hisa_read_relation(self._h, rid, ptrs, n, ctypes.byref(got), 0), self._h)
         return c0[:n], c1[:n]
+
+    # -- batched instances --
+    def load_instance(self, rel, instance: int, c0, c1):
+        rid = self.rel_ids[rel] if isinstance(rel, str) else rel
+        c0 = np.ascontiguousarray(c0, dtype=np.uint32)
+        c1 = np.ascontiguousarray(c1, dtype=np.uint32)
+        ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
+        _check(self._lib.hisa_load_instance(self._h, rid, instance, ptrs, len(c0), 0), self._h)
+
+    def instance_size(self, rel, instance: int) -> int:
+        rid = self.rel_ids[rel] if isinstance(rel, str) else rel
+        n = ctypes.c_uint64()
+        _check(self._lib.hisa_instance_size(self._h, rid, instance, ctypes.byref(n)), self._h)
+        return n.value
+
+    def read_instance(self, rel, instance: int):
+        rid = self.rel_ids[rel] if isinstance(rel, str) else rel
+        n = self.instance_size(rid, instance)
+        c0 = np.empty(max(n, 1), np.uint32)
+        c1 = np.empty(max(n, 1), np.uint32)
+        got = ctypes.c_uint64()
+        ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
+        _check(self._lib.hisa_read_instance(self._h, rid, instance, ptrs, n, ctypes.byref(got), 0), self._h)
+        return c0[:n], c1[:n]
+
+    def instance_delta_counts(self, rel, instance: int) -> list:
+        rid = self.rel_ids[rel] if isinstance(rel, str) else rel
+        k = ctypes.c_uint32()
+        self._lib.hisa_instance_delta_counts(self._h, rid, instance, None, 0, ctypes.byref(k))
+        out = (ctypes.c_uint64 * max(k.value, 1))()
+        _check(self._lib.hisa_instance_delta_counts(self._h, rid, instance, out, k.value, ctypes.byref(k)), self._h)
+        return [int(out[i]) for i in range(k.value)]
+
+    # -- serving --
+    def serve_open(self, max_instances: int, max_value: int, budget_bytes: int = 0):
+        _check(self._lib.hisa_serve_open(self._h, max_instances, max_value, budget_bytes), self._h)
+
+    def serve_submit(self, rel, c0, c1) -> int:
+        rid = self.rel_ids[rel] if isinstance(rel, str) else rel
+        c0 = np.ascontiguousarray(c0, dtype=np.uint32)
+        c1 = np.ascontiguousarray(c1, dtype=np.uint32)
+        ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
+        t = ctypes.c_uint64()
+        _check(self._lib.hisa_serve_submit(self._h, rid, ptrs, len(c0), ctypes.byref(t)), self._h)
+        return t.value
+
+    def serve_step(self, max_iterations: int = 1) -> dict:
+        st = ServeStats()
+        _check(self._lib.hisa_serve_step(self._h, max_iterations, ctypes.byref(st)), self._h)
+        return st.as_dict()
+
+    def serve_poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check(self._lib.hisa_serve_poll(self._h, ticket, ctypes.byref(d)), self._h)
+        return bool(d.value)
+
+    def serve_result(self, ticket: int, rel):
+        """(c0, c1, delta_counts) of a completed request for IDB relation ``rel``."""
+        rid = self.rel_ids[rel] if isinstance(rel, str) else rel
+        n = ctypes.c_uint64()
+        k = ctypes.c_uint32()
+        self._lib.hisa_serve_result(self._h, ticket, rid, None, 0, ctypes.byref(n), None, 0, ctypes.byref(k))
+        c0 = np.empty(max(n.value, 1), np.uint32)
+        c1 = np.empty(max(n.value, 1), np.uint32)
+        dl = (ctypes.c_uint64 * max(k.value, 1))()
+        ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
+        _check(self._lib.hisa_serve_result(self._h, ticket, rid, ptrs, n.value, ctypes.byref(n), dl, k.value,
+                                           ctypes.byref(k)), self._h)
+        return c0[:n.value], c1[:n.value], [int(dl[i]) for i in range(k.value)]
+
+    def serve_release(self, ticket: int):
+        _check(self._lib.hisa_serve_release(self._h, ticket), self._h)
 
     def kernel_stats(self) -> list:
         """Per-kernel launches, device ms and algorithmic bytes of the last run

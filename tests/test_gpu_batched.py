@@ -1,0 +1,113 @@
+"""Batched and served evaluation of independent REACH instances: every
+instance's tuples and delta counts must equal those of the oracle run on that
+instance alone, whether it ran in a static batch or was admitted into (and
+retired from) a running serving session."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_02206_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2311_02206_gb300 import build
+    build.build()
+
+
+def instances(count, seed, nmax=60):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(2, nmax))
+        m = int(rng.integers(0, 3 * n))
+        s = rng.integers(0, n, m).astype(np.uint32)
+        d = rng.integers(0, n, m).astype(np.uint32)
+        out.append((s, d))
+    return out
+
+
+def check(ref, c0, c1, counts):
+    w0, w1 = ref.relations["Reach"]
+    assert np.array_equal(c0, w0) and np.array_equal(c1, w1)
+    assert counts == ref.delta_counts["Reach"]
+
+
+def test_static_batch_matches_each_instance_alone():
+    from paper_2311_02206_gb300 import hisa
+    inst = instances(48, 1)
+    with hisa.Context() as ctx:
+        ctx.program(*oracle.REACH)
+        for i, (s, d) in enumerate(inst):
+            ctx.load_instance("Edge", i, s, d)
+        ctx.run()
+        for i, (s, d) in enumerate(inst):
+            c0, c1 = ctx.read_instance("Reach", i)
+            check(oracle.reach(s, d), c0, c1, ctx.instance_delta_counts("Reach", i))
+
+
+def test_serving_continuous_admission_and_slot_reuse():
+    """8 slots, 40 requests submitted in three waves while the session runs:
+    requests wait for free slots, are admitted at iteration boundaries next to
+    running ones, and slots of finished requests are reused."""
+    from paper_2311_02206_gb300 import hisa
+    inst = instances(40, 2)
+    with hisa.Context() as ctx:
+        ctx.program(*oracle.REACH)
+        ctx.serve_open(8, 63)
+        tickets = {}
+        for i in range(15):
+            tickets[ctx.serve_submit("Edge", *inst[i])] = i
+        steps = 0
+        nxt = 15
+        while True:
+            st = ctx.serve_step(1)
+            steps += 1
+            if steps in (2, 5) or (steps > 5 and nxt < len(inst)):
+                for i in range(nxt, min(nxt + 10, len(inst))):
+                    tickets[ctx.serve_submit("Edge", *inst[i])] = i
+                nxt = min(nxt + 10, len(inst))
+            if st["active"] == 0 and st["pending"] == 0 and nxt == len(inst):
+                break
+            assert steps < 2000
+        for t, i in tickets.items():
+            assert ctx.serve_poll(t)
+            c0, c1, counts = ctx.serve_result(t, "Reach")
+            check(oracle.reach(*inst[i]), c0, c1, counts)
+            ctx.serve_release(t)
+
+
+def test_serving_budget_limits_admission():
+    from paper_2311_02206_gb300 import hisa
+    inst = [workloads.er_graph(40, 100, k) for k in range(6)]
+    with hisa.Context() as ctx:
+        ctx.program(*oracle.REACH)
+        ctx.serve_open(16, 63, budget_bytes=1)      # at most one instance at a time
+        tickets = [ctx.serve_submit("Edge", s, d) for s, d in inst]
+        st = ctx.serve_step(1)
+        assert st["admitted"] == 1 and st["pending"] == 5
+        while st["active"] or st["pending"]:
+            st = ctx.serve_step(4)
+        for t, (s, d) in zip(tickets, inst):
+            c0, c1, counts = ctx.serve_result(t, "Reach")
+            check(oracle.reach(s, d), c0, c1, counts)
+
+
+def test_batch_of_config_shapes():
+    """Instances with the config's size law (log-uniform n, degree 1.5-4),
+    scaled down to 64 instances with n <= 512."""
+    from paper_2311_02206_gb300 import hisa
+    specs = workloads.batch_instances(64, 4, n_lo_log2=6, n_hi_log2=9)
+    graphs = [workloads.er_graph(n, m, sd) for n, m, sd in specs]
+    with hisa.Context() as ctx:
+        ctx.program(*oracle.REACH)
+        for i, (s, d) in enumerate(graphs):
+            ctx.load_instance("Edge", i, s, d)
+        ctx.run()
+        for i in range(0, 64, 7):
+            c0, c1 = ctx.read_instance("Reach", i)
+            check(oracle.reach(*graphs[i]), c0, c1, ctx.instance_delta_counts("Reach", i))
