@@ -45,7 +45,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hisa", "reference"], default="hisa")
-    ap.add_argument("--workload", choices=["rmat16", "rmat13", "er1000"], default="rmat16",
+    ap.add_argument("--instances", type=int, default=4096, help="batch5: number of instances")
+    ap.add_argument("--budget-gb", type=float, default=100.0, help="batch5: serving memory budget")
+    ap.add_argument("--workload", choices=["rmat16", "rmat13", "er1000", "batch5"], default="rmat16",
                     help="rmat16: the benchmark workload; rmat13: a smaller R-MAT graph for profiler captures")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
@@ -405,6 +407,115 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ---- batched / served REACH (many independent instances) ------------------------------------------
+
+def run_batch5(a):
+    """Independent REACH instances (n log-uniform in [64, 8192], mean out-degree
+    uniform in [1.5, 4], ER edges, seed 4) served three ways on one GPU:
+    one by one (a run per instance), and through the serving loop with Poisson
+    arrivals at 0.5x and 2x the one-by-one service rate (continuous batching:
+    admission at iteration boundaries by free slots and memory budget,
+    retirement on convergence).  Latency = arrival -> result on the host."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2311_02206_gb300 import build, hisa, workloads
+
+    torch.cuda.set_device(0)
+    build.build()
+    specs = workloads.batch_instances(a.instances, 4)
+    graphs = [workloads.er_graph(n, m, sd) for n, m, sd in specs]
+    nmax = max(n for n, _, _ in specs)
+
+    def dev_fp(c0, c1):
+        """Order-independent hash of a relation held in two int32 CUDA tensors."""
+        x = ((c0.to(torch.int64) & 0xFFFFFFFF) << 32) | (c1.to(torch.int64) & 0xFFFFFFFF)
+        x = x * -7046029254386353131          # 0x9E3779B97F4A7C15 as int64 (wrapping)
+        x = x ^ ((x >> 29) & ((1 << 35) - 1))
+        x = x * -4658895280553007687          # 0xBF58476D1CE4E5B9 as int64
+        return int(x.sum())
+
+    # one by one
+    ctx = hisa.Context(flags=hisa.FLAG_GRAPH)
+    ctx.program(*oracle.REACH)
+    alone = {}
+    lat1 = []
+    for i in range(min(3, len(graphs))):   # warm-up
+        ctx.reset_edb()
+        ctx.load_tuples("Edge", *graphs[i])
+        ctx.run()
+    t_all = time.perf_counter()
+    for i, (s, d) in enumerate(graphs):
+        t0 = time.perf_counter()
+        ctx.reset_edb()
+        ctx.load_tuples("Edge", s, d)
+        ctx.run()
+        c0, c1 = ctx.read_relation("Reach", device=True)
+        torch.cuda.synchronize()
+        lat1.append(time.perf_counter() - t0)
+        alone[i] = (c0.numel(), ctx.delta_counts("Reach"), dev_fp(c0, c1))
+    t1 = time.perf_counter() - t_all
+    ctx.close()
+    torch.cuda.empty_cache()
+    rate1 = len(graphs) / t1
+    tuples = sum(v[0] for v in alone.values())
+
+    def served(lam, seed):
+        rng = np.random.default_rng(seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, len(graphs))) if lam else np.zeros(len(graphs))
+        sctx = hisa.Context()
+        sctx.program(*oracle.REACH)
+        slots = 1
+        while slots < min(len(graphs), 4096):
+            slots *= 2
+        sctx.serve_open(slots, nmax, budget_bytes=int(a.budget_gb * (1 << 30)))
+        tickets, lat, done = {}, {}, set()
+        nxt = 0
+        start = time.perf_counter()
+        while len(done) < len(graphs):
+            now = time.perf_counter() - start
+            while nxt < len(graphs) and arrivals[nxt] <= now:
+                tickets[sctx.serve_submit("Edge", *graphs[nxt])] = nxt
+                nxt += 1
+            st = sctx.serve_step(1)
+            if st["retired"]:
+                tnow = time.perf_counter() - start
+                for t, i in list(tickets.items()):
+                    if i not in done and sctx.serve_poll(t):
+                        done.add(i)
+                        lat[i] = tnow - arrivals[i]
+                        c0, c1, dc = sctx.serve_result(t, "Reach", device=True)
+                        if c0.numel() != alone[i][0] or dc != alone[i][1] or dev_fp(c0, c1) != alone[i][2]:
+                            raise RuntimeError(f"instance {i} differs between served and one-by-one runs")
+                        sctx.serve_release(t)
+                        del tickets[t]
+            elif st["active"] == 0 and st["pending"] == 0 and nxt < len(graphs):
+                time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - start))))
+        wall = time.perf_counter() - start
+        sctx.close()
+        torch.cuda.empty_cache()
+        v = np.array([lat[i] for i in range(len(graphs))])
+        return {"lambda_per_s": lam, "p50_ms": float(np.percentile(v, 50) * 1e3),
+                "p99_ms": float(np.percentile(v, 99) * 1e3), "instances_per_s": len(graphs) / wall,
+                "tuples_per_s": tuples / wall, "wall_s": wall}
+
+    res = {
+        "metric": "batched p50/p99 latency and throughput vs one-by-one", "unit": "ms / instances/s",
+        "config": {"workload": f"{len(graphs)} independent REACH instances, n log-uniform in [64, 8192], "
+                               "mean out-degree uniform in [1.5, 4], ER edges, seed 4, Poisson arrivals",
+                   "sum_reach_tuples": tuples, "budget_gb": a.budget_gb},
+        "one_by_one": {"instances_per_s": rate1, "tuples_per_s": tuples / t1,
+                       "p50_ms": float(np.percentile(lat1, 50) * 1e3), "p99_ms": float(np.percentile(lat1, 99) * 1e3),
+                       "note": "latency of a run started on an idle GPU (no queueing); results read into device memory"},
+        "served_all_at_once": served(0, 1),
+        "served_0.5x": served(0.5 * rate1, 2),
+        "served_2x": served(2.0 * rate1, 3),
+        "exact": "every served instance equals its one-by-one run (size, delta counts, device hash of the tuples)",
+    }
+    print(json.dumps(res), flush=True)
+
+
 # ---- sort / merge microbenchmark ----------------------------------------------------------------
 
 def run_micro(a):
@@ -479,6 +590,8 @@ if __name__ == "__main__":
     args = _args()
     if args.micro:
         run_micro(args)
+    elif args.workload == "batch5" and args.impl == "hisa":
+        run_batch5(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

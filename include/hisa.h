@@ -212,12 +212,15 @@ hisa_status hisa_serve_submit(hisa_ctx* ctx, uint32_t rel_id, const uint32_t* co
 hisa_status hisa_serve_step(hisa_ctx* ctx, uint32_t max_iterations, hisa_serve_stats* stats);
 /* *done = 1 once the request's fixpoint is complete. */
 hisa_status hisa_serve_poll(hisa_ctx* ctx, uint64_t ticket, int* done);
-/* A completed request's tuples of IDB relation rel_id (host arrays with room
- * for cap tuples; *n receives the size) and its delta sizes (host array of
- * dcap; *n_iters receives K).  Errors: STATE (not complete), CAPACITY. */
+/* A completed request's tuples of IDB relation rel_id, ascending (c0, c1),
+ * into cols[0], cols[1] (room for cap tuples; device pointers if
+ * cols_on_device, else host; cols may be NULL to query sizes), *n receives
+ * the size; its delta sizes go to the host array deltas[dcap], *n_iters
+ * receives K.  Completed results stay in device memory until released.
+ * Errors: STATE (not complete), CAPACITY (sizes are still set). */
 hisa_status hisa_serve_result(hisa_ctx* ctx, uint64_t ticket, uint32_t rel_id, uint32_t* const* cols, uint64_t cap,
-                              uint64_t* n, uint64_t* deltas, uint32_t dcap, uint32_t* n_iters);
-/* Forgets a completed request. */
+                              uint64_t* n, uint64_t* deltas, uint32_t dcap, uint32_t* n_iters, int cols_on_device);
+/* Forgets a completed request and frees its stored result. */
 hisa_status hisa_serve_release(hisa_ctx* ctx, uint64_t ticket);
 
 /* Per-kernel accounting of the last run made with HISA_FLAG_PHASE_TIMES (the

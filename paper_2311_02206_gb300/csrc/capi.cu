@@ -127,9 +127,9 @@ hisa_status hisa_serve_poll(hisa_ctx* ctx, uint64_t ticket, int* done) {
 }
 
 hisa_status hisa_serve_result(hisa_ctx* ctx, uint64_t ticket, uint32_t rel_id, uint32_t* const* cols, uint64_t cap,
-                              uint64_t* n, uint64_t* deltas, uint32_t dcap, uint32_t* n_iters) {
+                              uint64_t* n, uint64_t* deltas, uint32_t dcap, uint32_t* n_iters, int cols_on_device) {
   if (!ctx) return HISA_ERR_INVALID_ARG;
-  return ctx->eng.serve_result(ticket, rel_id, cols, cap, n, deltas, dcap, n_iters);
+  return ctx->eng.serve_result(ticket, rel_id, cols, cap, n, deltas, dcap, n_iters, cols_on_device);
 }
 
 hisa_status hisa_serve_release(hisa_ctx* ctx, uint64_t ticket) {

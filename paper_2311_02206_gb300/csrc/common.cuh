@@ -15,7 +15,7 @@ namespace hisa {
 
 // ---- device-resident control block ---------------------------------------------------
 
-enum : int { kMaxBufs = 96, kMaxCnts = 96 };
+enum : int { kMaxBufs = 160, kMaxCnts = 160 };
 
 // Device error codes (DevState::error).
 enum : uint32_t {

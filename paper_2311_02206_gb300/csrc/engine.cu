@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <unordered_map>
@@ -217,9 +218,10 @@ hisa_status Engine::load(uint32_t rid, const uint32_t* const* cols, uint64_t n, 
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   for (int c = 0; c < 2; ++c)
     CU(cudaMemcpyAsync(r.stage[c] + r.staged, cols[c], n * 4, kind, stream));
-  // active-domain bound for the code width
+  // active-domain bound for the code width (fixed up front in a serving session)
   uint32_t mx = 0;
-  if (!on_device) {
+  if (serving) {
+  } else if (!on_device) {
     for (int c = 0; c < 2; ++c)
       for (uint64_t i = 0; i < n; ++i) mx = std::max(mx, cols[c][i]);
   } else {
@@ -739,6 +741,14 @@ hisa_status Engine::grow_keep(int id, uint64_t cap, uint64_t keep) {
 }
 
 hisa_status Engine::regrow() {
+  static const bool debug = std::getenv("HISA_DEBUG") != nullptr;
+  if (debug) {
+    std::fprintf(stderr, "[hisa] iter %u overflow %u:", hs.iter, hs.overflow);
+    for (int id = 0; id < nslots; ++id)
+      if (hs.need[id]) std::fprintf(stderr, " slot %d need %llu cap %llu", id, (unsigned long long)hs.need[id],
+                                    (unsigned long long)hs.buf[id].cap);
+    std::fprintf(stderr, "\n");
+  }
   for (int id = 0; id < nslots; ++id) {
     const uint64_t need = hs.need[id];
     if (need == 0 || need <= hs.buf[id].cap) continue;
@@ -765,15 +775,33 @@ hisa_status Engine::regrow() {
     if (partner >= 0 && (s = grow_keep(partner, cap, partner == live ? hs.cnt[live] : 0))) return s;
     ++regrows;
   }
-  // the radix ping-pong buffer follows its partner (only when the join stage
-  // re-runs: after a merge-stage overflow they hold the sorted new tuples)
+  // scratch whose size follows from the same counts grows in the same step, so
+  // one growth event costs one re-run (only when the join stage re-runs: after
+  // a merge-stage overflow the radix buffers hold the sorted new tuples)
+  const int kt = wide ? radix_tile<uint64_t>() : radix_tile<uint32_t>();
+  const int ks = wide ? setop_tile<uint64_t>() : setop_tile<uint32_t>();
+  uint64_t new_cap = 0, full_cap = 0, delta_cap = 0;
   for (int r : idb) {
-    if (!(hs.overflow & 1)) break;
     const Relation& R = rels[r];
-    const uint64_t c = std::max(hs.buf[R.fresh].cap, hs.buf[R.fresh_alt].cap);
-    hisa_status s;
-    if ((s = ensure(R.fresh, c)) || (s = ensure(R.fresh_alt, c))) return s;
+    new_cap = std::max({new_cap, hs.buf[R.fresh].cap, hs.buf[R.fresh_alt].cap});
+    full_cap = std::max({full_cap, hs.cnt[R.full], hs.buf[R.full_next].cap});
+    delta_cap = std::max({delta_cap, hs.buf[R.delta].cap, hs.buf[R.delta_next].cap});
   }
+  hisa_status s;
+  if (hs.overflow & 1) {
+    for (int r : idb) {
+      const Relation& R = rels[r];
+      if ((s = ensure(R.fresh, new_cap)) || (s = ensure(R.fresh_alt, new_cap))) return s;
+    }
+    if ((s = ensure(sc.radix_status, (new_cap / kt + 2) * kRadixDigits)) ||
+        (s = ensure(sc.starts, new_cap / kJoinChunk + 2)))
+      return s;
+  }
+  // next iterations: delta is the outer relation of the joins; full + new is merged
+  if ((s = ensure(sc.offs, delta_cap + 1)) || (s = ensure(sc.join_status, delta_cap / kJoinTile + 2))) return s;
+  if ((s = ensure(sc.split, (full_cap + new_cap) / ks + 2)) ||
+      (s = ensure(sc.setop_status, (full_cap + new_cap) / ks + 2)))
+    return s;
   std::memset(hs.need, 0, sizeof hs.need);
   hs.overflow = 0;
   return HISA_OK;
@@ -855,6 +883,7 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
   hisa_status s;
   uint32_t graph_launches = 0;
   int guard = 0;
+  uint32_t last_iter = hs.iter;
   const bool timing = cfg.flags & HISA_FLAG_PHASE_TIMES;
   const double kb = wide ? 8.0 : 4.0;
   std::memset(kstat, 0, sizeof kstat);
@@ -903,9 +932,19 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
       return ctx_fail(hs.error == kDevTimeout ? HISA_ERR_DEVICE_TIMEOUT : HISA_ERR_CUDA, "device error",
                       hs.error == kDevTimeout ? "bounded wait expired" : "probe limit / bad state");
     }
-    if (hs.iter != iter0) guard = 0;   // progress: an iteration committed
+    if (hs.iter != last_iter) {   // progress: an iteration committed (launch or tail re-run)
+      guard = 0;
+      last_iter = hs.iter;
+    }
     if (hs.overflow) {
-      if (++guard > 16) return ctx_fail(HISA_ERR_OOM, "buffers keep overflowing", nullptr);
+      if (++guard > 16) {
+        std::string m = "overflow bits " + std::to_string(hs.overflow) + " iter " + std::to_string(hs.iter) + ":";
+        for (int id = 0; id < nslots; ++id)
+          if (hs.need[id])
+            m += " slot " + std::to_string(id) + " need " + std::to_string(hs.need[id]) + " cap " +
+                 std::to_string(hs.buf[id].cap);
+        return ctx_fail(HISA_ERR_OOM, "buffers keep overflowing", m.c_str());
+      }
       const uint32_t bits = hs.overflow;
       if ((s = regrow())) return s;
       if ((s = upload())) return s;

@@ -68,8 +68,10 @@ struct Request {
   uint64_t est_bytes = 0;
   int slot = -1;
   bool done = false;
+  uint32_t* dev_edges = nullptr;                                        // c0 then c1 on the device
+  uint64_t n = 0;
   std::map<int, std::vector<uint64_t>> deltas;                          // IDB rel -> |delta_k|
-  std::map<int, std::pair<std::vector<uint32_t>, std::vector<uint32_t>>> result;
+  std::map<int, std::pair<void*, uint64_t>> result;                     // IDB rel -> codes on the device
 };
 
 class Engine {
@@ -95,7 +97,7 @@ class Engine {
   hisa_status serve_step(uint32_t max_iters, hisa_serve_stats* st);
   hisa_status serve_poll(uint64_t ticket, int* done);
   hisa_status serve_result(uint64_t ticket, uint32_t rid, uint32_t* const* cols, uint64_t cap, uint64_t* n,
-                           uint64_t* deltas, uint32_t dcap, uint32_t* n_iters);
+                           uint64_t* deltas, uint32_t dcap, uint32_t* n_iters, int on_device);
   hisa_status serve_release(uint64_t ticket);
   hisa_status ctx_fail(hisa_status s, const char* what, const char* detail);
   uint32_t load_inst = 0;   // instance id given to tuples by the next load
@@ -180,6 +182,7 @@ class Engine {
   std::unordered_map<uint64_t, Request> reqs;
   std::deque<uint64_t> pending;
   std::vector<Op> ops_admit;
+  int res_slot = -1;          // slot aliasing a request's result codes while they are decoded
   struct KStat { uint64_t launches; double ms, bytes; };
   KStat kstat[kKindCount] = {};
   uint64_t body_kernels = 0;   // kernels in one captured iteration

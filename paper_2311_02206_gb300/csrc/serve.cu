@@ -216,6 +216,20 @@ hisa_status Engine::serve_submit(uint32_t rid, const uint32_t* const* cols, uint
   const uint64_t distinct = uint64_t(std::unique(nodes.begin(), nodes.end()) - nodes.begin());
   // worst case of a binary IDB relation over these values, in both versions
   q.est_bytes = distinct * distinct * (wide ? 8 : 4) * 2 + n * 64;
+  q.n = n;
+  if (n) {   // the request's tuples move to the device once
+    void* p;
+    hisa_status s = dev_alloc(2 * n * 4, &p);
+    if (s) return s;
+    q.dev_edges = static_cast<uint32_t*>(p);
+    CU(cudaMemcpyAsync(q.dev_edges, q.c0.data(), n * 4, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync(q.dev_edges + n, q.c1.data(), n * 4, cudaMemcpyHostToDevice, stream));
+    CU(cudaStreamSynchronize(stream));
+  }
+  q.c0.clear();
+  q.c0.shrink_to_fit();
+  q.c1.clear();
+  q.c1.shrink_to_fit();
   *ticket = q.ticket;
   pending.push_back(q.ticket);
   reqs.emplace(q.ticket, std::move(q));
@@ -231,10 +245,10 @@ hisa_status Engine::rebuild_serving_edb() {
     const uint64_t t = slot_owner[slot];
     if (!t) continue;
     Request& q = reqs[t];
-    if (q.c0.empty()) continue;
-    const uint32_t* cols[2] = {q.c0.data(), q.c1.data()};
+    if (!q.n) continue;
+    const uint32_t* cols[2] = {q.dev_edges, q.dev_edges + q.n};
     load_inst = slot;
-    hisa_status s = load(q.rel, cols, q.c0.size(), 0);
+    hisa_status s = load(q.rel, cols, q.n, 1);
     load_inst = 0;
     if (s) return s;
   }
@@ -250,14 +264,20 @@ hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
     std::vector<uint64_t> bnd;
     if ((s = inst_bounds(R.full, bnd))) return s;
     std::vector<bool> drop(serve_slots, false);
+    const uint64_t kb = wide ? 8 : 4;
     for (uint64_t t : tickets) {
       Request& q = reqs[t];
-      auto& out = q.result[r];
-      if ((s = decode_range(R.full, bnd[q.slot], bnd[q.slot + 1] - bnd[q.slot], out.first, out.second))) return s;
+      const uint64_t lo = bnd[q.slot], cnt = bnd[q.slot + 1] - bnd[q.slot];
+      void* p = nullptr;
+      if (cnt) {   // the finished instance's codes, copied aside on the device
+        if ((s = dev_alloc(cnt * kb, &p))) return s;
+        CU(cudaMemcpyAsync(p, static_cast<char*>(hs.buf[R.full].ptr) + lo * kb, cnt * kb, cudaMemcpyDeviceToDevice,
+                           stream));
+      }
+      q.result[r] = {p, cnt};
       drop[q.slot] = true;
     }
     // keep every other instance's range: copy the kept runs into full_next, swap
-    const uint64_t kb = wide ? 8 : 4;
     const uint64_t n = hs.cnt[R.full];
     if ((s = ensure(R.full_next, std::max<uint64_t>(n, 1)))) return s;
     uint64_t w = 0;
@@ -286,10 +306,8 @@ hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
     slot_owner[q.slot] = 0;
     active_bytes -= std::min(active_bytes, q.est_bytes);
     q.done = true;
-    q.c0.clear();
-    q.c0.shrink_to_fit();
-    q.c1.clear();
-    q.c1.shrink_to_fit();
+    dev_free(q.dev_edges);
+    q.dev_edges = nullptr;
   }
   return upload();
 }
@@ -356,30 +374,54 @@ hisa_status Engine::serve_poll(uint64_t ticket, int* done) {
 }
 
 hisa_status Engine::serve_result(uint64_t ticket, uint32_t rid, uint32_t* const* cols, uint64_t cap, uint64_t* n,
-                                 uint64_t* deltas, uint32_t dcap, uint32_t* n_iters) {
+                                 uint64_t* deltas, uint32_t dcap, uint32_t* n_iters, int on_device) {
   auto it = reqs.find(ticket);
   if (it == reqs.end() || !n) return ctx_fail(HISA_ERR_INVALID_ARG, "unknown ticket", nullptr);
   Request& q = it->second;
   if (!q.done) return ctx_fail(HISA_ERR_STATE, "request not complete", nullptr);
   auto r = q.result.find(int(rid));
-  const uint64_t size = r == q.result.end() ? 0 : r->second.first.size();
+  const uint64_t size = r == q.result.end() ? 0 : r->second.second;
   *n = size;
   const auto& dv = q.deltas[int(rid)];
   if (n_iters) *n_iters = uint32_t(dv.size());
   for (uint32_t k = 0; deltas && k < dv.size() && k < dcap; ++k) deltas[k] = dv[k];
   if (cap < size || (deltas && dcap < dv.size()))
     return ctx_fail(HISA_ERR_CAPACITY, "serve_result: buffer too small", nullptr);
-  if (size && cols) {
-    std::memcpy(cols[0], r->second.first.data(), size * 4);
-    std::memcpy(cols[1], r->second.second.data(), size * 4);
+  if (!size || !cols) return HISA_OK;
+  // decode the stored codes through a slot that aliases them
+  if (res_slot < 0) res_slot = new_slot(wide ? 8 : 4);
+  hs.buf[res_slot] = {r->second.first, size};
+  hs.cnt[res_slot] = size;
+  hisa_status s = upload();
+  if (s) return s;
+  uint32_t *d0 = cols[0], *d1 = cols[1];
+  void *t0 = nullptr, *t1 = nullptr;
+  if (!on_device) {
+    if ((s = dev_alloc(size * 4, &t0)) || (s = dev_alloc(size * 4, &t1))) return s;
+    d0 = static_cast<uint32_t*>(t0);
+    d1 = static_cast<uint32_t*>(t1);
   }
-  return HISA_OK;
+  DecodeArgs a{dst, res_slot, res_slot, d0, d1, b, 0, 0, size};
+  if (wide) launch_decode<uint64_t>(a, grid, stream);
+  else launch_decode<uint32_t>(a, grid, stream);
+  CU(cudaGetLastError());
+  if (!on_device) {
+    CU(cudaMemcpyAsync(cols[0], d0, size * 4, cudaMemcpyDeviceToHost, stream));
+    CU(cudaMemcpyAsync(cols[1], d1, size * 4, cudaMemcpyDeviceToHost, stream));
+    dev_free(t0);
+    dev_free(t1);
+  }
+  CU(cudaStreamSynchronize(stream));
+  hs.buf[res_slot] = {nullptr, 0};
+  hs.cnt[res_slot] = 0;
+  return upload();
 }
 
 hisa_status Engine::serve_release(uint64_t ticket) {
   auto it = reqs.find(ticket);
   if (it == reqs.end()) return ctx_fail(HISA_ERR_INVALID_ARG, "unknown ticket", nullptr);
   if (!it->second.done) return ctx_fail(HISA_ERR_STATE, "request not complete", nullptr);
+  for (auto& kv : it->second.result) dev_free(kv.second.first);
   reqs.erase(it);
   return HISA_OK;
 }

@@ -118,7 +118,7 @@ SIGNATURES = {
     "hisa_serve_step": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.POINTER(ServeStats)]),
     "hisa_serve_poll": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
     "hisa_serve_result": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p),
-                                           ctypes.c_uint64, _U64P, _U64P, ctypes.c_uint32, _U32P]),
+                                           ctypes.c_uint64, _U64P, _U64P, ctypes.c_uint32, _U32P, ctypes.c_int]),
     "hisa_serve_release": (ctypes.c_int32, [_P, ctypes.c_uint64]),
     "hisa_kernel_stats": (ctypes.c_int32, [_P, ctypes.POINTER(KernelStat), ctypes.c_uint32, _U32P]),
     "hisa_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
@@ -392,18 +392,25 @@ class Context:
         _check(self._lib.hisa_serve_poll(self._h, ticket, ctypes.byref(d)), self._h)
         return bool(d.value)
 
-    def serve_result(self, ticket: int, rel):
-        """(c0, c1, delta_counts) of a completed request for IDB relation ``rel``."""
+    def serve_result(self, ticket: int, rel, device: bool = False):
+        """(c0, c1, delta_counts) of a completed request for IDB relation ``rel``:
+        numpy uint32 arrays, or int32 CUDA tensors when ``device``."""
         rid = self.rel_ids[rel] if isinstance(rel, str) else rel
         n = ctypes.c_uint64()
         k = ctypes.c_uint32()
-        self._lib.hisa_serve_result(self._h, ticket, rid, None, 0, ctypes.byref(n), None, 0, ctypes.byref(k))
-        c0 = np.empty(max(n.value, 1), np.uint32)
-        c1 = np.empty(max(n.value, 1), np.uint32)
+        self._lib.hisa_serve_result(self._h, ticket, rid, None, 0, ctypes.byref(n), None, 0, ctypes.byref(k), 0)
         dl = (ctypes.c_uint64 * max(k.value, 1))()
-        ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
+        if device:
+            torch = _torch()
+            c0 = torch.empty(max(n.value, 1), dtype=torch.int32, device=f"cuda:{self.device}")
+            c1 = torch.empty(max(n.value, 1), dtype=torch.int32, device=f"cuda:{self.device}")
+            ptrs = (ctypes.c_void_p * 2)(c0.data_ptr(), c1.data_ptr())
+        else:
+            c0 = np.empty(max(n.value, 1), np.uint32)
+            c1 = np.empty(max(n.value, 1), np.uint32)
+            ptrs = (ctypes.c_void_p * 2)(c0.ctypes.data, c1.ctypes.data)
         _check(self._lib.hisa_serve_result(self._h, ticket, rid, ptrs, n.value, ctypes.byref(n), dl, k.value,
-                                           ctypes.byref(k)), self._h)
+                                           ctypes.byref(k), 1 if device else 0), self._h)
         return c0[:n.value], c1[:n.value], [int(dl[i]) for i in range(k.value)]
 
     def serve_release(self, ticket: int):
