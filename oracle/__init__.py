@@ -158,6 +158,31 @@ SG = (
 )
 
 
+# A context-sensitive points-to style program over Assign / Dereference (written
+# for this project; the paper elides its CSPA query, stating only that five rules
+# initialise and five mutually recursive rules propagate, that the first
+# recursive rule makes ValueFlow transitive and that the second makes two values
+# flowing into the same variable aliases).  ValueFlow(a, b): the value of b flows
+# into a; Assign(a, b): a = b; Dereference(a, b): a is the dereference of b.
+CSPA = (
+    {"Assign": "edb", "Dereference": "edb", "ValueFlow": "idb", "MemoryAlias": "idb", "ValueAlias": "idb"},
+    [
+        (("ValueFlow", ("y", "x")), [("Assign", ("y", "x"))], []),
+        (("ValueFlow", ("x", "x")), [("Assign", ("x", "y"))], []),
+        (("ValueFlow", ("x", "x")), [("Assign", ("y", "x"))], []),
+        (("MemoryAlias", ("x", "x")), [("Assign", ("y", "x"))], []),
+        (("MemoryAlias", ("x", "x")), [("Assign", ("x", "y"))], []),
+        (("ValueFlow", ("x", "y")), [("ValueFlow", ("x", "z")), ("ValueFlow", ("z", "y"))], []),
+        (("ValueAlias", ("x", "y")), [("ValueFlow", ("z", "x")), ("ValueFlow", ("z", "y"))], []),
+        (("ValueFlow", ("x", "y")), [("Assign", ("x", "z")), ("MemoryAlias", ("z", "y"))], []),
+        (("MemoryAlias", ("x", "w")), [("Dereference", ("y", "x")), ("ValueAlias", ("y", "z")),
+                                       ("Dereference", ("z", "w"))], []),
+        (("ValueAlias", ("x", "y")), [("ValueFlow", ("z", "x")), ("MemoryAlias", ("z", "w")),
+                                      ("ValueFlow", ("w", "y"))], []),
+    ],
+)
+
+
 def fingerprint(c0, c1) -> int:
     """Order-independent fingerprint of a binary relation: the sum modulo 2**64
     of the SplitMix64 finaliser of (c0 << 32 | c1) over its tuples."""

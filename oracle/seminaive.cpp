@@ -18,7 +18,8 @@
 //   * stop when every delta is empty (the fixpoint).
 // A body is evaluated as a nested-loop join: the delta atom is scanned first
 // (the outer relation of Algorithm 3), every later atom is range-queried on its
-// already-bound columns (the inner relation).  Filters x != y are checked on
+// already-bound columns (the inner relation), atoms sharing a bound variable
+// taken first.  Filters x != y are checked on
 // the complete binding.  Relations are sets: loading drops duplicate tuples.
 //
 // Delta-count convention: counts[k-1] = |delta_k| for k = 1..K, where K is the
@@ -111,15 +112,32 @@ void eval_atoms(Program& P, const Rule& R, const std::vector<int>& order,
   }
 }
 
+// Atom order: the delta atom (else the first atom) is scanned; each further
+// position takes the first remaining atom that shares a variable already bound,
+// so it is range-queried rather than scanned (the order changes the cost, not
+// the set of bindings).
 void eval_rule(Program& P, const Rule& R, int delta_atom) {
+  const int nb = (int)R.body.size();
   std::vector<int> order;
-  std::vector<bool> use_delta(R.body.size(), false);
+  std::vector<bool> use_delta(nb, false), used(nb, false);
+  bool bound[kMaxVars] = {};
+  auto take = [&](int j) {
+    order.push_back(j);
+    used[j] = true;
+    bound[R.body[j].var[0]] = bound[R.body[j].var[1]] = true;
+  };
   if (delta_atom >= 0) {
-    order.push_back(delta_atom);
     use_delta[delta_atom] = true;
+    take(delta_atom);
   }
-  for (int j = 0; j < (int)R.body.size(); ++j)
-    if (j != delta_atom) order.push_back(j);
+  while ((int)order.size() < nb) {
+    int pick = -1;
+    for (int j = 0; j < nb && pick < 0; ++j)
+      if (!used[j] && (bound[R.body[j].var[0]] || bound[R.body[j].var[1]])) pick = j;
+    for (int j = 0; j < nb && pick < 0; ++j)
+      if (!used[j]) pick = j;
+    take(pick);
+  }
   Binding b;
   for (auto& v : b.v) v = -1;
   eval_atoms(P, R, order, use_delta, 0, b);

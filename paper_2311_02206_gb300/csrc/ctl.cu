@@ -22,6 +22,23 @@ __global__ void k_ctl(CtlArgs a) {
       case kCtlSetCnt: st->cnt[c.a] = uint64_t(c.b); break;
       case kCtlAddCnt: st->cnt[c.a] += st->cnt[c.b]; break;
       case kCtlCopyCnt: st->cnt[c.a] = st->cnt[c.b]; break;
+      case kCtlSwapIfCnt:
+        if (st->cnt[c.c] > 0) {
+          const DBuf t = st->buf[c.a];
+          st->buf[c.a] = st->buf[c.b];
+          st->buf[c.b] = t;
+          st->cnt[c.a] = st->cnt[c.b];
+        }
+        break;
+      case kCtlCheckTable: {
+        // runs * 1024 <= cap * lf1024, else ask for a larger power of two
+        const uint64_t runs = st->cnt[c.b], cap = st->buf[c.a].cap;
+        if (runs * 1024ull > cap * uint64_t(c.c)) {
+          atomicMax((unsigned long long*)&st->need[c.a], (unsigned long long)((runs * 1024ull) / uint64_t(c.c) + 1));
+          atomicOr(&st->overflow, 1u);
+        }
+        break;
+      }
       default: st->error = kDevBadState; break;
     }
   }
@@ -87,7 +104,7 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
 
 const char* const kKernelNames[kKindCount] = {
     "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
-    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero"};
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols"};
 
 thread_local KernelTimer* g_timer = nullptr;
 thread_local uint64_t g_launches = 0;

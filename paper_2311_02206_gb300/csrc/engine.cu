@@ -332,8 +332,9 @@ hisa_status Engine::plan_variant(const hisa_rule& R, int delta_atom, std::vector
       const int ov = int(A.var[1 - c]);
       if (ov != jv && src_of[ov] >= 0)
         return ctx_fail(HISA_ERR_UNSUPPORTED, "join on two columns", nullptr);
+      // an IDB inner relation is read from full (column 0) or from its
+      // reverse-order mirror (column 1), indexed again every iteration
       Relation& ir = rels[A.rel];
-      if (ir.idb) return ctx_fail(HISA_ERR_UNSUPPORTED, "IDB relation as a range-probed inner relation", nullptr);
       ir.need_idx[c] = true;
       sp.has_inner = true;
       sp.inner_rel = int(A.rel);
@@ -432,6 +433,7 @@ hisa_status Engine::compile() {
       r.rev = new_slot(kb);
       r.table[0] = new_slot(16);
       r.table[1] = new_slot(16);
+      slot_pow2[r.table[0]] = slot_pow2[r.table[1]] = true;
       if (r.idb) {
         r.full = r.base;
         r.full_next = new_slot(kb);
@@ -441,9 +443,15 @@ hisa_status Engine::compile() {
         r.fresh_alt = new_slot(kb);
         r.hist = new_slot(8);
         r.history = new_slot(8);
+        r.rev_next = new_slot(kb);
+        r.rswap = new_slot(kb);
+        r.rswap_alt = new_slot(kb);
+        r.runs_cnt[0] = nslots++;
+        r.runs_cnt[1] = nslots++;
       }
     }
-    for (int id : {r.base, r.rev, r.full_next, r.delta, r.delta_next, r.fresh, r.fresh_alt})
+    for (int id : {r.base, r.rev, r.full_next, r.delta, r.delta_next, r.fresh, r.fresh_alt, r.rev_next, r.rswap,
+                   r.rswap_alt})
       if (id >= 0 && slot_elem[id] != kb) {
         dev_free(hs.buf[id].ptr);
         hs.buf[id] = {nullptr, 0};
@@ -535,8 +543,79 @@ void Engine::emit_join(std::vector<Op>& ops, const StepPlan& sp) {
   ops.push_back(o);
 }
 
+// Indexes of the IDB relations probed as inner relations, for the iteration
+// about to run (Algorithm 2 over the current full; Section 4.2 orders the
+// columns join column first).  Column 1 is served by the reverse-order mirror
+// of full: the delta of the last iteration, columns exchanged and sorted,
+// merged into it (delta and full are disjoint, so the merge drops nothing).
+// Every step is idempotent, so an iteration re-run after a regrow repeats it
+// safely.
+void Engine::emit_idb_index(std::vector<Op>& ops) {
+  auto ctl = [&](std::initializer_list<CtlCmd> cmds) {
+    Op c{};
+    c.kind = Op::CTL;
+    c.ctl.st = dst;
+    c.ctl.skip_mask = 1;
+    for (const CtlCmd& x : cmds) c.ctl.cmd[c.ctl.n++] = x;
+    ops.push_back(c);
+  };
+  const long long lf1024 = std::max(1LL, (long long)(cfg.load_factor * 1024.f));
+  for (int r : idb) {
+    const Relation& R = rels[r];
+    if (R.need_idx[1]) {
+      Op w{};
+      w.kind = Op::SWAP;
+      w.swap = SwapArgs{dst, R.delta, R.delta, R.rswap, R.rswap, b, 1, 0};
+      ops.push_back(w);
+      ctl({{kCtlZeroSmall, sc.hist, 8 * 256, 0}});
+      Op h{};
+      h.kind = Op::HIST;
+      h.hist = RadixHistArgs{dst, R.rswap, R.rswap, sc.hist, passes, 1};
+      ops.push_back(h);
+      emit_sort(ops, R.rswap, R.rswap_alt, R.rswap, sc.hist, 1, 0);
+      Op m{};
+      m.kind = Op::SETOP;
+      SetopArgs& a = m.setop;
+      a.st = dst;
+      a.a_buf = R.rev;
+      a.a_cnt = R.rev;
+      a.b_buf = (passes & 1) ? R.rswap_alt : R.rswap;
+      a.b_cnt = R.rswap;
+      a.split_buf = sc.split;
+      a.status_buf = sc.setop_status;
+      a.d_buf = -1;
+      a.d_cnt = -1;
+      a.f_buf = R.rev_next;
+      a.f_cnt = R.rev_next;
+      a.ctr = 2;
+      a.skip_mask = 1;
+      a.stage_bit = 0;
+      ops.push_back(m);
+      ctl({{kCtlSwapIfCnt, R.rev, R.rev_next, R.rswap}});
+    }
+    for (int col = 0; col < 2; ++col) {
+      if (!R.need_idx[col]) continue;
+      const int keys = col == 0 ? R.full : R.rev;
+      ctl({{kCtlSetCnt, R.runs_cnt[col], 0, 0}});
+      Op u{};
+      u.kind = Op::RUNS;
+      u.runs = RunsArgs{dst, keys, keys, b, R.runs_cnt[col], 1};
+      ops.push_back(u);
+      ctl({{kCtlCheckTable, R.table[col], R.runs_cnt[col], lf1024}});
+      Op z{};
+      z.kind = Op::ZERO;
+      z.zero = ZeroArgs{dst, R.table[col], 16, 1};
+      ops.push_back(z);
+      Op i{};
+      i.kind = Op::INDEX;
+      i.index = IndexArgs{dst, keys, keys, R.table[col], b, -1, 1};
+      ops.push_back(i);
+    }
+  }
+}
+
 // Join stage of one iteration: clear new, run every variant, sort each new.
-void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepPlan>>& plans) {
+void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepPlan>>& plans, bool idb_inner) {
   Op c{};
   c.kind = Op::CTL;
   c.ctl.st = dst;
@@ -546,6 +625,7 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
     c.ctl.cmd[c.ctl.n++] = {kCtlZeroSmall, rels[r].hist, 8 * 256};
   }
   ops.push_back(c);
+  if (idb_inner) emit_idb_index(ops);
   for (auto& v : plans) {
     if (v.size() > 1) {
       Op t{};
@@ -632,6 +712,10 @@ hisa_status Engine::exec_t(const std::vector<Op>& ops) {
       case Op::HIST: launch_radix_hist<K>(o.hist, grid, stream); break;
       case Op::SETOP: launch_setop<K>(o.setop, grid, stream); break;
       case Op::COMMIT: launch_commit(o.commit, stream); break;
+      case Op::RUNS: launch_count_runs<K>(o.runs, grid, stream); break;
+      case Op::INDEX: launch_index<K>(o.index, grid, stream); break;
+      case Op::ZERO: launch_zero(o.zero, grid, stream); break;
+      case Op::SWAP: launch_swap<K>(o.swap, grid, stream); break;
     }
   }
   return check_launch("kernel launch");
@@ -690,7 +774,7 @@ hisa_status Engine::prepare_rel_t(Relation& r, int order, int slot) {
   if (r.need_idx[order]) {
     hs.cnt[sc.runs] = 0;
     if ((s = upload())) return s;
-    RunsArgs ra{dst, slot, slot, b, sc.runs};
+    RunsArgs ra{dst, slot, slot, b, sc.runs, 0};
     launch_count_runs<K>(ra, grid, stream);
     if ((s = download())) return s;
     const uint64_t runs = hs.cnt[sc.runs];
@@ -753,15 +837,21 @@ hisa_status Engine::regrow() {
     const uint64_t need = hs.need[id];
     if (need == 0 || need <= hs.buf[id].cap) continue;
     uint64_t cap = need + need / 8 + 1024;
+    if (slot_pow2[id]) {   // hash table: the probe mask needs a power of two
+      cap = 16;
+      while (cap < need) cap <<= 1;
+    }
     int partner = -1, live = -1;
     for (int r : idb) {
       const Relation& R = rels[r];
-      if (id == R.full_next || id == R.full) {
+      if (id == R.full_next || id == R.full || id == R.rev_next || id == R.rev) {
         // eager buffer management: full + k * delta, and at least a quarter more
-        const uint64_t delta = need > hs.cnt[R.full] ? need - hs.cnt[R.full] : need;
+        const bool rv = id == R.rev_next || id == R.rev;
+        const int cur = rv ? R.rev : R.full;
+        const uint64_t delta = need > hs.cnt[cur] ? need - hs.cnt[cur] : need;
         cap = need + std::max(uint64_t(cfg.ebm_k * double(delta)), need / 4) + 1024;
-        partner = id == R.full_next ? R.full : R.full_next;
-        live = R.full;
+        partner = rv ? (id == R.rev_next ? R.rev : R.rev_next) : (id == R.full_next ? R.full : R.full_next);
+        live = cur;
       } else if (id == R.delta_next || id == R.delta) {
         cap = need + need / 4 + 1024;
         partner = id == R.delta_next ? R.delta : R.delta_next;
@@ -792,15 +882,17 @@ hisa_status Engine::regrow() {
     for (int r : idb) {
       const Relation& R = rels[r];
       if ((s = ensure(R.fresh, new_cap)) || (s = ensure(R.fresh_alt, new_cap))) return s;
+      // the column-swapped delta sorted into the reverse-order mirror
+      if (R.need_idx[1] && ((s = ensure(R.rswap, delta_cap)) || (s = ensure(R.rswap_alt, delta_cap)))) return s;
     }
-    if ((s = ensure(sc.radix_status, (new_cap / kt + 2) * kRadixDigits)) ||
+    if ((s = ensure(sc.radix_status, (std::max(new_cap, delta_cap) / kt + 2) * kRadixDigits)) ||
         (s = ensure(sc.starts, new_cap / kJoinChunk + 2)))
       return s;
   }
   // next iterations: delta is the outer relation of the joins; full + new is merged
   if ((s = ensure(sc.offs, delta_cap + 1)) || (s = ensure(sc.join_status, delta_cap / kJoinTile + 2))) return s;
-  if ((s = ensure(sc.split, (full_cap + new_cap) / ks + 2)) ||
-      (s = ensure(sc.setop_status, (full_cap + new_cap) / ks + 2)))
+  if ((s = ensure(sc.split, (full_cap + std::max(new_cap, delta_cap)) / ks + 2)) ||
+      (s = ensure(sc.setop_status, (full_cap + std::max(new_cap, delta_cap)) / ks + 2)))
     return s;
   std::memset(hs.need, 0, sizeof hs.need);
   hs.overflow = 0;
@@ -823,9 +915,9 @@ hisa_status Engine::run(hisa_run_stats* stats) {
     ops1.clear();
     opsN.clear();
     tail.clear();
-    emit_head(ops1, plan1);
+    emit_head(ops1, plan1, false);
     emit_tail(ops1, false);
-    emit_head(opsN, planN);
+    emit_head(opsN, planN, true);
     emit_tail(opsN, false);
     emit_tail(tail, false);
   } else {
@@ -854,6 +946,18 @@ hisa_status Engine::init_run_state() {
     if ((s = ensure(R.hist, 8 * 256)) || (s = ensure(R.history, std::min<uint64_t>(cfg.max_iters + 1, 1u << 20))))
       return s;
     for (int id : {R.full, R.full_next, R.delta, R.delta_next, R.fresh}) hs.cnt[id] = 0;
+    if (R.need_idx[1]) {
+      for (int id : {R.rev, R.rev_next, R.rswap, R.rswap_alt})
+        if ((s = ensure(id, 4 * nedb))) return s;
+      hs.cnt[R.rev] = hs.cnt[R.rev_next] = hs.cnt[R.rswap] = 0;
+    }
+    for (int col = 0; col < 2; ++col) {
+      if (!R.need_idx[col]) continue;
+      uint64_t cap = 1024;
+      while (double(cap) * cfg.load_factor < double(nedb)) cap <<= 1;
+      if ((s = ensure(R.table[col], cap))) return s;
+      hs.cnt[R.runs_cnt[col]] = 0;
+    }
   }
   hs.cnt[sc.tmp_cnt] = 0;
   if ((s = ensure(sc.radix_status, (4 * nedb / kt + 2) * 256)) || (s = ensure(sc.offs, 4 * nedb + 1)) ||
@@ -925,6 +1029,18 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
           if (nn > 0) kstat[kKSetop].bytes += (m + nn) * kb + (m + 2.0 * nd) * kb;
           kstat[kKJoinWrite].bytes += 2.0 * nn * kb + dp * (kb + 8.0);
           kstat[kKJoinCount].bytes += dp * (kb + 8.0 + 16.0);
+          // inner-relation upkeep at the head of this iteration
+          if (!first && R.need_idx[1]) {
+            kstat[kKSwap].bytes += 2.0 * dp * kb;
+            kstat[kKRadixPass].bytes += passes * 2.0 * dp * kb;
+            kstat[kKSetop].bytes += 2.0 * m * kb;
+          }
+          for (int col = 0; col < 2 && !first; ++col) {
+            if (!R.need_idx[col]) continue;
+            kstat[kKRuns].bytes += m * kb;
+            kstat[kKIndex].bytes += m * kb + double(hs.cnt[R.runs_cnt[col]]) * 16.0;
+            kstat[kKZero].bytes += double(hs.buf[R.table[col]].cap) * 16.0;
+          }
         }
       }
     }

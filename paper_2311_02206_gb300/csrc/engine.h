@@ -30,6 +30,11 @@ struct Relation {
   int full = -1, full_next = -1, delta = -1, delta_next = -1;
   int fresh = -1, fresh_alt = -1;   // "new" and its radix ping-pong partner
   int hist = -1;                    // digit histograms of new
+  // an IDB relation probed as an inner relation: its full in reverse order
+  // (kept as full's mirror by merging each sorted, column-swapped delta) and
+  // the sort buffers of that delta; run counts feeding the index rebuilds
+  int rev_next = -1, rswap = -1, rswap_alt = -1;
+  int runs_cnt[2] = {-1, -1};
   int history = -1;                 // |delta_k| per iteration
   std::vector<uint64_t> delta_counts;
 };
@@ -46,13 +51,17 @@ struct StepPlan {
 };
 
 struct Op {
-  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT } kind;
+  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP } kind;
   CtlArgs ctl;
   JoinArgs join;
   RadixPassArgs pass;
   RadixHistArgs hist;
   SetopArgs setop;
   CommitArgs commit;
+  RunsArgs runs;
+  IndexArgs index;
+  ZeroArgs zero;
+  SwapArgs swap;
 };
 
 struct Scratch {
@@ -116,7 +125,8 @@ class Engine {
   hisa_status compile();
   hisa_status plan_variant(const hisa_rule& R, int delta_atom, std::vector<StepPlan>& out);
   void emit_join(std::vector<Op>& ops, const StepPlan& sp);
-  void emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepPlan>>& plans);
+  void emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepPlan>>& plans, bool idb_inner);
+  void emit_idb_index(std::vector<Op>& ops);
   void emit_sort(std::vector<Op>& ops, int in, int alt, int cnt, int hist, int skip_mask, int stage_bit);
   void emit_tail(std::vector<Op>& ops, bool force);
   template <typename K> hisa_status exec_t(const std::vector<Op>& ops);
@@ -134,6 +144,7 @@ class Engine {
                            std::vector<uint32_t>& c1);
   hisa_status rebuild_serving_edb();
   hisa_status retire(const std::vector<uint64_t>& tickets);
+  hisa_status compact(int slot, int next, const std::vector<uint64_t>& bnd, const std::vector<bool>& drop);
   hisa_status launch_graph();
   hisa_status build_graph();
 
@@ -148,6 +159,7 @@ class Engine {
   int nslots = 0;
   int slot_elem[kMaxBufs] = {};
   bool slot_zero[kMaxBufs] = {};   // zero on allocation (look-back status words)
+  bool slot_pow2[kMaxBufs] = {};   // capacity must be a power of two (hash tables)
   std::unordered_map<void*, size_t> allocs;
   uint64_t bytes_in_use = 0, peak_bytes = 0;
   uint32_t regrows = 0;

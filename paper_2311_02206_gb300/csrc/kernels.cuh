@@ -19,11 +19,14 @@ enum : int {
   kCtlAddCnt,        // cnt[a] += cnt[b]
   kCtlCopyCnt,       // cnt[a] = cnt[b]
   kCtlZeroSmall,     // zero the first b u64 words of buffer a
+  kCtlSwapIfCnt,     // if cnt[c] > 0: exchange buffers a and b, cnt[a] = cnt[b]
+  kCtlCheckTable,    // hash table a must hold cnt[b] runs at load factor c / 1024
 };
 
 struct CtlCmd {
   int op, a;
   long long b;
+  long long c;
 };
 constexpr int kMaxCtl = 24;
 struct CtlArgs {
@@ -81,13 +84,23 @@ struct ZeroArgs {
 struct RunsArgs {
   DevState* st;
   int keys_buf, keys_cnt, b, out_cnt;
+  int skip_mask;
+};
+
+// Column exchange of packed codes: (inst, c0, c1) -> (inst, c1, c0).
+struct SwapArgs {
+  DevState* st;
+  int in_buf, in_cnt;
+  int out_buf, out_cnt;   // written from 0; cnt[out_cnt] = cnt[in_cnt]
+  int b;
+  int skip_mask, stage_bit;
 };
 
 // ---- launch accounting -----------------------------------------------------------------
 
 enum KernelKind : int {
   kKEncode, kKDecode, kKRuns, kKHist, kKRadixPass, kKSetopPartition, kKSetop, kKIndex,
-  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKindCount
+  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKindCount
 };
 extern const char* const kKernelNames[kKindCount];
 
@@ -136,6 +149,7 @@ template <typename K> void launch_radix_pass(const RadixPassArgs& a, const Grid&
 template <typename K> void launch_setop(const SetopArgs& a, const Grid& g, cudaStream_t s);   // partition + merge
 template <typename K> void launch_index(const IndexArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_count_runs(const RunsArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_swap(const SwapArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_hist(const InstArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_bounds(const InstArgs& a, const Grid& g, cudaStream_t s);
 void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStream_t s);

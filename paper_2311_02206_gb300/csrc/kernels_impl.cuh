@@ -32,6 +32,7 @@ __global__ void k_decode(DecodeArgs a) {
 template <typename K>
 __global__ void k_count_runs(RunsArgs a) {
   DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
   const K* keys = static_cast<const K*>(st->buf[a.keys_buf].ptr);
   const uint64_t n = st->cnt[a.keys_cnt];
   uint32_t runs = 0;
@@ -39,6 +40,31 @@ __global__ void k_count_runs(RunsArgs a) {
     runs += (i == 0 || (uint64_t(keys[i - 1]) >> a.b) != (uint64_t(keys[i]) >> a.b));
   for (int o = 16; o > 0; o >>= 1) runs += __shfl_xor_sync(0xffffffffu, runs, o);
   if ((threadIdx.x & 31) == 0 && runs) atomicAdd((unsigned long long*)&st->cnt[a.out_cnt], (unsigned long long)runs);
+}
+
+// (inst, c0, c1) -> (inst, c1, c0): the reverse-order copy of a delta, sorted
+// afterwards and merged into the reverse-order full of an IDB relation.
+template <typename K>
+__global__ void k_swap_cols(SwapArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t n = st->cnt[a.in_cnt];
+  if (n > st->buf[a.out_buf].cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)n);
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    return;
+  }
+  const K* in = static_cast<const K*>(st->buf[a.in_buf].ptr);
+  K* out = static_cast<K*>(st->buf[a.out_buf].ptr);
+  const uint64_t m = a.b >= 32 ? 0xFFFFFFFFull : ((1ull << a.b) - 1);
+  const uint64_t im = 2 * a.b >= 64 ? 0ull : ~((1ull << (2 * a.b)) - 1);
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t c = in[i];
+    out[i] = K((c & im) | ((c & m) << a.b) | ((c >> a.b) & m));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->cnt[a.out_cnt] = n;
 }
 
 // Counts of each instance id in a sorted code array: every thread walks a
@@ -103,6 +129,10 @@ void launch_decode(const DecodeArgs& a, const Grid& g, cudaStream_t s) {
 template <typename K>
 void launch_count_runs(const RunsArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKRuns, s, (k_count_runs<K><<<g.small, 256, 0, s>>>(a)));
+}
+template <typename K>
+void launch_swap(const SwapArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKSwap, s, (k_swap_cols<K><<<g.small, 256, 0, s>>>(a)));
 }
 template <typename K>
 void launch_radix_hist(const RadixHistArgs& a, const Grid& g, cudaStream_t s) {
@@ -174,6 +204,7 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_encode<K>(const EncodeArgs&, const Grid&, cudaStream_t);          \
   template void launch_decode<K>(const DecodeArgs&, const Grid&, cudaStream_t);          \
   template void launch_count_runs<K>(const RunsArgs&, const Grid&, cudaStream_t);        \
+  template void launch_swap<K>(const SwapArgs&, const Grid&, cudaStream_t);              \
   template void launch_radix_hist<K>(const RadixHistArgs&, const Grid&, cudaStream_t);   \
   template void launch_radix_pass<K>(const RadixPassArgs&, const Grid&, cudaStream_t);   \
   template void launch_setop<K>(const SetopArgs&, const Grid&, cudaStream_t);            \

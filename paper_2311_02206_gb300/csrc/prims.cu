@@ -185,7 +185,7 @@ hisa_status join_t(const void* outer, uint64_t no, const void* inner, uint64_t n
   const int runs = P.count();
   hisa_status s = P.upload();
   if (s) return s;
-  RunsArgs ra{P.d, I, I, b, runs};
+  RunsArgs ra{P.d, I, I, b, runs, 0};
   launch_count_runs<K>(ra, P.g, P.s);
   if ((s = P.download())) return s;
   uint64_t tcap = 16;

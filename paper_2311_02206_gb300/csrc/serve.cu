@@ -187,9 +187,9 @@ hisa_status Engine::serve_open(uint32_t max_instances, uint32_t max_value, uint6
   ops_admit.clear();
   std::vector<std::vector<StepPlan>> both = plan1;
   both.insert(both.end(), planN.begin(), planN.end());
-  emit_head(ops_admit, both);
+  emit_head(ops_admit, both, true);
   emit_tail(ops_admit, false);
-  emit_head(opsN, planN);
+  emit_head(opsN, planN, true);
   emit_tail(opsN, false);
   emit_tail(tail, false);
   if ((s = init_run_state())) return s;
@@ -255,6 +255,35 @@ hisa_status Engine::rebuild_serving_edb() {
   return prepare_edb();
 }
 
+// Keeps the instance ranges of `slot` (bounds `bnd`) not marked in `drop`:
+// the kept runs are copied into `next`, which then becomes `slot`.
+hisa_status Engine::compact(int slot, int next, const std::vector<uint64_t>& bnd, const std::vector<bool>& drop) {
+  const uint64_t kb = wide ? 8 : 4;
+  const uint64_t n = hs.cnt[slot];
+  hisa_status s;
+  if ((s = ensure(next, std::max<uint64_t>(n, 1)))) return s;
+  uint64_t w = 0;
+  uint32_t i = 0;
+  while (i < serve_slots) {
+    if (drop[i]) {
+      ++i;
+      continue;
+    }
+    uint32_t j = i;
+    while (j < serve_slots && !drop[j]) ++j;
+    const uint64_t lo = bnd[i], hi = bnd[j];
+    if (hi > lo)
+      CU(cudaMemcpyAsync(static_cast<char*>(hs.buf[next].ptr) + w * kb, static_cast<char*>(hs.buf[slot].ptr) + lo * kb,
+                         (hi - lo) * kb, cudaMemcpyDeviceToDevice, stream));
+    w += hi - lo;
+    i = j;
+  }
+  std::swap(hs.buf[slot], hs.buf[next]);
+  hs.cnt[slot] = w;
+  hs.cnt[next] = 0;
+  return HISA_OK;
+}
+
 // Copies out and removes the tuples of finished requests.
 hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
   if (tickets.empty()) return HISA_OK;
@@ -277,29 +306,12 @@ hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
       q.result[r] = {p, cnt};
       drop[q.slot] = true;
     }
-    // keep every other instance's range: copy the kept runs into full_next, swap
-    const uint64_t n = hs.cnt[R.full];
-    if ((s = ensure(R.full_next, std::max<uint64_t>(n, 1)))) return s;
-    uint64_t w = 0;
-    uint32_t i = 0;
-    while (i < serve_slots) {
-      if (drop[i]) {
-        ++i;
-        continue;
-      }
-      uint32_t j = i;
-      while (j < serve_slots && !drop[j]) ++j;
-      const uint64_t lo = bnd[i], hi = bnd[j];
-      if (hi > lo)
-        CU(cudaMemcpyAsync(static_cast<char*>(hs.buf[R.full_next].ptr) + w * kb,
-                           static_cast<char*>(hs.buf[R.full].ptr) + lo * kb, (hi - lo) * kb,
-                           cudaMemcpyDeviceToDevice, stream));
-      w += hi - lo;
-      i = j;
+    if ((s = compact(R.full, R.full_next, bnd, drop))) return s;
+    // the reverse-order mirror of full loses the same instances
+    if (R.need_idx[1]) {
+      if ((s = inst_bounds(R.rev, bnd))) return s;
+      if ((s = compact(R.rev, R.rev_next, bnd, drop))) return s;
     }
-    std::swap(hs.buf[R.full], hs.buf[R.full_next]);
-    hs.cnt[R.full] = w;
-    hs.cnt[R.full_next] = 0;
   }
   for (uint64_t t : tickets) {
     Request& q = reqs[t];

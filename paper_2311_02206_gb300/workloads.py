@@ -204,6 +204,76 @@ def batch_instances(count: int, seed: int, n_lo_log2: int = 6, n_hi_log2: int = 
     return out
 
 
+# ---- Zipf draws with IEEE basic operations only ------------------------------------------
+
+_LN2 = 0.6931471805599453
+
+
+def _ln(x: np.ndarray) -> np.ndarray:
+    """Natural log of positive doubles: frexp range reduction and the atanh
+    series 2 (t + t^3/3 + ...) with t = (m - 1) / (m + 1), m in [sqrt(1/2), sqrt(2))."""
+    m, e = np.frexp(np.asarray(x, np.float64))
+    small = m < 0.7071067811865476
+    m = np.where(small, m * 2.0, m)
+    e = np.where(small, e - 1, e).astype(np.float64)
+    t = (m - 1.0) / (m + 1.0)
+    t2 = t * t
+    acc = np.zeros_like(t)
+    for k in range(41, 0, -2):
+        acc = acc * t2 + 1.0 / k
+    return 2.0 * t * acc + e * _LN2
+
+
+def _exp(x: np.ndarray) -> np.ndarray:
+    """e**x for moderate x: x = k ln2 + r, |r| <= ln2/2, Taylor series of e**r."""
+    x = np.asarray(x, np.float64)
+    k = np.floor(x / _LN2 + 0.5)
+    r = x - k * _LN2
+    acc = np.ones_like(r)
+    term = np.ones_like(r)
+    for i in range(1, 24):
+        term = term * r / i
+        acc = acc + term
+    return np.ldexp(acc, k.astype(np.int64))
+
+
+def zipf_ranks(count: int, n: int, s: float, seed: int, stream: int) -> np.ndarray:
+    """Ranks 0..n-1 with P(rank k) proportional to (k+1)**-s, by inverse CDF
+    of uniform 53-bit draws over the exact (IEEE basic-operation) CDF table."""
+    w = _exp(-s * _ln(np.arange(1, n + 1, dtype=np.float64)))
+    cdf = np.cumsum(w)
+    u = (rand_u64(seed, stream, 0, count) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    return np.minimum(np.searchsorted(cdf, u * cdf[-1], side="right"), n - 1).astype(np.int64)
+
+
+def cspa_inputs(n_assign: int = 400_000, n_deref: int = 200_000, ids: int = 300_000, window: int = 1024,
+                p_window: float = 0.8, s: float = 1.1, seed: int = 2):
+    """Assign and Dereference pairs over ids [0, ids): the first id is Zipf(s)
+    (rank - 1), the second with probability p_window uniform in the same
+    aligned window of `window` ids, else Zipf(s); self-pairs and repeats are
+    dropped until the requested number of distinct pairs."""
+    out = []
+    for rel, (count, stream) in enumerate([(n_assign, 10), (n_deref, 20)]):
+        pairs_a, pairs_b = np.zeros(0, np.int64), np.zeros(0, np.int64)
+        drawn, batch = 0, 2 * count
+        while True:
+            a = zipf_ranks(batch, ids, s, seed + drawn, stream)
+            z = zipf_ranks(batch, ids, s, seed + drawn, stream + 1)
+            r = rand_u64(seed + drawn, stream + 2, 0, batch)
+            inwin = (r >> np.uint64(11)).astype(np.float64) / float(1 << 53) < p_window
+            off = (((r & _MASK32) * np.uint64(window)) >> np.uint64(32)).astype(np.int64)
+            b = np.where(inwin, np.minimum((a // window) * window + off, ids - 1), z)
+            pairs_a = np.concatenate([pairs_a, a])
+            pairs_b = np.concatenate([pairs_b, b])
+            x, y, got = _first_distinct(pairs_a.astype(np.uint64), pairs_b.astype(np.uint64), count,
+                                        pairs_a != pairs_b)
+            drawn += 1
+            if got >= count:
+                out.append((x.astype(np.uint32), y.astype(np.uint32)))
+                break
+    return {"Assign": out[0], "Dereference": out[1]}
+
+
 def config_reach_er(seed: int = 0):
     """REACH on ER n=1,000, m=3,000 (the small single-instance case)."""
     return er_graph(1000, 3000, seed)

@@ -13,6 +13,7 @@ import pytest
 import oracle
 from oracle import naive, primitives
 from paper_2311_02206_gb300 import workloads
+from programs import PROGRAMS, TC_NONLINEAR
 
 
 # ---- REACH against BFS ---------------------------------------------------------------
@@ -122,25 +123,6 @@ def _tiny_graph(seed, n=9, m=14):
     return s, d
 
 
-PROGRAMS = {
-    "reach": oracle.REACH,
-    "sg": oracle.SG,
-    # non-linear closure: both body atoms are IDB
-    "tc_nonlinear": ({"E": "edb", "T": "idb"}, [
-        (("T", ("x", "y")), [("E", ("x", "y"))], []),
-        (("T", ("x", "z")), [("T", ("x", "y")), ("T", ("y", "z"))], []),
-    ]),
-    # mutual recursion over two IDB relations, a column-1 lookup and a filter
-    "mutual": ({"A": "edb", "B": "edb", "P": "idb", "Q": "idb"}, [
-        (("P", ("x", "y")), [("A", ("x", "y"))], []),
-        (("Q", ("y", "x")), [("B", ("x", "y"))], []),
-        (("P", ("x", "z")), [("Q", ("x", "y")), ("P", ("y", "z"))], []),
-        (("Q", ("x", "z")), [("P", ("y", "x")), ("B", ("y", "z"))], [("x", "z")]),
-        (("Q", ("x", "x")), [("P", ("x", "w")), ("Q", ("w", "v"))], []),
-    ]),
-}
-
-
 @pytest.mark.parametrize("name", sorted(PROGRAMS))
 @pytest.mark.parametrize("seed", range(12))
 def test_seminaive_equals_naive(name, seed):
@@ -156,6 +138,46 @@ def test_seminaive_equals_naive(name, seed):
     k = max(len(c) for c in counts.values())
     for n in counts:
         assert r.delta_counts[n] == counts[n] + [0] * (k - len(counts[n])), n
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_cspa_seminaive_equals_naive(seed):
+    """The ten-rule points-to program (three IDB relations in mutual
+    recursion, two three-atom rules) on tiny skewed inputs."""
+    edb = workloads.cspa_inputs(25 + seed, 12, 14, window=4, seed=seed)
+    r = oracle.seminaive(*oracle.CSPA, edb)
+    want, counts = naive.naive(*oracle.CSPA, edb)
+    for n in want:
+        assert list(zip(*(x.tolist() for x in r.relations[n]))) == want[n], n
+    k = max(len(c) for c in counts.values())
+    for n in counts:
+        assert r.delta_counts[n] == counts[n] + [0] * (k - len(counts[n])), n
+
+
+def doubling_counts(n_pairs_at, longest):
+    """|delta_k| of the non-linear closure when the pairs at shortest distance
+    l number n_pairs_at(l): iteration 1 finds l = 1, iteration k >= 2 the
+    lengths in (2**(k-2), 2**(k-1)] (paths of both halves are already known)."""
+    out = [n_pairs_at(1)]
+    k = 2
+    while (1 << (k - 2)) < longest:
+        out.append(sum(n_pairs_at(l) for l in range((1 << (k - 2)) + 1, min(1 << (k - 1), longest) + 1)))
+        k += 1
+    return out
+
+
+@pytest.mark.parametrize("n", [2, 3, 17, 64, 100])
+def test_tc_nonlinear_path_closed_form(n):
+    r = oracle.seminaive(*TC_NONLINEAR, {"E": workloads.path_graph(n)})
+    assert r.size("T") == n * (n - 1) // 2
+    assert r.delta_counts["T"] == doubling_counts(lambda l: n - l, n - 1)
+
+
+@pytest.mark.parametrize("n", [1, 5, 32, 33])
+def test_tc_nonlinear_cycle_closed_form(n):
+    r = oracle.seminaive(*TC_NONLINEAR, {"E": workloads.cycle_graph(n)})
+    assert r.size("T") == n * n
+    assert r.delta_counts["T"] == doubling_counts(lambda l: n, n)
 
 
 # ---- the paper's worked examples -----------------------------------------------------
