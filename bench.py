@@ -1,7 +1,7 @@
 """Benchmark of the semi-naive fixpoint hot path on one GB300 (or N replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hisa|reference]
-                    [--workload rmat16|er1000]
+                    [--workload rmat16|rmat13|er1000|sg20k|sg20k-literal|cspa|batch5]
 
 Workload (default): REACH, Reach(f,t) <- Edge(f,t); Reach(f,t) <- Edge(f,m),
 Reach(m,t), on an R-MAT graph of scale 16 (65,536 nodes) with 2**19 distinct
@@ -19,6 +19,13 @@ sample of the same workload, and the end-to-end number through the C-ABI with
 host buffers.  With N > 1 (torchrun) every rank runs an independent replica
 (the path does not shard across GPUs in this build): weak scaling, value =
 tuples of all ranks / slowest rank's time.
+
+Other workloads (same line format, metric = all IDB tuples at the fixpoint per
+second): sg20k (SG with x != y on both rules on the 20,000-node DAG; the
+literal variant filters rule 1 only), cspa (the ten-rule points-to program on
+the skewed Assign/Dereference inputs divided by 250, windows of 128 ids; the
+undivided inputs derive more than a GPU holds), batch5 (many independent REACH
+instances, one-by-one vs served).
 """
 from __future__ import annotations
 
@@ -47,7 +54,8 @@ def _args():
     ap.add_argument("--impl", choices=["hisa", "reference"], default="hisa")
     ap.add_argument("--instances", type=int, default=4096, help="batch5: number of instances")
     ap.add_argument("--budget-gb", type=float, default=100.0, help="batch5: serving memory budget")
-    ap.add_argument("--workload", choices=["rmat16", "rmat13", "er1000", "batch5"], default="rmat16",
+    ap.add_argument("--workload", choices=["rmat16", "rmat13", "er1000", "sg20k", "sg20k-literal", "cspa", "batch5"],
+                    default="rmat16",
                     help="rmat16: the benchmark workload; rmat13: a smaller R-MAT graph for profiler captures")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
@@ -71,6 +79,46 @@ def _workload(name):
         return s, d, "REACH (2 rules) on R-MAT scale 13: 8,192 nodes, 2^16 distinct edges, seed 3", 1 << 13
     s, d = workloads.config_reach_er()
     return s, d, "REACH (2 rules) on Erdos-Renyi n=1,000, m=3,000, seed 0", 1000
+
+
+def _program_workload(name):
+    """(program, EDB columns, description, CPU-sample function) of the
+    non-REACH workloads.  The CPU sample runs the oracle as it stands."""
+    import numpy as np
+    import oracle
+    from paper_2311_02206_gb300 import workloads
+    if name.startswith("sg20k"):
+        prog = oracle.SG_LITERAL if name.endswith("literal") else oracle.SG
+        s, d = workloads.config_sg_dag()
+        desc = ("SG (%s) on a random DAG: 20,000 nodes, 40,000 distinct edges u<v, v-u in [1,256], seed 1"
+                % ("x != y on rule 1 only" if name.endswith("literal") else "x != y on both rules"))
+
+        def sample(nodes=3000):
+            # edges point to larger ids, so every derivation of SG(x, y) with
+            # x, y < N uses nodes < N only: SG of the induced subgraph on
+            # [0, N) is exactly SG restricted to [0, N)^2
+            keep = (s < nodes) & (d < nodes)
+            t0 = time.perf_counter()
+            r = oracle.seminaive(*prog, {"Edge": (s[keep], d[keep])})
+            el = time.perf_counter() - t0
+            n = r.size("SG")
+            return n, el, f"SG restricted to nodes [0, {nodes}) of 20,000 (the induced subgraph; exact)"
+        return prog, {"Edge": (s, d)}, desc, sample
+    if name == "cspa":
+        edb = workloads.config_cspa()
+        desc = ("ten-rule points-to program (ValueFlow/MemoryAlias/ValueAlias) on Assign %d / Dereference %d "
+                "pairs over 1,200 ids (the 400k/200k/300k inputs divided by 250), Zipf 1.1, 80%% of pairs in "
+                "aligned windows of 128 ids, seed 2" % (len(edb["Assign"][0]), len(edb["Dereference"][0])))
+
+        def sample():
+            small = workloads.config_cspa(1000, 32)
+            t0 = time.perf_counter()
+            r = oracle.seminaive(*oracle.CSPA, small)
+            el = time.perf_counter() - t0
+            n = sum(r.size(k) for k in ("ValueFlow", "MemoryAlias", "ValueAlias"))
+            return n, el, "the same program and generator divided by 1,000 (windows of 32 ids)"
+        return oracle.CSPA, edb, desc, sample
+    raise ValueError(name)
 
 
 # ---- distributed plumbing -------------------------------------------------------------------
@@ -239,18 +287,26 @@ def run_hisa(a):
     torch.cuda.set_device(local)
     _init_pg(world)
     build.build()
-    s, d, desc, nodes = _workload(a.workload)
-    dev_s = torch.from_numpy(s.view(np.int32)).cuda()
-    dev_d = torch.from_numpy(d.view(np.int32)).cuda()
+    reach = a.workload in ("rmat16", "rmat13", "er1000")
+    if reach:
+        s, d, desc, nodes = _workload(a.workload)
+        prog, edb, sample = oracle.REACH, {"Edge": (s, d)}, None
+    else:
+        prog, edb, desc, sample = _program_workload(a.workload)
+    idb_names = [k for k, v in prog[0].items() if v == "idb"]
+    dev_edb = {k: (torch.from_numpy(c0.view(np.int32)).cuda(), torch.from_numpy(c1.view(np.int32)).cuda())
+               for k, (c0, c1) in edb.items()}
+    edb_bytes = sum(c0.nbytes + c1.nbytes for c0, c1 in edb.values())
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 18, dtype=torch.int32, device="cuda")   # 512 MiB > 129 MB L2
 
     ctx = hisa.Context(device=local, flags=hisa.FLAG_PHASE_TIMES)
-    ctx.program(*oracle.REACH)
+    ctx.program(*prog)
 
     def step():
         ctx.reset_edb()
-        ctx.load_tuples("Edge", dev_s, dev_d)
+        for k, (c0, c1) in dev_edb.items():
+            ctx.load_tuples(k, c0, c1)
         return ctx.run()
 
     for _ in range(a.warmup):
@@ -283,7 +339,8 @@ def run_hisa(a):
     torch.cuda.synchronize()
     _barrier(world)
     wall = time.perf_counter() - wall0
-    n_reach = ctx.relation_size("Reach")
+    n_reach = sum(ctx.relation_size(k) for k in idb_names)
+    sizes = {k: ctx.relation_size(k) for k in idb_names}
     iters = st.iterations
     total_s = sum(ms) / 1e3
     slowest = _max_over_ranks(total_s, world)
@@ -313,42 +370,53 @@ def run_hisa(a):
     # end to end through the C-ABI with host buffers (pinned), copies inside the timing
     e2e = None
     if not a.no_e2e:
-        hs_ = torch.from_numpy(s.view(np.int32)).pin_memory().numpy().view(np.uint32)
-        hd_ = torch.from_numpy(d.view(np.int32)).pin_memory().numpy().view(np.uint32)
-        out0 = torch.empty(n_reach, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
-        out1 = torch.empty(n_reach, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        def pinned(x):
+            return torch.from_numpy(x.view(np.int32)).pin_memory().numpy().view(np.uint32)
+
+        host_edb = {k: (pinned(c0), pinned(c1)) for k, (c0, c1) in edb.items()}
+        outs = {k: (torch.empty(sizes[k], dtype=torch.int32).pin_memory().numpy().view(np.uint32),
+                    torch.empty(sizes[k], dtype=torch.int32).pin_memory().numpy().view(np.uint32))
+                for k in idb_names}
         ectx = hisa.Context(device=local)   # default flags: device-side loop in a CUDA graph
-        ectx.program(*oracle.REACH)
+        ectx.program(*prog)
 
         def estep():
             ectx.reset_edb()
-            ectx.load_tuples("Edge", hs_, hd_)
+            for k, (c0, c1) in host_edb.items():
+                ectx.load_tuples(k, c0, c1)
             ectx.run()
-            return ectx.read_relation("Reach", out=(out0, out1))
+            return sum(len(ectx.read_relation(k, out=outs[k])[0]) for k in idb_names)
 
         estep()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(a.e2e_steps):
-            r0, _r1 = estep()
+            got = estep()
         torch.cuda.synchronize()
         et = time.perf_counter() - t0
-        assert len(r0) == n_reach
+        assert got == n_reach
         ev = _sum_over_ranks(float(n_reach) * a.e2e_steps, world) / _max_over_ranks(et, world)
-        e2e = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": int(s.nbytes + d.nbytes),
+        e2e = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": int(edb_bytes),
                "d2h_bytes_per_step": int(8 * n_reach), "steps": a.e2e_steps,
                "loop": "CUDA graph while node (device-side termination test)"}
         ectx.close()
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = cpu_baseline(s, d, nodes)
+        if reach:
+            cpu = cpu_baseline(s, d, nodes)
+        else:
+            n_s, el, what = sample()
+            cpu = {"value": n_s / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{what}: {n_s} tuples in {el:.1f} s"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_s * 1e3 / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": desc, "reach_tuples": n_reach, "iterations": iters, "edges": int(len(s)),
+        "config": {"workload": desc, "idb_tuples": sizes, "iterations": iters,
+                   "edb_tuples": {k: int(len(c0)) for k, (c0, c1) in edb.items()},
+                   "tuples_joined_last_step": int(st.tuples_joined),
                    "l2": "flushed by a 512 MiB write between steps (outside the timed events)",
                    "loop": "host-driven, CUDA events around every kernel",
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -375,6 +443,8 @@ def run_reference(a):
     world, rank, _ = _dist()
     if rank != 0:
         return
+    if a.workload not in ("rmat16", "rmat13", "er1000"):
+        return run_reference_program(a)
     s, d, desc, nodes = _workload(a.workload)
     rng = np.random.default_rng(11)
     per_step_targets = 16 if a.workload == "rmat16" else nodes
@@ -402,6 +472,31 @@ def run_reference(a):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": desc},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_program(a):
+    """The oracle on the bounded sample of a non-REACH workload, every step."""
+    import oracle
+    world, _, _ = _dist()
+    oracle.build()
+    _prog, _edb, desc, sample = _program_workload(a.workload)
+    for _ in range(a.warmup):
+        sample()
+    tot_n, tot_t, what = 0, 0.0, ""
+    for _ in range(a.steps):
+        n, t, what = sample()
+        tot_n += n
+        tot_t += t
+    value = tot_n / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": tot_t * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "each step: " + what},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

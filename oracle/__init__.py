@@ -157,6 +157,16 @@ SG = (
     ],
 )
 
+# SG as the workload description prints it: the filter on the first rule only
+# (on a DAG whose nodes have several parents, rule 2 then also derives SG(x,x)).
+SG_LITERAL = (
+    {"Edge": "edb", "SG": "idb"},
+    [
+        (("SG", ("x", "y")), [("Edge", ("p", "x")), ("Edge", ("p", "y"))], [("x", "y")]),
+        (("SG", ("x", "y")), [("Edge", ("a", "x")), ("SG", ("a", "b")), ("Edge", ("b", "y"))], []),
+    ],
+)
+
 
 # A context-sensitive points-to style program over Assign / Dereference (written
 # for this project; the paper elides its CSPA query, stating only that five rules

@@ -13,7 +13,12 @@ its delta at iteration k is delta_k restricted to V x T.  Sizes, delta counts
 and fingerprints of the blocks add up to those of the whole relation.
 
 ``sg_dag``: SG (both rules with x != y) on the random DAG of 20,000 nodes and
-40,000 edges (seed 1), evaluated in one piece.
+40,000 edges (seed 1), evaluated in one piece; ``--literal`` takes the filter
+on the first rule only.
+
+``cspa``: the ten-rule points-to program on the skewed Assign/Dereference
+inputs divided by ``--div`` (windows of ``--window`` ids, seed 2), evaluated
+in one piece.
 """
 from __future__ import annotations
 
@@ -75,30 +80,58 @@ def reach_rmat(procs: int, block: int):
     print(json.dumps(out))
 
 
-def sg_dag():
+def sg_dag(literal: bool):
     t0 = time.time()
     s, d = workloads.config_sg_dag()
-    r = oracle.seminaive(*oracle.SG, {"Edge": (s, d)})
+    r = oracle.seminaive(*(oracle.SG_LITERAL if literal else oracle.SG), {"Edge": (s, d)})
     c0, c1 = r.relations["SG"]
     out = {
-        "workload": "SG (x != y on both rules) on a random DAG, n=20,000, m=40,000, gaps in [1,256], seed 1",
+        "workload": ("SG (x != y on rule 1 only)" if literal else "SG (x != y on both rules)")
+                    + " on a random DAG, n=20,000, m=40,000, gaps in [1,256], seed 1",
         "sg_size": int(r.size("SG")),
         "delta_counts": r.delta_counts["SG"],
         "fingerprint": str(oracle.fingerprint(c0, c1)),
         "oracle_cpu_seconds": round(time.time() - t0, 1),
     }
-    with open(os.path.join(HERE, "sg_dag_20k.json"), "w") as f:
+    with open(os.path.join(HERE, "sg_literal_dag_20k.json" if literal else "sg_dag_20k.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
+
+
+def cspa(div: int, window: int):
+    t0 = time.time()
+    edb = workloads.config_cspa(div, window)
+    r = oracle.seminaive(*oracle.CSPA, edb)
+    out = {
+        "workload": "points-to program, Assign %d / Dereference %d over %d ids, Zipf 1.1, 80%% in windows of %d, seed 2"
+                    % (len(edb["Assign"][0]), len(edb["Dereference"][0]), 300_000 // div, window),
+        "div": div,
+        "window": window,
+        "iterations": r.iterations,
+        "oracle_cpu_seconds": None,
+    }
+    for name in ("ValueFlow", "MemoryAlias", "ValueAlias"):
+        c0, c1 = r.relations[name]
+        out[name] = {"size": int(r.size(name)), "delta_counts": r.delta_counts[name],
+                     "fingerprint": str(oracle.fingerprint(c0, c1))}
+    out["oracle_cpu_seconds"] = round(time.time() - t0, 1)
+    with open(os.path.join(HERE, "cspa_d%d_w%d.json" % (div, window)), "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps(out))
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["reach_rmat", "sg_dag"])
+    ap.add_argument("which", choices=["reach_rmat", "sg_dag", "cspa"])
+    ap.add_argument("--literal", action="store_true", help="sg_dag: filter on rule 1 only")
+    ap.add_argument("--div", type=int, default=250)
+    ap.add_argument("--window", type=int, default=128)
     ap.add_argument("--procs", type=int, default=os.cpu_count())
     ap.add_argument("--block", type=int, default=256)
     a = ap.parse_args()
     if a.which == "reach_rmat":
         reach_rmat(a.procs, a.block)
+    elif a.which == "cspa":
+        cspa(a.div, a.window)
     else:
-        sg_dag()
+        sg_dag(a.literal)

@@ -174,21 +174,46 @@ def test_reach_rmat_full_size_golden_and_sampled():
         assert np.array_equal(g0, ref.relations["Reach"][0]) and np.array_equal(g1, ref.relations["Reach"][1])
 
 
-def test_sg_dag_full_size_golden():
-    """SG (x != y on both rules) on the 20,000-node DAG: size, all 104 delta
-    counts and the fingerprint of the whole relation against the oracle's
-    stored values."""
-    path = os.path.join(GOLDEN, "sg_dag_20k.json")
+@pytest.mark.parametrize("literal", [False, True])
+def test_sg_dag_full_size_golden(literal):
+    """SG on the 20,000-node DAG (x != y on both rules, or on rule 1 only as
+    the workload description prints it): size, every delta count and the
+    fingerprint of the whole relation against the oracle's stored values."""
+    path = os.path.join(GOLDEN, "sg_literal_dag_20k.json" if literal else "sg_dag_20k.json")
     if not os.path.exists(path):
         pytest.skip("golden values not generated")
     g = json.load(open(path))
     from paper_2311_02206_gb300 import hisa
     s, d = workloads.config_sg_dag()
     with hisa.Context() as ctx:
-        ctx.program(*oracle.SG)
+        ctx.program(*(oracle.SG_LITERAL if literal else oracle.SG))
         ctx.load_tuples("Edge", s, d)
         ctx.run()
         assert ctx.delta_counts("SG") == g["delta_counts"]
         assert ctx.relation_size("SG") == g["sg_size"]
         c0, c1 = ctx.read_relation("SG", device=True)
         assert fingerprint_device(c0, c1) == int(g["fingerprint"])
+
+
+@pytest.mark.parametrize("div,window", [(500, 32), (250, 128)])
+def test_cspa_golden(div, window):
+    """The points-to program on the skewed inputs divided by `div`: sizes,
+    delta counts and fingerprints of the three IDB relations against the
+    oracle's stored values (1/250 derives ~4.6e9 raw tuples on the GPU)."""
+    path = os.path.join(GOLDEN, "cspa_d%d_w%d.json" % (div, window))
+    if not os.path.exists(path):
+        pytest.skip("golden values not generated")
+    g = json.load(open(path))
+    from paper_2311_02206_gb300 import hisa
+    edb = workloads.config_cspa(div, window)
+    with hisa.Context() as ctx:
+        ctx.program(*oracle.CSPA)
+        for name, (c0, c1) in edb.items():
+            ctx.load_tuples(name, c0, c1)
+        st = ctx.run()
+        assert st.iterations == g["iterations"]
+        for name in ("ValueFlow", "MemoryAlias", "ValueAlias"):
+            assert ctx.relation_size(name) == g[name]["size"], name
+            assert ctx.delta_counts(name) == g[name]["delta_counts"], name
+            c0, c1 = ctx.read_relation(name, device=True)
+            assert fingerprint_device(c0, c1) == int(g[name]["fingerprint"]), name
