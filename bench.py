@@ -57,6 +57,8 @@ def _args():
     ap.add_argument("--workload", choices=["rmat16", "rmat13", "er1000", "sg20k", "sg20k-literal", "cspa", "batch5"],
                     default="rmat16",
                     help="rmat16: the benchmark workload; rmat13: a smaller R-MAT graph for profiler captures")
+    ap.add_argument("--single-full", action="store_true",
+                    help="keep full as one sorted array (without HISA_FLAG_LOG_FULL)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -300,7 +302,8 @@ def run_hisa(a):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 18, dtype=torch.int32, device="cuda")   # 512 MiB > 129 MB L2
 
-    ctx = hisa.Context(device=local, flags=hisa.FLAG_PHASE_TIMES)
+    extra = 0 if a.single_full else hisa.FLAG_LOG_FULL
+    ctx = hisa.Context(device=local, flags=hisa.FLAG_PHASE_TIMES | extra)
     ctx.program(*prog)
 
     def step():
@@ -377,7 +380,7 @@ def run_hisa(a):
         outs = {k: (torch.empty(sizes[k], dtype=torch.int32).pin_memory().numpy().view(np.uint32),
                     torch.empty(sizes[k], dtype=torch.int32).pin_memory().numpy().view(np.uint32))
                 for k in idb_names}
-        ectx = hisa.Context(device=local)   # default flags: device-side loop in a CUDA graph
+        ectx = hisa.Context(device=local, flags=hisa.FLAG_GRAPH | extra)   # device-side loop in a CUDA graph
         ectx.program(*prog)
 
         def estep():
@@ -419,6 +422,7 @@ def run_hisa(a):
                    "tuples_joined_last_step": int(st.tuples_joined),
                    "l2": "flushed by a 512 MiB write between steps (outside the timed events)",
                    "loop": "host-driven, CUDA events around every kernel",
+                   "full": "one sorted array" if a.single_full else "two sorted levels (log-structured)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "step_ms": [round(x, 3) for x in ms], "wall_s_timed_region": round(wall, 3)},
         "roofline": roofline,

@@ -61,6 +61,16 @@ typedef void (*hisa_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 
 #define HISA_FLAG_GRAPH 1u        /* run iterations >= 2 as one CUDA graph with a device-side while loop */
 #define HISA_FLAG_PHASE_TIMES 2u  /* record per-phase CUDA-event times (host-driven loop only) */
+/* Keep full as two sorted levels where no rule probes it (it is only
+ * differenced and merged: REACH, SG; not in batched runs): when new is small
+ * against the large level it is differenced against it by sorted probes and
+ * its delta merged into the small level; when new is large (|new| > |full|/2)
+ * the small level is folded in and new is merged into the large level as
+ * with one array.  The small level is merged into the large one when it
+ * exceeds 1/8 of it and at the end of the run.  Same results; the per-
+ * iteration merge no longer rewrites all of full (Section 5.1's merge, which
+ * the paper measures at 42-45% of CSPA time).  Set by hisa_config_default. */
+#define HISA_FLAG_LOG_FULL 4u
 
 typedef struct {
   hisa_alloc_fn alloc;      /* NULL: cudaMallocAsync from a private pool */
@@ -71,7 +81,7 @@ typedef struct {
   float load_factor;        /* hash-index load factor; 0 = 0.8 (Section 6.2) */
   float ebm_k;              /* eager buffer growth factor k of Section 5.3; 0 = 2 */
   uint32_t max_iters;       /* iteration cap; 0 = 1,000,000 */
-  uint32_t flags;           /* HISA_FLAG_* */
+  uint32_t flags;           /* HISA_FLAG_*; default HISA_FLAG_LOG_FULL */
   int32_t device;           /* CUDA device ordinal; -1 = the current device */
 } hisa_config;
 

@@ -16,7 +16,7 @@ hisa_status hisa_config_default(hisa_config* cfg) {
   cfg->load_factor = 0.8f;
   cfg->ebm_k = 2.0f;
   cfg->max_iters = 1000000;
-  cfg->flags = 0;
+  cfg->flags = HISA_FLAG_LOG_FULL;
   cfg->device = -1;
   return HISA_OK;
 }

@@ -39,6 +39,24 @@ __global__ void k_ctl(CtlArgs a) {
         }
         break;
       }
+      case kCtlMergeGate: {
+        // log-structured full: the small level is merged into the large one
+        // once it holds more than 1/ratio of it, or before new is merged
+        // straight into the large level
+        const uint64_t small = st->cnt[c.b], large = st->cnt[int(c.c >> 32)];
+        const bool forced = st->cnt[int((c.c >> 16) & 0xFFFF)] != 0;
+        st->cnt[c.a] = (small * uint64_t(c.c & 0xFFFF) > large || forced) ? small : 0;
+        break;
+      }
+      case kCtlBigFlag:
+        st->cnt[c.a] = st->cnt[c.b] * uint64_t(c.c & 0xFFFF) > st->cnt[int(c.c >> 16)] ? 1 : 0;
+        break;
+      case kCtlNot:
+        st->cnt[c.a] = st->cnt[c.b] ? 0 : 1;
+        break;
+      case kCtlZeroIfCnt:
+        if (st->cnt[c.c] > 0) st->cnt[c.a] = 0;
+        break;
       default: st->error = kDevBadState; break;
     }
   }
@@ -60,10 +78,12 @@ __global__ void k_commit(CommitArgs a) {
   for (int r = 0; r < a.nrel; ++r) {
     const uint64_t nd = st->cnt[a.delta_next[r]];
     if (nd > 0) {
-      DBuf t = st->buf[a.full[r]];
-      st->buf[a.full[r]] = st->buf[a.full_next[r]];
-      st->buf[a.full_next[r]] = t;
-      st->cnt[a.full[r]] = st->cnt[a.full_next[r]];
+      const bool alt = a.alt_flag1[r] > 0 && st->cnt[a.alt_flag1[r] - 1] != 0;
+      const int f = alt ? a.alt_full[r] : a.full[r], fn = alt ? a.alt_full_next[r] : a.full_next[r];
+      DBuf t = st->buf[f];
+      st->buf[f] = st->buf[fn];
+      st->buf[fn] = t;
+      st->cnt[f] = st->cnt[fn];
       any = true;
     }
     DBuf t = st->buf[a.delta[r]];
@@ -104,7 +124,7 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
 
 const char* const kKernelNames[kKindCount] = {
     "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
-    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols"};
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe"};
 
 thread_local KernelTimer* g_timer = nullptr;
 thread_local uint64_t g_launches = 0;

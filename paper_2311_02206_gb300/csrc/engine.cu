@@ -448,10 +448,16 @@ hisa_status Engine::compile() {
         r.rswap_alt = new_slot(kb);
         r.runs_cnt[0] = nslots++;
         r.runs_cnt[1] = nslots++;
+        r.l1 = new_slot(kb);
+        r.l1_next = new_slot(kb);
+        r.newp = new_slot(kb);
+        r.gate = nslots++;
+        r.bigf = nslots++;
+        r.smallf = nslots++;
       }
     }
     for (int id : {r.base, r.rev, r.full_next, r.delta, r.delta_next, r.fresh, r.fresh_alt, r.rev_next, r.rswap,
-                   r.rswap_alt})
+                   r.rswap_alt, r.l1, r.l1_next, r.newp})
       if (id >= 0 && slot_elem[id] != kb) {
         dev_free(hs.buf[id].ptr);
         hs.buf[id] = {nullptr, 0};
@@ -490,6 +496,12 @@ hisa_status Engine::compile() {
         planN.push_back(v);
       }
     }
+  }
+  // log-structured full where nothing probes full (it is only differenced
+  // and merged): REACH and SG, not CSPA's inner IDB atoms nor batched runs
+  for (int r : idb) {
+    Relation& R = rels[r];
+    R.log = (cfg.flags & HISA_FLAG_LOG_FULL) && !batched && !R.need_idx[0] && !R.need_idx[1];
   }
   compiled = true;
   graph_stale = true;
@@ -662,10 +674,113 @@ void Engine::emit_sort(std::vector<Op>& ops, int in, int alt, int cnt, int hist,
   }
 }
 
-// Populate delta, merge, commit.
+// Log-structured full, step 0.  When new is large against the large level
+// (|new| * kBigRatio > |full|) probing it costs more than streaming full, so
+// this iteration merges new straight into full (bigf) after the small level
+// has been folded in; otherwise new is probed (smallf).  The small level is
+// merged into the large one when it has grown past 1/kLevelRatio of it, when
+// bigf is set, or always (`force`); both levels are sorted and disjoint, so
+// the merge drops nothing.  Idempotent: a re-run finds the small level empty
+// and takes the same decision.
+constexpr int kLevelRatio = 8;
+constexpr int kBigRatio = 2;
+void Engine::emit_level_merge(std::vector<Op>& ops, const Relation& R, bool force) {
+  Op g{};
+  g.kind = Op::CTL;
+  g.ctl.st = dst;
+  g.ctl.skip_mask = 3;
+  if (force) {
+    g.ctl.cmd[g.ctl.n++] = {kCtlCopyCnt, R.gate, R.l1, 0};
+  } else {
+    g.ctl.cmd[g.ctl.n++] = {kCtlBigFlag, R.bigf, R.fresh, ((long long)R.full << 16) | kBigRatio};
+    g.ctl.cmd[g.ctl.n++] = {kCtlNot, R.smallf, R.bigf, 0};
+    g.ctl.cmd[g.ctl.n++] = {kCtlMergeGate, R.gate, R.l1,
+                            ((long long)R.full << 32) | ((long long)R.bigf << 16) | kLevelRatio};
+  }
+  ops.push_back(g);
+  Op m{};
+  m.kind = Op::SETOP;
+  SetopArgs& a = m.setop;
+  a.st = dst;
+  a.a_buf = R.full;
+  a.a_cnt = R.full;
+  a.b_buf = R.l1;
+  a.b_cnt = R.gate;
+  a.split_buf = sc.split;
+  a.status_buf = sc.setop_status;
+  a.d_buf = -1;
+  a.d_cnt = -1;
+  a.f_buf = R.full_next;
+  a.f_cnt = R.full_next;
+  a.ctr = 2;
+  a.skip_mask = 3;
+  a.stage_bit = 1;
+  ops.push_back(m);
+  Op c{};
+  c.kind = Op::CTL;
+  c.ctl.st = dst;
+  c.ctl.skip_mask = 3;
+  c.ctl.cmd[c.ctl.n++] = {kCtlSwapIfCnt, R.full, R.full_next, R.gate};
+  c.ctl.cmd[c.ctl.n++] = {kCtlZeroIfCnt, R.l1, 0, R.gate};
+  ops.push_back(c);
+}
+
+// Populate delta, merge, commit.  With a log-structured full: level merge,
+// new minus the large level by sorted probes, then difference and merge
+// against the small level (which becomes l1 at the commit).
 void Engine::emit_tail(std::vector<Op>& ops, bool force) {
   for (int r : idb) {
     const Relation& R = rels[r];
+    if (R.log) {
+      const int sorted_new = (passes & 1) ? R.fresh_alt : R.fresh;
+      emit_level_merge(ops, R, false);
+      // large new: difference + merge against the large level (commit swaps it)
+      Op big{};
+      big.kind = Op::SETOP;
+      SetopArgs& m = big.setop;
+      m.st = dst;
+      m.a_buf = R.full;
+      m.a_cnt = R.full;
+      m.b_buf = sorted_new;
+      m.b_cnt = R.fresh;
+      m.split_buf = sc.split;
+      m.status_buf = sc.setop_status;
+      m.d_buf = R.delta_next;
+      m.d_cnt = R.delta_next;
+      m.f_buf = R.full_next;
+      m.f_cnt = R.full_next;
+      m.ctr = 2;
+      m.skip_mask = 3;
+      m.stage_bit = 1;
+      m.gate1 = R.bigf + 1;
+      ops.push_back(big);
+      // small new: probe the large level, then difference + merge against the small one
+      Op d{};
+      d.kind = Op::DIFF;
+      d.diff = DiffArgs{dst, R.full, R.full, sorted_new, R.fresh, R.newp, R.newp, sc.setop_status, 2, 3, 1,
+                        R.smallf + 1};
+      ops.push_back(d);
+      Op o{};
+      o.kind = Op::SETOP;
+      SetopArgs& a = o.setop;
+      a.gate1 = R.smallf + 1;
+      a.st = dst;
+      a.a_buf = R.l1;
+      a.a_cnt = R.l1;
+      a.b_buf = R.newp;
+      a.b_cnt = R.newp;
+      a.split_buf = sc.split;
+      a.status_buf = sc.setop_status;
+      a.d_buf = R.delta_next;
+      a.d_cnt = R.delta_next;
+      a.f_buf = R.l1_next;
+      a.f_cnt = R.l1_next;
+      a.ctr = 2;
+      a.skip_mask = 3;
+      a.stage_bit = 1;
+      ops.push_back(o);
+      continue;
+    }
     Op o{};
     o.kind = Op::SETOP;
     SetopArgs& a = o.setop;
@@ -691,8 +806,11 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
   c.commit.nrel = int(idb.size());
   for (size_t i = 0; i < idb.size(); ++i) {
     const Relation& R = rels[idb[i]];
-    c.commit.full[i] = R.full;
-    c.commit.full_next[i] = R.full_next;
+    c.commit.full[i] = R.log ? R.l1 : R.full;          // the level that absorbed delta
+    c.commit.full_next[i] = R.log ? R.l1_next : R.full_next;
+    c.commit.alt_full[i] = R.full;
+    c.commit.alt_full_next[i] = R.full_next;
+    c.commit.alt_flag1[i] = R.log ? R.bigf + 1 : 0;
     c.commit.delta[i] = R.delta;
     c.commit.delta_next[i] = R.delta_next;
     c.commit.history[i] = R.history;
@@ -716,6 +834,7 @@ hisa_status Engine::exec_t(const std::vector<Op>& ops) {
       case Op::INDEX: launch_index<K>(o.index, grid, stream); break;
       case Op::ZERO: launch_zero(o.zero, grid, stream); break;
       case Op::SWAP: launch_swap<K>(o.swap, grid, stream); break;
+      case Op::DIFF: launch_diff<K>(o.diff, grid, stream); break;
     }
   }
   return check_launch("kernel launch");
@@ -844,13 +963,16 @@ hisa_status Engine::regrow() {
     int partner = -1, live = -1;
     for (int r : idb) {
       const Relation& R = rels[r];
-      if (id == R.full_next || id == R.full || id == R.rev_next || id == R.rev) {
+      if (id == R.full_next || id == R.full || id == R.rev_next || id == R.rev || id == R.l1 || id == R.l1_next) {
         // eager buffer management: full + k * delta, and at least a quarter more
         const bool rv = id == R.rev_next || id == R.rev;
-        const int cur = rv ? R.rev : R.full;
+        const bool small = id == R.l1 || id == R.l1_next;
+        const int cur = rv ? R.rev : small ? R.l1 : R.full;
         const uint64_t delta = need > hs.cnt[cur] ? need - hs.cnt[cur] : need;
         cap = need + std::max(uint64_t(cfg.ebm_k * double(delta)), need / 4) + 1024;
-        partner = rv ? (id == R.rev_next ? R.rev : R.rev_next) : (id == R.full_next ? R.full : R.full_next);
+        partner = rv      ? (id == R.rev_next ? R.rev : R.rev_next)
+                  : small ? (id == R.l1_next ? R.l1 : R.l1_next)
+                          : (id == R.full_next ? R.full : R.full_next);
         live = cur;
       } else if (id == R.delta_next || id == R.delta) {
         cap = need + need / 4 + 1024;
@@ -876,6 +998,7 @@ hisa_status Engine::regrow() {
     new_cap = std::max({new_cap, hs.buf[R.fresh].cap, hs.buf[R.fresh_alt].cap});
     full_cap = std::max({full_cap, hs.cnt[R.full], hs.buf[R.full_next].cap});
     delta_cap = std::max({delta_cap, hs.buf[R.delta].cap, hs.buf[R.delta_next].cap});
+    if (R.log) full_cap = std::max({full_cap, hs.cnt[R.full] + hs.buf[R.l1].cap, hs.buf[R.l1_next].cap});
   }
   hisa_status s;
   if (hs.overflow & 1) {
@@ -885,6 +1008,10 @@ hisa_status Engine::regrow() {
       // the column-swapped delta sorted into the reverse-order mirror
       if (R.need_idx[1] && ((s = ensure(R.rswap, delta_cap)) || (s = ensure(R.rswap_alt, delta_cap)))) return s;
     }
+  }
+  for (int r : idb) {   // new minus the large level holds at most |new|
+    const Relation& R = rels[r];
+    if (R.log && (s = ensure(R.newp, new_cap))) return s;
     if ((s = ensure(sc.radix_status, (std::max(new_cap, delta_cap) / kt + 2) * kRadixDigits)) ||
         (s = ensure(sc.starts, new_cap / kJoinChunk + 2)))
       return s;
@@ -892,7 +1019,8 @@ hisa_status Engine::regrow() {
   // next iterations: delta is the outer relation of the joins; full + new is merged
   if ((s = ensure(sc.offs, delta_cap + 1)) || (s = ensure(sc.join_status, delta_cap / kJoinTile + 2))) return s;
   if ((s = ensure(sc.split, (full_cap + std::max(new_cap, delta_cap)) / ks + 2)) ||
-      (s = ensure(sc.setop_status, (full_cap + std::max(new_cap, delta_cap)) / ks + 2)))
+      (s = ensure(sc.setop_status,
+                  std::max((full_cap + std::max(new_cap, delta_cap)) / ks, new_cap / kDiffTile) + 2)))
     return s;
   std::memset(hs.need, 0, sizeof hs.need);
   hs.overflow = 0;
@@ -951,6 +1079,12 @@ hisa_status Engine::init_run_state() {
         if ((s = ensure(id, 4 * nedb))) return s;
       hs.cnt[R.rev] = hs.cnt[R.rev_next] = hs.cnt[R.rswap] = 0;
     }
+    if (R.log) {
+      for (int id : {R.l1, R.l1_next, R.newp})
+        if ((s = ensure(id, 4 * nedb))) return s;
+      hs.cnt[R.l1] = hs.cnt[R.l1_next] = hs.cnt[R.newp] = hs.cnt[R.gate] = 0;
+      hs.cnt[R.bigf] = hs.cnt[R.smallf] = 0;
+    }
     for (int col = 0; col < 2; ++col) {
       if (!R.need_idx[col]) continue;
       uint64_t cap = 1024;
@@ -1002,10 +1136,11 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
     const bool first = hs.iter == 0;
     const bool use_graph = !first && (cfg.flags & HISA_FLAG_GRAPH) && !timing && !batched;
     const size_t rec0 = timer.recs.size();
-    std::vector<uint64_t> m_prev, d_prev;
+    std::vector<uint64_t> m_prev, d_prev, l_prev;
     for (int r : idb) {
       m_prev.push_back(hs.cnt[rels[r].full]);
       d_prev.push_back(hs.cnt[rels[r].delta]);
+      l_prev.push_back(rels[r].log ? hs.cnt[rels[r].l1] : 0);
     }
     const uint32_t iter0 = hs.iter;
     if (use_graph) {
@@ -1026,7 +1161,24 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
           const double nn = double(hs.cnt[R.fresh]), nd = double(hs.cnt[R.delta]);
           const double m = double(m_prev[i]), dp = double(d_prev[i]);
           kstat[kKRadixPass].bytes += passes * 2.0 * nn * kb;
-          if (nn > 0) kstat[kKSetop].bytes += (m + nn) * kb + (m + 2.0 * nd) * kb;
+          if (R.log && hs.cnt[R.bigf]) {
+            // small level folded in, then new merged into the large level
+            const double lp = double(l_prev[i]);
+            if (lp > 0) kstat[kKSetop].bytes += 2.0 * (m + lp) * kb;
+            if (nn > 0) kstat[kKSetop].bytes += (m + lp + nn) * kb + (m + lp + 2.0 * nd) * kb;
+          } else if (R.log) {
+            // level merge (when the large level changed), new minus the large
+            // level (read new, write new'), small-level difference + merge
+            const double m_after = double(hs.cnt[R.full]), np = double(hs.cnt[R.newp]);
+            const double l1 = m_after != m ? 0.0 : double(l_prev[i]);
+            if (m_after != m) kstat[kKSetop].bytes += 2.0 * m_after * kb;
+            if (nn > 0) {
+              kstat[kKDiffProbe].bytes += (nn + np) * kb;
+              kstat[kKSetop].bytes += (l1 + np) * kb + (l1 + 2.0 * nd) * kb;
+            }
+          } else if (nn > 0) {
+            kstat[kKSetop].bytes += (m + nn) * kb + (m + 2.0 * nd) * kb;
+          }
           kstat[kKJoinWrite].bytes += 2.0 * nn * kb + dp * (kb + 8.0);
           kstat[kKJoinCount].bytes += dp * (kb + 8.0 + 16.0);
           // inner-relation upkeep at the head of this iteration
@@ -1089,6 +1241,7 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
     }
     if (!hs.go) break;
   }
+  if ((s = merge_levels())) return s;
   if (hs.iter >= cfg.max_iters && hs.aux[0] == hs.iter)
     return ctx_fail(HISA_ERR_NOT_CONVERGED, "max_iters reached", nullptr);
   // delta histories
@@ -1119,6 +1272,30 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
   if (stats) *stats = last_stats;
   ran = true;
   return HISA_OK;
+}
+
+// End of a run with a log-structured full: the small level is merged into the
+// large one, so full holds the whole relation for reading.
+hisa_status Engine::merge_levels() {
+  std::vector<Op> ops;
+  std::vector<double> before;
+  for (int r : idb)
+    if (rels[r].log) {
+      emit_level_merge(ops, rels[r], true);
+      before.push_back(double(hs.cnt[rels[r].full] + hs.cnt[rels[r].l1]));
+    }
+  if (ops.empty()) return HISA_OK;
+  hisa_status s;
+  for (int guard = 0; guard < 16; ++guard) {
+    if ((s = exec(ops)) || (s = download())) return s;
+    if (hs.error) return ctx_fail(HISA_ERR_CUDA, "device error", "level merge");
+    if (!hs.overflow) {
+      for (double n : before) kstat[kKSetop].bytes += 2.0 * n * (wide ? 8.0 : 4.0);
+      return HISA_OK;
+    }
+    if ((s = regrow()) || (s = upload())) return s;
+  }
+  return ctx_fail(HISA_ERR_OOM, "buffers keep overflowing", "level merge");
 }
 
 // Runs one iteration with `ops` (host-driven) until it commits, growing

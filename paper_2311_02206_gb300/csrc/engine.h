@@ -35,6 +35,12 @@ struct Relation {
   // the sort buffers of that delta; run counts feeding the index rebuilds
   int rev_next = -1, rswap = -1, rswap_alt = -1;
   int runs_cnt[2] = {-1, -1};
+  // log-structured full (HISA_FLAG_LOG_FULL): full holds the large level,
+  // l1 the small one that absorbs each delta; newp = new minus the large level;
+  // gate = |l1| when l1 is due to be merged into full, else 0
+  bool log = false;
+  int l1 = -1, l1_next = -1, newp = -1, gate = -1;
+  int bigf = -1, smallf = -1;   // this iteration merges new straight into full / probes it
   int history = -1;                 // |delta_k| per iteration
   std::vector<uint64_t> delta_counts;
 };
@@ -51,7 +57,7 @@ struct StepPlan {
 };
 
 struct Op {
-  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP } kind;
+  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF } kind;
   CtlArgs ctl;
   JoinArgs join;
   RadixPassArgs pass;
@@ -62,6 +68,7 @@ struct Op {
   IndexArgs index;
   ZeroArgs zero;
   SwapArgs swap;
+  DiffArgs diff;
 };
 
 struct Scratch {
@@ -129,6 +136,8 @@ class Engine {
   void emit_idb_index(std::vector<Op>& ops);
   void emit_sort(std::vector<Op>& ops, int in, int alt, int cnt, int hist, int skip_mask, int stage_bit);
   void emit_tail(std::vector<Op>& ops, bool force);
+  void emit_level_merge(std::vector<Op>& ops, const Relation& R, bool force);
+  hisa_status merge_levels();
   template <typename K> hisa_status exec_t(const std::vector<Op>& ops);
   hisa_status exec(const std::vector<Op>& ops);
   template <typename K> hisa_status prepare_rel_t(Relation& r, int order, int slot);

@@ -21,6 +21,11 @@ enum : int {
   kCtlZeroSmall,     // zero the first b u64 words of buffer a
   kCtlSwapIfCnt,     // if cnt[c] > 0: exchange buffers a and b, cnt[a] = cnt[b]
   kCtlCheckTable,    // hash table a must hold cnt[b] runs at load factor c / 1024
+  kCtlMergeGate,     // cnt[a] = cnt[b] if cnt[b] * r > cnt[L] or cnt[F] != 0, else 0;
+                     //   c = (L << 32) | (F << 16) | r
+  kCtlBigFlag,       // cnt[a] = (cnt[b] * (c & 0xFFFF) > cnt[c >> 16]) ? 1 : 0
+  kCtlNot,           // cnt[a] = cnt[b] ? 0 : 1
+  kCtlZeroIfCnt,     // if cnt[c] > 0: cnt[a] = 0
 };
 
 struct CtlCmd {
@@ -40,6 +45,9 @@ struct CommitArgs {
   DevState* st;
   int nrel;
   int full[8], full_next[8], delta[8], delta_next[8], history[8], fresh[8];
+  // a second (full, full_next) pair swapped instead when cnt[alt_flag1 - 1]
+  // is non-zero (log-structured full: delta merged into the large level)
+  int alt_full[8], alt_full_next[8], alt_flag1[8];
   int force;   // commit even when no delta is non-empty (first iteration)
 };
 
@@ -100,7 +108,7 @@ struct SwapArgs {
 
 enum KernelKind : int {
   kKEncode, kKDecode, kKRuns, kKHist, kKRadixPass, kKSetopPartition, kKSetop, kKIndex,
-  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKindCount
+  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKindCount
 };
 extern const char* const kKernelNames[kKindCount];
 
@@ -150,6 +158,7 @@ template <typename K> void launch_setop(const SetopArgs& a, const Grid& g, cudaS
 template <typename K> void launch_index(const IndexArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_count_runs(const RunsArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_swap(const SwapArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_diff(const DiffArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_hist(const InstArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_bounds(const InstArgs& a, const Grid& g, cudaStream_t s);
 void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStream_t s);

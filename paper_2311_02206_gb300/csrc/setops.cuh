@@ -43,7 +43,12 @@ struct SetopArgs {
   int ctr;
   int skip_mask;           // st->overflow bits that cancel this launch
   int stage_bit;           // overflow bit raised when an output is too small
+  int gate1;               // 1 + cnt slot that must be non-zero for the launch to run (0: always)
 };
+
+__device__ __forceinline__ bool gated_off(const DevState* st, int gate1) {
+  return gate1 > 0 && st->cnt[gate1 - 1] == 0;
+}
 
 // Number of A elements among the first d merged elements (ties take A first).
 template <typename K>
@@ -62,7 +67,7 @@ template <typename K>
 __global__ void k_setop_partition(SetopArgs a) {
   constexpr int C = setop_tile<K>();
   DevState* st = a.st;
-  if (st->overflow & a.skip_mask) return;
+  if ((st->overflow & a.skip_mask) || gated_off(st, a.gate1)) return;
   const uint64_t na = st->cnt[a.a_cnt], nb = st->cnt[a.b_cnt];
   const uint64_t D = na + nb;
   const uint64_t ntiles = (D + C - 1) / C;
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
   __shared__ int s_hasA, s_hasB;
 
   DevState* st = a.st;
-  if (st->overflow & a.skip_mask) return;
+  if ((st->overflow & a.skip_mask) || gated_off(st, a.gate1)) return;
   const uint64_t na = st->cnt[a.a_cnt], nb = st->cnt[a.b_cnt];
   if (nb == 0) return;   // nothing new: delta stays empty, full' is not needed
   const uint64_t D = na + nb;
@@ -238,6 +243,160 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
         over = true;
       }
       if (over) atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- difference by sorted probes (log-structured full) ------------------------------
+//
+// C = adjacent-unique(B) \ A for a sorted B (with repeats) and a sorted,
+// duplicate-free A that is much larger than B.  Only B is streamed: every
+// thread locates its first item in A by binary search inside the A-range of
+// its tile, then gallops forward for the following (ascending) items, so A
+// is read only where B's items fall (Section 5.1 "populating delta" against
+// the large level of a log-structured full).  Kept items are compacted in
+// order through a decoupled look-back over the tiles.
+
+struct DiffArgs {
+  DevState* st;
+  int a_buf, a_cnt;        // sorted, unique
+  int b_buf, b_cnt;        // sorted, repeats allowed
+  int out_buf, out_cnt;    // C, written from 0
+  int status_buf;          // u64 [tiles] look-back
+  int ctr;
+  int skip_mask, stage_bit;
+  int gate1;               // as in SetopArgs
+};
+
+constexpr int kDiffThreads = 256;
+constexpr int kDiffItems = 8;
+constexpr int kDiffTile = kDiffThreads * kDiffItems;
+
+// First position in A[lo, hi) holding a value >= x.
+template <typename K>
+__device__ __forceinline__ uint64_t lower_bound_k(const K* A, uint64_t lo, uint64_t hi, K x) {
+  while (lo < hi) {
+    const uint64_t m = (lo + hi) >> 1;
+    if (A[m] < x) lo = m + 1;
+    else hi = m;
+  }
+  return lo;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kDiffThreads) k_diff_probe(DiffArgs a) {
+  __shared__ K s_b[kDiffTile];
+  __shared__ uint64_t s_scan[32];
+  __shared__ uint64_t s_base, s_lo, s_hi;
+  __shared__ uint32_t s_tile;
+  __shared__ K s_prev;
+  __shared__ int s_has_prev;
+  DevState* st = a.st;
+  if ((st->overflow & a.skip_mask) || gated_off(st, a.gate1)) return;
+  const uint64_t na = st->cnt[a.a_cnt], nb = st->cnt[a.b_cnt];
+  if (nb == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->cnt[a.out_cnt] = 0;
+    return;
+  }
+  const uint64_t ntiles = (nb + kDiffTile - 1) / kDiffTile;
+  if (st->buf[a.status_buf].cap < ntiles) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicMax((unsigned long long*)&st->need[a.status_buf], (unsigned long long)ntiles);
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    return;
+  }
+  const K* A = static_cast<const K*>(st->buf[a.a_buf].ptr);
+  const K* B = static_cast<const K*>(st->buf[a.b_buf].ptr);
+  K* out = static_cast<K*>(st->buf[a.out_buf].ptr);
+  const uint64_t ocap = st->buf[a.out_buf].cap;
+  uint64_t* status = static_cast<uint64_t*>(st->buf[a.status_buf].ptr);
+  const uint32_t epoch = st->epoch;
+  const int tid = threadIdx.x;
+  while (true) {
+    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    const uint64_t b0 = tile * kDiffTile;
+    const int nT = int(min(uint64_t(kDiffTile), nb - b0));
+    for (int i = tid; i < nT; i += kDiffThreads) s_b[i] = B[b0 + i];
+    if (tid == 0) {
+      s_has_prev = b0 > 0;
+      if (b0 > 0) s_prev = B[b0 - 1];
+    }
+    __syncthreads();
+    if (tid == 0) s_lo = lower_bound_k(A, 0, na, s_b[0]);
+    if (tid == 32) {   // one past the last A value <= the tile's largest item
+      const K last = s_b[nT - 1];
+      uint64_t lo = 0, hi = na;
+      while (lo < hi) {
+        const uint64_t m = (lo + hi) >> 1;
+        if (A[m] <= last) lo = m + 1;
+        else hi = m;
+      }
+      s_hi = lo;
+    }
+    __syncthreads();
+    const uint64_t lo = s_lo, hi = s_hi;
+    const int i0 = tid * kDiffItems;
+    const int nmine = max(0, min(kDiffItems, nT - i0));
+    uint32_t keep = 0;
+    if (nmine > 0) {
+      uint64_t p = lower_bound_k(A, lo, hi, s_b[i0]);
+      bool hp = i0 > 0 || s_has_prev;
+      K prev = i0 > 0 ? s_b[i0 - 1] : s_prev;
+#pragma unroll
+      for (int k = 0; k < kDiffItems; ++k) {
+        if (k >= nmine) break;
+        const K x = s_b[i0 + k];
+        if (!(hp && prev == x)) {
+          // gallop from p to the first A value >= x
+          if (p < hi && A[p] < x) {
+            uint64_t step = 1, q = p;
+            while (q + step < hi && A[q + step] < x) {
+              q += step;
+              step <<= 1;
+            }
+            p = lower_bound_k(A, q + 1, min(hi, q + step + 1), x);
+          }
+          if (!(p < hi && A[p] == x)) keep |= 1u << k;
+        }
+        prev = x;
+        hp = true;
+      }
+    }
+    const uint32_t kept = __popc(keep);
+    uint64_t tile_kept;
+    const uint64_t kexcl = block_exclusive_sum<uint64_t>(kept, s_scan, &tile_kept);
+    if (tid < 32) {
+      const uint64_t base = lookback_warp(status, tile, tile_kept, epoch, &st->error);
+      if (tid == 0) s_base = base;
+    }
+    __syncthreads();
+    // compact in order: kept items of this thread go to s_b[kexcl ...]; every
+    // thread reads its items into registers first
+    K v[kDiffItems];
+#pragma unroll
+    for (int k = 0; k < kDiffItems; ++k)
+      if (k < nmine) v[k] = s_b[i0 + k];
+    __syncthreads();
+    int w = int(kexcl);
+#pragma unroll
+    for (int k = 0; k < kDiffItems; ++k)
+      if (keep & (1u << k)) s_b[w++] = v[k];
+    __syncthreads();
+    const uint64_t base = s_base;
+    for (int i = tid; i < int(tile_kept); i += kDiffThreads)
+      if (base + i < ocap) out[base + i] = s_b[i];
+    if (tile == ntiles - 1 && tid == 0) {
+      const uint64_t n = base + tile_kept;
+      st->cnt[a.out_cnt] = n;
+      if (n > ocap) {
+        atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)n);
+        atomicOr(&st->overflow, 1u << a.stage_bit);
+      }
     }
     __syncthreads();
   }

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libhisa.so")
 HISA_OK = 0
 FLAG_GRAPH = 1
 FLAG_PHASE_TIMES = 2
+FLAG_LOG_FULL = 4
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -180,7 +181,7 @@ def _torch():
 class Context:
     """One engine instance on one CUDA device and stream (include/hisa.h)."""
 
-    def __init__(self, device: int = 0, stream=None, flags: int = FLAG_GRAPH, max_iters: int = 0,
+    def __init__(self, device: int = 0, stream=None, flags: int = FLAG_GRAPH | FLAG_LOG_FULL, max_iters: int = 0,
                  load_factor: float = 0.0, ebm_k: float = 0.0, hbm_budget_bytes: int = 0,
                  torch_allocator: bool = True):
         lib = load_library()

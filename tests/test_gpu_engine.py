@@ -23,8 +23,9 @@ def _lib():
 
 
 def modes():
+    """host-driven, graph-captured, and both with the log-structured full"""
     from paper_2311_02206_gb300 import hisa
-    return [0, hisa.FLAG_GRAPH]
+    return [0, hisa.FLAG_GRAPH, hisa.FLAG_LOG_FULL, hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL]
 
 
 @pytest.mark.parametrize("seed", range(40))
@@ -41,10 +42,13 @@ def test_reach_random_small(seed):
 
 
 @pytest.mark.parametrize("shape,n", [("path", 300), ("cycle", 64), ("dag", 120), ("path", 2)])
-def test_reach_closed_forms(shape, n):
+@pytest.mark.parametrize("log_full", [False, True])
+def test_reach_closed_forms(shape, n, log_full):
+    from paper_2311_02206_gb300 import hisa
     src, dst = {"path": workloads.path_graph, "cycle": workloads.cycle_graph,
                 "dag": workloads.complete_dag}[shape](n)
-    rels, counts, st = gpu_eval(*oracle.REACH, {"Edge": (src, dst)})
+    rels, counts, st = gpu_eval(*oracle.REACH, {"Edge": (src, dst)},
+                                flags=hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0))
     size = len(rels["Reach"][0])
     if shape == "path":
         assert size == n * (n - 1) // 2 and counts["Reach"] == [n - k for k in range(1, n)]
@@ -148,7 +152,8 @@ def test_sg_random_dag(seed):
         assert_same(rels, counts, ref)
 
 
-def test_reach_rmat_full_size_golden_and_sampled():
+@pytest.mark.parametrize("log_full", [False, True])
+def test_reach_rmat_full_size_golden_and_sampled(log_full):
     """REACH on R-MAT scale 16 / 2**19 edges, in the launch configuration the
     benchmark times: total size, delta counts and fingerprint against the
     oracle's stored values, and 16 sampled target columns element by element."""
@@ -158,7 +163,7 @@ def test_reach_rmat_full_size_golden_and_sampled():
     g = json.load(open(path))
     from paper_2311_02206_gb300 import hisa
     s, d = workloads.config_reach_rmat()
-    with hisa.Context() as ctx:
+    with hisa.Context(flags=hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0)) as ctx:
         ctx.program(*oracle.REACH)
         ctx.load_tuples("Edge", s, d)
         ctx.run()
@@ -174,8 +179,8 @@ def test_reach_rmat_full_size_golden_and_sampled():
         assert np.array_equal(g0, ref.relations["Reach"][0]) and np.array_equal(g1, ref.relations["Reach"][1])
 
 
-@pytest.mark.parametrize("literal", [False, True])
-def test_sg_dag_full_size_golden(literal):
+@pytest.mark.parametrize("literal,log_full", [(False, False), (True, False), (False, True)])
+def test_sg_dag_full_size_golden(literal, log_full):
     """SG on the 20,000-node DAG (x != y on both rules, or on rule 1 only as
     the workload description prints it): size, every delta count and the
     fingerprint of the whole relation against the oracle's stored values."""
@@ -185,7 +190,7 @@ def test_sg_dag_full_size_golden(literal):
     g = json.load(open(path))
     from paper_2311_02206_gb300 import hisa
     s, d = workloads.config_sg_dag()
-    with hisa.Context() as ctx:
+    with hisa.Context(flags=hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0)) as ctx:
         ctx.program(*(oracle.SG_LITERAL if literal else oracle.SG))
         ctx.load_tuples("Edge", s, d)
         ctx.run()
