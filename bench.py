@@ -59,6 +59,8 @@ def _args():
                     help="rmat16: the benchmark workload; rmat13: a smaller R-MAT graph for profiler captures")
     ap.add_argument("--single-full", action="store_true",
                     help="keep full as one sorted array (without HISA_FLAG_LOG_FULL)")
+    ap.add_argument("--no-dense", action="store_true",
+                    help="sort raw join results instead of the grouped bitmap join (HISA_FLAG_NO_DENSE)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -302,7 +304,7 @@ def run_hisa(a):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 18, dtype=torch.int32, device="cuda")   # 512 MiB > 129 MB L2
 
-    extra = 0 if a.single_full else hisa.FLAG_LOG_FULL
+    extra = (0 if a.single_full else hisa.FLAG_LOG_FULL) | (hisa.FLAG_NO_DENSE if a.no_dense else 0)
     ctx = hisa.Context(device=local, flags=hisa.FLAG_PHASE_TIMES | extra)
     ctx.program(*prog)
 
@@ -423,6 +425,8 @@ def run_hisa(a):
                    "l2": "flushed by a 512 MiB write between steps (outside the timed events)",
                    "loop": "host-driven, CUDA events around every kernel",
                    "full": "one sorted array" if a.single_full else "two sorted levels (log-structured)",
+                   "dedup": "sort of raw join results" if a.no_dense else
+                            "grouped bitmap join where it applies, else sort of raw join results",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "step_ms": [round(x, 3) for x in ms], "wall_s_timed_region": round(wall, 3)},
         "roofline": roofline,

@@ -71,6 +71,15 @@ typedef void (*hisa_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
  * iteration merge no longer rewrites all of full (Section 5.1's merge, which
  * the paper measures at 42-45% of CSPA time).  Set by hisa_config_default. */
 #define HISA_FLAG_LOG_FULL 4u
+/* Never use the grouped join with bitmap deduplication.  By default, an IDB
+ * relation whose only writer in iterations >= 2 is one binary join of its
+ * delta with an EDB relation (REACH's recursive rule) is stored with the
+ * column the join keeps first, and that join marks each kept value's results
+ * in a shared-memory bitmap over the active domain (b <= 18 bits), writing
+ * new already sorted and duplicate-free instead of sorting raw results
+ * (Algorithm 3 and Section 4.2's sort + unique in one pass).  Same results;
+ * not in batched runs. */
+#define HISA_FLAG_NO_DENSE 8u
 
 typedef struct {
   hisa_alloc_fn alloc;      /* NULL: cudaMallocAsync from a private pool */

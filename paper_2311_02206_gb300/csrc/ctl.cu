@@ -54,6 +54,12 @@ __global__ void k_ctl(CtlArgs a) {
       case kCtlNot:
         st->cnt[c.a] = st->cnt[c.b] ? 0 : 1;
         break;
+      case kCtlSwap: {
+        const DBuf t = st->buf[c.a];
+        st->buf[c.a] = st->buf[int(c.b)];
+        st->buf[int(c.b)] = t;
+        break;
+      }
       case kCtlZeroIfCnt:
         if (st->cnt[c.c] > 0) st->cnt[c.a] = 0;
         break;
@@ -124,7 +130,7 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
 
 const char* const kKernelNames[kKindCount] = {
     "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
-    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe"};
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_starts", "join_dense"};
 
 thread_local KernelTimer* g_timer = nullptr;
 thread_local uint64_t g_launches = 0;

@@ -1,0 +1,244 @@
+// Grouped join with dense-domain deduplication: the join of Algorithm 3 and
+// the sort + unique of new (Section 4.2) in one pass, for a join step whose
+// results are grouped by a column of the outer relation.
+//
+// Applies when the outer (a delta) is stored as (g, k) -- g the column the
+// result keeps, k the join column -- and the result is (g, o) with o the
+// inner relation's other column, as in REACH's recursive rule with Reach
+// stored target-first.  The outer tuples of one g are contiguous, so one CTA
+// takes a whole group: every outer (g, k) probes the inner index on k and
+// marks the inner run's o values in a shared-memory bitmap over the active
+// domain (2^b bits); the group's results are then the set bits in ascending
+// order.  Groups are taken in order and placed by a decoupled look-back, so
+// new comes out sorted and duplicate-free, and no raw result is ever written
+// to HBM (they were 15x the distinct ones on R-MAT 16).
+#pragma once
+#include "common.cuh"
+#include "join.cuh"
+
+namespace hisa {
+
+// Start position of every run of equal g = code >> b in a sorted code array,
+// compacted in order; cnt[out_cnt] = number of groups and out[groups] = n.
+struct GroupArgs {
+  DevState* st;
+  int in_buf, in_cnt;
+  int b;
+  int out_buf, out_cnt;   // u64 starts
+  int status_buf;         // u64 [tiles] look-back
+  int ctr;
+  int skip_mask, stage_bit;
+};
+
+struct DenseArgs {
+  DevState* st;
+  int outer_buf, outer_cnt;     // (g, k) codes, sorted
+  int groups_buf, groups_cnt;   // group starts (GroupArgs output)
+  int inner_buf, table_buf;     // inner codes (k, o) and their run index
+  int b;
+  int out_buf, out_cnt;         // results appended after cnt[out_cnt] (read only)
+  int total_cnt;                // receives the number of results
+  int raw_cnt;                  // cnt slot accumulating raw (pre-dedup) results
+  int status_buf;               // u64 [groups] look-back
+  int ctr;
+  int skip_mask, stage_bit;
+};
+
+constexpr int kGroupThreads = 256, kGroupItems = 8, kGroupTile = kGroupThreads * kGroupItems;
+constexpr int kDenseThreads = 256;
+constexpr int kDenseMaxBits = 18;   // bitmap of 2^18 bits = 32 KB of shared memory
+
+template <typename K>
+__global__ void __launch_bounds__(kGroupThreads) k_group_starts(GroupArgs a) {
+  __shared__ uint64_t s_scan[32];
+  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_tile;
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t n = st->cnt[a.in_cnt];
+  uint64_t* out = static_cast<uint64_t*>(st->buf[a.out_buf].ptr);
+  const uint64_t ocap = st->buf[a.out_buf].cap;
+  if (n == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->cnt[a.out_cnt] = 0;
+      if (ocap >= 1) out[0] = 0;
+    }
+    return;
+  }
+  const uint64_t ntiles = (n + kGroupTile - 1) / kGroupTile;
+  if (st->buf[a.status_buf].cap < ntiles) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicMax((unsigned long long*)&st->need[a.status_buf], (unsigned long long)ntiles);
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    return;
+  }
+  const K* in = static_cast<const K*>(st->buf[a.in_buf].ptr);
+  uint64_t* status = static_cast<uint64_t*>(st->buf[a.status_buf].ptr);
+  const uint32_t epoch = st->epoch;
+  const int tid = threadIdx.x;
+  while (true) {
+    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    const uint64_t i0 = tile * kGroupTile + uint64_t(tid) * kGroupItems;
+    uint32_t heads = 0;
+    uint64_t prev = i0 > 0 && i0 <= n ? uint64_t(in[i0 - 1]) >> a.b : ~0ull;
+#pragma unroll
+    for (int k = 0; k < kGroupItems; ++k) {
+      const uint64_t i = i0 + k;
+      if (i >= n) break;
+      const uint64_t g = uint64_t(in[i]) >> a.b;
+      if (i == 0 || g != prev) heads |= 1u << k;
+      prev = g;
+    }
+    uint64_t tile_heads;
+    const uint64_t excl = block_exclusive_sum<uint64_t>(__popc(heads), s_scan, &tile_heads);
+    if (tid < 32) {
+      const uint64_t base = lookback_warp(status, tile, tile_heads, epoch, &st->error);
+      if (tid == 0) s_base = base;
+    }
+    __syncthreads();
+    uint64_t w = s_base + excl;
+#pragma unroll
+    for (int k = 0; k < kGroupItems; ++k)
+      if (heads & (1u << k)) {
+        if (w < ocap) out[w] = i0 + k;
+        ++w;
+      }
+    if (tile == ntiles - 1 && tid == 0) {
+      const uint64_t total = s_base + tile_heads;
+      st->cnt[a.out_cnt] = total;
+      if (total + 1 <= ocap) out[total] = n;   // sentinel: end of the last group
+      else {
+        atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)(total + 1));
+        atomicOr(&st->overflow, 1u << a.stage_bit);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kDenseThreads) k_join_dense(DenseArgs a) {
+  extern __shared__ __align__(16) uint32_t s_bm[];   // 2^b bits
+  __shared__ uint64_t s_scan[32];
+  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_group;
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t ngroups = st->cnt[a.groups_cnt];
+  if (ngroups == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->cnt[a.total_cnt] = 0;
+    return;
+  }
+  if (st->buf[a.status_buf].cap < ngroups) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicMax((unsigned long long*)&st->need[a.status_buf], (unsigned long long)ngroups);
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    return;
+  }
+  const K* outer = static_cast<const K*>(st->buf[a.outer_buf].ptr);
+  const uint64_t* gs = static_cast<const uint64_t*>(st->buf[a.groups_buf].ptr);
+  const K* inner = static_cast<const K*>(st->buf[a.inner_buf].ptr);
+  const Slot* table = static_cast<const Slot*>(st->buf[a.table_buf].ptr);
+  const uint64_t tmask = st->buf[a.table_buf].cap - 1;
+  K* out = static_cast<K*>(st->buf[a.out_buf].ptr);
+  const uint64_t out0 = st->cnt[a.out_cnt];
+  const uint64_t ocap = st->buf[a.out_buf].cap;
+  uint64_t* status = static_cast<uint64_t*>(st->buf[a.status_buf].ptr);
+  const uint32_t epoch = st->epoch;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nwarps = kDenseThreads / 32;
+  const uint32_t vmask = a.b >= 32 ? 0xFFFFFFFFu : ((1u << a.b) - 1);
+  const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
+  const int wper = (nwords + kDenseThreads - 1) / kDenseThreads;   // words per thread, contiguous
+  for (int j = tid; j < nwords; j += kDenseThreads) s_bm[j] = 0;
+  unsigned long long raw = 0;
+  while (true) {
+    if (tid == 0) s_group = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+    __syncthreads();
+    const uint64_t gi = s_group;
+    if (gi >= ngroups) break;
+    const uint64_t s = gs[gi], e = gs[gi + 1];
+    const uint64_t gcode = uint64_t(outer[s]) >> a.b;   // (inst, g): the result's high part
+    // mark the inner runs of the group's outer tuples: a warp takes 32 outer
+    // tuples at once (32 probes in flight), then its lanes stride over the
+    // concatenation of their runs, each element finding its run by a binary
+    // search over the warp's inclusive run-length prefix
+    for (uint64_t ob = s + uint64_t(warp) * 32; ob < e; ob += uint64_t(nwarps) * 32) {
+      const uint64_t o = ob + lane;
+      uint64_t begin = 0;
+      uint32_t len = 0;
+      if (o < e) {
+        const K code = outer[o];
+        const uint32_t key = join_key(inst_of(code, a.b), colv(code, 1, a.b), a.b);
+        if (!probe(table, tmask, key, &begin, &len, &st->error)) len = 0;
+      }
+      uint32_t incl = len;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const uint32_t excl = incl - len;
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      if (lane == 0) raw += total;
+      for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        int owner = 0;   // lanes whose inclusive prefix is <= q
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const uint32_t v = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+          if (v <= q) owner += step;
+        }
+        const uint64_t ob_begin = __shfl_sync(0xffffffffu, begin, owner & 31);
+        const uint32_t ob_excl = __shfl_sync(0xffffffffu, excl, owner & 31);
+        if (q < total) {
+          const uint32_t v = uint32_t(inner[ob_begin + (q - ob_excl)]) & vmask;
+          atomicOr(&s_bm[v >> 5], 1u << (v & 31));
+        }
+      }
+    }
+    __syncthreads();
+    // the group's results: set bits, each thread owning `wper` consecutive words
+    const int j0 = tid * wper;
+    uint32_t mine = 0;
+    for (int q = 0; q < wper; ++q)
+      if (j0 + q < nwords) mine += __popc(s_bm[j0 + q]);
+    uint64_t gtotal;
+    const uint64_t excl = block_exclusive_sum<uint64_t>(mine, s_scan, &gtotal);
+    if (tid < 32) {
+      const uint64_t base = lookback_warp(status, gi, gtotal, epoch, &st->error);
+      if (tid == 0) s_base = base;
+    }
+    __syncthreads();
+    uint64_t w = out0 + s_base + excl;
+    for (int q = 0; q < wper; ++q) {
+      const int j = j0 + q;
+      if (j >= nwords) break;
+      uint32_t bits = s_bm[j];
+      s_bm[j] = 0;   // cleared for the next group (only this thread reads word j)
+      while (bits) {
+        const int t = __ffs(bits) - 1;
+        bits &= bits - 1;
+        if (w < ocap) out[w] = K((gcode << a.b) | uint64_t(uint32_t(j) * 32u + uint32_t(t)));
+        ++w;
+      }
+    }
+    if (gi == ngroups - 1 && tid == 0) {
+      const uint64_t total = s_base + gtotal;
+      st->cnt[a.total_cnt] = total;
+      if (out0 + total > ocap) {
+        atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)(out0 + total));
+        atomicOr(&st->overflow, 1u << a.stage_bit);
+      }
+    }
+    __syncthreads();
+  }
+  if (lane == 0 && raw) atomicAdd((unsigned long long*)&st->cnt[a.raw_cnt], raw);
+}
+
+}  // namespace hisa

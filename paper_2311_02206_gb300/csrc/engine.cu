@@ -157,7 +157,12 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.runs = nslots++;
   sc.total = nslots++;
   sc.tmp_cnt = nslots++;
+  sc.groups = new_slot(8);
+  sc.dense_status = new_slot(8);
+  sc.group_cnt = nslots++;
+  sc.raw_cnt = nslots++;
   slot_zero[sc.radix_status] = slot_zero[sc.setop_status] = slot_zero[sc.join_status] = true;
+  slot_zero[sc.dense_status] = true;
   if ((s = ensure(sc.empty, 1)) || (s = ensure(sc.hist, 8 * 256))) return s;
   return upload();
 }
@@ -282,8 +287,9 @@ hisa_status Engine::plan_variant(const hisa_rule& R, int delta_atom, std::vector
   for (int j = 0; j < nb; ++j)
     if (j != first) rest.push_back(j);
   // current tuple: its two columns and the variables they carry
-  int cur_var[2] = {int(R.body[first].var[0]), int(R.body[first].var[1])};
+  // the code's high half holds the relation's first stored column
   const Relation& r0 = rels[R.body[first].rel];
+  int cur_var[2] = {int(R.body[first].var[r0.order]), int(R.body[first].var[1 - r0.order])};
   int cur_slot, cur_cnt;
   if (delta_atom >= 0) {
     cur_slot = r0.delta;
@@ -332,13 +338,14 @@ hisa_status Engine::plan_variant(const hisa_rule& R, int delta_atom, std::vector
       const int ov = int(A.var[1 - c]);
       if (ov != jv && src_of[ov] >= 0)
         return ctx_fail(HISA_ERR_UNSUPPORTED, "join on two columns", nullptr);
-      // an IDB inner relation is read from full (column 0) or from its
-      // reverse-order mirror (column 1), indexed again every iteration
+      // an IDB inner relation is read from full (its first stored column) or
+      // from its reverse-order mirror, indexed again every iteration
       Relation& ir = rels[A.rel];
-      ir.need_idx[c] = true;
+      const int scol = ir.order == 0 ? c : 1 - c;
+      ir.need_idx[scol] = true;
       sp.has_inner = true;
       sp.inner_rel = int(A.rel);
-      sp.inner_col = c;
+      sp.inner_col = scol;
       sp.outer_kcol = src_of[jv] == kSrcOuter0 ? 0 : 1;
       src_of[jv] = src_of[jv];  // the key equals the outer value
       if (ov == jv) {
@@ -362,8 +369,9 @@ hisa_status Engine::plan_variant(const hisa_rule& R, int delta_atom, std::vector
       applied[f] = true;
     }
     if (rest.empty()) {
-      sp.proj0 = src_of[R.head.var[0]];
-      sp.proj1 = src_of[R.head.var[1]];
+      const int ho = rels[R.head.rel].order;
+      sp.proj0 = src_of[R.head.var[ho]];
+      sp.proj1 = src_of[R.head.var[1 - ho]];
       sp.out_rel = int(R.head.rel);
       sp.to_tmp = false;
       out.push_back(sp);
@@ -475,11 +483,75 @@ hisa_status Engine::compile() {
   for (size_t i = 0; i < rels.size(); ++i)
     if (rels[i].idb) idb.push_back(int(i));
   if (idb.empty()) return ctx_fail(HISA_ERR_INVALID_ARG, "no IDB relation", nullptr);
-  // semi-naive variants (Section 2): iteration 1 runs the rules without IDB
-  // atoms; later iterations run each rule once per IDB atom, that atom read
-  // from delta and the others from full
+  hisa_status s;
+  for (int r : idb) rels[r].order = 0;
+  if ((s = plan_all())) return s;
+  // grouped join with bitmap deduplication: an IDB relation R whose only
+  // writer in iterations >= 2 is one binary join of delta_R with an EDB
+  // relation is stored with the non-join column first, so delta's tuples
+  // of one kept value are contiguous (dense.cuh)
+  const bool dense_on = !(cfg.flags & HISA_FLAG_NO_DENSE) && !batched && b <= kDenseMaxBits;
+  auto writers = [&](int r) {
+    std::vector<const std::vector<StepPlan>*> w;
+    for (auto& v : planN)
+      if (!v.empty() && !v.back().to_tmp && v.back().out_rel == r) w.push_back(&v);
+    return w;
+  };
+  auto dense_ok = [&](const std::vector<StepPlan>& v, int r) {
+    if (v.size() != 1) return false;
+    const StepPlan& sp = v[0];
+    return sp.out_rel == r && sp.outer_slot == rels[r].delta && sp.has_inner && !rels[sp.inner_rel].idb &&
+           sp.nfilt == 0 && sp.outer_kcol == 1 && sp.proj0 == kSrcOuter0 && sp.proj1 == kSrcOther;
+  };
+  bool reorder = false;
+  if (dense_on)
+    for (int r : idb) {
+      auto w = writers(r);
+      if (w.size() != 1 || w[0]->size() != 1) continue;
+      const StepPlan& sp = (*w[0])[0];
+      if (sp.outer_slot != rels[r].delta || !sp.has_inner || rels[sp.inner_rel].idb || sp.nfilt) continue;
+      if (sp.outer_kcol == 0) {   // join column first in (c0, c1): store (c1, c0)
+        rels[r].order = 1;
+        reorder = true;
+      }
+    }
+  if (reorder && (s = plan_all())) return s;
+  for (int r : idb) {
+    auto w = writers(r);
+    const bool ok = dense_on && w.size() == 1 && dense_ok(*w[0], r);
+    if (!ok && rels[r].order) {   // the reordered plan does not fit: back to (c0, c1)
+      rels[r].order = 0;
+      if ((s = plan_all())) return s;
+    }
+  }
+  for (auto& v : planN)
+    for (auto& sp : v) sp.dense = false;
+  if (dense_on)
+    for (int r : idb) {
+      auto w = writers(r);
+      if (w.size() == 1 && dense_ok(*w[0], r)) {
+        for (auto& v : planN)
+          if (&v == w[0]) v[0].dense = true;
+      }
+    }
+  // log-structured full where nothing probes full (it is only differenced
+  // and merged): REACH and SG, not CSPA's inner IDB atoms nor batched runs
+  for (int r : idb) {
+    Relation& R = rels[r];
+    R.log = (cfg.flags & HISA_FLAG_LOG_FULL) && !batched && !R.need_idx[0] && !R.need_idx[1];
+  }
+  compiled = true;
+  graph_stale = true;
+  return HISA_OK;
+}
+
+// Semi-naive variants (Section 2): iteration 1 runs the rules without IDB
+// atoms; later iterations run each rule once per IDB atom, that atom read
+// from delta and the others from full.
+hisa_status Engine::plan_all() {
   plan1.clear();
   planN.clear();
+  for (auto& r : rels) r.need_idx[0] = r.need_idx[1] = false;
   for (auto& R : rules) {
     std::vector<int> idb_atoms;
     for (uint32_t j = 0; j < R.n_body; ++j)
@@ -497,14 +569,6 @@ hisa_status Engine::compile() {
       }
     }
   }
-  // log-structured full where nothing probes full (it is only differenced
-  // and merged): REACH and SG, not CSPA's inner IDB atoms nor batched runs
-  for (int r : idb) {
-    Relation& R = rels[r];
-    R.log = (cfg.flags & HISA_FLAG_LOG_FULL) && !batched && !R.need_idx[0] && !R.need_idx[1];
-  }
-  compiled = true;
-  graph_stale = true;
   return HISA_OK;
 }
 
@@ -626,6 +690,21 @@ void Engine::emit_idb_index(std::vector<Op>& ops) {
   }
 }
 
+void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp) {
+  const Relation& ir = rels[sp.inner_rel];
+  const Relation& hr = rels[sp.out_rel];
+  Op g{};
+  g.kind = Op::GROUPS;
+  g.groups = GroupArgs{dst, sp.outer_slot, sp.outer_cnt, b, sc.groups, sc.group_cnt, sc.join_status, 3, 1, 0};
+  ops.push_back(g);
+  Op d{};
+  d.kind = Op::DENSE;
+  d.dense = DenseArgs{dst, sp.outer_slot, sp.outer_cnt, sc.groups, sc.group_cnt,
+                      sp.inner_col == 0 ? ir.base : ir.rev, ir.table[sp.inner_col], b,
+                      hr.fresh, hr.fresh, sc.total, sc.raw_cnt, sc.dense_status, 4, 1, 0};
+  ops.push_back(d);
+}
+
 // Join stage of one iteration: clear new, run every variant, sort each new.
 void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepPlan>>& plans, bool idb_inner) {
   Op c{};
@@ -636,6 +715,7 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
     c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, rels[r].fresh, 0};
     c.ctl.cmd[c.ctl.n++] = {kCtlZeroSmall, rels[r].hist, 8 * 256};
   }
+  c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, sc.raw_cnt, 0};
   ops.push_back(c);
   if (idb_inner) emit_idb_index(ops);
   for (auto& v : plans) {
@@ -647,9 +727,32 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
       t.ctl.cmd[t.ctl.n++] = {kCtlSetCnt, sc.tmp_cnt, 0};
       ops.push_back(t);
     }
-    for (auto& sp : v) emit_join(ops, sp);
+    for (auto& sp : v) {
+      if (sp.dense) emit_dense(ops, sp);
+      else emit_join(ops, sp);
+    }
   }
-  for (int r : idb) emit_sort(ops, rels[r].fresh, rels[r].fresh_alt, rels[r].fresh, rels[r].hist, 1, 0);
+  // sort each new, unless every writer of it is a dense join (sorted and
+  // duplicate-free already); the sorted new always ends in `fresh`
+  for (int r : idb) {
+    bool any = false, all_dense = true;
+    for (auto& v : plans)
+      if (!v.empty() && !v.back().to_tmp && v.back().out_rel == r) {
+        any = true;
+        all_dense = all_dense && v.size() == 1 && v[0].dense;
+      }
+    if (any && all_dense) continue;
+    const Relation& R = rels[r];
+    emit_sort(ops, R.fresh, R.fresh_alt, R.fresh, R.hist, 1, 0);
+    if (passes & 1) {
+      Op w{};
+      w.kind = Op::CTL;
+      w.ctl.st = dst;
+      w.ctl.skip_mask = 1;
+      w.ctl.cmd[w.ctl.n++] = {kCtlSwap, R.fresh, R.fresh_alt, 0};
+      ops.push_back(w);
+    }
+  }
 }
 
 // LSD passes ping-ponging between `in` and `alt`; the result lands in `in`
@@ -732,7 +835,7 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
   for (int r : idb) {
     const Relation& R = rels[r];
     if (R.log) {
-      const int sorted_new = (passes & 1) ? R.fresh_alt : R.fresh;
+      const int sorted_new = R.fresh;
       emit_level_merge(ops, R, false);
       // large new: difference + merge against the large level (commit swaps it)
       Op big{};
@@ -787,7 +890,7 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
     a.st = dst;
     a.a_buf = R.full;
     a.a_cnt = R.full;
-    a.b_buf = (passes & 1) ? R.fresh_alt : R.fresh;
+    a.b_buf = R.fresh;   // sorted new (emit_head leaves it there)
     a.b_cnt = R.fresh;
     a.split_buf = sc.split;
     a.status_buf = sc.setop_status;
@@ -835,6 +938,8 @@ hisa_status Engine::exec_t(const std::vector<Op>& ops) {
       case Op::ZERO: launch_zero(o.zero, grid, stream); break;
       case Op::SWAP: launch_swap<K>(o.swap, grid, stream); break;
       case Op::DIFF: launch_diff<K>(o.diff, grid, stream); break;
+      case Op::GROUPS: launch_group_starts<K>(o.groups, grid, stream); break;
+      case Op::DENSE: launch_join_dense<K>(o.dense, grid, stream); break;
     }
   }
   return check_launch("kernel launch");
@@ -1018,6 +1123,9 @@ hisa_status Engine::regrow() {
   }
   // next iterations: delta is the outer relation of the joins; full + new is merged
   if ((s = ensure(sc.offs, delta_cap + 1)) || (s = ensure(sc.join_status, delta_cap / kJoinTile + 2))) return s;
+  if ((s = ensure(sc.groups, delta_cap + 2)) ||
+      (s = ensure(sc.dense_status, std::min<uint64_t>(delta_cap, 1ull << (b + inst_bits)) + 2)))
+    return s;
   if ((s = ensure(sc.split, (full_cap + std::max(new_cap, delta_cap)) / ks + 2)) ||
       (s = ensure(sc.setop_status,
                   std::max((full_cap + std::max(new_cap, delta_cap)) / ks, new_cap / kDiffTile) + 2)))
@@ -1094,6 +1202,10 @@ hisa_status Engine::init_run_state() {
     }
   }
   hs.cnt[sc.tmp_cnt] = 0;
+  hs.cnt[sc.raw_cnt] = hs.cnt[sc.group_cnt] = 0;
+  if ((s = ensure(sc.groups, 4 * nedb + 2)) ||
+      (s = ensure(sc.dense_status, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)))
+    return s;
   if ((s = ensure(sc.radix_status, (4 * nedb / kt + 2) * 256)) || (s = ensure(sc.offs, 4 * nedb + 1)) ||
       (s = ensure(sc.join_status, 4 * nedb / kJoinTile + 2)) || (s = ensure(sc.starts, 4 * nedb / kJoinChunk + 2)) ||
       (s = ensure(sc.split, 8 * nedb / 2048 + 2)) || (s = ensure(sc.setop_status, 8 * nedb / 2048 + 2)) ||
@@ -1160,7 +1272,18 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
           const Relation& R = rels[idb[i]];
           const double nn = double(hs.cnt[R.fresh]), nd = double(hs.cnt[R.delta]);
           const double m = double(m_prev[i]), dp = double(d_prev[i]);
-          kstat[kKRadixPass].bytes += passes * 2.0 * nn * kb;
+          bool dense = false;
+          for (auto& v : planN)
+            if (!first && v.size() == 1 && v[0].dense && v[0].out_rel == idb[i]) dense = true;
+          if (dense) {
+            // group starts: read delta, write starts; dense join: read delta,
+            // probe, read the inner runs (raw results), write new
+            const double raw = double(hs.cnt[sc.raw_cnt]);
+            kstat[kKGroups].bytes += dp * kb + 8.0 * double(hs.cnt[sc.group_cnt]);
+            kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + nn * kb;
+          } else {
+            kstat[kKRadixPass].bytes += passes * 2.0 * nn * kb;
+          }
           if (R.log && hs.cnt[R.bigf]) {
             // small level folded in, then new merged into the large level
             const double lp = double(l_prev[i]);
@@ -1179,8 +1302,10 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
           } else if (nn > 0) {
             kstat[kKSetop].bytes += (m + nn) * kb + (m + 2.0 * nd) * kb;
           }
-          kstat[kKJoinWrite].bytes += 2.0 * nn * kb + dp * (kb + 8.0);
-          kstat[kKJoinCount].bytes += dp * (kb + 8.0 + 16.0);
+          if (!dense) {
+            kstat[kKJoinWrite].bytes += 2.0 * nn * kb + dp * (kb + 8.0);
+            kstat[kKJoinCount].bytes += dp * (kb + 8.0 + 16.0);
+          }
           // inner-relation upkeep at the head of this iteration
           if (!first && R.need_idx[1]) {
             kstat[kKSwap].bytes += 2.0 * dp * kb;
@@ -1399,12 +1524,40 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
   uint32_t* d1 = cols[1];
   void *t0 = nullptr, *t1 = nullptr;
   hisa_status s;
+  int src = r.idb ? r.full : r.base;
+  if (r.idb && r.order == 1) {
+    // stored (c1, c0): exchange the columns and sort, so the caller gets the
+    // lexicographic order of the declared columns
+    const int kt = wide ? radix_tile<uint64_t>() : radix_tile<uint32_t>();
+    if ((s = ensure(sc.tmp_a, size)) || (s = ensure(sc.tmp_b, size)) ||
+        (s = ensure(sc.radix_status, (size / kt + 2) * kRadixDigits)))
+      return s;
+    if ((s = upload())) return s;
+    std::vector<Op> ops;
+    Op w{};
+    w.kind = Op::SWAP;
+    w.swap = SwapArgs{dst, r.full, r.full, sc.tmp_a, sc.tmp_cnt, b, 0, 0};
+    ops.push_back(w);
+    Op z{};
+    z.kind = Op::CTL;
+    z.ctl.st = dst;
+    z.ctl.cmd[z.ctl.n++] = {kCtlZeroSmall, sc.hist, 8 * 256, 0};
+    ops.push_back(z);
+    Op h{};
+    h.kind = Op::HIST;
+    h.hist = RadixHistArgs{dst, sc.tmp_a, sc.tmp_cnt, sc.hist, passes, 0};
+    ops.push_back(h);
+    emit_sort(ops, sc.tmp_a, sc.tmp_b, sc.tmp_cnt, sc.hist, 0, 0);
+    if ((s = exec(ops)) || (s = download())) return s;
+    if (hs.overflow || hs.error) return ctx_fail(HISA_ERR_CUDA, "read_relation: re-sort", nullptr);
+    src = (passes & 1) ? sc.tmp_b : sc.tmp_a;
+  }
   if (!on_device) {
     if ((s = dev_alloc(size * 4, &t0)) || (s = dev_alloc(size * 4, &t1))) return s;
     d0 = static_cast<uint32_t*>(t0);
     d1 = static_cast<uint32_t*>(t1);
   }
-  DecodeArgs a{dst, r.idb ? r.full : r.base, 0, d0, d1, b, 0, 0, size};
+  DecodeArgs a{dst, src, 0, d0, d1, b, 0, 0, size};
   if (wide) launch_decode<uint64_t>(a, grid, stream);
   else launch_decode<uint32_t>(a, grid, stream);
   if ((s = check_launch("decode"))) return s;

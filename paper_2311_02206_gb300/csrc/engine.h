@@ -39,6 +39,7 @@ struct Relation {
   // l1 the small one that absorbs each delta; newp = new minus the large level;
   // gate = |l1| when l1 is due to be merged into full, else 0
   bool log = false;
+  int order = 0;   // storage order of an IDB relation: 0 = (c0, c1), 1 = (c1, c0)
   int l1 = -1, l1_next = -1, newp = -1, gate = -1;
   int bigf = -1, smallf = -1;   // this iteration merges new straight into full / probes it
   int history = -1;                 // |delta_k| per iteration
@@ -54,10 +55,11 @@ struct StepPlan {
   int nfilt, fop[2], fa[2], fb[2];
   bool to_tmp;
   int out_rel;
+  bool dense;   // grouped join with bitmap deduplication (dense.cuh)
 };
 
 struct Op {
-  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF } kind;
+  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, GROUPS, DENSE } kind;
   CtlArgs ctl;
   JoinArgs join;
   RadixPassArgs pass;
@@ -69,11 +71,15 @@ struct Op {
   ZeroArgs zero;
   SwapArgs swap;
   DiffArgs diff;
+  GroupArgs groups;
+  DenseArgs dense;
 };
 
 struct Scratch {
   int empty, hist, radix_status, split, setop_status, offs, join_status, starts, tmp_a, tmp_b;
   int runs, total, tmp_cnt;   // count-only slots
+  int groups, dense_status;   // group starts of a delta and the dense join's look-back
+  int group_cnt, raw_cnt;     // count-only slots
 };
 
 // One request of the serving loop: the EDB tuples of an independent instance.
@@ -132,6 +138,8 @@ class Engine {
   hisa_status compile();
   hisa_status plan_variant(const hisa_rule& R, int delta_atom, std::vector<StepPlan>& out);
   void emit_join(std::vector<Op>& ops, const StepPlan& sp);
+  void emit_dense(std::vector<Op>& ops, const StepPlan& sp);
+  hisa_status plan_all();
   void emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepPlan>>& plans, bool idb_inner);
   void emit_idb_index(std::vector<Op>& ops);
   void emit_sort(std::vector<Op>& ops, int in, int alt, int cnt, int hist, int skip_mask, int stage_bit);

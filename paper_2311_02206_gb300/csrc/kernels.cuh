@@ -6,6 +6,7 @@
 #include "join.cuh"
 #include "radix.cuh"
 #include "setops.cuh"
+#include "dense.cuh"
 #include <vector>
 
 namespace hisa {
@@ -25,6 +26,7 @@ enum : int {
                      //   c = (L << 32) | (F << 16) | r
   kCtlBigFlag,       // cnt[a] = (cnt[b] * (c & 0xFFFF) > cnt[c >> 16]) ? 1 : 0
   kCtlNot,           // cnt[a] = cnt[b] ? 0 : 1
+  kCtlSwap,          // exchange buffers a and b (counts untouched)
   kCtlZeroIfCnt,     // if cnt[c] > 0: cnt[a] = 0
 };
 
@@ -108,7 +110,7 @@ struct SwapArgs {
 
 enum KernelKind : int {
   kKEncode, kKDecode, kKRuns, kKHist, kKRadixPass, kKSetopPartition, kKSetop, kKIndex,
-  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKindCount
+  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKindCount
 };
 extern const char* const kKernelNames[kKindCount];
 
@@ -159,6 +161,8 @@ template <typename K> void launch_index(const IndexArgs& a, const Grid& g, cudaS
 template <typename K> void launch_count_runs(const RunsArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_swap(const SwapArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_diff(const DiffArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_group_starts(const GroupArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_hist(const InstArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_bounds(const InstArgs& a, const Grid& g, cudaStream_t s);
 void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStream_t s);

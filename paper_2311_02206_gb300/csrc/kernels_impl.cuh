@@ -178,6 +178,35 @@ void launch_diff(const DiffArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKDiffProbe, s, (k_diff_probe<K><<<g.setop, kDiffThreads, 0, s>>>(a)));
 }
 template <typename K>
+void launch_group_starts(const GroupArgs& a, const Grid& g, cudaStream_t s) {
+  CtlArgs c{};
+  c.st = a.st;
+  c.skip_mask = a.skip_mask;
+  c.n = 2;
+  c.cmd[0] = {kCtlEpoch, 0, 0};
+  c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
+  launch_ctl(c, s);
+  HISA_LAUNCH(kKGroups, s, (k_group_starts<K><<<g.setop, kGroupThreads, 0, s>>>(a)));
+}
+template <typename K>
+void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s) {
+  CtlArgs c{};
+  c.st = a.st;
+  c.skip_mask = a.skip_mask;
+  c.n = 2;
+  c.cmd[0] = {kCtlEpoch, 0, 0};
+  c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
+  launch_ctl(c, s);
+  const size_t smem = size_t(a.b >= 5 ? (1u << (a.b - 5)) : 1u) * 4;
+  HISA_LAUNCH(kKJoinDense, s, (k_join_dense<K><<<g.join, kDenseThreads, smem, s>>>(a)));
+  CtlArgs d{};
+  d.st = a.st;
+  d.skip_mask = a.skip_mask;
+  d.n = 1;
+  d.cmd[0] = {kCtlAddCnt, a.out_cnt, a.total_cnt};
+  launch_ctl(d, s);
+}
+template <typename K>
 void launch_index(const IndexArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKIndex, s, (k_index_build<K><<<g.small, 256, 0, s>>>(a)));
 }
@@ -217,6 +246,8 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_count_runs<K>(const RunsArgs&, const Grid&, cudaStream_t);        \
   template void launch_swap<K>(const SwapArgs&, const Grid&, cudaStream_t);              \
   template void launch_diff<K>(const DiffArgs&, const Grid&, cudaStream_t);              \
+  template void launch_group_starts<K>(const GroupArgs&, const Grid&, cudaStream_t);     \
+  template void launch_join_dense<K>(const DenseArgs&, const Grid&, cudaStream_t);       \
   template void launch_radix_hist<K>(const RadixHistArgs&, const Grid&, cudaStream_t);   \
   template void launch_radix_pass<K>(const RadixPassArgs&, const Grid&, cudaStream_t);   \
   template void launch_setop<K>(const SetopArgs&, const Grid&, cudaStream_t);            \

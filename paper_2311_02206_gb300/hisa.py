@@ -21,6 +21,7 @@ HISA_OK = 0
 FLAG_GRAPH = 1
 FLAG_PHASE_TIMES = 2
 FLAG_LOG_FULL = 4
+FLAG_NO_DENSE = 8
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

@@ -23,9 +23,11 @@ def _lib():
 
 
 def modes():
-    """host-driven, graph-captured, and both with the log-structured full"""
+    """host-driven, graph-captured, both with the log-structured full, and
+    graph-captured without the grouped bitmap join"""
     from paper_2311_02206_gb300 import hisa
-    return [0, hisa.FLAG_GRAPH, hisa.FLAG_LOG_FULL, hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL]
+    return [0, hisa.FLAG_GRAPH, hisa.FLAG_LOG_FULL, hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL,
+            hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE]
 
 
 @pytest.mark.parametrize("seed", range(40))
@@ -152,8 +154,8 @@ def test_sg_random_dag(seed):
         assert_same(rels, counts, ref)
 
 
-@pytest.mark.parametrize("log_full", [False, True])
-def test_reach_rmat_full_size_golden_and_sampled(log_full):
+@pytest.mark.parametrize("log_full,no_dense", [(False, True), (True, True), (True, False)])
+def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense):
     """REACH on R-MAT scale 16 / 2**19 edges, in the launch configuration the
     benchmark times: total size, delta counts and fingerprint against the
     oracle's stored values, and 16 sampled target columns element by element."""
@@ -163,7 +165,8 @@ def test_reach_rmat_full_size_golden_and_sampled(log_full):
     g = json.load(open(path))
     from paper_2311_02206_gb300 import hisa
     s, d = workloads.config_reach_rmat()
-    with hisa.Context(flags=hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0)) as ctx:
+    flags = hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0) | (hisa.FLAG_NO_DENSE if no_dense else 0)
+    with hisa.Context(flags=flags) as ctx:
         ctx.program(*oracle.REACH)
         ctx.load_tuples("Edge", s, d)
         ctx.run()
