@@ -46,6 +46,7 @@ struct DenseArgs {
 
 constexpr int kGroupThreads = 256, kGroupItems = 8, kGroupTile = kGroupThreads * kGroupItems;
 constexpr int kDenseThreads = 256;
+constexpr int kDenseCtasPerSm = 8;   // latency-bound (L2 probes and run reads): full occupancy
 constexpr int kDenseMaxBits = 18;   // bitmap of 2^18 bits = 32 KB of shared memory
 
 template <typename K>
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_starts(GroupArgs a) {
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kDenseThreads) k_join_dense(DenseArgs a) {
+__global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_join_dense(DenseArgs a) {
   extern __shared__ __align__(16) uint32_t s_bm[];   // 2^b bits
   __shared__ uint64_t s_scan[32];
   __shared__ uint64_t s_base;
@@ -198,7 +199,10 @@ __global__ void __launch_bounds__(kDenseThreads) k_join_dense(DenseArgs a) {
         const uint32_t ob_excl = __shfl_sync(0xffffffffu, excl, owner & 31);
         if (q < total) {
           const uint32_t v = uint32_t(inner[ob_begin + (q - ob_excl)]) & vmask;
-          atomicOr(&s_bm[v >> 5], 1u << (v & 31));
+          const uint32_t bit = 1u << (v & 31);
+          // most values are marked already (many outer tuples share inner
+          // values): a plain read skips the serialised same-word atomics
+          if (!(s_bm[v >> 5] & bit)) atomicOr(&s_bm[v >> 5], bit);
         }
       }
     }
