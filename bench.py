@@ -54,9 +54,10 @@ def _args():
     ap.add_argument("--impl", choices=["hisa", "reference"], default="hisa")
     ap.add_argument("--instances", type=int, default=4096, help="batch5: number of instances")
     ap.add_argument("--budget-gb", type=float, default=100.0, help="batch5: serving memory budget")
-    ap.add_argument("--workload", choices=["rmat16", "rmat13", "er1000", "sg20k", "sg20k-literal", "cspa", "batch5"],
+    ap.add_argument("--workload", choices=["rmat16", "rmat15", "rmat13", "er1000", "sg20k", "sg20k-literal", "cspa",
+                                           "batch5"],
                     default="rmat16",
-                    help="rmat16: the benchmark workload; rmat13: a smaller R-MAT graph for profiler captures")
+                    help="rmat16: the benchmark workload; rmat15/rmat13: smaller R-MAT graphs for profiler captures")
     ap.add_argument("--single-full", action="store_true",
                     help="keep full as one sorted array (without HISA_FLAG_LOG_FULL)")
     ap.add_argument("--no-dense", action="store_true",
@@ -78,6 +79,9 @@ def _workload(name):
         desc = ("REACH (2 rules) on R-MAT scale 16: 65,536 nodes, 2^19 distinct edges, "
                 "(a,b,c,d)=(.57,.19,.19,.05), no self-loops, seed 3")
         return s, d, desc, 65536
+    if name == "rmat15":
+        s, d = workloads.rmat_graph(15, 1 << 18, 3)
+        return s, d, "REACH (2 rules) on R-MAT scale 15: 32,768 nodes, 2^18 distinct edges, seed 3", 1 << 15
     if name == "rmat13":
         s, d = workloads.rmat_graph(13, 1 << 16, 3)
         return s, d, "REACH (2 rules) on R-MAT scale 13: 8,192 nodes, 2^16 distinct edges, seed 3", 1 << 13
@@ -233,6 +237,8 @@ KERNEL_SOURCES = {   # the sources a kernel's counters depend on
     "setop_diff_merge": ["setops.cuh", "common.cuh"],
     "join_write": ["join.cuh", "common.cuh"],
     "join_count": ["join.cuh", "common.cuh"],
+    "join_dense_mark": ["dense.cuh", "join.cuh", "common.cuh"],
+    "setop_diff_probe": ["setops.cuh", "common.cuh"],
 }
 
 
@@ -291,7 +297,7 @@ def run_hisa(a):
     torch.cuda.set_device(local)
     _init_pg(world)
     build.build()
-    reach = a.workload in ("rmat16", "rmat13", "er1000")
+    reach = a.workload in ("rmat16", "rmat15", "rmat13", "er1000")
     if reach:
         s, d, desc, nodes = _workload(a.workload)
         prog, edb, sample = oracle.REACH, {"Edge": (s, d)}, None
@@ -451,7 +457,7 @@ def run_reference(a):
     world, rank, _ = _dist()
     if rank != 0:
         return
-    if a.workload not in ("rmat16", "rmat13", "er1000"):
+    if a.workload not in ("rmat16", "rmat15", "rmat13", "er1000"):
         return run_reference_program(a)
     s, d, desc, nodes = _workload(a.workload)
     rng = np.random.default_rng(11)

@@ -9,9 +9,11 @@
 // takes a whole group: every outer (g, k) probes the inner index on k and
 // marks the inner run's o values in a shared-memory bitmap over the active
 // domain (2^b bits); the group's results are then the set bits in ascending
-// order.  Groups are taken in order and placed by a decoupled look-back, so
+// order.  Groups are placed by their offsets in group order, so
 // new comes out sorted and duplicate-free, and no raw result is ever written
-// to HBM (they were 15x the distinct ones on R-MAT 16).
+// to HBM (they were 8.5x the distinct ones on R-MAT 16).  Three launches:
+// mark (each group's bitmap and count, groups in any order), scan (offsets),
+// emit (each group's set bits at its offset).
 #pragma once
 #include "common.cuh"
 #include "join.cuh"
@@ -39,14 +41,15 @@ struct DenseArgs {
   int out_buf, out_cnt;         // results appended after cnt[out_cnt] (read only)
   int total_cnt;                // receives the number of results
   int raw_cnt;                  // cnt slot accumulating raw (pre-dedup) results
-  int status_buf;               // u64 [groups] look-back
+  int bm_buf;                   // u32 [groups][2^b / 32]: each group's bitmap
+  int offs_buf;                 // u64 [groups]: result count, then its offset
   int ctr;
   int skip_mask, stage_bit;
 };
 
 constexpr int kGroupThreads = 256, kGroupItems = 8, kGroupTile = kGroupThreads * kGroupItems;
-constexpr int kDenseThreads = 256;
-constexpr int kDenseCtasPerSm = 8;   // latency-bound (L2 probes and run reads): full occupancy
+constexpr int kDenseThreads = 128;
+constexpr int kDenseCtasPerSm = 16;   // latency-bound (L2 probes and run reads): full occupancy
 constexpr int kDenseMaxBits = 18;   // bitmap of 2^18 bits = 32 KB of shared memory
 
 template <typename K>
@@ -121,22 +124,26 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_starts(GroupArgs a) {
   }
 }
 
+// Phase 1: one group per CTA (taken in any order, so a large group delays
+// no other): mark the inner runs of the group's outer tuples -- a warp takes
+// 32 outer tuples at once (32 probes in flight), then its lanes stride over
+// the concatenation of their runs, each element finding its run by a binary
+// search over the warp's inclusive run-length prefix -- then store the
+// bitmap and its population count.
 template <typename K>
-__global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_join_dense(DenseArgs a) {
+__global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(DenseArgs a) {
   extern __shared__ __align__(16) uint32_t s_bm[];   // 2^b bits
   __shared__ uint64_t s_scan[32];
-  __shared__ uint64_t s_base;
   __shared__ uint32_t s_group;
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
   const uint64_t ngroups = st->cnt[a.groups_cnt];
-  if (ngroups == 0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->cnt[a.total_cnt] = 0;
-    return;
-  }
-  if (st->buf[a.status_buf].cap < ngroups) {
+  if (ngroups == 0) return;
+  const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
+  if (st->buf[a.bm_buf].cap < ngroups * uint64_t(nwords) || st->buf[a.offs_buf].cap < ngroups + 1) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      atomicMax((unsigned long long*)&st->need[a.status_buf], (unsigned long long)ngroups);
+      atomicMax((unsigned long long*)&st->need[a.bm_buf], (unsigned long long)(ngroups * uint64_t(nwords)));
+      atomicMax((unsigned long long*)&st->need[a.offs_buf], (unsigned long long)(ngroups + 1));
       atomicOr(&st->overflow, 1u << a.stage_bit);
     }
     return;
@@ -146,16 +153,11 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_join_dense(D
   const K* inner = static_cast<const K*>(st->buf[a.inner_buf].ptr);
   const Slot* table = static_cast<const Slot*>(st->buf[a.table_buf].ptr);
   const uint64_t tmask = st->buf[a.table_buf].cap - 1;
-  K* out = static_cast<K*>(st->buf[a.out_buf].ptr);
-  const uint64_t out0 = st->cnt[a.out_cnt];
-  const uint64_t ocap = st->buf[a.out_buf].cap;
-  uint64_t* status = static_cast<uint64_t*>(st->buf[a.status_buf].ptr);
-  const uint32_t epoch = st->epoch;
+  uint32_t* bm = static_cast<uint32_t*>(st->buf[a.bm_buf].ptr);
+  uint64_t* counts = static_cast<uint64_t*>(st->buf[a.offs_buf].ptr);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nwarps = kDenseThreads / 32;
   const uint32_t vmask = a.b >= 32 ? 0xFFFFFFFFu : ((1u << a.b) - 1);
-  const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
-  const int wper = (nwords + kDenseThreads - 1) / kDenseThreads;   // words per thread, contiguous
   for (int j = tid; j < nwords; j += kDenseThreads) s_bm[j] = 0;
   unsigned long long raw = 0;
   while (true) {
@@ -164,11 +166,6 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_join_dense(D
     const uint64_t gi = s_group;
     if (gi >= ngroups) break;
     const uint64_t s = gs[gi], e = gs[gi + 1];
-    const uint64_t gcode = uint64_t(outer[s]) >> a.b;   // (inst, g): the result's high part
-    // mark the inner runs of the group's outer tuples: a warp takes 32 outer
-    // tuples at once (32 probes in flight), then its lanes stride over the
-    // concatenation of their runs, each element finding its run by a binary
-    // search over the warp's inclusive run-length prefix
     for (uint64_t ob = s + uint64_t(warp) * 32; ob < e; ob += uint64_t(nwarps) * 32) {
       const uint64_t o = ob + lane;
       uint64_t begin = 0;
@@ -207,42 +204,86 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_join_dense(D
       }
     }
     __syncthreads();
-    // the group's results: set bits, each thread owning `wper` consecutive words
-    const int j0 = tid * wper;
+    // store the bitmap (coalesced) and clear it; count its bits
+    uint32_t* gbm = bm + gi * uint64_t(nwords);
     uint32_t mine = 0;
-    for (int q = 0; q < wper; ++q)
-      if (j0 + q < nwords) mine += __popc(s_bm[j0 + q]);
+    for (int j = tid; j < nwords; j += kDenseThreads) {
+      const uint32_t w = s_bm[j];
+      gbm[j] = w;
+      mine += __popc(w);
+      s_bm[j] = 0;
+    }
     uint64_t gtotal;
-    const uint64_t excl = block_exclusive_sum<uint64_t>(mine, s_scan, &gtotal);
-    if (tid < 32) {
-      const uint64_t base = lookback_warp(status, gi, gtotal, epoch, &st->error);
-      if (tid == 0) s_base = base;
-    }
-    __syncthreads();
-    uint64_t w = out0 + s_base + excl;
-    for (int q = 0; q < wper; ++q) {
-      const int j = j0 + q;
-      if (j >= nwords) break;
-      uint32_t bits = s_bm[j];
-      s_bm[j] = 0;   // cleared for the next group (only this thread reads word j)
-      while (bits) {
-        const int t = __ffs(bits) - 1;
-        bits &= bits - 1;
-        if (w < ocap) out[w] = K((gcode << a.b) | uint64_t(uint32_t(j) * 32u + uint32_t(t)));
-        ++w;
-      }
-    }
-    if (gi == ngroups - 1 && tid == 0) {
-      const uint64_t total = s_base + gtotal;
-      st->cnt[a.total_cnt] = total;
-      if (out0 + total > ocap) {
-        atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)(out0 + total));
-        atomicOr(&st->overflow, 1u << a.stage_bit);
-      }
-    }
+    block_exclusive_sum<uint64_t>(mine, s_scan, &gtotal);
+    if (tid == 0) counts[gi] = gtotal;
     __syncthreads();
   }
   if (lane == 0 && raw) atomicAdd((unsigned long long*)&st->cnt[a.raw_cnt], raw);
+}
+
+// Phase 2 (one CTA): counts -> exclusive offsets; total and capacity check.
+template <typename K>
+__global__ void k_dense_scan(DenseArgs a) {
+  __shared__ uint64_t s_scan[32];
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t ngroups = st->cnt[a.groups_cnt];
+  uint64_t* offs = static_cast<uint64_t*>(st->buf[a.offs_buf].ptr);
+  uint64_t carry = 0;
+  for (uint64_t c0 = 0; c0 < ngroups; c0 += blockDim.x) {
+    const uint64_t i = c0 + threadIdx.x;
+    const uint64_t v = i < ngroups ? offs[i] : 0;
+    uint64_t tot;
+    const uint64_t ex = block_exclusive_sum<uint64_t>(v, s_scan, &tot);
+    if (i < ngroups) offs[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    st->cnt[a.total_cnt] = carry;
+    const uint64_t out0 = st->cnt[a.out_cnt];
+    if (out0 + carry > st->buf[a.out_buf].cap) {
+      atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)(out0 + carry));
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+  }
+}
+
+// Phase 3: each group's set bits, in order, at its offset (groups in any order).
+template <typename K>
+__global__ void __launch_bounds__(kDenseThreads) k_dense_emit(DenseArgs a) {
+  __shared__ uint64_t s_scan[32];
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t ngroups = st->cnt[a.groups_cnt];
+  const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
+  const int wper = (nwords + kDenseThreads - 1) / kDenseThreads;   // words per thread, contiguous
+  const K* outer = static_cast<const K*>(st->buf[a.outer_buf].ptr);
+  const uint64_t* gs = static_cast<const uint64_t*>(st->buf[a.groups_buf].ptr);
+  const uint32_t* bm = static_cast<const uint32_t*>(st->buf[a.bm_buf].ptr);
+  const uint64_t* offs = static_cast<const uint64_t*>(st->buf[a.offs_buf].ptr);
+  K* out = static_cast<K*>(st->buf[a.out_buf].ptr) + st->cnt[a.out_cnt];
+  const int tid = threadIdx.x;
+  for (uint64_t gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
+    const uint64_t gcode = uint64_t(outer[gs[gi]]) >> a.b;   // (inst, g): the result's high part
+    const uint32_t* gbm = bm + gi * uint64_t(nwords);
+    const int j0 = tid * wper;
+    uint32_t mine = 0;
+    for (int q = 0; q < wper; ++q)
+      if (j0 + q < nwords) mine += __popc(gbm[j0 + q]);
+    uint64_t gtotal;
+    const uint64_t excl = block_exclusive_sum<uint64_t>(mine, s_scan, &gtotal);
+    uint64_t w = offs[gi] + excl;
+    for (int q = 0; q < wper; ++q) {
+      const int j = j0 + q;
+      if (j >= nwords) break;
+      uint32_t bits = gbm[j];
+      while (bits) {
+        const int t = __ffs(bits) - 1;
+        bits &= bits - 1;
+        out[w++] = K((gcode << a.b) | uint64_t(uint32_t(j) * 32u + uint32_t(t)));
+      }
+    }
+  }
 }
 
 }  // namespace hisa

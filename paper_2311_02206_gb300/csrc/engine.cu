@@ -159,6 +159,7 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.tmp_cnt = nslots++;
   sc.groups = new_slot(8);
   sc.dense_status = new_slot(8);
+  sc.dense_bm = new_slot(4);
   sc.group_cnt = nslots++;
   sc.raw_cnt = nslots++;
   slot_zero[sc.radix_status] = slot_zero[sc.setop_status] = slot_zero[sc.join_status] = true;
@@ -701,7 +702,7 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp) {
   d.kind = Op::DENSE;
   d.dense = DenseArgs{dst, sp.outer_slot, sp.outer_cnt, sc.groups, sc.group_cnt,
                       sp.inner_col == 0 ? ir.base : ir.rev, ir.table[sp.inner_col], b,
-                      hr.fresh, hr.fresh, sc.total, sc.raw_cnt, sc.dense_status, 4, 1, 0};
+                      hr.fresh, hr.fresh, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0};
   ops.push_back(d);
 }
 
@@ -1276,11 +1277,15 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
           for (auto& v : planN)
             if (!first && v.size() == 1 && v[0].dense && v[0].out_rel == idb[i]) dense = true;
           if (dense) {
-            // group starts: read delta, write starts; dense join: read delta,
-            // probe, read the inner runs (raw results), write new
-            const double raw = double(hs.cnt[sc.raw_cnt]);
-            kstat[kKGroups].bytes += dp * kb + 8.0 * double(hs.cnt[sc.group_cnt]);
-            kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + nn * kb;
+            // group starts: read delta, write starts; mark: read delta, probe,
+            // read the inner runs (raw results), write the bitmaps; scan:
+            // counts; emit: read the bitmaps, write new
+            const double raw = double(hs.cnt[sc.raw_cnt]), ng = double(hs.cnt[sc.group_cnt]);
+            const double bmb = ng * double(b >= 5 ? (1u << (b - 5)) : 1u) * 4.0;
+            kstat[kKGroups].bytes += dp * kb + 8.0 * ng;
+            kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + bmb;
+            kstat[kKDenseScan].bytes += 16.0 * ng;
+            kstat[kKDenseEmit].bytes += bmb + nn * kb;
           } else {
             kstat[kKRadixPass].bytes += passes * 2.0 * nn * kb;
           }

@@ -78,7 +78,8 @@ struct Op {
 struct Scratch {
   int empty, hist, radix_status, split, setop_status, offs, join_status, starts, tmp_a, tmp_b;
   int runs, total, tmp_cnt;   // count-only slots
-  int groups, dense_status;   // group starts of a delta and the dense join's look-back
+  int groups, dense_status;   // group starts of a delta and the dense join's per-group counts/offsets
+  int dense_bm;               // the dense join's per-group bitmaps
   int group_cnt, raw_cnt;     // count-only slots
 };
 

@@ -110,7 +110,7 @@ struct SwapArgs {
 
 enum KernelKind : int {
   kKEncode, kKDecode, kKRuns, kKHist, kKRadixPass, kKSetopPartition, kKSetop, kKIndex,
-  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKindCount
+  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKindCount
 };
 extern const char* const kKernelNames[kKindCount];
 
