@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_starts(GroupArgs a) {
 template <typename K>
 __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(DenseArgs a) {
   extern __shared__ __align__(16) uint32_t s_bm[];   // 2^b bits
-  __shared__ uint64_t s_scan[32];
+  __shared__ unsigned long long s_cnt;
   __shared__ uint32_t s_group;
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
   constexpr int nwarps = kDenseThreads / 32;
   const uint32_t vmask = a.b >= 32 ? 0xFFFFFFFFu : ((1u << a.b) - 1);
   for (int j = tid; j < nwords; j += kDenseThreads) s_bm[j] = 0;
+  if (tid == 0) s_cnt = 0;
   unsigned long long raw = 0;
   while (true) {
     if (tid == 0) s_group = atomicAdd(&st->tile_ctr[a.ctr], 1u);
@@ -213,10 +214,14 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
       mine += __popc(w);
       s_bm[j] = 0;
     }
-    uint64_t gtotal;
-    block_exclusive_sum<uint64_t>(mine, s_scan, &gtotal);
-    if (tid == 0) counts[gi] = gtotal;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0 && mine) atomicAdd(&s_cnt, (unsigned long long)mine);
     __syncthreads();
+    if (tid == 0) {
+      counts[gi] = s_cnt;
+      s_cnt = 0;   // read again only after the next group's first barrier
+    }
   }
   if (lane == 0 && raw) atomicAdd((unsigned long long*)&st->cnt[a.raw_cnt], raw);
 }
@@ -248,41 +253,65 @@ __global__ void k_dense_scan(DenseArgs a) {
   }
 }
 
-// Phase 3: each group's set bits, in order, at its offset (groups in any order).
+// Phase 3: each group's set bits, in order, at its offset (groups in any
+// order).  Each warp owns a contiguous quarter of the group's bitmap: a first
+// coalesced pass counts its bits (the warps' counts give their bases), a
+// second pass takes 32 words per step, stages the step's values in shared
+// memory and writes them out coalesced.
 template <typename K>
 __global__ void __launch_bounds__(kDenseThreads) k_dense_emit(DenseArgs a) {
-  __shared__ uint64_t s_scan[32];
+  constexpr int nwarps = kDenseThreads / 32;
+  __shared__ K s_stage[nwarps][32 * 32];          // one 32-word step of a warp
+  __shared__ uint32_t s_wtot[nwarps];
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
   const uint64_t ngroups = st->cnt[a.groups_cnt];
   const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
-  const int wper = (nwords + kDenseThreads - 1) / kDenseThreads;   // words per thread, contiguous
+  const int wrange = (nwords + nwarps - 1) / nwarps;        // words per warp
   const K* outer = static_cast<const K*>(st->buf[a.outer_buf].ptr);
   const uint64_t* gs = static_cast<const uint64_t*>(st->buf[a.groups_buf].ptr);
   const uint32_t* bm = static_cast<const uint32_t*>(st->buf[a.bm_buf].ptr);
   const uint64_t* offs = static_cast<const uint64_t*>(st->buf[a.offs_buf].ptr);
   K* out = static_cast<K*>(st->buf[a.out_buf].ptr) + st->cnt[a.out_cnt];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (uint64_t gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
     const uint64_t gcode = uint64_t(outer[gs[gi]]) >> a.b;   // (inst, g): the result's high part
     const uint32_t* gbm = bm + gi * uint64_t(nwords);
-    const int j0 = tid * wper;
-    uint32_t mine = 0;
-    for (int q = 0; q < wper; ++q)
-      if (j0 + q < nwords) mine += __popc(gbm[j0 + q]);
-    uint64_t gtotal;
-    const uint64_t excl = block_exclusive_sum<uint64_t>(mine, s_scan, &gtotal);
-    uint64_t w = offs[gi] + excl;
-    for (int q = 0; q < wper; ++q) {
-      const int j = j0 + q;
-      if (j >= nwords) break;
-      uint32_t bits = gbm[j];
-      while (bits) {
-        const int t = __ffs(bits) - 1;
-        bits &= bits - 1;
-        out[w++] = K((gcode << a.b) | uint64_t(uint32_t(j) * 32u + uint32_t(t)));
+    const int w0 = warp * wrange, w1 = min(nwords, w0 + wrange);
+    uint32_t cnt = 0;
+    for (int j = w0 + lane; j < w1; j += 32) cnt += __popc(gbm[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) s_wtot[warp] = cnt;
+    __syncthreads();
+    uint64_t base = offs[gi];
+    for (int w = 0; w < warp; ++w) base += s_wtot[w];
+    for (int j0 = w0; j0 < w1; j0 += 32) {
+      const int j = j0 + lane;
+      const uint32_t bits = j < w1 ? gbm[j] : 0u;
+      const uint32_t c = __popc(bits);
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
       }
+      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      if (tot == 0) continue;
+      uint32_t pos = incl - c;
+      const uint32_t vbase = uint32_t(j) * 32u;
+      uint32_t rest = bits;
+      while (rest) {
+        const int t = __ffs(rest) - 1;
+        rest &= rest - 1;
+        s_stage[warp][pos++] = K((gcode << a.b) | uint64_t(vbase + uint32_t(t)));
+      }
+      __syncwarp();
+      for (uint32_t i = lane; i < tot; i += 32) out[base + i] = s_stage[warp][i];
+      __syncwarp();
+      base += tot;
     }
+    __syncthreads();   // s_wtot is rewritten by the next group
   }
 }
 
