@@ -62,6 +62,7 @@ def _args():
                     help="keep full as one sorted array (without HISA_FLAG_LOG_FULL)")
     ap.add_argument("--no-dense", action="store_true",
                     help="sort raw join results instead of the grouped bitmap join (HISA_FLAG_NO_DENSE)")
+    ap.add_argument("--load-factor", type=float, default=0.0, help="hash-index load factor (0: the library default)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -311,7 +312,7 @@ def run_hisa(a):
     flush = torch.empty(512 << 18, dtype=torch.int32, device="cuda")   # 512 MiB > 129 MB L2
 
     extra = (0 if a.single_full else hisa.FLAG_LOG_FULL) | (hisa.FLAG_NO_DENSE if a.no_dense else 0)
-    ctx = hisa.Context(device=local, flags=hisa.FLAG_PHASE_TIMES | extra)
+    ctx = hisa.Context(device=local, flags=hisa.FLAG_PHASE_TIMES | extra, load_factor=a.load_factor)
     ctx.program(*prog)
 
     def step():
@@ -388,7 +389,8 @@ def run_hisa(a):
         outs = {k: (torch.empty(sizes[k], dtype=torch.int32).pin_memory().numpy().view(np.uint32),
                     torch.empty(sizes[k], dtype=torch.int32).pin_memory().numpy().view(np.uint32))
                 for k in idb_names}
-        ectx = hisa.Context(device=local, flags=hisa.FLAG_GRAPH | extra)   # device-side loop in a CUDA graph
+        ectx = hisa.Context(device=local, flags=hisa.FLAG_GRAPH | extra,   # device-side loop in a CUDA graph
+                            load_factor=a.load_factor)
         ectx.program(*prog)
 
         def estep():

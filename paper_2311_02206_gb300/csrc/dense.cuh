@@ -185,22 +185,32 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
       const uint32_t excl = incl - len;
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
       if (lane == 0) raw += total;
-      for (uint32_t q0 = 0; q0 < total; q0 += 32) {
-        const uint32_t q = q0 + lane;
-        int owner = 0;   // lanes whose inclusive prefix is <= q
+      // two elements per lane per step: both loads are in flight before
+      // either is marked
+      for (uint32_t q0 = 0; q0 < total; q0 += 64) {
+        uint32_t v[2];
+        bool ok[2];
 #pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-          const uint32_t v = __shfl_sync(0xffffffffu, incl, owner + step - 1);
-          if (v <= q) owner += step;
+        for (int u = 0; u < 2; ++u) {
+          const uint32_t q = q0 + uint32_t(u) * 32 + lane;
+          int owner = 0;   // lanes whose inclusive prefix is <= q
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t x = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+            if (x <= q) owner += step;
+          }
+          const uint64_t ob_begin = __shfl_sync(0xffffffffu, begin, owner & 31);
+          const uint32_t ob_excl = __shfl_sync(0xffffffffu, excl, owner & 31);
+          ok[u] = q < total;
+          v[u] = ok[u] ? uint32_t(inner[ob_begin + (q - ob_excl)]) & vmask : 0u;
         }
-        const uint64_t ob_begin = __shfl_sync(0xffffffffu, begin, owner & 31);
-        const uint32_t ob_excl = __shfl_sync(0xffffffffu, excl, owner & 31);
-        if (q < total) {
-          const uint32_t v = uint32_t(inner[ob_begin + (q - ob_excl)]) & vmask;
-          const uint32_t bit = 1u << (v & 31);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (!ok[u]) continue;
+          const uint32_t bit = 1u << (v[u] & 31);
           // most values are marked already (many outer tuples share inner
           // values): a plain read skips the serialised same-word atomics
-          if (!(s_bm[v >> 5] & bit)) atomicOr(&s_bm[v >> 5], bit);
+          if (!(s_bm[v[u] >> 5] & bit)) atomicOr(&s_bm[v[u] >> 5], bit);
         }
       }
     }
