@@ -80,6 +80,11 @@ typedef void (*hisa_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
  * (Algorithm 3 and Section 4.2's sort + unique in one pass).  Same results;
  * not in batched runs. */
 #define HISA_FLAG_NO_DENSE 8u
+/* Always index join columns by the hashed run index of Section 4.3.  By
+ * default a key domain of at most 2^20 values (domain bits + instance bits)
+ * is indexed directly: first position of every key, the run of key k being
+ * [first[k], first[k+1]) -- one probe instead of a slot walk. */
+#define HISA_FLAG_HASH_INDEX 16u
 
 typedef struct {
   hisa_alloc_fn alloc;      /* NULL: cudaMallocAsync from a private pool */

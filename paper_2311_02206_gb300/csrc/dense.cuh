@@ -45,6 +45,7 @@ struct DenseArgs {
   int offs_buf;                 // u64 [groups]: result count, then its offset
   int ctr;
   int skip_mask, stage_bit;
+  int index_direct;             // the inner index is direct-addressed
 };
 
 constexpr int kGroupThreads = 256, kGroupItems = 8, kGroupTile = kGroupThreads * kGroupItems;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
       if (o < e) {
         const K code = outer[o];
         const uint32_t key = join_key(inst_of(code, a.b), colv(code, 1, a.b), a.b);
-        if (!probe(table, tmask, key, &begin, &len, &st->error)) len = 0;
+        if (!probe_run(table, tmask, a.index_direct, key, &begin, &len, &st->error)) len = 0;
       }
       uint32_t incl = len;
 #pragma unroll

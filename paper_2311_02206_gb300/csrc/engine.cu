@@ -428,6 +428,7 @@ hisa_status Engine::compile() {
   if (inst_bits + b > 32)
     return ctx_fail(HISA_ERR_UNSUPPORTED, "instance bits + domain bits exceed the 32-bit join key", nullptr);
   wide = 2 * b + inst_bits > 32;
+  direct_bits = (b + inst_bits <= kDirectMaxBits && !(cfg.flags & HISA_FLAG_HASH_INDEX)) ? b + inst_bits : 0;
   passes = (2 * b + inst_bits + 7) / 8;
   const int kb = wide ? 8 : 4;
   if (inst_row < 0) {
@@ -617,6 +618,7 @@ void Engine::emit_join(std::vector<Op>& ops, const StepPlan& sp) {
   a.ctr = 0;
   a.skip_mask = 1;
   a.stage_bit = 0;
+  a.index_direct = direct_bits > 0;
   ops.push_back(o);
 }
 
@@ -673,6 +675,13 @@ void Engine::emit_idb_index(std::vector<Op>& ops) {
     for (int col = 0; col < 2; ++col) {
       if (!R.need_idx[col]) continue;
       const int keys = col == 0 ? R.full : R.rev;
+      if (direct_bits) {
+        Op i{};
+        i.kind = Op::INDEX;
+        i.index = IndexArgs{dst, keys, keys, R.table[col], b, -1, 1, direct_bits};
+        ops.push_back(i);
+        continue;
+      }
       ctl({{kCtlSetCnt, R.runs_cnt[col], 0, 0}});
       Op u{};
       u.kind = Op::RUNS;
@@ -702,7 +711,8 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp) {
   d.kind = Op::DENSE;
   d.dense = DenseArgs{dst, sp.outer_slot, sp.outer_cnt, sc.groups, sc.group_cnt,
                       sp.inner_col == 0 ? ir.base : ir.rev, ir.table[sp.inner_col], b,
-                      hr.fresh, hr.fresh, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0};
+                      hr.fresh, hr.fresh, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0,
+                      direct_bits > 0};
   ops.push_back(d);
 }
 
@@ -995,8 +1005,13 @@ hisa_status Engine::prepare_rel_t(Relation& r, int order, int slot) {
   if ((s = exec_t<K>(ops))) return s;
   if ((s = download())) return s;
   if (hs.overflow || hs.error) return ctx_fail(HISA_ERR_CUDA, "EDB preparation overflowed", nullptr);
-  // hash index over the runs of the join column
-  if (r.need_idx[order]) {
+  // run index of the join column: direct-addressed over a small key domain
+  if (r.need_idx[order] && direct_bits) {
+    if ((s = ensure(r.table[order], ((1ull << direct_bits) + 2) / 2 + 1)) || (s = upload())) return s;
+    IndexArgs ia{dst, slot, slot, r.table[order], b, -1, 0, direct_bits};
+    launch_index<K>(ia, grid, stream);
+    if ((s = check_launch("index build"))) return s;
+  } else if (r.need_idx[order]) {   // else hashed over its runs
     hs.cnt[sc.runs] = 0;
     if ((s = upload())) return s;
     RunsArgs ra{dst, slot, slot, b, sc.runs, 0};
@@ -1197,7 +1212,9 @@ hisa_status Engine::init_run_state() {
     for (int col = 0; col < 2; ++col) {
       if (!R.need_idx[col]) continue;
       uint64_t cap = 1024;
-      while (double(cap) * cfg.load_factor < double(nedb)) cap <<= 1;
+      if (direct_bits) cap = ((1ull << direct_bits) + 2) / 2 + 1;
+      else
+        while (double(cap) * cfg.load_factor < double(nedb)) cap <<= 1;
       if ((s = ensure(R.table[col], cap))) return s;
       hs.cnt[R.runs_cnt[col]] = 0;
     }

@@ -191,6 +191,7 @@ class Engine {
   int b = 1;           // domain bits
   bool wide = false;   // 64-bit codes
   int passes = 1;      // radix passes over 2b bits
+  int direct_bits = 0; // > 0: run indexes are direct-addressed over this many key bits
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_stale = true;

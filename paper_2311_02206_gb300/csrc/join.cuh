@@ -38,10 +38,11 @@ enum : int { kFiltNone = 0, kFiltNeq = 1, kFiltEq = 2 };
 struct IndexArgs {
   DevState* st;
   int keys_buf, keys_cnt;   // sorted codes
-  int table_buf;            // Slot[cap], cap a power of two, zeroed
+  int table_buf;            // Slot[cap], cap a power of two, zeroed; or the direct array
   int b;                    // domain bits: key = code >> b
   int runs_cnt;             // cnt slot receiving the number of runs (-1: none)
   int skip_mask;
+  int direct;               // > 0: direct-addressed index over `direct` key bits (below)
 };
 
 struct JoinArgs {
@@ -62,6 +63,7 @@ struct JoinArgs {
   int hist_buf, hist_passes; // fused digit histogram of the results (-1: none)
   int ctr;
   int skip_mask, stage_bit;
+  int index_direct;          // the inner index is direct-addressed (k_index_direct)
 };
 
 constexpr int kJoinThreads = 256;
@@ -99,6 +101,43 @@ __device__ __forceinline__ bool probe(const Slot* table, uint64_t mask, uint32_t
   }
   atomicExch(err, kDevProbeLimit);
   return false;
+}
+
+// Direct-addressed run index, for key domains of at most 2^kDirectMaxBits
+// values: u64 first[k] for every key k in [0, 2^bits], so the run of key k is
+// [first[k], first[k+1]) -- one probe instead of a hash-slot walk.  Built by
+// a lower-bound search per key over the sorted codes.
+constexpr int kDirectMaxBits = 20;
+
+__device__ __forceinline__ bool probe_run(const void* table, uint64_t mask, int direct, uint32_t key,
+                                          uint64_t* begin, uint32_t* len, uint32_t* err) {
+  if (direct) {
+    const uint64_t* first = static_cast<const uint64_t*>(table);
+    const uint64_t b0 = first[key], b1 = first[key + 1];
+    *begin = b0;
+    *len = uint32_t(b1 - b0);
+    return b1 > b0;
+  }
+  return probe(static_cast<const Slot*>(table), mask, key, begin, len, err);
+}
+
+template <typename K>
+__global__ void k_index_direct(IndexArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const K* keys = static_cast<const K*>(st->buf[a.keys_buf].ptr);
+  const uint64_t n = st->cnt[a.keys_cnt];
+  uint64_t* first = static_cast<uint64_t*>(st->buf[a.table_buf].ptr);
+  const uint64_t nk = 1ull << a.direct;
+  for (uint64_t k = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; k <= nk; k += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const uint64_t m = (lo + hi) >> 1;
+      if ((uint64_t(keys[m]) >> a.b) < k) lo = m + 1;
+      else hi = m;
+    }
+    first[k] = lo;
+  }
 }
 
 // First position in inner[lo, lo+len) whose other column is >= v.
@@ -184,7 +223,7 @@ __device__ __forceinline__ Probe do_probe(const JoinArgs& a, K code, const K* in
   uint32_t len = 1;
   if (a.has_inner) {
     const uint32_t key = join_key(inst_of(code, a.b), v, a.b);
-    if (!probe(table, mask, key, &p.begin, &len, err)) return p;
+    if (!probe_run(table, mask, a.index_direct, key, &p.begin, &len, err)) return p;
   }
   // filters (at most two; unrolled so the argument arrays stay in registers)
 #pragma unroll

@@ -210,7 +210,8 @@ void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s) {
 }
 template <typename K>
 void launch_index(const IndexArgs& a, const Grid& g, cudaStream_t s) {
-  HISA_LAUNCH(kKIndex, s, (k_index_build<K><<<g.small, 256, 0, s>>>(a)));
+  if (a.direct) HISA_LAUNCH(kKIndex, s, (k_index_direct<K><<<g.small, 256, 0, s>>>(a)));
+  else HISA_LAUNCH(kKIndex, s, (k_index_build<K><<<g.small, 256, 0, s>>>(a)));
 }
 template <typename K>
 void launch_join(const JoinArgs& a, const Grid& g, cudaStream_t s) {

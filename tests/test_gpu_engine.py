@@ -23,11 +23,11 @@ def _lib():
 
 
 def modes():
-    """host-driven, graph-captured, both with the log-structured full, and
-    graph-captured without the grouped bitmap join"""
+    """host-driven, graph-captured, both with the log-structured full,
+    graph-captured without the grouped bitmap join, and with hashed indexes"""
     from paper_2311_02206_gb300 import hisa
     return [0, hisa.FLAG_GRAPH, hisa.FLAG_LOG_FULL, hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL,
-            hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE]
+            hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE, hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE | hisa.FLAG_HASH_INDEX]
 
 
 @pytest.mark.parametrize("seed", range(40))

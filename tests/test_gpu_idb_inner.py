@@ -22,8 +22,9 @@ def _lib():
 
 
 def modes():
+    """host-driven and graph-captured; graph-captured with hashed indexes"""
     from paper_2311_02206_gb300 import hisa
-    return [0, hisa.FLAG_GRAPH]
+    return [0, hisa.FLAG_GRAPH, hisa.FLAG_GRAPH | hisa.FLAG_HASH_INDEX]
 
 
 def random_graph(seed, nmax=60, dmax=4):
