@@ -122,7 +122,40 @@ void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStr
   HISA_LAUNCH(kKZero, s, (k_fill_u32<<<g.small, 256, 0, s>>>(p, n, v)));
 }
 
+// Group starts from a direct index over the delta's kept column (first[g]
+// for g in [0, 2^bits], GroupArgs::in_buf): the non-empty groups' starts in
+// order, then the sentinel n.  One CTA walks the 2^bits keys.
+__global__ void k_group_compact(GroupArgs a, int bits) {
+  __shared__ uint64_t s_scan[32];
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t* first = static_cast<const uint64_t*>(st->buf[a.in_buf].ptr);
+  uint64_t* out = static_cast<uint64_t*>(st->buf[a.out_buf].ptr);
+  const uint64_t ocap = st->buf[a.out_buf].cap;
+  const uint64_t nk = 1ull << bits;
+  uint64_t carry = 0;
+  for (uint64_t c0 = 0; c0 < nk; c0 += blockDim.x) {
+    const uint64_t g = c0 + threadIdx.x;
+    const bool head = g < nk && first[g + 1] > first[g];
+    uint64_t tot;
+    const uint64_t ex = block_exclusive_sum<uint64_t>(head ? 1 : 0, s_scan, &tot);
+    if (head && carry + ex < ocap) out[carry + ex] = first[g];
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    st->cnt[a.out_cnt] = carry;
+    if (carry + 1 <= ocap) out[carry] = first[nk];
+    else {
+      atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)(carry + 1));
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+  }
+}
+
 void launch_ctl(const CtlArgs& a, cudaStream_t s) { HISA_LAUNCH(kKCtl, s, (k_ctl<<<1, 256, 0, s>>>(a))); }
+void launch_group_compact(const GroupArgs& a, int bits, cudaStream_t s) {
+  HISA_LAUNCH(kKGroups, s, (k_group_compact<<<1, 1024, 0, s>>>(a, bits)));
+}
 void launch_commit(const CommitArgs& a, cudaStream_t s) { HISA_LAUNCH(kKCommit, s, (k_commit<<<1, 32, 0, s>>>(a))); }
 void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKZero, s, (k_zero<<<g.small, 256, 0, s>>>(a)));
@@ -130,7 +163,7 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
 
 const char* const kKernelNames[kKindCount] = {
     "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
-    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_starts", "join_dense_mark", "join_dense_scan", "join_dense_emit"};
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit"};
 
 thread_local KernelTimer* g_timer = nullptr;
 thread_local uint64_t g_launches = 0;

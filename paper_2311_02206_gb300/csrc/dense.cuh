@@ -21,7 +21,8 @@
 namespace hisa {
 
 // Start position of every run of equal g = code >> b in a sorted code array,
-// compacted in order; cnt[out_cnt] = number of groups and out[groups] = n.
+// compacted in order; cnt[out_cnt] = number of groups and out[groups] = n
+// (k_group_compact, from a direct index of the array by g).
 struct GroupArgs {
   DevState* st;
   int in_buf, in_cnt;
@@ -46,84 +47,15 @@ struct DenseArgs {
   int ctr;
   int skip_mask, stage_bit;
   int index_direct;             // the inner index is direct-addressed
+  // full of the head relation (its large and small level; -1: none), each
+  // with a direct index by the kept column: their tuples are removed from
+  // each group's bitmap, so the join writes delta = new \ full itself
+  int full0_buf, first0_buf, full1_buf, first1_buf;
 };
 
-constexpr int kGroupThreads = 256, kGroupItems = 8, kGroupTile = kGroupThreads * kGroupItems;
 constexpr int kDenseThreads = 128;
 constexpr int kDenseCtasPerSm = 16;   // latency-bound (L2 probes and run reads): full occupancy
 constexpr int kDenseMaxBits = 18;   // bitmap of 2^18 bits = 32 KB of shared memory
-
-template <typename K>
-__global__ void __launch_bounds__(kGroupThreads) k_group_starts(GroupArgs a) {
-  __shared__ uint64_t s_scan[32];
-  __shared__ uint64_t s_base;
-  __shared__ uint32_t s_tile;
-  DevState* st = a.st;
-  if (st->overflow & a.skip_mask) return;
-  const uint64_t n = st->cnt[a.in_cnt];
-  uint64_t* out = static_cast<uint64_t*>(st->buf[a.out_buf].ptr);
-  const uint64_t ocap = st->buf[a.out_buf].cap;
-  if (n == 0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      st->cnt[a.out_cnt] = 0;
-      if (ocap >= 1) out[0] = 0;
-    }
-    return;
-  }
-  const uint64_t ntiles = (n + kGroupTile - 1) / kGroupTile;
-  if (st->buf[a.status_buf].cap < ntiles) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      atomicMax((unsigned long long*)&st->need[a.status_buf], (unsigned long long)ntiles);
-      atomicOr(&st->overflow, 1u << a.stage_bit);
-    }
-    return;
-  }
-  const K* in = static_cast<const K*>(st->buf[a.in_buf].ptr);
-  uint64_t* status = static_cast<uint64_t*>(st->buf[a.status_buf].ptr);
-  const uint32_t epoch = st->epoch;
-  const int tid = threadIdx.x;
-  while (true) {
-    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    if (tile >= ntiles) break;
-    const uint64_t i0 = tile * kGroupTile + uint64_t(tid) * kGroupItems;
-    uint32_t heads = 0;
-    uint64_t prev = i0 > 0 && i0 <= n ? uint64_t(in[i0 - 1]) >> a.b : ~0ull;
-#pragma unroll
-    for (int k = 0; k < kGroupItems; ++k) {
-      const uint64_t i = i0 + k;
-      if (i >= n) break;
-      const uint64_t g = uint64_t(in[i]) >> a.b;
-      if (i == 0 || g != prev) heads |= 1u << k;
-      prev = g;
-    }
-    uint64_t tile_heads;
-    const uint64_t excl = block_exclusive_sum<uint64_t>(__popc(heads), s_scan, &tile_heads);
-    if (tid < 32) {
-      const uint64_t base = lookback_warp(status, tile, tile_heads, epoch, &st->error);
-      if (tid == 0) s_base = base;
-    }
-    __syncthreads();
-    uint64_t w = s_base + excl;
-#pragma unroll
-    for (int k = 0; k < kGroupItems; ++k)
-      if (heads & (1u << k)) {
-        if (w < ocap) out[w] = i0 + k;
-        ++w;
-      }
-    if (tile == ntiles - 1 && tid == 0) {
-      const uint64_t total = s_base + tile_heads;
-      st->cnt[a.out_cnt] = total;
-      if (total + 1 <= ocap) out[total] = n;   // sentinel: end of the last group
-      else {
-        atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)(total + 1));
-        atomicOr(&st->overflow, 1u << a.stage_bit);
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // Phase 1: one group per CTA (taken in any order, so a large group delays
 // no other): mark the inner runs of the group's outer tuples -- a warp takes
@@ -213,6 +145,24 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
           // values): a plain read skips the serialised same-word atomics
           if (!(s_bm[v[u] >> 5] & bit)) atomicOr(&s_bm[v[u] >> 5], bit);
         }
+      }
+    }
+    __syncthreads();
+    // set difference against full (Section 5.1 "populating delta"): clear the
+    // bits of the group's tuples already in full; both levels hold the same
+    // kept value first, so each contributes one contiguous run
+#pragma unroll
+    for (int lv = 0; lv < 2; ++lv) {
+      const int fb = lv ? a.full1_buf : a.full0_buf;
+      if (fb < 0) continue;
+      const uint64_t* first = static_cast<const uint64_t*>(st->buf[lv ? a.first1_buf : a.first0_buf].ptr);
+      const K* fl = static_cast<const K*>(st->buf[fb].ptr);
+      const uint64_t g = uint64_t(outer[s]) >> a.b;
+      const uint64_t r0 = first[g], r1 = first[g + 1];
+      for (uint64_t i = r0 + tid; i < r1; i += kDenseThreads) {
+        const uint32_t v = uint32_t(fl[i]) & vmask;
+        const uint32_t bit = 1u << (v & 31);
+        if (s_bm[v >> 5] & bit) atomicAnd(&s_bm[v >> 5], ~bit);
       }
     }
     __syncthreads();

@@ -160,6 +160,9 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.groups = new_slot(8);
   sc.dense_status = new_slot(8);
   sc.dense_bm = new_slot(4);
+  sc.dense_first = new_slot(8);
+  sc.first_l0 = new_slot(8);
+  sc.first_l1 = new_slot(8);
   sc.group_cnt = nslots++;
   sc.raw_cnt = nslots++;
   slot_zero[sc.radix_status] = slot_zero[sc.setop_status] = slot_zero[sc.join_status] = true;
@@ -528,12 +531,14 @@ hisa_status Engine::compile() {
   }
   for (auto& v : planN)
     for (auto& sp : v) sp.dense = false;
+  for (int r : idb) rels[r].dense_head = false;
   if (dense_on)
     for (int r : idb) {
       auto w = writers(r);
       if (w.size() == 1 && dense_ok(*w[0], r)) {
         for (auto& v : planN)
           if (&v == w[0]) v[0].dense = true;
+        rels[r].dense_head = true;
       }
     }
   // log-structured full where nothing probes full (it is only differenced
@@ -703,16 +708,31 @@ void Engine::emit_idb_index(std::vector<Op>& ops) {
 void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp) {
   const Relation& ir = rels[sp.inner_rel];
   const Relation& hr = rels[sp.out_rel];
+  // direct indexes of the head's full levels by the kept column (they change
+  // every iteration; one search per value of the domain)
+  for (int lv = 0; lv < (hr.log ? 2 : 1); ++lv) {
+    Op f{};
+    f.kind = Op::INDEX;
+    const int lvl = lv ? hr.l1 : hr.full;
+    f.index = IndexArgs{dst, lvl, lvl, lv ? sc.first_l1 : sc.first_l0, b, -1, 1, b};
+    ops.push_back(f);
+  }
+  // group starts: a direct index of delta by the kept column, compacted to
+  // the non-empty groups
+  Op x{};
+  x.kind = Op::INDEX;
+  x.index = IndexArgs{dst, sp.outer_slot, sp.outer_cnt, sc.dense_first, b, -1, 1, b};
+  ops.push_back(x);
   Op g{};
-  g.kind = Op::GROUPS;
-  g.groups = GroupArgs{dst, sp.outer_slot, sp.outer_cnt, b, sc.groups, sc.group_cnt, sc.join_status, 3, 1, 0};
+  g.kind = Op::GCOMPACT;
+  g.groups = GroupArgs{dst, sc.dense_first, sp.outer_cnt, b, sc.groups, sc.group_cnt, sc.join_status, 3, 1, 0};
   ops.push_back(g);
   Op d{};
   d.kind = Op::DENSE;
   d.dense = DenseArgs{dst, sp.outer_slot, sp.outer_cnt, sc.groups, sc.group_cnt,
                       sp.inner_col == 0 ? ir.base : ir.rev, ir.table[sp.inner_col], b,
                       hr.fresh, hr.fresh, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0,
-                      direct_bits > 0};
+                      direct_bits > 0, hr.full, sc.first_l0, hr.log ? hr.l1 : -1, sc.first_l1};
   ops.push_back(d);
 }
 
@@ -868,12 +888,16 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
       m.stage_bit = 1;
       m.gate1 = R.bigf + 1;
       ops.push_back(big);
-      // small new: probe the large level, then difference + merge against the small one
-      Op d{};
-      d.kind = Op::DIFF;
-      d.diff = DiffArgs{dst, R.full, R.full, sorted_new, R.fresh, R.newp, R.newp, sc.setop_status, 2, 3, 1,
-                        R.smallf + 1};
-      ops.push_back(d);
+      // small new: probe the large level, then difference + merge against
+      // the small one (a dense join wrote new minus full already, and in
+      // iteration 1 full is empty: no probe)
+      if (!R.dense_head) {
+        Op d{};
+        d.kind = Op::DIFF;
+        d.diff = DiffArgs{dst, R.full, R.full, sorted_new, R.fresh, R.newp, R.newp, sc.setop_status, 2, 3, 1,
+                          R.smallf + 1};
+        ops.push_back(d);
+      }
       Op o{};
       o.kind = Op::SETOP;
       SetopArgs& a = o.setop;
@@ -881,8 +905,8 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
       a.st = dst;
       a.a_buf = R.l1;
       a.a_cnt = R.l1;
-      a.b_buf = R.newp;
-      a.b_cnt = R.newp;
+      a.b_buf = R.dense_head ? R.fresh : R.newp;
+      a.b_cnt = R.dense_head ? R.fresh : R.newp;
       a.split_buf = sc.split;
       a.status_buf = sc.setop_status;
       a.d_buf = R.delta_next;
@@ -949,7 +973,7 @@ hisa_status Engine::exec_t(const std::vector<Op>& ops) {
       case Op::ZERO: launch_zero(o.zero, grid, stream); break;
       case Op::SWAP: launch_swap<K>(o.swap, grid, stream); break;
       case Op::DIFF: launch_diff<K>(o.diff, grid, stream); break;
-      case Op::GROUPS: launch_group_starts<K>(o.groups, grid, stream); break;
+      case Op::GCOMPACT: launch_group_compact(o.groups, o.groups.b, stream); break;
       case Op::DENSE: launch_join_dense<K>(o.dense, grid, stream); break;
     }
   }
@@ -1139,7 +1163,7 @@ hisa_status Engine::regrow() {
   }
   // next iterations: delta is the outer relation of the joins; full + new is merged
   if ((s = ensure(sc.offs, delta_cap + 1)) || (s = ensure(sc.join_status, delta_cap / kJoinTile + 2))) return s;
-  if ((s = ensure(sc.groups, delta_cap + 2)) ||
+  if ((s = ensure(sc.groups, std::min<uint64_t>(delta_cap, 1ull << (b + inst_bits)) + 2)) ||
       (s = ensure(sc.dense_status, std::min<uint64_t>(delta_cap, 1ull << (b + inst_bits)) + 2)))
     return s;
   if ((s = ensure(sc.split, (full_cap + std::max(new_cap, delta_cap)) / ks + 2)) ||
@@ -1221,7 +1245,10 @@ hisa_status Engine::init_run_state() {
   }
   hs.cnt[sc.tmp_cnt] = 0;
   hs.cnt[sc.raw_cnt] = hs.cnt[sc.group_cnt] = 0;
-  if ((s = ensure(sc.groups, 4 * nedb + 2)) ||
+  if (b <= kDenseMaxBits && ((s = ensure(sc.dense_first, (1ull << b) + 2)) ||
+                             (s = ensure(sc.first_l0, (1ull << b) + 2)) || (s = ensure(sc.first_l1, (1ull << b) + 2))))
+    return s;
+  if ((s = ensure(sc.groups, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
       (s = ensure(sc.dense_status, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)))
     return s;
   if ((s = ensure(sc.radix_status, (4 * nedb / kt + 2) * 256)) || (s = ensure(sc.offs, 4 * nedb + 1)) ||
@@ -1294,13 +1321,15 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
           for (auto& v : planN)
             if (!first && v.size() == 1 && v[0].dense && v[0].out_rel == idb[i]) dense = true;
           if (dense) {
-            // group starts: read delta, write starts; mark: read delta, probe,
+            // group starts: direct index of delta, compaction; mark: read delta, probe,
             // read the inner runs (raw results), write the bitmaps; scan:
             // counts; emit: read the bitmaps, write new
             const double raw = double(hs.cnt[sc.raw_cnt]), ng = double(hs.cnt[sc.group_cnt]);
             const double bmb = ng * double(b >= 5 ? (1u << (b - 5)) : 1u) * 4.0;
-            kstat[kKGroups].bytes += dp * kb + 8.0 * ng;
-            kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + bmb;
+            kstat[kKIndex].bytes += 8.0 * double(1u << b);
+            kstat[kKGroups].bytes += 16.0 * double(1u << b) + 8.0 * ng;
+            // (+ the full levels' runs read for the set difference)
+            kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + bmb + (m + double(l_prev[i])) * kb;
             kstat[kKDenseScan].bytes += 16.0 * ng;
             kstat[kKDenseEmit].bytes += bmb + nn * kb;
           } else {

@@ -39,6 +39,7 @@ struct Relation {
   // l1 the small one that absorbs each delta; newp = new minus the large level;
   // gate = |l1| when l1 is due to be merged into full, else 0
   bool log = false;
+  bool dense_head = false;   // its writer in iterations >= 2 is a dense join (writes delta itself)
   int order = 0;   // storage order of an IDB relation: 0 = (c0, c1), 1 = (c1, c0)
   int l1 = -1, l1_next = -1, newp = -1, gate = -1;
   int bigf = -1, smallf = -1;   // this iteration merges new straight into full / probes it
@@ -59,7 +60,7 @@ struct StepPlan {
 };
 
 struct Op {
-  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, GROUPS, DENSE } kind;
+  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT } kind;
   CtlArgs ctl;
   JoinArgs join;
   RadixPassArgs pass;
@@ -80,6 +81,8 @@ struct Scratch {
   int runs, total, tmp_cnt;   // count-only slots
   int groups, dense_status;   // group starts of a delta and the dense join's per-group counts/offsets
   int dense_bm;               // the dense join's per-group bitmaps
+  int dense_first;            // direct index of a delta by its kept column (group starts)
+  int first_l0, first_l1;     // direct indexes of the head's full levels by the kept column
   int group_cnt, raw_cnt;     // count-only slots
 };
 
