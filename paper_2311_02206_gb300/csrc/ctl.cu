@@ -83,7 +83,13 @@ __global__ void k_commit(CommitArgs a) {
   const uint32_t it = st->iter;
   for (int r = 0; r < a.nrel; ++r) {
     const uint64_t nd = st->cnt[a.delta_next[r]];
-    if (nd > 0) {
+    if (nd > 0 && a.append_nlv1[r] > 0) {
+      // delta was appended to full as a new level
+      st->cnt[a.full[r]] += nd;
+      const uint64_t lv = ++st->cnt[a.append_nlv1[r] - 1];
+      if (lv >= uint64_t(a.max_levels)) st->aux[2] = 1;   // the host merges the levels
+      any = true;
+    } else if (nd > 0) {
       const bool alt = a.alt_flag1[r] > 0 && st->cnt[a.alt_flag1[r] - 1] != 0;
       const int f = alt ? a.alt_full[r] : a.full[r], fn = alt ? a.alt_full_next[r] : a.full_next[r];
       DBuf t = st->buf[f];
@@ -101,7 +107,7 @@ __global__ void k_commit(CommitArgs a) {
     st->aux[1] += st->cnt[a.fresh[r]];   // tuples joined (|new| before dedup)
   }
   st->iter = it + 1;
-  st->go = (any || a.force) && st->iter < st->max_iters ? 1u : 0u;
+  st->go = (any || a.force) && st->iter < st->max_iters && !st->aux[2] ? 1u : 0u;
   if (any) st->aux[0] = st->iter;   // last iteration that produced a tuple
 }
 
@@ -163,7 +169,7 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
 
 const char* const kKernelNames[kKindCount] = {
     "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
-    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit"};
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level"};
 
 thread_local KernelTimer* g_timer = nullptr;
 thread_local uint64_t g_launches = 0;

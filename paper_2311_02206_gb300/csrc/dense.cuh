@@ -47,10 +47,11 @@ struct DenseArgs {
   int ctr;
   int skip_mask, stage_bit;
   int index_direct;             // the inner index is direct-addressed
-  // full of the head relation (its large and small level; -1: none), each
-  // with a direct index by the kept column: their tuples are removed from
-  // each group's bitmap, so the join writes delta = new \ full itself
-  int full0_buf, first0_buf, full1_buf, first1_buf;
+  // full of the head relation (append-only: one sorted, duplicate-free level
+  // per iteration) with each level's direct index by the kept column: their
+  // tuples are removed from each group's bitmap, so the join writes
+  // delta = new \ full itself (-1: no difference)
+  int full_buf, lvidx_buf, nlv_cnt;
 };
 
 constexpr int kDenseThreads = 128;
@@ -151,18 +152,18 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
     // set difference against full (Section 5.1 "populating delta"): clear the
     // bits of the group's tuples already in full; both levels hold the same
     // kept value first, so each contributes one contiguous run
-#pragma unroll
-    for (int lv = 0; lv < 2; ++lv) {
-      const int fb = lv ? a.full1_buf : a.full0_buf;
-      if (fb < 0) continue;
-      const uint64_t* first = static_cast<const uint64_t*>(st->buf[lv ? a.first1_buf : a.first0_buf].ptr);
-      const K* fl = static_cast<const K*>(st->buf[fb].ptr);
+    if (a.full_buf >= 0) {
+      const uint64_t nlv = st->cnt[a.nlv_cnt], nk = (1ull << a.b) + 1;
+      const uint64_t* lvidx = static_cast<const uint64_t*>(st->buf[a.lvidx_buf].ptr);
+      const K* fl = static_cast<const K*>(st->buf[a.full_buf].ptr);
       const uint64_t g = uint64_t(outer[s]) >> a.b;
-      const uint64_t r0 = first[g], r1 = first[g + 1];
-      for (uint64_t i = r0 + tid; i < r1; i += kDenseThreads) {
-        const uint32_t v = uint32_t(fl[i]) & vmask;
-        const uint32_t bit = 1u << (v & 31);
-        if (s_bm[v >> 5] & bit) atomicAnd(&s_bm[v >> 5], ~bit);
+      for (uint64_t lv = 0; lv < nlv; ++lv) {
+        const uint64_t r0 = lvidx[lv * nk + g], r1 = lvidx[lv * nk + g + 1];
+        for (uint64_t i = r0 + tid; i < r1; i += kDenseThreads) {
+          const uint32_t v = uint32_t(fl[i]) & vmask;
+          const uint32_t bit = 1u << (v & 31);
+          if (s_bm[v >> 5] & bit) atomicAnd(&s_bm[v >> 5], ~bit);
+        }
       }
     }
     __syncthreads();

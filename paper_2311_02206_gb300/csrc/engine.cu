@@ -161,8 +161,6 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.dense_status = new_slot(8);
   sc.dense_bm = new_slot(4);
   sc.dense_first = new_slot(8);
-  sc.first_l0 = new_slot(8);
-  sc.first_l1 = new_slot(8);
   sc.group_cnt = nslots++;
   sc.raw_cnt = nslots++;
   slot_zero[sc.radix_status] = slot_zero[sc.setop_status] = slot_zero[sc.join_status] = true;
@@ -467,6 +465,9 @@ hisa_status Engine::compile() {
         r.gate = nslots++;
         r.bigf = nslots++;
         r.smallf = nslots++;
+        r.lvidx = new_slot(8);
+        r.nlv = nslots++;
+        r.sortf = nslots++;
       }
     }
     for (int id : {r.base, r.rev, r.full_next, r.delta, r.delta_next, r.fresh, r.fresh_alt, r.rev_next, r.rswap,
@@ -531,21 +532,21 @@ hisa_status Engine::compile() {
   }
   for (auto& v : planN)
     for (auto& sp : v) sp.dense = false;
-  for (int r : idb) rels[r].dense_head = false;
+  for (int r : idb) rels[r].dense_head = rels[r].append = false;
   if (dense_on)
     for (int r : idb) {
       auto w = writers(r);
       if (w.size() == 1 && dense_ok(*w[0], r)) {
         for (auto& v : planN)
           if (&v == w[0]) v[0].dense = true;
-        rels[r].dense_head = true;
+        rels[r].dense_head = rels[r].append = true;
       }
     }
   // log-structured full where nothing probes full (it is only differenced
   // and merged): REACH and SG, not CSPA's inner IDB atoms nor batched runs
   for (int r : idb) {
     Relation& R = rels[r];
-    R.log = (cfg.flags & HISA_FLAG_LOG_FULL) && !batched && !R.need_idx[0] && !R.need_idx[1];
+    R.log = (cfg.flags & HISA_FLAG_LOG_FULL) && !batched && !R.need_idx[0] && !R.need_idx[1] && !R.append;
   }
   compiled = true;
   graph_stale = true;
@@ -708,15 +709,6 @@ void Engine::emit_idb_index(std::vector<Op>& ops) {
 void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp) {
   const Relation& ir = rels[sp.inner_rel];
   const Relation& hr = rels[sp.out_rel];
-  // direct indexes of the head's full levels by the kept column (they change
-  // every iteration; one search per value of the domain)
-  for (int lv = 0; lv < (hr.log ? 2 : 1); ++lv) {
-    Op f{};
-    f.kind = Op::INDEX;
-    const int lvl = lv ? hr.l1 : hr.full;
-    f.index = IndexArgs{dst, lvl, lvl, lv ? sc.first_l1 : sc.first_l0, b, -1, 1, b};
-    ops.push_back(f);
-  }
   // group starts: a direct index of delta by the kept column, compacted to
   // the non-empty groups
   Op x{};
@@ -727,13 +719,24 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp) {
   g.kind = Op::GCOMPACT;
   g.groups = GroupArgs{dst, sc.dense_first, sp.outer_cnt, b, sc.groups, sc.group_cnt, sc.join_status, 3, 1, 0};
   ops.push_back(g);
+  // with an append-only full the join writes delta itself, into delta_next
+  const int out = hr.append ? hr.delta_next : hr.fresh;
   Op d{};
   d.kind = Op::DENSE;
   d.dense = DenseArgs{dst, sp.outer_slot, sp.outer_cnt, sc.groups, sc.group_cnt,
                       sp.inner_col == 0 ? ir.base : ir.rev, ir.table[sp.inner_col], b,
-                      hr.fresh, hr.fresh, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0,
-                      direct_bits > 0, hr.full, sc.first_l0, hr.log ? hr.l1 : -1, sc.first_l1};
+                      out, out, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0,
+                      direct_bits > 0, hr.append ? hr.full : -1, hr.lvidx, hr.nlv};
   ops.push_back(d);
+  if (hr.append) {   // no unique pass in the tail; |new| (statistics) = |delta|
+    Op f{};
+    f.kind = Op::CTL;
+    f.ctl.st = dst;
+    f.ctl.skip_mask = 1;
+    f.ctl.cmd[f.ctl.n++] = {kCtlSetCnt, hr.sortf, 0, 0};
+    f.ctl.cmd[f.ctl.n++] = {kCtlCopyCnt, hr.fresh, hr.delta_next, 0};
+    ops.push_back(f);
+  }
 }
 
 // Join stage of one iteration: clear new, run every variant, sort each new.
@@ -745,6 +748,10 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
   for (int r : idb) {
     c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, rels[r].fresh, 0};
     c.ctl.cmd[c.ctl.n++] = {kCtlZeroSmall, rels[r].hist, 8 * 256};
+    if (rels[r].append) {
+      c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, rels[r].delta_next, 0};
+      c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, rels[r].sortf, 1};
+    }
   }
   c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, sc.raw_cnt, 0};
   ops.push_back(c);
@@ -817,6 +824,7 @@ void Engine::emit_sort(std::vector<Op>& ops, int in, int alt, int cnt, int hist,
 // the merge drops nothing.  Idempotent: a re-run finds the small level empty
 // and takes the same decision.
 constexpr int kLevelRatio = 8;
+constexpr int kMaxLevels = 32;   // levels of an append-only full before the host merges them
 constexpr int kBigRatio = 2;
 void Engine::emit_level_merge(std::vector<Op>& ops, const Relation& R, bool force) {
   Op g{};
@@ -865,6 +873,34 @@ void Engine::emit_level_merge(std::vector<Op>& ops, const Relation& R, bool forc
 void Engine::emit_tail(std::vector<Op>& ops, bool force) {
   for (int r : idb) {
     const Relation& R = rels[r];
+    if (R.append) {
+      // delta = unique(new) (the dense join already removed full's tuples; in
+      // iteration 1 full is empty), appended to full as a new level
+      Op o{};
+      o.kind = Op::SETOP;
+      SetopArgs& a = o.setop;
+      a.st = dst;
+      a.a_buf = sc.empty;
+      a.a_cnt = sc.empty;
+      a.b_buf = R.fresh;
+      a.b_cnt = R.fresh;
+      a.split_buf = sc.split;
+      a.status_buf = sc.setop_status;
+      a.d_buf = R.delta_next;
+      a.d_cnt = R.delta_next;
+      a.f_buf = -1;
+      a.f_cnt = -1;
+      a.ctr = 2;
+      a.skip_mask = 3;
+      a.stage_bit = 1;
+      a.gate1 = R.sortf + 1;   // skipped when the dense join wrote delta
+      ops.push_back(o);
+      Op p{};
+      p.kind = Op::APPEND;
+      p.append = AppendArgs{dst, R.delta_next, R.delta_next, R.full, R.full, R.lvidx, R.nlv, b, b, 3, 1};
+      ops.push_back(p);
+      continue;
+    }
     if (R.log) {
       const int sorted_new = R.fresh;
       emit_level_merge(ops, R, false);
@@ -953,7 +989,9 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
     c.commit.delta_next[i] = R.delta_next;
     c.commit.history[i] = R.history;
     c.commit.fresh[i] = R.fresh;
+    c.commit.append_nlv1[i] = R.append ? R.nlv + 1 : 0;
   }
+  c.commit.max_levels = kMaxLevels;
   c.commit.force = force;
   ops.push_back(c);
 }
@@ -974,6 +1012,7 @@ hisa_status Engine::exec_t(const std::vector<Op>& ops) {
       case Op::SWAP: launch_swap<K>(o.swap, grid, stream); break;
       case Op::DIFF: launch_diff<K>(o.diff, grid, stream); break;
       case Op::GCOMPACT: launch_group_compact(o.groups, o.groups.b, stream); break;
+      case Op::APPEND: launch_append<K>(o.append, grid, stream); break;
       case Op::DENSE: launch_join_dense<K>(o.dense, grid, stream); break;
     }
   }
@@ -1100,6 +1139,19 @@ hisa_status Engine::regrow() {
   for (int id = 0; id < nslots; ++id) {
     const uint64_t need = hs.need[id];
     if (need == 0 || need <= hs.buf[id].cap) continue;
+    // an append-only full and its level indexes are live: grow them in place
+    bool kept = false;
+    for (int r : idb) {
+      const Relation& R = rels[r];
+      if (!R.append || (id != R.full && id != R.lvidx)) continue;
+      const uint64_t live = id == R.full ? hs.cnt[R.full] : hs.cnt[R.nlv] * ((1ull << b) + 1);
+      const uint64_t grow = id == R.full ? std::max(uint64_t(cfg.ebm_k * double(need - live)), need / 4) : need;
+      hisa_status s = grow_keep(id, need + grow + 1024, live);
+      if (s) return s;
+      ++regrows;
+      kept = true;
+    }
+    if (kept) continue;
     uint64_t cap = need + need / 8 + 1024;
     if (slot_pow2[id]) {   // hash table: the probe mask needs a power of two
       cap = 16;
@@ -1227,6 +1279,11 @@ hisa_status Engine::init_run_state() {
         if ((s = ensure(id, 4 * nedb))) return s;
       hs.cnt[R.rev] = hs.cnt[R.rev_next] = hs.cnt[R.rswap] = 0;
     }
+    if (R.append) {
+      if ((s = ensure(R.lvidx, 8 * ((1ull << b) + 1)))) return s;
+      hs.cnt[R.nlv] = 0;
+      hs.cnt[R.sortf] = 1;
+    }
     if (R.log) {
       for (int id : {R.l1, R.l1_next, R.newp})
         if ((s = ensure(id, 4 * nedb))) return s;
@@ -1245,9 +1302,7 @@ hisa_status Engine::init_run_state() {
   }
   hs.cnt[sc.tmp_cnt] = 0;
   hs.cnt[sc.raw_cnt] = hs.cnt[sc.group_cnt] = 0;
-  if (b <= kDenseMaxBits && ((s = ensure(sc.dense_first, (1ull << b) + 2)) ||
-                             (s = ensure(sc.first_l0, (1ull << b) + 2)) || (s = ensure(sc.first_l1, (1ull << b) + 2))))
-    return s;
+  if (b <= kDenseMaxBits && (s = ensure(sc.dense_first, (1ull << b) + 2))) return s;
   if ((s = ensure(sc.groups, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
       (s = ensure(sc.dense_status, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)))
     return s;
@@ -1329,13 +1384,18 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
             kstat[kKIndex].bytes += 8.0 * double(1u << b);
             kstat[kKGroups].bytes += 16.0 * double(1u << b) + 8.0 * ng;
             // (+ the full levels' runs read for the set difference)
-            kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + bmb + (m + double(l_prev[i])) * kb;
+            kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + bmb + m * kb;
             kstat[kKDenseScan].bytes += 16.0 * ng;
             kstat[kKDenseEmit].bytes += bmb + nn * kb;
           } else {
             kstat[kKRadixPass].bytes += passes * 2.0 * nn * kb;
           }
-          if (R.log && hs.cnt[R.bigf]) {
+          if (R.append) {
+            // unique of new into delta, then delta copied behind full with its
+            // level index
+            if (nn > 0 && !dense) kstat[kKSetop].bytes += (nn + nd) * kb;
+            if (nd > 0) kstat[kKAppend].bytes += 2.0 * nd * kb + 8.0 * double((1u << b) + 1);
+          } else if (R.log && hs.cnt[R.bigf]) {
             // small level folded in, then new merged into the large level
             const double lp = double(l_prev[i]);
             if (lp > 0) kstat[kKSetop].bytes += 2.0 * (m + lp) * kb;
@@ -1415,7 +1475,16 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
         for (size_t q = 0; q < rows[i].size(); ++q) h[q].push_back(rows[i][q]);
       }
     }
-    if (!hs.go) break;
+    if (!hs.go) {
+      if (hs.aux[2]) {   // an append-only full reached kMaxLevels: merge its levels, go on
+        if ((s = compact_levels())) return s;
+        hs.aux[2] = 0;
+        hs.go = 1;
+        if ((s = upload())) return s;
+        continue;
+      }
+      break;
+    }
   }
   if ((s = merge_levels())) return s;
   if (hs.iter >= cfg.max_iters && hs.aux[0] == hs.iter)
@@ -1472,6 +1541,46 @@ hisa_status Engine::merge_levels() {
     if ((s = regrow()) || (s = upload())) return s;
   }
   return ctx_fail(HISA_ERR_OOM, "buffers keep overflowing", "level merge");
+}
+
+// An append-only full with kMaxLevels levels: sort it (its levels are
+// disjoint, so the sort leaves it duplicate-free) and index it as one level.
+hisa_status Engine::compact_levels() {
+  hisa_status s;
+  for (int r : idb) {
+    Relation& R = rels[r];
+    if (!R.append || hs.cnt[R.nlv] <= 1) continue;
+    const uint64_t n = hs.cnt[R.full];
+    const int kt = wide ? radix_tile<uint64_t>() : radix_tile<uint32_t>();
+    if ((s = ensure(R.full_next, n)) || (s = ensure(sc.radix_status, (n / kt + 2) * kRadixDigits))) return s;
+    if ((s = upload())) return s;
+    std::vector<Op> ops;
+    Op z{};
+    z.kind = Op::CTL;
+    z.ctl.st = dst;
+    z.ctl.cmd[z.ctl.n++] = {kCtlZeroSmall, sc.hist, 8 * 256, 0};
+    ops.push_back(z);
+    Op h{};
+    h.kind = Op::HIST;
+    h.hist = RadixHistArgs{dst, R.full, R.full, sc.hist, passes, 0};
+    ops.push_back(h);
+    emit_sort(ops, R.full, R.full_next, R.full, sc.hist, 0, 0);
+    if (passes & 1) {
+      Op w{};
+      w.kind = Op::CTL;
+      w.ctl.st = dst;
+      w.ctl.cmd[w.ctl.n++] = {kCtlSwap, R.full, R.full_next, 0};
+      ops.push_back(w);
+    }
+    Op x{};
+    x.kind = Op::INDEX;
+    x.index = IndexArgs{dst, R.full, R.full, R.lvidx, b, -1, 0, b};
+    ops.push_back(x);
+    if ((s = exec(ops)) || (s = download())) return s;
+    if (hs.overflow || hs.error) return ctx_fail(HISA_ERR_CUDA, "level merge of an append-only full", nullptr);
+    hs.cnt[R.nlv] = 1;
+  }
+  return upload();
 }
 
 // Runs one iteration with `ops` (host-driven) until it commits, growing
@@ -1576,19 +1685,29 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
   void *t0 = nullptr, *t1 = nullptr;
   hisa_status s;
   int src = r.idb ? r.full : r.base;
-  if (r.idb && r.order == 1) {
-    // stored (c1, c0): exchange the columns and sort, so the caller gets the
-    // lexicographic order of the declared columns
+  if (r.idb && (r.order == 1 || r.append)) {
+    // stored (c1, c0), or as unmerged levels: (exchange the columns and) sort,
+    // so the caller gets the lexicographic order of the declared columns
     const int kt = wide ? radix_tile<uint64_t>() : radix_tile<uint32_t>();
     if ((s = ensure(sc.tmp_a, size)) || (s = ensure(sc.tmp_b, size)) ||
         (s = ensure(sc.radix_status, (size / kt + 2) * kRadixDigits)))
       return s;
     if ((s = upload())) return s;
     std::vector<Op> ops;
-    Op w{};
-    w.kind = Op::SWAP;
-    w.swap = SwapArgs{dst, r.full, r.full, sc.tmp_a, sc.tmp_cnt, b, 0, 0};
-    ops.push_back(w);
+    if (r.order == 1) {
+      Op w{};
+      w.kind = Op::SWAP;
+      w.swap = SwapArgs{dst, r.full, r.full, sc.tmp_a, sc.tmp_cnt, b, 0, 0};
+      ops.push_back(w);
+    } else {
+      CU(cudaMemcpyAsync(hs.buf[sc.tmp_a].ptr, hs.buf[r.full].ptr, size * (wide ? 8 : 4), cudaMemcpyDeviceToDevice,
+                         stream));
+      Op c{};
+      c.kind = Op::CTL;
+      c.ctl.st = dst;
+      c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, sc.tmp_cnt, (long long)size, 0};
+      ops.push_back(c);
+    }
     Op z{};
     z.kind = Op::CTL;
     z.ctl.st = dst;

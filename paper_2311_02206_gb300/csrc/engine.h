@@ -40,6 +40,11 @@ struct Relation {
   // gate = |l1| when l1 is due to be merged into full, else 0
   bool log = false;
   bool dense_head = false;   // its writer in iterations >= 2 is a dense join (writes delta itself)
+  // append-only full (dense_head relations): one sorted level per iteration,
+  // lvidx = each level's direct index by the kept column, nlv = levels
+  bool append = false;
+  int lvidx = -1, nlv = -1;
+  int sortf = -1;   // 1 unless a dense join wrote this iteration's delta itself
   int order = 0;   // storage order of an IDB relation: 0 = (c0, c1), 1 = (c1, c0)
   int l1 = -1, l1_next = -1, newp = -1, gate = -1;
   int bigf = -1, smallf = -1;   // this iteration merges new straight into full / probes it
@@ -60,7 +65,7 @@ struct StepPlan {
 };
 
 struct Op {
-  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT } kind;
+  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT, APPEND } kind;
   CtlArgs ctl;
   JoinArgs join;
   RadixPassArgs pass;
@@ -73,6 +78,7 @@ struct Op {
   SwapArgs swap;
   DiffArgs diff;
   GroupArgs groups;
+  AppendArgs append;
   DenseArgs dense;
 };
 
@@ -82,7 +88,7 @@ struct Scratch {
   int groups, dense_status;   // group starts of a delta and the dense join's per-group counts/offsets
   int dense_bm;               // the dense join's per-group bitmaps
   int dense_first;            // direct index of a delta by its kept column (group starts)
-  int first_l0, first_l1;     // direct indexes of the head's full levels by the kept column
+
   int group_cnt, raw_cnt;     // count-only slots
 };
 
@@ -150,6 +156,7 @@ class Engine {
   void emit_tail(std::vector<Op>& ops, bool force);
   void emit_level_merge(std::vector<Op>& ops, const Relation& R, bool force);
   hisa_status merge_levels();
+  hisa_status compact_levels();
   template <typename K> hisa_status exec_t(const std::vector<Op>& ops);
   hisa_status exec(const std::vector<Op>& ops);
   template <typename K> hisa_status prepare_rel_t(Relation& r, int order, int slot);

@@ -50,7 +50,26 @@ struct CommitArgs {
   // a second (full, full_next) pair swapped instead when cnt[alt_flag1 - 1]
   // is non-zero (log-structured full: delta merged into the large level)
   int alt_full[8], alt_full_next[8], alt_flag1[8];
+  // append-only full (dense-join relations): 1 + cnt slot of its level count
+  // (0: not append-only); the commit adds delta's size to full's count and
+  // one level, and asks the host to compact past max_levels
+  int append_nlv1[8];
+  int max_levels;
   int force;   // commit even when no delta is non-empty (first iteration)
+};
+
+// Appends a sorted, duplicate-free delta to an append-only full as a new
+// level: copies it behind full's cnt tuples and writes the level's direct
+// index (first position of every kept value g in [0, 2^bits], absolute in
+// full).  Counts are bumped by the commit, so a re-run rewrites the same
+// places.
+struct AppendArgs {
+  DevState* st;
+  int src_buf, src_cnt;
+  int full_buf, full_cnt;
+  int lvidx_buf, nlv_cnt;   // u64 [levels][2^bits + 1]
+  int b, bits;
+  int skip_mask, stage_bit;
 };
 
 struct EncodeArgs {
@@ -110,7 +129,7 @@ struct SwapArgs {
 
 enum KernelKind : int {
   kKEncode, kKDecode, kKRuns, kKHist, kKRadixPass, kKSetopPartition, kKSetop, kKIndex,
-  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKindCount
+  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKAppend, kKindCount
 };
 extern const char* const kKernelNames[kKindCount];
 
@@ -162,6 +181,7 @@ template <typename K> void launch_count_runs(const RunsArgs& a, const Grid& g, c
 template <typename K> void launch_swap(const SwapArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_diff(const DiffArgs& a, const Grid& g, cudaStream_t s);
 void launch_group_compact(const GroupArgs& a, int bits, cudaStream_t s);
+template <typename K> void launch_append(const AppendArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_hist(const InstArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_bounds(const InstArgs& a, const Grid& g, cudaStream_t s);

@@ -119,6 +119,43 @@ void launch_inst_bounds(const InstArgs& a, const Grid& g, cudaStream_t s) {
 }
 
 template <typename K>
+__global__ void k_append(AppendArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t n = st->cnt[a.src_cnt];
+  if (n == 0) return;
+  const uint64_t base = st->cnt[a.full_cnt], lv = st->cnt[a.nlv_cnt];
+  const uint64_t nk = (1ull << a.bits) + 1;
+  if (base + n > st->buf[a.full_buf].cap || (lv + 1) * nk > st->buf[a.lvidx_buf].cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicMax((unsigned long long*)&st->need[a.full_buf], (unsigned long long)(base + n));
+      atomicMax((unsigned long long*)&st->need[a.lvidx_buf], (unsigned long long)((lv + 1) * nk));
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    return;
+  }
+  const K* src = static_cast<const K*>(st->buf[a.src_buf].ptr);
+  K* full = static_cast<K*>(st->buf[a.full_buf].ptr) + base;
+  uint64_t* idx = static_cast<uint64_t*>(st->buf[a.lvidx_buf].ptr) + lv * nk;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += stride) full[i] = src[i];
+  for (uint64_t k = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; k < nk; k += stride) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const uint64_t m = (lo + hi) >> 1;
+      if ((uint64_t(src[m]) >> a.b) < k) lo = m + 1;
+      else hi = m;
+    }
+    idx[k] = base + lo;
+  }
+}
+
+template <typename K>
+void launch_append(const AppendArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKAppend, s, (k_append<K><<<g.small * 2, 256, 0, s>>>(a)));
+}
+
+template <typename K>
 void launch_encode(const EncodeArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKEncode, s, (k_encode<K><<<g.small, 256, 0, s>>>(a)));
 }
@@ -238,6 +275,7 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_count_runs<K>(const RunsArgs&, const Grid&, cudaStream_t);        \
   template void launch_swap<K>(const SwapArgs&, const Grid&, cudaStream_t);              \
   template void launch_diff<K>(const DiffArgs&, const Grid&, cudaStream_t);              \
+  template void launch_append<K>(const AppendArgs&, const Grid&, cudaStream_t);          \
   template void launch_join_dense<K>(const DenseArgs&, const Grid&, cudaStream_t);       \
   template void launch_radix_hist<K>(const RadixHistArgs&, const Grid&, cudaStream_t);   \
   template void launch_radix_pass<K>(const RadixPassArgs&, const Grid&, cudaStream_t);   \
