@@ -400,17 +400,22 @@ def run_hisa(a):
             ectx.run()
             return sum(len(ectx.read_relation(k, out=outs[k])[0]) for k in idb_names)
 
+        estep()   # first use: buffers grow and caching-allocator blocks are created
         estep()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        e_ms = []
         for _ in range(a.e2e_steps):
+            ts = time.perf_counter()
             got = estep()
+            torch.cuda.synchronize()
+            e_ms.append(round((time.perf_counter() - ts) * 1e3, 2))
         torch.cuda.synchronize()
         et = time.perf_counter() - t0
         assert got == n_reach
         ev = _sum_over_ranks(float(n_reach) * a.e2e_steps, world) / _max_over_ranks(et, world)
         e2e = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": int(edb_bytes),
-               "d2h_bytes_per_step": int(8 * n_reach), "steps": a.e2e_steps,
+               "d2h_bytes_per_step": int(8 * n_reach), "steps": a.e2e_steps, "step_ms": e_ms,
                "loop": "CUDA graph while node (device-side termination test)"}
         ectx.close()
 
