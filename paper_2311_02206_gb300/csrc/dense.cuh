@@ -52,6 +52,7 @@ struct DenseArgs {
   // tuples are removed from each group's bitmap, so the join writes
   // delta = new \ full itself (-1: no difference)
   int full_buf, lvidx_buf, nlv_cnt;
+  int drop_self;                // the rule's filter kept != other: drop bit g in group g
 };
 
 constexpr int kDenseThreads = 128;
@@ -152,6 +153,10 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
     // set difference against full (Section 5.1 "populating delta"): clear the
     // bits of the group's tuples already in full; both levels hold the same
     // kept value first, so each contributes one contiguous run
+    if (a.drop_self && tid == 0) {
+      const uint32_t g = uint32_t(uint64_t(outer[s]) >> a.b) & vmask;
+      atomicAnd(&s_bm[g >> 5], ~(1u << (g & 31)));
+    }
     if (a.full_buf >= 0) {
       const uint64_t nlv = st->cnt[a.nlv_cnt], nk = (1ull << a.b) + 1;
       const uint64_t* lvidx = static_cast<const uint64_t*>(st->buf[a.lvidx_buf].ptr);

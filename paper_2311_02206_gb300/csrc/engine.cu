@@ -160,6 +160,7 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.groups = new_slot(8);
   sc.dense_status = new_slot(8);
   sc.dense_bm = new_slot(4);
+  sc.tmp_hist = new_slot(8);
   sc.dense_first = new_slot(8);
   sc.group_cnt = nslots++;
   sc.raw_cnt = nslots++;
@@ -397,6 +398,10 @@ hisa_status Engine::plan_variant(const hisa_rule& R, int delta_atom, std::vector
       }
     if (need.size() > 2) return ctx_fail(HISA_ERR_UNSUPPORTED, "Tmp relation needs more than two columns", nullptr);
     if (need.size() == 1) need.push_back(need[0]);
+    // the head's first stored variable first: the final join then keeps the
+    // high half of Tmp (what the grouped bitmap join needs), and any join
+    // reads either half
+    if (need[1] == int(R.head.var[rels[R.head.rel].order])) std::swap(need[0], need[1]);
     sp.proj0 = src_of[need[0]];
     sp.proj1 = src_of[need[1]];
     sp.to_tmp = true;
@@ -503,11 +508,23 @@ hisa_status Engine::compile() {
       if (!v.empty() && !v.back().to_tmp && v.back().out_rel == r) w.push_back(&v);
     return w;
   };
+  // the last step of a one- or two-step variant: delta (or Tmp, sorted by
+  // its kept column first) joined with an EDB relation on its low half,
+  // keeping the high half and the inner's other column, with at most the
+  // filter kept != other
   auto dense_ok = [&](const std::vector<StepPlan>& v, int r) {
-    if (v.size() != 1) return false;
-    const StepPlan& sp = v[0];
-    return sp.out_rel == r && sp.outer_slot == rels[r].delta && sp.has_inner && !rels[sp.inner_rel].idb &&
-           sp.nfilt == 0 && sp.outer_kcol == 1 && sp.proj0 == kSrcOuter0 && sp.proj1 == kSrcOther;
+    if (v.empty() || v.size() > 2) return false;
+    const StepPlan& sp = v.back();
+    const bool outer_ok = v.size() == 1 ? sp.outer_slot == rels[r].delta : sp.outer_slot == sc.tmp_a;
+    const bool filt_ok = sp.nfilt == 0 ||
+                         (sp.nfilt == 1 && sp.fop[0] == kFiltNeq &&
+                          ((sp.fa[0] == kSrcOuter0 && sp.fb[0] == kSrcOther) ||
+                           (sp.fa[0] == kSrcOther && sp.fb[0] == kSrcOuter0)));
+    // and nothing probes r (its full becomes append-only levels, not one
+    // sorted array an index could be built over)
+    return outer_ok && filt_ok && sp.out_rel == r && sp.has_inner && !rels[sp.inner_rel].idb &&
+           sp.outer_kcol == 1 && sp.proj0 == kSrcOuter0 && sp.proj1 == kSrcOther && !rels[r].need_idx[0] &&
+           !rels[r].need_idx[1];
   };
   bool reorder = false;
   if (dense_on)
@@ -515,7 +532,9 @@ hisa_status Engine::compile() {
       auto w = writers(r);
       if (w.size() != 1 || w[0]->size() != 1) continue;
       const StepPlan& sp = (*w[0])[0];
-      if (sp.outer_slot != rels[r].delta || !sp.has_inner || rels[sp.inner_rel].idb || sp.nfilt) continue;
+      if (sp.outer_slot != rels[r].delta || !sp.has_inner || rels[sp.inner_rel].idb || sp.nfilt ||
+          rels[r].need_idx[0] || rels[r].need_idx[1])
+        continue;
       if (sp.outer_kcol == 0) {   // join column first in (c0, c1): store (c1, c0)
         rels[r].order = 1;
         reorder = true;
@@ -538,7 +557,7 @@ hisa_status Engine::compile() {
       auto w = writers(r);
       if (w.size() == 1 && dense_ok(*w[0], r)) {
         for (auto& v : planN)
-          if (&v == w[0]) v[0].dense = true;
+          if (&v == w[0]) v.back().dense = true;
         rels[r].dense_head = rels[r].append = true;
       }
     }
@@ -726,7 +745,7 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp) {
   d.dense = DenseArgs{dst, sp.outer_slot, sp.outer_cnt, sc.groups, sc.group_cnt,
                       sp.inner_col == 0 ? ir.base : ir.rev, ir.table[sp.inner_col], b,
                       out, out, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0,
-                      direct_bits > 0, hr.append ? hr.full : -1, hr.lvidx, hr.nlv};
+                      direct_bits > 0, hr.append ? hr.full : -1, hr.lvidx, hr.nlv, sp.nfilt > 0};
   ops.push_back(d);
   if (hr.append) {   // no unique pass in the tail; |new| (statistics) = |delta|
     Op f{};
@@ -757,17 +776,29 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
   ops.push_back(c);
   if (idb_inner) emit_idb_index(ops);
   for (auto& v : plans) {
+    const bool tmp_dense = v.size() > 1 && v.back().dense;
     if (v.size() > 1) {
       Op t{};
       t.kind = Op::CTL;
       t.ctl.st = dst;
       t.ctl.skip_mask = 1;
       t.ctl.cmd[t.ctl.n++] = {kCtlSetCnt, sc.tmp_cnt, 0};
+      if (tmp_dense) t.ctl.cmd[t.ctl.n++] = {kCtlZeroSmall, sc.tmp_hist, 8 * 256};
       ops.push_back(t);
     }
     for (auto& sp : v) {
-      if (sp.dense) emit_dense(ops, sp);
-      else emit_join(ops, sp);
+      if (sp.dense && sp.outer_slot == sc.tmp_a) {
+        // Tmp sorted (kept column first) so its groups are contiguous
+        emit_sort(ops, sc.tmp_a, sc.tmp_b, sc.tmp_cnt, sc.tmp_hist, 1, 0);
+        StepPlan d = sp;
+        d.outer_slot = (passes & 1) ? sc.tmp_b : sc.tmp_a;
+        emit_dense(ops, d);
+      } else if (sp.dense) {
+        emit_dense(ops, sp);
+      } else {
+        emit_join(ops, sp);
+        if (sp.to_tmp && tmp_dense) ops.back().join.hist_buf = sc.tmp_hist, ops.back().join.hist_passes = passes;
+      }
     }
   }
   // sort each new, unless every writer of it is a dense join (sorted and
@@ -777,7 +808,7 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
     for (auto& v : plans)
       if (!v.empty() && !v.back().to_tmp && v.back().out_rel == r) {
         any = true;
-        all_dense = all_dense && v.size() == 1 && v[0].dense;
+        all_dense = all_dense && v.back().dense;
       }
     if (any && all_dense) continue;
     const Relation& R = rels[r];
@@ -824,7 +855,7 @@ void Engine::emit_sort(std::vector<Op>& ops, int in, int alt, int cnt, int hist,
 // the merge drops nothing.  Idempotent: a re-run finds the small level empty
 // and takes the same decision.
 constexpr int kLevelRatio = 8;
-constexpr int kMaxLevels = 32;   // levels of an append-only full before the host merges them
+constexpr int kMaxLevels = 128;   // levels of an append-only full before the host merges them
 constexpr int kBigRatio = 2;
 void Engine::emit_level_merge(std::vector<Op>& ops, const Relation& R, bool force) {
   Op g{};
@@ -1205,13 +1236,15 @@ hisa_status Engine::regrow() {
       // the column-swapped delta sorted into the reverse-order mirror
       if (R.need_idx[1] && ((s = ensure(R.rswap, delta_cap)) || (s = ensure(R.rswap_alt, delta_cap)))) return s;
     }
+    // radix look-back words for new, the swapped delta and a sorted Tmp; Tmp's
+    // sort partner; the join's write chunks
+    if ((s = ensure(sc.radix_status, (std::max({new_cap, delta_cap, hs.buf[sc.tmp_a].cap}) / kt + 2) * kRadixDigits)) ||
+        (s = ensure(sc.tmp_b, hs.buf[sc.tmp_a].cap)) || (s = ensure(sc.starts, new_cap / kJoinChunk + 2)))
+      return s;
   }
   for (int r : idb) {   // new minus the large level holds at most |new|
     const Relation& R = rels[r];
     if (R.log && (s = ensure(R.newp, new_cap))) return s;
-    if ((s = ensure(sc.radix_status, (std::max(new_cap, delta_cap) / kt + 2) * kRadixDigits)) ||
-        (s = ensure(sc.starts, new_cap / kJoinChunk + 2)))
-      return s;
   }
   // next iterations: delta is the outer relation of the joins; full + new is merged
   if ((s = ensure(sc.offs, delta_cap + 1)) || (s = ensure(sc.join_status, delta_cap / kJoinTile + 2))) return s;
@@ -1303,6 +1336,7 @@ hisa_status Engine::init_run_state() {
   hs.cnt[sc.tmp_cnt] = 0;
   hs.cnt[sc.raw_cnt] = hs.cnt[sc.group_cnt] = 0;
   if (b <= kDenseMaxBits && (s = ensure(sc.dense_first, (1ull << b) + 2))) return s;
+  if ((s = ensure(sc.tmp_hist, 8 * 256)) || (s = ensure(sc.tmp_b, 4 * nedb))) return s;
   if ((s = ensure(sc.groups, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
       (s = ensure(sc.dense_status, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)))
     return s;
@@ -1372,9 +1406,18 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
           const Relation& R = rels[idb[i]];
           const double nn = double(hs.cnt[R.fresh]), nd = double(hs.cnt[R.delta]);
           const double m = double(m_prev[i]), dp = double(d_prev[i]);
-          bool dense = false;
+          bool dense = false, via_tmp = false;
           for (auto& v : planN)
-            if (!first && v.size() == 1 && v[0].dense && v[0].out_rel == idb[i]) dense = true;
+            if (!first && !v.empty() && v.back().dense && v.back().out_rel == idb[i]) {
+              dense = true;
+              via_tmp = v.size() > 1;
+            }
+          if (via_tmp) {   // first join into Tmp, Tmp sorted by its kept column
+            const double tm = double(hs.cnt[sc.tmp_cnt]);
+            kstat[kKJoinWrite].bytes += 2.0 * tm * kb + dp * (kb + 8.0);
+            kstat[kKJoinCount].bytes += dp * (kb + 8.0 + 16.0);
+            kstat[kKRadixPass].bytes += passes * 2.0 * tm * kb;
+          }
           if (dense) {
             // group starts: direct index of delta, compaction; mark: read delta, probe,
             // read the inner runs (raw results), write the bitmaps; scan:

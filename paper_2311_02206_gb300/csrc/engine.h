@@ -87,6 +87,7 @@ struct Scratch {
   int runs, total, tmp_cnt;   // count-only slots
   int groups, dense_status;   // group starts of a delta and the dense join's per-group counts/offsets
   int dense_bm;               // the dense join's per-group bitmaps
+  int tmp_hist;               // digit histograms of a Tmp relation sorted before a dense join
   int dense_first;            // direct index of a delta by its kept column (group starts)
 
   int group_cnt, raw_cnt;     // count-only slots
