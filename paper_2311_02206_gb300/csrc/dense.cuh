@@ -59,6 +59,82 @@ constexpr int kDenseThreads = 128;
 constexpr int kDenseCtasPerSm = 16;   // latency-bound (L2 probes and run reads): full occupancy
 constexpr int kDenseMaxBits = 18;   // bitmap of 2^18 bits = 32 KB of shared memory
 
+// Group starts by one pass over a sorted array (heads of runs of equal
+// g = code >> b, compacted in order by a decoupled look-back over tiles): for
+// key spaces too large for a direct index (batched runs).
+constexpr int kGroupThreads = 256, kGroupItems = 8, kGroupTile = kGroupThreads * kGroupItems;
+template <typename K>
+__global__ void __launch_bounds__(kGroupThreads) k_group_starts(GroupArgs a) {
+  __shared__ uint64_t s_scan[32];
+  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_tile;
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t n = st->cnt[a.in_cnt];
+  uint64_t* out = static_cast<uint64_t*>(st->buf[a.out_buf].ptr);
+  const uint64_t ocap = st->buf[a.out_buf].cap;
+  if (n == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->cnt[a.out_cnt] = 0;
+      if (ocap >= 1) out[0] = 0;
+    }
+    return;
+  }
+  const uint64_t ntiles = (n + kGroupTile - 1) / kGroupTile;
+  if (st->buf[a.status_buf].cap < ntiles) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicMax((unsigned long long*)&st->need[a.status_buf], (unsigned long long)ntiles);
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    return;
+  }
+  const K* in = static_cast<const K*>(st->buf[a.in_buf].ptr);
+  uint64_t* status = static_cast<uint64_t*>(st->buf[a.status_buf].ptr);
+  const uint32_t epoch = st->epoch;
+  const int tid = threadIdx.x;
+  while (true) {
+    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    const uint64_t i0 = tile * kGroupTile + uint64_t(tid) * kGroupItems;
+    uint32_t heads = 0;
+    uint64_t prev = i0 > 0 && i0 <= n ? uint64_t(in[i0 - 1]) >> a.b : ~0ull;
+#pragma unroll
+    for (int k = 0; k < kGroupItems; ++k) {
+      const uint64_t i = i0 + k;
+      if (i >= n) break;
+      const uint64_t g = uint64_t(in[i]) >> a.b;
+      if (i == 0 || g != prev) heads |= 1u << k;
+      prev = g;
+    }
+    uint64_t tile_heads;
+    const uint64_t excl = block_exclusive_sum<uint64_t>(__popc(heads), s_scan, &tile_heads);
+    if (tid < 32) {
+      const uint64_t base = lookback_warp(status, tile, tile_heads, epoch, &st->error);
+      if (tid == 0) s_base = base;
+    }
+    __syncthreads();
+    uint64_t w = s_base + excl;
+#pragma unroll
+    for (int k = 0; k < kGroupItems; ++k)
+      if (heads & (1u << k)) {
+        if (w < ocap) out[w] = i0 + k;
+        ++w;
+      }
+    if (tile == ntiles - 1 && tid == 0) {
+      const uint64_t total = s_base + tile_heads;
+      st->cnt[a.out_cnt] = total;
+      if (total + 1 <= ocap) out[total] = n;   // sentinel: end of the last group
+      else {
+        atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)(total + 1));
+        atomicOr(&st->overflow, 1u << a.stage_bit);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Phase 1: one group per CTA (taken in any order, so a large group delays
 // no other): mark the inner runs of the group's outer tuples -- a warp takes
 // 32 outer tuples at once (32 probes in flight), then its lanes stride over

@@ -161,6 +161,7 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.dense_status = new_slot(8);
   sc.dense_bm = new_slot(4);
   sc.tmp_hist = new_slot(8);
+  sc.gather = new_slot(4);
   sc.dense_first = new_slot(8);
   sc.group_cnt = nslots++;
   sc.raw_cnt = nslots++;
@@ -172,6 +173,10 @@ hisa_status Engine::init(const hisa_config& c) {
 
 Engine::~Engine() {
   if (stream || dst) cudaStreamSynchronize(stream);
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (once_exec) cudaGraphExecDestroy(once_exec);
+  if (once_graph) cudaGraphDestroy(once_graph);
   for (auto& kv : std::vector<std::pair<void*, size_t>>(allocs.begin(), allocs.end())) dev_free(kv.first);
   if (stream) cudaStreamSynchronize(stream);
   if (pool) cudaMemPoolDestroy(pool);
@@ -483,8 +488,8 @@ hisa_status Engine::compile() {
         slot_elem[id] = kb;
       }
   }
-  if (slot_elem[sc.tmp_a] != kb) {
-    for (int id : {sc.tmp_a, sc.tmp_b}) {
+  if (slot_elem[sc.tmp_a] != kb || slot_elem[sc.gather] != kb) {
+    for (int id : {sc.tmp_a, sc.tmp_b, sc.gather}) {
       dev_free(hs.buf[id].ptr);
       hs.buf[id] = {nullptr, 0};
       slot_elem[id] = kb;
@@ -501,7 +506,7 @@ hisa_status Engine::compile() {
   // writer in iterations >= 2 is one binary join of delta_R with an EDB
   // relation is stored with the non-join column first, so delta's tuples
   // of one kept value are contiguous (dense.cuh)
-  const bool dense_on = !(cfg.flags & HISA_FLAG_NO_DENSE) && !batched && b <= kDenseMaxBits;
+  const bool dense_on = !(cfg.flags & HISA_FLAG_NO_DENSE) && b <= kDenseMaxBits;
   auto writers = [&](int r) {
     std::vector<const std::vector<StepPlan>*> w;
     for (auto& v : planN)
@@ -558,17 +563,19 @@ hisa_status Engine::compile() {
       if (w.size() == 1 && dense_ok(*w[0], r)) {
         for (auto& v : planN)
           if (&v == w[0]) v.back().dense = true;
-        rels[r].dense_head = rels[r].append = true;
+        rels[r].dense_head = true;
+        rels[r].append = !batched;   // batched runs keep one sorted full (retirement cuts it by instance)
       }
     }
   // log-structured full where nothing probes full (it is only differenced
   // and merged): REACH and SG, not CSPA's inner IDB atoms nor batched runs
   for (int r : idb) {
     Relation& R = rels[r];
-    R.log = (cfg.flags & HISA_FLAG_LOG_FULL) && !batched && !R.need_idx[0] && !R.need_idx[1] && !R.append;
+    R.log = (cfg.flags & HISA_FLAG_LOG_FULL) && !R.need_idx[0] && !R.need_idx[1] && !R.append;
   }
   compiled = true;
   graph_stale = true;
+  once_stale = true;
   return HISA_OK;
 }
 
@@ -729,15 +736,23 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp) {
   const Relation& ir = rels[sp.inner_rel];
   const Relation& hr = rels[sp.out_rel];
   // group starts: a direct index of delta by the kept column, compacted to
-  // the non-empty groups
-  Op x{};
-  x.kind = Op::INDEX;
-  x.index = IndexArgs{dst, sp.outer_slot, sp.outer_cnt, sc.dense_first, b, -1, 1, b};
-  ops.push_back(x);
-  Op g{};
-  g.kind = Op::GCOMPACT;
-  g.groups = GroupArgs{dst, sc.dense_first, sp.outer_cnt, b, sc.groups, sc.group_cnt, sc.join_status, 3, 1, 0};
-  ops.push_back(g);
+  // the non-empty groups; one pass over delta when instance ids make the key
+  // space too large for a direct index
+  if (b + inst_bits <= kDirectMaxBits) {
+    Op x{};
+    x.kind = Op::INDEX;
+    x.index = IndexArgs{dst, sp.outer_slot, sp.outer_cnt, sc.dense_first, b, -1, 1, b + inst_bits};
+    ops.push_back(x);
+    Op g{};
+    g.kind = Op::GCOMPACT;
+    g.groups = GroupArgs{dst, sc.dense_first, sp.outer_cnt, b + inst_bits, sc.groups, sc.group_cnt, sc.join_status, 3, 1, 0};
+    ops.push_back(g);
+  } else {
+    Op g{};
+    g.kind = Op::GROUPS;
+    g.groups = GroupArgs{dst, sp.outer_slot, sp.outer_cnt, b, sc.groups, sc.group_cnt, sc.join_status, 3, 1, 0};
+    ops.push_back(g);
+  }
   // with an append-only full the join writes delta itself, into delta_next
   const int out = hr.append ? hr.delta_next : hr.fresh;
   Op d{};
@@ -804,14 +819,30 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
   // sort each new, unless every writer of it is a dense join (sorted and
   // duplicate-free already); the sorted new always ends in `fresh`
   for (int r : idb) {
-    bool any = false, all_dense = true;
+    bool any = false, all_dense = true, any_dense = false;
     for (auto& v : plans)
       if (!v.empty() && !v.back().to_tmp && v.back().out_rel == r) {
         any = true;
         all_dense = all_dense && v.back().dense;
+        any_dense = any_dense || v.back().dense;
       }
     if (any && all_dense) continue;
     const Relation& R = rels[r];
+    if (any_dense) {
+      // a dense join wrote part of new without digit histograms (a serving
+      // admission iteration runs it beside the non-recursive rules): count
+      // all of new again
+      Op z{};
+      z.kind = Op::CTL;
+      z.ctl.st = dst;
+      z.ctl.skip_mask = 1;
+      z.ctl.cmd[z.ctl.n++] = {kCtlZeroSmall, R.hist, 8 * 256, 0};
+      ops.push_back(z);
+      Op h{};
+      h.kind = Op::HIST;
+      h.hist = RadixHistArgs{dst, R.fresh, R.fresh, R.hist, passes, 1};
+      ops.push_back(h);
+    }
     emit_sort(ops, R.fresh, R.fresh_alt, R.fresh, R.hist, 1, 0);
     if (passes & 1) {
       Op w{};
@@ -956,15 +987,12 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
       m.gate1 = R.bigf + 1;
       ops.push_back(big);
       // small new: probe the large level, then difference + merge against
-      // the small one (a dense join wrote new minus full already, and in
-      // iteration 1 full is empty: no probe)
-      if (!R.dense_head) {
-        Op d{};
-        d.kind = Op::DIFF;
-        d.diff = DiffArgs{dst, R.full, R.full, sorted_new, R.fresh, R.newp, R.newp, sc.setop_status, 2, 3, 1,
-                          R.smallf + 1};
-        ops.push_back(d);
-      }
+      // the small one
+      Op d{};
+      d.kind = Op::DIFF;
+      d.diff = DiffArgs{dst, R.full, R.full, sorted_new, R.fresh, R.newp, R.newp, sc.setop_status, 2, 3, 1,
+                        R.smallf + 1};
+      ops.push_back(d);
       Op o{};
       o.kind = Op::SETOP;
       SetopArgs& a = o.setop;
@@ -972,8 +1000,8 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
       a.st = dst;
       a.a_buf = R.l1;
       a.a_cnt = R.l1;
-      a.b_buf = R.dense_head ? R.fresh : R.newp;
-      a.b_cnt = R.dense_head ? R.fresh : R.newp;
+      a.b_buf = R.newp;
+      a.b_cnt = R.newp;
       a.split_buf = sc.split;
       a.status_buf = sc.setop_status;
       a.d_buf = R.delta_next;
@@ -1044,6 +1072,7 @@ hisa_status Engine::exec_t(const std::vector<Op>& ops) {
       case Op::DIFF: launch_diff<K>(o.diff, grid, stream); break;
       case Op::GCOMPACT: launch_group_compact(o.groups, o.groups.b, stream); break;
       case Op::APPEND: launch_append<K>(o.append, grid, stream); break;
+      case Op::GROUPS: launch_group_starts<K>(o.groups, grid, stream); break;
       case Op::DENSE: launch_join_dense<K>(o.dense, grid, stream); break;
     }
   }
@@ -1335,7 +1364,7 @@ hisa_status Engine::init_run_state() {
   }
   hs.cnt[sc.tmp_cnt] = 0;
   hs.cnt[sc.raw_cnt] = hs.cnt[sc.group_cnt] = 0;
-  if (b <= kDenseMaxBits && (s = ensure(sc.dense_first, (1ull << b) + 2))) return s;
+  if (b + inst_bits <= kDirectMaxBits && (s = ensure(sc.dense_first, (1ull << (b + inst_bits)) + 2))) return s;
   if ((s = ensure(sc.tmp_hist, 8 * 256)) || (s = ensure(sc.tmp_b, 4 * nedb))) return s;
   if ((s = ensure(sc.groups, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
       (s = ensure(sc.dense_status, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)))
@@ -1381,6 +1410,9 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
   while (true) {
     const bool first = hs.iter == 0;
     const bool use_graph = !first && (cfg.flags & HISA_FLAG_GRAPH) && !timing && !batched;
+    // batched runs read per-instance counts after every iteration: one
+    // iteration per graph launch
+    const bool use_once = !first && (cfg.flags & HISA_FLAG_GRAPH) && !timing && batched;
     const size_t rec0 = timer.recs.size();
     std::vector<uint64_t> m_prev, d_prev, l_prev;
     for (int r : idb) {
@@ -1392,6 +1424,10 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
     if (use_graph) {
       if ((s = launch_graph())) return s;
       ++graph_launches;
+    } else if (use_once) {
+      if ((s = launch_once())) return s;
+      ++graph_launches;
+      graph_kernels += body_kernels;
     } else {
       if ((s = exec(first ? ops1 : opsN))) return s;
     }
@@ -1632,7 +1668,11 @@ hisa_status Engine::iterate_once(const std::vector<Op>& ops) {
   hisa_status s;
   bool rerun_all = true;
   for (int guard = 0; guard < 16; ++guard) {
-    if ((s = exec(rerun_all ? ops : tail))) return s;
+    if (guard == 0 && &ops == &opsN && (cfg.flags & HISA_FLAG_GRAPH) && !(cfg.flags & HISA_FLAG_PHASE_TIMES)) {
+      if ((s = launch_once())) return s;
+    } else if ((s = exec(rerun_all ? ops : tail))) {
+      return s;
+    }
     if ((s = download())) return s;
     if (hs.error)
       return ctx_fail(hs.error == kDevTimeout ? HISA_ERR_DEVICE_TIMEOUT : HISA_ERR_CUDA, "device error",
@@ -1651,6 +1691,42 @@ hisa_status Engine::launch_graph() {
     if (s) return s;
   }
   CU(cudaGraphLaunch(graph_exec, stream));
+  return HISA_OK;
+}
+
+hisa_status Engine::launch_once() {
+  if (!once_exec || once_stale) {
+    if (once_exec) {
+      cudaGraphExecDestroy(once_exec);
+      once_exec = nullptr;
+    }
+    if (once_graph) {
+      cudaGraphDestroy(once_graph);
+      once_graph = nullptr;
+    }
+    cudaStream_t cs;
+    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t saved = stream;
+    stream = cs;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      stream = saved;
+      cudaStreamDestroy(cs);
+      return ctx_fail(HISA_ERR_CUDA, "cudaStreamBeginCapture", cudaGetErrorString(e));
+    }
+    const uint64_t l0 = g_launches;
+    hisa_status s = exec(opsN);
+    body_kernels = g_launches - l0;
+    g_launches = l0;
+    e = cudaStreamEndCapture(cs, &once_graph);
+    stream = saved;
+    cudaStreamDestroy(cs);
+    if (s) return s;
+    if (e != cudaSuccess) return ctx_fail(HISA_ERR_CUDA, "cudaStreamEndCapture", cudaGetErrorString(e));
+    CU(cudaGraphInstantiate(&once_exec, once_graph, 0));
+    once_stale = false;
+  }
+  CU(cudaGraphLaunch(once_exec, stream));
   return HISA_OK;
 }
 

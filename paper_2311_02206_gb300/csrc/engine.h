@@ -65,7 +65,7 @@ struct StepPlan {
 };
 
 struct Op {
-  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT, APPEND } kind;
+  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT, APPEND, GROUPS } kind;
   CtlArgs ctl;
   JoinArgs join;
   RadixPassArgs pass;
@@ -88,6 +88,7 @@ struct Scratch {
   int groups, dense_status;   // group starts of a delta and the dense join's per-group counts/offsets
   int dense_bm;               // the dense join's per-group bitmaps
   int tmp_hist;               // digit histograms of a Tmp relation sorted before a dense join
+  int gather;                 // an instance's codes from both levels of a log-structured full
   int dense_first;            // direct index of a delta by its kept column (group starts)
 
   int group_cnt, raw_cnt;     // count-only slots
@@ -173,9 +174,13 @@ class Engine {
                            std::vector<uint32_t>& c1);
   hisa_status rebuild_serving_edb();
   hisa_status retire(const std::vector<uint64_t>& tickets);
+  hisa_status compact_dead();
   hisa_status compact(int slot, int next, const std::vector<uint64_t>& bnd, const std::vector<bool>& drop);
+  hisa_status declared_order(int slot, uint64_t begin, uint64_t count, int* out);
+  hisa_status resort(int slot, uint64_t begin, uint64_t count, bool swap, int* out);
   hisa_status launch_graph();
   hisa_status build_graph();
+  hisa_status launch_once();   // one iteration of opsN as a CUDA graph (batched / served loops)
 
   hisa_config cfg{};
   int device = 0;
@@ -206,6 +211,9 @@ class Engine {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_stale = true;
+  cudaGraph_t once_graph = nullptr;
+  cudaGraphExec_t once_exec = nullptr;
+  bool once_stale = true;
   hisa_run_stats last_stats{};
   KernelTimer timer;
   // batched instances: codes carry an instance id above the two columns
@@ -221,6 +229,8 @@ class Engine {
   uint32_t serve_slots = 0;
   uint64_t serve_budget = 0, active_bytes = 0, next_ticket = 1;
   std::vector<uint64_t> slot_owner;                  // ticket per slot, 0 = free
+  std::vector<char> slot_dirty;                      // a retired instance's tuples still in full
+  uint64_t dead_tuples = 0;                          // tuples of retired, not yet compacted instances
   std::unordered_map<uint64_t, Request> reqs;
   std::deque<uint64_t> pending;
   std::vector<Op> ops_admit;

@@ -181,6 +181,7 @@ template <typename K> void launch_count_runs(const RunsArgs& a, const Grid& g, c
 template <typename K> void launch_swap(const SwapArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_diff(const DiffArgs& a, const Grid& g, cudaStream_t s);
 void launch_group_compact(const GroupArgs& a, int bits, cudaStream_t s);
+template <typename K> void launch_group_starts(const GroupArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_append(const AppendArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_hist(const InstArgs& a, const Grid& g, cudaStream_t s);

@@ -151,6 +151,17 @@ __global__ void k_append(AppendArgs a) {
 }
 
 template <typename K>
+void launch_group_starts(const GroupArgs& a, const Grid& g, cudaStream_t s) {
+  CtlArgs c{};
+  c.st = a.st;
+  c.skip_mask = a.skip_mask;
+  c.n = 2;
+  c.cmd[0] = {kCtlEpoch, 0, 0};
+  c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
+  launch_ctl(c, s);
+  HISA_LAUNCH(kKGroups, s, (k_group_starts<K><<<g.setop, kGroupThreads, 0, s>>>(a)));
+}
+template <typename K>
 void launch_append(const AppendArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKAppend, s, (k_append<K><<<g.small * 2, 256, 0, s>>>(a)));
 }
@@ -276,6 +287,7 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_swap<K>(const SwapArgs&, const Grid&, cudaStream_t);              \
   template void launch_diff<K>(const DiffArgs&, const Grid&, cudaStream_t);              \
   template void launch_append<K>(const AppendArgs&, const Grid&, cudaStream_t);          \
+  template void launch_group_starts<K>(const GroupArgs&, const Grid&, cudaStream_t);     \
   template void launch_join_dense<K>(const DenseArgs&, const Grid&, cudaStream_t);       \
   template void launch_radix_hist<K>(const RadixHistArgs&, const Grid&, cudaStream_t);   \
   template void launch_radix_pass<K>(const RadixPassArgs&, const Grid&, cudaStream_t);   \

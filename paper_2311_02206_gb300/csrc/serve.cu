@@ -109,6 +109,57 @@ hisa_status Engine::instance_size(uint32_t rid, uint32_t inst, uint64_t* n) {
   return HISA_OK;
 }
 
+// Codes [begin, begin + count) of `slot`, stored (c1, c0), exchanged and
+// sorted into the declared column order; *out receives the slot holding them
+// from position 0 (scratch, valid until the next run).
+hisa_status Engine::declared_order(int slot, uint64_t begin, uint64_t count, int* out) {
+  return resort(slot, begin, count, true, out);
+}
+
+// The same, with or without the column exchange.
+hisa_status Engine::resort(int slot, uint64_t begin, uint64_t count, bool swap, int* out) {
+  const uint64_t kb = wide ? 8 : 4;
+  const int kt = wide ? radix_tile<uint64_t>() : radix_tile<uint32_t>();
+  hisa_status s;
+  if ((s = ensure(sc.tmp_a, count)) || (s = ensure(sc.tmp_b, count)) ||
+      (s = ensure(sc.radix_status, (count / kt + 2) * kRadixDigits)))
+    return s;
+  if (res_slot < 0) res_slot = new_slot(int(kb));
+  hs.buf[res_slot] = {static_cast<char*>(hs.buf[slot].ptr) + begin * kb, count};
+  hs.cnt[res_slot] = count;
+  if ((s = upload())) return s;
+  std::vector<Op> ops;
+  if (swap) {
+    Op w{};
+    w.kind = Op::SWAP;
+    w.swap = SwapArgs{dst, res_slot, res_slot, sc.tmp_a, sc.tmp_cnt, b, 0, 0};
+    ops.push_back(w);
+  } else {
+    CU(cudaMemcpyAsync(hs.buf[sc.tmp_a].ptr, hs.buf[res_slot].ptr, count * kb, cudaMemcpyDeviceToDevice, stream));
+    Op c{};
+    c.kind = Op::CTL;
+    c.ctl.st = dst;
+    c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, sc.tmp_cnt, (long long)count, 0};
+    ops.push_back(c);
+  }
+  Op z{};
+  z.kind = Op::CTL;
+  z.ctl.st = dst;
+  z.ctl.cmd[z.ctl.n++] = {kCtlZeroSmall, sc.hist, 8 * 256, 0};
+  ops.push_back(z);
+  Op h{};
+  h.kind = Op::HIST;
+  h.hist = RadixHistArgs{dst, sc.tmp_a, sc.tmp_cnt, sc.hist, passes, 0};
+  ops.push_back(h);
+  emit_sort(ops, sc.tmp_a, sc.tmp_b, sc.tmp_cnt, sc.hist, 0, 0);
+  if ((s = exec(ops)) || (s = download())) return s;
+  hs.buf[res_slot] = {nullptr, 0};
+  hs.cnt[res_slot] = 0;
+  if (hs.overflow || hs.error) return ctx_fail(HISA_ERR_CUDA, "re-sort into the declared column order", nullptr);
+  *out = (passes & 1) ? sc.tmp_b : sc.tmp_a;
+  return upload();
+}
+
 hisa_status Engine::read_instance(uint32_t rid, uint32_t inst, uint32_t* const* cols, uint64_t cap, uint64_t* n,
                                   int on_device) {
   if (!cols || !n || rid >= rels.size()) return ctx_fail(HISA_ERR_INVALID_ARG, "read_instance", nullptr);
@@ -119,12 +170,18 @@ hisa_status Engine::read_instance(uint32_t rid, uint32_t inst, uint32_t* const* 
   std::vector<uint64_t> bnd;
   hisa_status s = inst_bounds(slot, bnd);
   if (s) return s;
-  const uint64_t lo = bnd[inst], cnt = bnd[inst + 1] - bnd[inst];
+  uint64_t lo = bnd[inst];
+  const uint64_t cnt = bnd[inst + 1] - bnd[inst];
   *n = cnt;
   if (cap < cnt) return ctx_fail(HISA_ERR_CAPACITY, "read_instance: buffer too small", nullptr);
   if (cnt == 0) return HISA_OK;
+  int src = slot;
+  if (r.idb && r.order == 1) {   // stored (c1, c0): into the declared order
+    if ((s = declared_order(slot, lo, cnt, &src))) return s;
+    lo = 0;
+  }
   if (on_device) {
-    DecodeArgs a{dst, slot, slot, cols[0], cols[1], b, 0, lo, cnt};
+    DecodeArgs a{dst, src, src, cols[0], cols[1], b, 0, lo, cnt};
     if (wide) launch_decode<uint64_t>(a, grid, stream);
     else launch_decode<uint32_t>(a, grid, stream);
     CU(cudaGetLastError());
@@ -132,7 +189,7 @@ hisa_status Engine::read_instance(uint32_t rid, uint32_t inst, uint32_t* const* 
     return HISA_OK;
   }
   std::vector<uint32_t> c0, c1;
-  if ((s = decode_range(slot, lo, cnt, c0, c1))) return s;
+  if ((s = decode_range(src, lo, cnt, c0, c1))) return s;
   std::memcpy(cols[0], c0.data(), cnt * 4);
   std::memcpy(cols[1], c1.data(), cnt * 4);
   return HISA_OK;
@@ -177,6 +234,8 @@ hisa_status Engine::serve_open(uint32_t max_instances, uint32_t max_value, uint6
   serve_budget = budget ? budget : cfg.hbm_budget_bytes;
   active_bytes = 0;
   slot_owner.assign(max_instances, 0);
+  slot_dirty.assign(max_instances, 0);
+  dead_tuples = 0;
   hisa_status s;
   if ((s = compile())) return s;
   // plans: ordinary iterations, and admission iterations that also run the
@@ -284,38 +343,74 @@ hisa_status Engine::compact(int slot, int next, const std::vector<uint64_t>& bnd
   return HISA_OK;
 }
 
-// Copies out and removes the tuples of finished requests.
+// Removes the tuples of retired instances from full (both levels) and its
+// mirror.  Deferred until a slot is reused or the dead tuples are half of the
+// live ones: a retired instance's tuples join nothing (its delta is empty and
+// instance ids keep codes apart), so they only cost merge traffic meanwhile.
+hisa_status Engine::compact_dead() {
+  hisa_status s;
+  std::vector<bool> drop(serve_slots, false);
+  bool any = false;
+  for (uint32_t i = 0; i < serve_slots; ++i)
+    if (slot_dirty[i]) drop[i] = any = true;
+  if (!any) return HISA_OK;
+  for (int r : idb) {
+    Relation& R = rels[r];
+    std::vector<uint64_t> bnd;
+    if ((s = inst_bounds(R.full, bnd)) || (s = compact(R.full, R.full_next, bnd, drop))) return s;
+    if (R.log && ((s = inst_bounds(R.l1, bnd)) || (s = compact(R.l1, R.l1_next, bnd, drop)))) return s;
+    if (R.need_idx[1] && ((s = inst_bounds(R.rev, bnd)) || (s = compact(R.rev, R.rev_next, bnd, drop)))) return s;
+  }
+  std::fill(slot_dirty.begin(), slot_dirty.end(), 0);
+  dead_tuples = 0;
+  return upload();
+}
+
+// Copies out the tuples of finished requests (they leave full lazily).
 hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
   if (tickets.empty()) return HISA_OK;
   hisa_status s;
   for (int r : idb) {
     Relation& R = rels[r];
-    std::vector<uint64_t> bnd;
+    std::vector<uint64_t> bnd, bnd1;
     if ((s = inst_bounds(R.full, bnd))) return s;
-    std::vector<bool> drop(serve_slots, false);
+    if (R.log && (s = inst_bounds(R.l1, bnd1))) return s;
     const uint64_t kb = wide ? 8 : 4;
     for (uint64_t t : tickets) {
       Request& q = reqs[t];
-      const uint64_t lo = bnd[q.slot], cnt = bnd[q.slot + 1] - bnd[q.slot];
+      const uint64_t lo = bnd[q.slot], cnt0 = bnd[q.slot + 1] - bnd[q.slot];
+      const uint64_t lo1 = R.log ? bnd1[q.slot] : 0, cnt1 = R.log ? bnd1[q.slot + 1] - bnd1[q.slot] : 0;
+      const uint64_t cnt = cnt0 + cnt1;
       void* p = nullptr;
       if (cnt) {   // the finished instance's codes, copied aside on the device
         if ((s = dev_alloc(cnt * kb, &p))) return s;
-        CU(cudaMemcpyAsync(p, static_cast<char*>(hs.buf[R.full].ptr) + lo * kb, cnt * kb, cudaMemcpyDeviceToDevice,
+        int src = R.full;
+        uint64_t from = lo;
+        if (cnt1) {   // in both levels of a log-structured full: gathered and sorted
+          if ((s = ensure(sc.gather, cnt))) return s;
+          char* g = static_cast<char*>(hs.buf[sc.gather].ptr);
+          if (cnt0)
+            CU(cudaMemcpyAsync(g, static_cast<char*>(hs.buf[R.full].ptr) + lo * kb, cnt0 * kb,
+                               cudaMemcpyDeviceToDevice, stream));
+          CU(cudaMemcpyAsync(g + cnt0 * kb, static_cast<char*>(hs.buf[R.l1].ptr) + lo1 * kb, cnt1 * kb,
+                             cudaMemcpyDeviceToDevice, stream));
+          if ((s = resort(sc.gather, 0, cnt, R.order == 1, &src))) return s;
+          from = 0;
+        } else if (R.order == 1) {   // stored (c1, c0): kept in the declared order
+          if ((s = declared_order(R.full, lo, cnt, &src))) return s;
+          from = 0;
+        }
+        CU(cudaMemcpyAsync(p, static_cast<char*>(hs.buf[src].ptr) + from * kb, cnt * kb, cudaMemcpyDeviceToDevice,
                            stream));
       }
       q.result[r] = {p, cnt};
-      drop[q.slot] = true;
-    }
-    if ((s = compact(R.full, R.full_next, bnd, drop))) return s;
-    // the reverse-order mirror of full loses the same instances
-    if (R.need_idx[1]) {
-      if ((s = inst_bounds(R.rev, bnd))) return s;
-      if ((s = compact(R.rev, R.rev_next, bnd, drop))) return s;
+      dead_tuples += cnt;
     }
   }
   for (uint64_t t : tickets) {
     Request& q = reqs[t];
     slot_owner[q.slot] = 0;
+    slot_dirty[q.slot] = 1;   // its tuples leave full at the next compaction
     active_bytes -= std::min(active_bytes, q.est_bytes);
     q.done = true;
     dev_free(q.dev_edges);
@@ -334,7 +429,17 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
     while (!pending.empty()) {
       const uint64_t t = pending.front();
       Request& q = reqs[t];
-      auto free_slot = std::find(slot_owner.begin(), slot_owner.end(), 0ull);
+      auto clean_free = [&] {
+        for (uint32_t i = 0; i < serve_slots; ++i)
+          if (!slot_owner[i] && !slot_dirty[i]) return slot_owner.begin() + i;
+        return slot_owner.end();
+      };
+      auto free_slot = clean_free();
+      if (free_slot == slot_owner.end() &&
+          std::find(slot_owner.begin(), slot_owner.end(), 0ull) != slot_owner.end()) {
+        if ((s = compact_dead())) return s;   // a retired slot is reused: its tuples go first
+        free_slot = clean_free();
+      }
       if (free_slot == slot_owner.end()) break;
       if (serve_budget && active_bytes + q.est_bytes > serve_budget && active_bytes > 0) break;
       q.slot = int(free_slot - slot_owner.begin());
@@ -371,6 +476,9 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
       }
     if ((s = retire(finished))) return s;
     out.retired += uint32_t(finished.size());
+    uint64_t live = 0;
+    for (int r : idb) live += hs.cnt[rels[r].full] + (rels[r].log ? hs.cnt[rels[r].l1] : 0);
+    if (dead_tuples * 2 > live && (s = compact_dead())) return s;
   }
   out.pending = uint32_t(pending.size());
   out.active = uint32_t(std::count_if(slot_owner.begin(), slot_owner.end(), [](uint64_t t) { return t != 0; }));
