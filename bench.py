@@ -53,7 +53,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hisa", "reference"], default="hisa")
     ap.add_argument("--instances", type=int, default=4096, help="batch5: number of instances")
-    ap.add_argument("--budget-gb", type=float, default=100.0, help="batch5: serving memory budget")
+    ap.add_argument("--budget-gb", type=float, default=60.0,
+                    help="batch5: serving admission budget (estimates; device memory in use peaked near 2.4x it)")
     ap.add_argument("--workload", choices=["rmat16", "rmat15", "rmat13", "er1000", "sg20k", "sg20k-literal", "cspa",
                                            "batch5"],
                     default="rmat16",

@@ -172,7 +172,7 @@ class Engine {
   hisa_status inst_bounds(int slot, std::vector<uint64_t>& bounds);
   hisa_status decode_range(int slot, uint64_t begin, uint64_t count, std::vector<uint32_t>& c0,
                            std::vector<uint32_t>& c1);
-  hisa_status rebuild_serving_edb();
+  hisa_status rebuild_serving_edb(const std::vector<uint64_t>& admitted);
   hisa_status retire(const std::vector<uint64_t>& tickets);
   hisa_status compact_dead();
   hisa_status compact(int slot, int next, const std::vector<uint64_t>& bnd, const std::vector<bool>& drop);
@@ -231,6 +231,8 @@ class Engine {
   std::vector<uint64_t> slot_owner;                  // ticket per slot, 0 = free
   std::vector<char> slot_dirty;                      // a retired instance's tuples still in full
   uint64_t dead_tuples = 0;                          // tuples of retired, not yet compacted instances
+  uint64_t dead_bytes = 0;                           // their admission estimates, released at compaction
+  bool edb_restage = true;                           // the staged EDB still holds retired instances' tuples
   std::unordered_map<uint64_t, Request> reqs;
   std::deque<uint64_t> pending;
   std::vector<Op> ops_admit;

@@ -236,6 +236,8 @@ hisa_status Engine::serve_open(uint32_t max_instances, uint32_t max_value, uint6
   slot_owner.assign(max_instances, 0);
   slot_dirty.assign(max_instances, 0);
   dead_tuples = 0;
+  dead_bytes = 0;
+  edb_restage = true;
   hisa_status s;
   if ((s = compile())) return s;
   // plans: ordinary iterations, and admission iterations that also run the
@@ -295,18 +297,28 @@ hisa_status Engine::serve_submit(uint32_t rid, const uint32_t* const* cols, uint
   return HISA_OK;
 }
 
-// The EDB of a serving session: the tuples of every active request, tagged
-// with its slot, staged and indexed again (after admissions).
-hisa_status Engine::rebuild_serving_edb() {
-  for (auto& r : rels)
-    if (!r.idb) r.staged = 0;
-  for (uint32_t slot = 0; slot < serve_slots; ++slot) {
-    const uint64_t t = slot_owner[slot];
-    if (!t) continue;
+// The EDB of a serving session: the tuples of the active requests, tagged
+// with their slots, then sorted and indexed again (after admissions).  The
+// newly admitted requests' tuples are appended to the staged ones; the
+// staging is rebuilt from the active requests only after a compaction (a
+// retired instance's staged tuples join nothing meanwhile: its delta is
+// empty and instance ids keep codes apart).
+hisa_status Engine::rebuild_serving_edb(const std::vector<uint64_t>& admitted) {
+  std::vector<uint64_t> add;
+  if (edb_restage) {
+    for (auto& r : rels)
+      if (!r.idb) r.staged = 0;
+    for (uint32_t slot = 0; slot < serve_slots; ++slot)
+      if (slot_owner[slot]) add.push_back(slot_owner[slot]);
+    edb_restage = false;
+  } else {
+    add = admitted;
+  }
+  for (uint64_t t : add) {
     Request& q = reqs[t];
     if (!q.n) continue;
     const uint32_t* cols[2] = {q.dev_edges, q.dev_edges + q.n};
-    load_inst = slot;
+    load_inst = uint32_t(q.slot);
     hisa_status s = load(q.rel, cols, q.n, 1);
     load_inst = 0;
     if (s) return s;
@@ -363,6 +375,9 @@ hisa_status Engine::compact_dead() {
   }
   std::fill(slot_dirty.begin(), slot_dirty.end(), 0);
   dead_tuples = 0;
+  active_bytes -= std::min(active_bytes, dead_bytes);
+  dead_bytes = 0;
+  edb_restage = true;
   return upload();
 }
 
@@ -411,7 +426,7 @@ hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
     Request& q = reqs[t];
     slot_owner[q.slot] = 0;
     slot_dirty[q.slot] = 1;   // its tuples leave full at the next compaction
-    active_bytes -= std::min(active_bytes, q.est_bytes);
+    dead_bytes += q.est_bytes;   // still in memory until the compaction
     q.done = true;
     dev_free(q.dev_edges);
     q.dev_edges = nullptr;
@@ -426,7 +441,12 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
   for (uint32_t it = 0; it < std::max(max_iters, 1u); ++it) {
     // admission at the iteration boundary: free slot and budget
     std::vector<uint64_t> admitted;
-    while (!pending.empty()) {
+    // an admission iteration re-stages and re-indexes the EDB and runs the
+    // non-recursive rules: while the budget is three-quarters used, wait
+    // for a quarter to free up so admissions come in groups
+    const bool busy = serve_budget && active_bytes > serve_budget / 4 * 3 &&
+                      std::any_of(slot_owner.begin(), slot_owner.end(), [](uint64_t t) { return t != 0; });
+    while (!pending.empty() && !busy) {
       const uint64_t t = pending.front();
       Request& q = reqs[t];
       auto clean_free = [&] {
@@ -441,6 +461,9 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
         free_slot = clean_free();
       }
       if (free_slot == slot_owner.end()) break;
+      if (serve_budget && active_bytes + q.est_bytes > serve_budget && dead_bytes > 0) {
+        if ((s = compact_dead())) return s;   // retired instances' memory counts until it is freed
+      }
       if (serve_budget && active_bytes + q.est_bytes > serve_budget && active_bytes > 0) break;
       q.slot = int(free_slot - slot_owner.begin());
       *free_slot = t;
@@ -449,7 +472,7 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
       pending.pop_front();
     }
     out.admitted += uint32_t(admitted.size());
-    if (!admitted.empty() && (s = rebuild_serving_edb())) return s;
+    if (!admitted.empty() && (s = rebuild_serving_edb(admitted))) return s;
     const bool any_active = std::any_of(slot_owner.begin(), slot_owner.end(), [](uint64_t t) { return t != 0; });
     if (!any_active) break;
     // one iteration of the shared fixpoint
