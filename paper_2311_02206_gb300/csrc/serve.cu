@@ -391,31 +391,59 @@ hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
     if ((s = inst_bounds(R.full, bnd))) return s;
     if (R.log && (s = inst_bounds(R.l1, bnd1))) return s;
     const uint64_t kb = wide ? 8 : 4;
+    if (!R.log && R.order == 0) {   // one sorted array in the declared order: copy the ranges
+      for (uint64_t t : tickets) {
+        Request& q = reqs[t];
+        const uint64_t lo = bnd[q.slot], cnt = bnd[q.slot + 1] - bnd[q.slot];
+        void* p = nullptr;
+        if (cnt) {   // the finished instance's codes, copied aside on the device
+          if ((s = dev_alloc(cnt * kb, &p))) return s;
+          CU(cudaMemcpyAsync(p, static_cast<char*>(hs.buf[R.full].ptr) + lo * kb, cnt * kb,
+                             cudaMemcpyDeviceToDevice, stream));
+        }
+        q.result[r] = {p, cnt};
+        dead_tuples += cnt;
+      }
+      continue;
+    }
+    // else every finished instance's codes from both levels are gathered and
+    // sorted together (instance ids keep them apart), then cut by instance
+    uint64_t total = 0;
+    for (uint64_t t : tickets) {
+      const Request& q = reqs[t];
+      total += bnd[q.slot + 1] - bnd[q.slot];
+      if (R.log) total += bnd1[q.slot + 1] - bnd1[q.slot];
+    }
+    if (total == 0) {
+      for (uint64_t t : tickets) reqs[t].result[r] = {nullptr, 0};
+      continue;
+    }
+    if ((s = ensure(sc.gather, total))) return s;
+    char* g = static_cast<char*>(hs.buf[sc.gather].ptr);
+    uint64_t w = 0;
+    for (uint64_t t : tickets) {
+      const Request& q = reqs[t];
+      for (int lv = 0; lv < (R.log ? 2 : 1); ++lv) {
+        const std::vector<uint64_t>& bb = lv ? bnd1 : bnd;
+        const uint64_t lo = bb[q.slot], cnt = bb[q.slot + 1] - bb[q.slot];
+        if (cnt)
+          CU(cudaMemcpyAsync(g + w * kb, static_cast<char*>(hs.buf[lv ? R.l1 : R.full].ptr) + lo * kb, cnt * kb,
+                             cudaMemcpyDeviceToDevice, stream));
+        w += cnt;
+      }
+    }
+    int src = -1;
+    if ((s = resort(sc.gather, 0, total, R.order == 1, &src))) return s;
+    hs.cnt[src] = total;
+    std::vector<uint64_t> sb;
+    if ((s = inst_bounds(src, sb))) return s;
     for (uint64_t t : tickets) {
       Request& q = reqs[t];
-      const uint64_t lo = bnd[q.slot], cnt0 = bnd[q.slot + 1] - bnd[q.slot];
-      const uint64_t lo1 = R.log ? bnd1[q.slot] : 0, cnt1 = R.log ? bnd1[q.slot + 1] - bnd1[q.slot] : 0;
-      const uint64_t cnt = cnt0 + cnt1;
+      const uint64_t lo = sb[q.slot], cnt = sb[q.slot + 1] - sb[q.slot];
       void* p = nullptr;
-      if (cnt) {   // the finished instance's codes, copied aside on the device
+      if (cnt) {
         if ((s = dev_alloc(cnt * kb, &p))) return s;
-        int src = R.full;
-        uint64_t from = lo;
-        if (cnt1) {   // in both levels of a log-structured full: gathered and sorted
-          if ((s = ensure(sc.gather, cnt))) return s;
-          char* g = static_cast<char*>(hs.buf[sc.gather].ptr);
-          if (cnt0)
-            CU(cudaMemcpyAsync(g, static_cast<char*>(hs.buf[R.full].ptr) + lo * kb, cnt0 * kb,
-                               cudaMemcpyDeviceToDevice, stream));
-          CU(cudaMemcpyAsync(g + cnt0 * kb, static_cast<char*>(hs.buf[R.l1].ptr) + lo1 * kb, cnt1 * kb,
-                             cudaMemcpyDeviceToDevice, stream));
-          if ((s = resort(sc.gather, 0, cnt, R.order == 1, &src))) return s;
-          from = 0;
-        } else if (R.order == 1) {   // stored (c1, c0): kept in the declared order
-          if ((s = declared_order(R.full, lo, cnt, &src))) return s;
-          from = 0;
-        }
-        CU(cudaMemcpyAsync(p, static_cast<char*>(hs.buf[src].ptr) + from * kb, cnt * kb, cudaMemcpyDeviceToDevice,
+        CU(cudaMemcpyAsync(p, static_cast<char*>(hs.buf[src].ptr) + lo * kb, cnt * kb, cudaMemcpyDeviceToDevice,
                            stream));
       }
       q.result[r] = {p, cnt};
