@@ -158,7 +158,9 @@ typedef struct {
   double ms_total;          /* wall time of the run */
   double ms_edb;            /* EDB encode, sort, dedup and index build */
   double ms_join, ms_sort, ms_merge; /* per-phase times (HISA_FLAG_PHASE_TIMES) */
-  uint64_t tuples_joined;   /* sum over iterations of |new| before dedup */
+  uint64_t tuples_joined;   /* sum over iterations of |new| as materialized: before dedup,
+                               except where the grouped bitmap join deduplicated (and
+                               differenced) it inside the join (HISA_FLAG_NO_DENSE) */
   uint64_t peak_bytes;      /* peak library-owned device memory */
   uint64_t kernel_launches; /* kernels launched by the run (graph-launched ones included) */
 } hisa_run_stats;
