@@ -1841,16 +1841,30 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
     if (hs.overflow || hs.error) return ctx_fail(HISA_ERR_CUDA, "read_relation: re-sort", nullptr);
     src = (passes & 1) ? sc.tmp_b : sc.tmp_a;
   }
+  // page-locked host columns are written by the decode kernel itself (over
+  // the host link, no device staging and no separate copy); pageable ones
+  // go through device buffers and a copy
+  bool mapped = false;
   if (!on_device) {
-    if ((s = dev_alloc(size * 4, &t0)) || (s = dev_alloc(size * 4, &t1))) return s;
-    d0 = static_cast<uint32_t*>(t0);
-    d1 = static_cast<uint32_t*>(t1);
+    cudaPointerAttributes pa0{}, pa1{};
+    if (cudaPointerGetAttributes(&pa0, cols[0]) == cudaSuccess &&
+        cudaPointerGetAttributes(&pa1, cols[1]) == cudaSuccess && pa0.type == cudaMemoryTypeHost &&
+        pa1.type == cudaMemoryTypeHost && pa0.devicePointer && pa1.devicePointer) {
+      d0 = static_cast<uint32_t*>(pa0.devicePointer);
+      d1 = static_cast<uint32_t*>(pa1.devicePointer);
+      mapped = true;
+    } else {
+      cudaGetLastError();
+      if ((s = dev_alloc(size * 4, &t0)) || (s = dev_alloc(size * 4, &t1))) return s;
+      d0 = static_cast<uint32_t*>(t0);
+      d1 = static_cast<uint32_t*>(t1);
+    }
   }
   DecodeArgs a{dst, src, 0, d0, d1, b, 0, 0, size};
   if (wide) launch_decode<uint64_t>(a, grid, stream);
   else launch_decode<uint32_t>(a, grid, stream);
   if ((s = check_launch("decode"))) return s;
-  if (!on_device) {
+  if (!on_device && !mapped) {
     CU(cudaMemcpyAsync(cols[0], d0, size * 4, cudaMemcpyDeviceToHost, stream));
     CU(cudaMemcpyAsync(cols[1], d1, size * 4, cudaMemcpyDeviceToHost, stream));
     dev_free(t0);
