@@ -30,6 +30,7 @@ instances, one-by-one vs served).
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -335,6 +336,7 @@ def run_hisa(a):
     _barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
+    gc.disable()   # no collector pause between a step's host-driven iterations
     with ClockSampler(uuid) as clk:
         for k in range(a.steps):
             flush.fill_(k)
@@ -350,6 +352,7 @@ def run_hisa(a):
                 acc["ms"] += e["ms"]
                 acc["bytes"] += e["bytes"]
     torch.cuda.synchronize()
+    gc.enable()
     _barrier(world)
     wall = time.perf_counter() - wall0
     n_reach = sum(ctx.relation_size(k) for k in idb_names)

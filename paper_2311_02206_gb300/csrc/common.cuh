@@ -217,6 +217,69 @@ __host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
   return h;
 }
 
+// Exclusive sum in place over v[0, n) by one CTA (blockDim.x a multiple of
+// 32, at most 1024); returns the total to every thread.  Each warp takes a
+// contiguous range, read coalesced with kB loads in flight per lane: the
+// pass over HBM/L2 is bound by bandwidth, not by one load's latency per
+// chunk.  smem holds >= 33 entries.
+__device__ __forceinline__ uint64_t cta_scan_inplace(uint64_t* v, uint64_t n, uint64_t* smem) {
+  constexpr int kB = 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint64_t wper = (((n + nw - 1) / nw) + 31) & ~31ull;
+  const uint64_t w0 = min(n, uint64_t(warp) * wper), w1 = min(n, w0 + wper);
+  uint64_t sum = 0;
+  for (uint64_t base = w0; base < w1; base += 32 * kB) {
+    uint64_t x[kB];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const uint64_t g = base + uint64_t(i) * 32 + lane;
+      x[i] = g < w1 ? v[g] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < kB; ++i) sum += x[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) smem[warp] = sum;
+  __syncthreads();
+  if (warp == 0) {
+    const uint64_t x0 = lane < nw ? smem[lane] : 0;
+    uint64_t x = x0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    smem[lane] = x - x0;
+    if (lane == 31) smem[32] = x;
+  }
+  __syncthreads();
+  uint64_t carry = smem[warp];
+  for (uint64_t base = w0; base < w1; base += 32 * kB) {
+    uint64_t x[kB];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const uint64_t g = base + uint64_t(i) * 32 + lane;
+      x[i] = g < w1 ? v[g] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      uint64_t incl = x[i];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint64_t g = base + uint64_t(i) * 32 + lane;
+      if (g < w1) v[g] = carry + incl - x[i];
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  const uint64_t total = smem[32];
+  __syncthreads();   // smem may be reused after return
+  return total;
+}
+
 template <typename T>
 __device__ __forceinline__ T block_exclusive_sum(T v, T* smem_warp, T* total) {
   // Exclusive sum over the block; smem_warp holds >= 32 entries.

@@ -130,31 +130,139 @@ void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStr
 
 // Group starts from a direct index over the delta's kept column (first[g]
 // for g in [0, 2^bits], GroupArgs::in_buf): the non-empty groups' starts in
-// order, then the sentinel n.  One CTA walks the 2^bits keys.
-__global__ void k_group_compact(GroupArgs a, int bits) {
-  __shared__ uint64_t s_scan[32];
+// order, then the sentinel n.  One CTA: each warp takes a contiguous range of
+// keys, read coalesced with eight loads in flight per lane, counts it, and
+// after a scan over the warps' counts writes it.
+__global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
+  __shared__ uint64_t s_gm[33], s_nu[33];
+  constexpr int kB = 8;   // 32-key chunks loaded before any is used
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
   const uint64_t* first = static_cast<const uint64_t*>(st->buf[a.in_buf].ptr);
   uint64_t* out = static_cast<uint64_t*>(st->buf[a.out_buf].ptr);
   const uint64_t ocap = st->buf[a.out_buf].cap;
   const uint64_t nk = 1ull << bits;
-  uint64_t carry = 0;
-  for (uint64_t c0 = 0; c0 < nk; c0 += blockDim.x) {
-    const uint64_t g = c0 + threadIdx.x;
-    const bool head = g < nk && first[g + 1] > first[g];
-    uint64_t tot;
-    const uint64_t ex = block_exclusive_sum<uint64_t>(head ? 1 : 0, s_scan, &tot);
-    if (head && carry + ex < ocap) out[carry + ex] = first[g];
-    carry += tot;
+  // with unit_size: the dense join's units per group, their first unit, the
+  // multi-unit slot (k_dense_units' outputs) in the same pass
+  const bool units_on = a.unit_size > 0;
+  const uint64_t usz = units_on ? uint64_t(a.unit_size) : 1;
+  uint64_t* units = units_on ? static_cast<uint64_t*>(st->buf[a.units_buf].ptr) : nullptr;
+  uint32_t* done = units_on ? static_cast<uint32_t*>(st->buf[a.done_buf].ptr) : nullptr;
+  uint32_t* mslot = units_on ? static_cast<uint32_t*>(st->buf[a.mslot_buf].ptr) : nullptr;
+  const uint64_t ucap = units_on ? min(st->buf[a.units_buf].cap, min(st->buf[a.done_buf].cap, st->buf[a.mslot_buf].cap))
+                                 : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint64_t wper = (((nk + nw - 1) / nw) + 31) & ~31ull;
+  const uint64_t w0 = min(nk, uint64_t(warp) * wper), w1 = min(nk, w0 + wper);
+  // pass 1: groups and multi-unit groups (packed, each < 2^32), units
+  uint64_t gm = 0, nus = 0;
+  for (uint64_t base = w0; base < w1; base += 32 * kB) {
+    uint64_t f0[kB], f1[kB];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const uint64_t g = base + uint64_t(i) * 32 + lane;
+      f0[i] = g < w1 ? first[g] : 0;
+      f1[i] = g < w1 ? first[g + 1] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < kB; ++i)
+      if (f1[i] > f0[i]) {
+        const uint64_t nu = (f1[i] - f0[i] + usz - 1) / usz;
+        gm += 1 + (uint64_t(nu > 1) << 32);
+        nus += nu;
+      }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gm += __shfl_xor_sync(0xffffffffu, gm, o);
+    nus += __shfl_xor_sync(0xffffffffu, nus, o);
+  }
+  if (lane == 0) {
+    s_gm[warp] = gm;
+    s_nu[warp] = nus;
+  }
+  __syncthreads();
+  if (warp == 0) {   // exclusive scan over the warps; totals in [32]
+    uint64_t x = lane < nw ? s_gm[lane] : 0, y = lane < nw ? s_nu[lane] : 0;
+    const uint64_t x0 = x, y0 = y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t xs = __shfl_up_sync(0xffffffffu, x, o), ys = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) {
+        x += xs;
+        y += ys;
+      }
+    }
+    s_gm[lane] = x - x0;
+    s_nu[lane] = y - y0;
+    if (lane == 31) {
+      s_gm[32] = x;
+      s_nu[32] = y;
+    }
+  }
+  __syncthreads();
+  // pass 2: write the groups' starts (and units) at their ranks
+  uint64_t c = s_gm[warp] & 0xFFFFFFFFull, m = s_gm[warp] >> 32, u = s_nu[warp];
+  const uint32_t lt = (1u << lane) - 1;
+  for (uint64_t base = w0; base < w1; base += 32 * kB) {
+    uint64_t f0[kB], f1[kB];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const uint64_t g = base + uint64_t(i) * 32 + lane;
+      f0[i] = g < w1 ? first[g] : 0;
+      f1[i] = g < w1 ? first[g + 1] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const bool head = f1[i] > f0[i];
+      const uint32_t hb = __ballot_sync(0xffffffffu, head);
+      const uint64_t pos = c + __popc(hb & lt);
+      if (head && pos < ocap) out[pos] = f0[i];
+      if (units_on) {
+        const uint64_t nu = head ? (f1[i] - f0[i] + usz - 1) / usz : 0;
+        const uint32_t mb = __ballot_sync(0xffffffffu, nu > 1);
+        uint64_t incl = nu;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (head && pos + 1 < ucap) {
+          units[pos] = u + incl - nu;
+          done[pos] = 0;
+          mslot[pos] = uint32_t(m + __popc(mb & lt));
+        }
+        u += __shfl_sync(0xffffffffu, incl, 31);
+        m += __popc(mb);
+      }
+      c += __popc(hb);
+    }
   }
   if (threadIdx.x == 0) {
+    const uint64_t carry = s_gm[32] & 0xFFFFFFFFull, mcarry = s_gm[32] >> 32, nu_tot = s_nu[32];
     st->cnt[a.out_cnt] = carry;
+    bool over = false;
     if (carry + 1 <= ocap) out[carry] = first[nk];
     else {
       atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)(carry + 1));
-      atomicOr(&st->overflow, 1u << a.stage_bit);
+      over = true;
     }
+    if (units_on) {
+      if (carry + 1 < ucap) {
+        units[carry] = nu_tot;
+        mslot[carry] = uint32_t(mcarry);
+        if (st->buf[a.bmm_buf].cap < mcarry * uint64_t(a.bm_words)) {
+          atomicMax((unsigned long long*)&st->need[a.bmm_buf], (unsigned long long)(mcarry * uint64_t(a.bm_words)));
+          over = true;
+        }
+      } else {
+        atomicMax((unsigned long long*)&st->need[a.units_buf], (unsigned long long)(carry + 2));
+        atomicMax((unsigned long long*)&st->need[a.done_buf], (unsigned long long)(carry + 2));
+        atomicMax((unsigned long long*)&st->need[a.mslot_buf], (unsigned long long)(carry + 2));
+        over = true;
+      }
+    }
+    if (over) atomicOr(&st->overflow, 1u << a.stage_bit);
   }
 }
 

@@ -31,6 +31,10 @@ struct GroupArgs {
   int status_buf;         // u64 [tiles] look-back
   int ctr;
   int skip_mask, stage_bit;
+  // k_group_compact only, when unit_size > 0: the dense join's work units
+  // per group (see DenseArgs), computed in the same pass
+  int units_buf, done_buf, mslot_buf, unit_size;
+  int bmm_buf, bm_words;   // multi-unit bitmaps: capacity checked here, bm_words per group
 };
 
 struct DenseArgs {
@@ -53,6 +57,15 @@ struct DenseArgs {
   // delta = new \ full itself (-1: no difference)
   int full_buf, lvidx_buf, nlv_cnt;
   int drop_self;                // the rule's filter kept != other: drop bit g in group g
+  // work units: a group of more than unit_size outer tuples is marked by
+  // several CTAs (first unit of group g: units[g], total in units[groups]);
+  // done[g] counts its finished units; such a group's CTAs OR their marks
+  // into its slot mslot[g] of bmm (multi-unit bitmaps, left zeroed; count
+  // in mslot[groups])
+  int units_buf, done_buf;
+  int unit_size;
+  int mslot_buf, bmm_buf;
+  int units_ready;              // computed by the group compaction (else k_dense_units runs)
 };
 
 constexpr int kDenseThreads = 128;
@@ -135,22 +148,81 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_starts(GroupArgs a) {
   }
 }
 
-// Phase 1: one group per CTA (taken in any order, so a large group delays
-// no other): mark the inner runs of the group's outer tuples -- a warp takes
-// 32 outer tuples at once (32 probes in flight), then its lanes stride over
-// the concatenation of their runs, each element finding its run by a binary
-// search over the warp's inclusive run-length prefix -- then store the
-// bitmap and its population count.
+// Phase 0 (one CTA): units per group (ceil(size / unit_size)) -> first unit
+// of each group, total units in units[groups]; done counters cleared.
+template <typename K>
+__global__ void k_dense_units(DenseArgs a) {
+  __shared__ uint64_t s_scan[32];
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t ngroups = st->cnt[a.groups_cnt];
+  if (st->buf[a.units_buf].cap < ngroups + 1 || st->buf[a.done_buf].cap < ngroups) {
+    if (threadIdx.x == 0) {
+      atomicMax((unsigned long long*)&st->need[a.units_buf], (unsigned long long)(ngroups + 1));
+      atomicMax((unsigned long long*)&st->need[a.done_buf], (unsigned long long)ngroups);
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    return;
+  }
+  if (st->buf[a.mslot_buf].cap < ngroups + 1) {
+    if (threadIdx.x == 0) {
+      atomicMax((unsigned long long*)&st->need[a.mslot_buf], (unsigned long long)(ngroups + 1));
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    return;
+  }
+  const uint64_t* gs = static_cast<const uint64_t*>(st->buf[a.groups_buf].ptr);
+  uint64_t* units = static_cast<uint64_t*>(st->buf[a.units_buf].ptr);
+  uint32_t* done = static_cast<uint32_t*>(st->buf[a.done_buf].ptr);
+  uint32_t* mslot = static_cast<uint32_t*>(st->buf[a.mslot_buf].ptr);
+  uint64_t carry = 0, mcarry = 0;
+  for (uint64_t c0 = 0; c0 < ngroups; c0 += blockDim.x) {
+    const uint64_t g = c0 + threadIdx.x;
+    const uint64_t nu = g < ngroups ? (gs[g + 1] - gs[g] + a.unit_size - 1) / a.unit_size : 0;
+    uint64_t tot, mtot;
+    const uint64_t ex = block_exclusive_sum<uint64_t>(nu, s_scan, &tot);
+    const uint64_t mex = block_exclusive_sum<uint64_t>(nu > 1 ? 1 : 0, s_scan, &mtot);
+    if (g < ngroups) {
+      units[g] = carry + ex;
+      done[g] = 0;
+      mslot[g] = uint32_t(mcarry + mex);
+    }
+    carry += tot;
+    mcarry += mtot;
+  }
+  if (threadIdx.x == 0) {
+    units[ngroups] = carry;
+    mslot[ngroups] = uint32_t(mcarry);
+    const uint64_t nwords = a.b >= 5 ? (1ull << (a.b - 5)) : 1;
+    if (st->buf[a.bmm_buf].cap < mcarry * nwords) {
+      atomicMax((unsigned long long*)&st->need[a.bmm_buf], (unsigned long long)(mcarry * nwords));
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+  }
+}
+
+// Phase 1: one unit per CTA (taken in any order, so a large group delays no
+// other and is spread over several CTAs): mark the inner runs of the unit's
+// outer tuples -- a warp takes 32 outer tuples at once (32 probes in
+// flight), then its lanes stride over the concatenation of their runs, each
+// element finding its run by a binary search over the warp's inclusive
+// run-length prefix.  A group of one unit is finished by its CTA (set
+// difference, count, store); the units of a larger group OR their bitmaps
+// into the group's (zeroed) bitmap in HBM and the last one to finish
+// finishes the group.
 template <typename K>
 __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(DenseArgs a) {
   extern __shared__ __align__(16) uint32_t s_bm[];   // 2^b bits
   __shared__ unsigned long long s_cnt;
-  __shared__ uint32_t s_group;
+  __shared__ uint64_t s_unit[3];   // the unit's outer range [start, end) and its group
+  __shared__ uint32_t s_nu;        // units in that group
+  __shared__ int s_last;
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
   const uint64_t ngroups = st->cnt[a.groups_cnt];
   if (ngroups == 0) return;
   const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
+  // (the multi-unit bitmaps' capacity is checked where the units are made)
   if (st->buf[a.bm_buf].cap < ngroups * uint64_t(nwords) || st->buf[a.offs_buf].cap < ngroups + 1) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       atomicMax((unsigned long long*)&st->need[a.bm_buf], (unsigned long long)(ngroups * uint64_t(nwords)));
@@ -173,17 +245,39 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
   if (tid == 0) s_cnt = 0;
   unsigned long long raw = 0;
   while (true) {
-    if (tid == 0) s_group = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+    // one thread finds the unit (its group: the last g with units[g] <= ui)
+    // and hands it to the CTA through shared memory, which keeps the
+    // marking loop's registers as they are without units
+    if (tid == 0) {
+      const uint64_t* units = static_cast<const uint64_t*>(st->buf[a.units_buf].ptr);
+      const uint64_t ui = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+      uint64_t gi = ~0ull;
+      if (ui < units[ngroups]) {
+        uint64_t lo = 0, hi = ngroups;
+        while (hi - lo > 1) {
+          const uint64_t m = (lo + hi) >> 1;
+          if (units[m] <= ui) lo = m;
+          else hi = m;
+        }
+        gi = lo;
+        const uint64_t s = gs[gi] + (ui - units[gi]) * uint64_t(a.unit_size);
+        s_unit[0] = s;
+        s_unit[1] = min(gs[gi + 1], s + uint64_t(a.unit_size));
+        s_nu = uint32_t(units[gi + 1] - units[gi]);
+      }
+      s_unit[2] = gi;
+    }
     __syncthreads();
-    const uint64_t gi = s_group;
-    if (gi >= ngroups) break;
-    const uint64_t s = gs[gi], e = gs[gi + 1];
-    for (uint64_t ob = s + uint64_t(warp) * 32; ob < e; ob += uint64_t(nwarps) * 32) {
-      const uint64_t o = ob + lane;
+    if (s_unit[2] == ~0ull) break;
+    // a unit spans at most unit_size (< 2^31) outer tuples: 32-bit offsets
+    const K* uo = outer + s_unit[0];
+    const uint32_t un = uint32_t(s_unit[1] - s_unit[0]);
+    for (uint32_t ob = uint32_t(warp) * 32; ob < un; ob += uint32_t(nwarps) * 32) {
+      const uint32_t o = ob + lane;
       uint64_t begin = 0;
       uint32_t len = 0;
-      if (o < e) {
-        const K code = outer[o];
+      if (o < un) {
+        const K code = uo[o];
         const uint32_t key = join_key(inst_of(code, a.b), colv(code, 1, a.b), a.b);
         if (!probe_run(table, tmask, a.index_direct, key, &begin, &len, &st->error)) len = 0;
       }
@@ -226,18 +320,44 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
       }
     }
     __syncthreads();
+    const uint64_t gi = s_unit[2];
+    uint32_t* gbm = bm + gi * uint64_t(nwords);
+    if (s_nu > 1) {
+      // this unit's marks into the group's multi-unit bitmap; the last unit
+      // takes it back (leaving it zeroed) and finishes the group
+      const uint32_t nu = s_nu;
+      uint32_t* done = static_cast<uint32_t*>(st->buf[a.done_buf].ptr);
+      uint32_t* mbm = static_cast<uint32_t*>(st->buf[a.bmm_buf].ptr) +
+                      uint64_t(static_cast<const uint32_t*>(st->buf[a.mslot_buf].ptr)[gi]) * nwords;
+      for (int j = tid; j < nwords; j += kDenseThreads) {
+        const uint32_t w = s_bm[j];
+        if (w) atomicOr(&mbm[j], w);
+        s_bm[j] = 0;
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) s_last = atomicAdd(&done[gi], 1u) == nu - 1;
+      __syncthreads();
+      if (!s_last) continue;
+      __threadfence();
+      for (int j = tid; j < nwords; j += kDenseThreads) {
+        s_bm[j] = __ldcg(&mbm[j]);
+        mbm[j] = 0;
+      }
+      __syncthreads();
+    }
     // set difference against full (Section 5.1 "populating delta"): clear the
-    // bits of the group's tuples already in full; both levels hold the same
-    // kept value first, so each contributes one contiguous run
+    // bits of the group's tuples already in full; every level holds the kept
+    // value first, so each contributes one contiguous run
     if (a.drop_self && tid == 0) {
-      const uint32_t g = uint32_t(uint64_t(outer[s]) >> a.b) & vmask;
+      const uint32_t g = uint32_t(uint64_t(outer[gs[gi]]) >> a.b) & vmask;
       atomicAnd(&s_bm[g >> 5], ~(1u << (g & 31)));
     }
     if (a.full_buf >= 0) {
       const uint64_t nlv = st->cnt[a.nlv_cnt], nk = (1ull << a.b) + 1;
       const uint64_t* lvidx = static_cast<const uint64_t*>(st->buf[a.lvidx_buf].ptr);
       const K* fl = static_cast<const K*>(st->buf[a.full_buf].ptr);
-      const uint64_t g = uint64_t(outer[s]) >> a.b;
+      const uint64_t g = uint64_t(outer[gs[gi]]) >> a.b;
       for (uint64_t lv = 0; lv < nlv; ++lv) {
         const uint64_t r0 = lvidx[lv * nk + g], r1 = lvidx[lv * nk + g + 1];
         for (uint64_t i = r0 + tid; i < r1; i += kDenseThreads) {
@@ -249,7 +369,6 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
     }
     __syncthreads();
     // store the bitmap (coalesced) and clear it; count its bits
-    uint32_t* gbm = bm + gi * uint64_t(nwords);
     uint32_t mine = 0;
     for (int j = tid; j < nwords; j += kDenseThreads) {
       const uint32_t w = s_bm[j];
@@ -271,21 +390,13 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
 
 // Phase 2 (one CTA): counts -> exclusive offsets; total and capacity check.
 template <typename K>
-__global__ void k_dense_scan(DenseArgs a) {
-  __shared__ uint64_t s_scan[32];
+__global__ void __launch_bounds__(1024) k_dense_scan(DenseArgs a) {
+  __shared__ uint64_t s_scan[33];
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
   const uint64_t ngroups = st->cnt[a.groups_cnt];
   uint64_t* offs = static_cast<uint64_t*>(st->buf[a.offs_buf].ptr);
-  uint64_t carry = 0;
-  for (uint64_t c0 = 0; c0 < ngroups; c0 += blockDim.x) {
-    const uint64_t i = c0 + threadIdx.x;
-    const uint64_t v = i < ngroups ? offs[i] : 0;
-    uint64_t tot;
-    const uint64_t ex = block_exclusive_sum<uint64_t>(v, s_scan, &tot);
-    if (i < ngroups) offs[i] = carry + ex;
-    carry += tot;
-  }
+  const uint64_t carry = cta_scan_inplace(offs, ngroups, s_scan);
   if (threadIdx.x == 0) {
     st->cnt[a.total_cnt] = carry;
     const uint64_t out0 = st->cnt[a.out_cnt];
@@ -354,6 +465,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_emit(DenseArgs a) {
       __syncwarp();
       base += tot;
     }
+
     __syncthreads();   // s_wtot is rewritten by the next group
   }
 }

@@ -163,10 +163,15 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.tmp_hist = new_slot(8);
   sc.gather = new_slot(4);
   sc.dense_first = new_slot(8);
+  sc.dense_units = new_slot(8);
+  sc.dense_done = new_slot(4);
+  sc.dense_mslot = new_slot(4);
+  sc.dense_bmm = new_slot(4);
   sc.group_cnt = nslots++;
   sc.raw_cnt = nslots++;
   slot_zero[sc.radix_status] = slot_zero[sc.setop_status] = slot_zero[sc.join_status] = true;
   slot_zero[sc.dense_status] = true;
+  slot_zero[sc.dense_bmm] = true;   // split groups' units OR into these; each is zeroed again after use
   if ((s = ensure(sc.empty, 1)) || (s = ensure(sc.hist, 8 * 256))) return s;
   return upload();
 }
@@ -555,7 +560,7 @@ hisa_status Engine::compile() {
     }
   }
   for (auto& v : planN)
-    for (auto& sp : v) sp.dense = false;
+    for (auto& sp : v) sp.dense = sp.resort = false;
   for (int r : idb) rels[r].dense_head = rels[r].append = false;
   if (dense_on)
     for (int r : idb) {
@@ -566,6 +571,27 @@ hisa_status Engine::compile() {
         rels[r].dense_head = true;
         rels[r].append = !batched;   // batched runs keep one sorted full (retirement cuts it by instance)
       }
+    }
+  // any other writer's last step of the right shape (the head keeps one
+  // column of the outer and the inner's other column, at most the filter
+  // kept != other) joins densely too, into new beside the other writers;
+  // a delta outer stored join column first is exchanged and sorted by the
+  // kept column first (Tmp already holds the head's first variable first)
+  if (dense_on)
+    for (auto& v : planN) {
+      StepPlan& sp = v.back();
+      if (sp.dense || sp.to_tmp || !sp.has_inner || rels[sp.out_rel].append) continue;
+      const bool tmp = v.size() > 1;
+      const int kept = sp.outer_kcol == 0 ? kSrcOuter1 : kSrcOuter0;
+      if (tmp && sp.outer_kcol != 1) continue;
+      if (sp.proj0 != kept || sp.proj1 != kSrcOther) continue;
+      const bool filt_ok = sp.nfilt == 0 ||
+                           (sp.nfilt == 1 && sp.fop[0] == kFiltNeq &&
+                            ((sp.fa[0] == kept && sp.fb[0] == kSrcOther) ||
+                             (sp.fa[0] == kSrcOther && sp.fb[0] == kept)));
+      if (!filt_ok) continue;
+      sp.dense = true;
+      sp.resort = !tmp && sp.outer_kcol == 0;
     }
   // log-structured full where nothing probes full (it is only differenced
   // and merged): REACH and SG, not CSPA's inner IDB atoms nor batched runs
@@ -755,12 +781,25 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp) {
   }
   // with an append-only full the join writes delta itself, into delta_next
   const int out = hr.append ? hr.delta_next : hr.fresh;
+  // a unit holds enough outer tuples to outweigh its bitmap
+  const int unit_size = int(std::max<uint64_t>(256, std::min<uint64_t>(32768, 16ull << (b >= 5 ? b - 5 : 0))));
+  const bool units_ready = b + inst_bits <= kDirectMaxBits;
+  if (units_ready) {
+    GroupArgs& ga = ops.back().groups;
+    ga.units_buf = sc.dense_units;
+    ga.done_buf = sc.dense_done;
+    ga.mslot_buf = sc.dense_mslot;
+    ga.unit_size = unit_size;
+    ga.bmm_buf = sc.dense_bmm;
+    ga.bm_words = b >= 5 ? 1 << (b - 5) : 1;
+  }
   Op d{};
   d.kind = Op::DENSE;
   d.dense = DenseArgs{dst, sp.outer_slot, sp.outer_cnt, sc.groups, sc.group_cnt,
                       sp.inner_col == 0 ? ir.base : ir.rev, ir.table[sp.inner_col], b,
                       out, out, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0,
-                      direct_bits > 0, hr.append ? hr.full : -1, hr.lvidx, hr.nlv, sp.nfilt > 0};
+                      direct_bits > 0, hr.append ? hr.full : -1, hr.lvidx, hr.nlv, sp.nfilt > 0,
+                      sc.dense_units, sc.dense_done, unit_size, sc.dense_mslot, sc.dense_bmm, units_ready};
   ops.push_back(d);
   if (hr.append) {   // no unique pass in the tail; |new| (statistics) = |delta|
     Op f{};
@@ -808,6 +847,30 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
         StepPlan d = sp;
         d.outer_slot = (passes & 1) ? sc.tmp_b : sc.tmp_a;
         emit_dense(ops, d);
+      } else if (sp.dense && sp.resort) {
+        // delta (join column first) exchanged into Tmp's buffers and sorted
+        // kept column first
+        Op w{};
+        w.kind = Op::SWAP;
+        w.swap = SwapArgs{dst, sp.outer_slot, sp.outer_cnt, sc.tmp_a, sc.tmp_cnt, b, 1, 0};
+        ops.push_back(w);
+        Op z{};
+        z.kind = Op::CTL;
+        z.ctl.st = dst;
+        z.ctl.skip_mask = 1;
+        z.ctl.cmd[z.ctl.n++] = {kCtlZeroSmall, sc.tmp_hist, 8 * 256, 0};
+        ops.push_back(z);
+        Op h{};
+        h.kind = Op::HIST;
+        h.hist = RadixHistArgs{dst, sc.tmp_a, sc.tmp_cnt, sc.tmp_hist, passes, 1};
+        ops.push_back(h);
+        emit_sort(ops, sc.tmp_a, sc.tmp_b, sc.tmp_cnt, sc.tmp_hist, 1, 0);
+        StepPlan d = sp;
+        d.outer_slot = (passes & 1) ? sc.tmp_b : sc.tmp_a;
+        d.outer_cnt = sc.tmp_cnt;
+        d.outer_kcol = 1;
+        d.proj0 = kSrcOuter0;
+        emit_dense(ops, d);
       } else if (sp.dense) {
         emit_dense(ops, sp);
       } else {
@@ -819,14 +882,17 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
   // sort each new, unless every writer of it is a dense join (sorted and
   // duplicate-free already); the sorted new always ends in `fresh`
   for (int r : idb) {
-    bool any = false, all_dense = true, any_dense = false;
+    int writers_n = 0;
+    bool all_dense = true, any_dense = false;
     for (auto& v : plans)
       if (!v.empty() && !v.back().to_tmp && v.back().out_rel == r) {
-        any = true;
+        ++writers_n;
         all_dense = all_dense && v.back().dense;
         any_dense = any_dense || v.back().dense;
       }
-    if (any && all_dense) continue;
+    // one dense writer: new is sorted and duplicate-free already; several
+    // writers' outputs are sorted (and deduplicated) together
+    if (writers_n == 1 && all_dense) continue;
     const Relation& R = rels[r];
     if (any_dense) {
       // a dense join wrote part of new without digit histograms (a serving
@@ -1278,7 +1344,10 @@ hisa_status Engine::regrow() {
   // next iterations: delta is the outer relation of the joins; full + new is merged
   if ((s = ensure(sc.offs, delta_cap + 1)) || (s = ensure(sc.join_status, delta_cap / kJoinTile + 2))) return s;
   if ((s = ensure(sc.groups, std::min<uint64_t>(delta_cap, 1ull << (b + inst_bits)) + 2)) ||
-      (s = ensure(sc.dense_status, std::min<uint64_t>(delta_cap, 1ull << (b + inst_bits)) + 2)))
+      (s = ensure(sc.dense_status, std::min<uint64_t>(delta_cap, 1ull << (b + inst_bits)) + 2)) ||
+      (s = ensure(sc.dense_units, std::min<uint64_t>(delta_cap, 1ull << (b + inst_bits)) + 2)) ||
+      (s = ensure(sc.dense_done, std::min<uint64_t>(delta_cap, 1ull << (b + inst_bits)) + 2)) ||
+      (s = ensure(sc.dense_mslot, std::min<uint64_t>(delta_cap, 1ull << (b + inst_bits)) + 2)))
     return s;
   if ((s = ensure(sc.split, (full_cap + std::max(new_cap, delta_cap)) / ks + 2)) ||
       (s = ensure(sc.setop_status,
@@ -1367,7 +1436,10 @@ hisa_status Engine::init_run_state() {
   if (b + inst_bits <= kDirectMaxBits && (s = ensure(sc.dense_first, (1ull << (b + inst_bits)) + 2))) return s;
   if ((s = ensure(sc.tmp_hist, 8 * 256)) || (s = ensure(sc.tmp_b, 4 * nedb))) return s;
   if ((s = ensure(sc.groups, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
-      (s = ensure(sc.dense_status, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)))
+      (s = ensure(sc.dense_status, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
+      (s = ensure(sc.dense_units, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
+      (s = ensure(sc.dense_done, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
+      (s = ensure(sc.dense_mslot, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)))
     return s;
   if ((s = ensure(sc.radix_status, (4 * nedb / kt + 2) * 256)) || (s = ensure(sc.offs, 4 * nedb + 1)) ||
       (s = ensure(sc.join_status, 4 * nedb / kJoinTile + 2)) || (s = ensure(sc.starts, 4 * nedb / kJoinChunk + 2)) ||

@@ -62,6 +62,7 @@ struct StepPlan {
   bool to_tmp;
   int out_rel;
   bool dense;   // grouped join with bitmap deduplication (dense.cuh)
+  bool resort;  // its outer (a delta stored join column first) is exchanged and sorted by the kept column first
 };
 
 struct Op {
@@ -90,6 +91,8 @@ struct Scratch {
   int tmp_hist;               // digit histograms of a Tmp relation sorted before a dense join
   int gather;                 // an instance's codes from both levels of a log-structured full
   int dense_first;            // direct index of a delta by its kept column (group starts)
+  int dense_units, dense_done;  // the dense join's first unit per group and finished-unit counters
+  int dense_mslot, dense_bmm;   // multi-unit groups' bitmap slot and those bitmaps (kept zeroed)
 
   int group_cnt, raw_cnt;     // count-only slots
 };

@@ -235,6 +235,7 @@ void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s) {
   c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
   launch_ctl(c, s);
   const size_t smem = size_t(a.b >= 5 ? (1u << (a.b - 5)) : 1u) * 4;
+  if (!a.units_ready) HISA_LAUNCH(kKDenseScan, s, (k_dense_units<K><<<1, 1024, 0, s>>>(a)));
   HISA_LAUNCH(kKJoinDense, s, (k_dense_mark<K><<<g.sms * kDenseCtasPerSm, kDenseThreads, smem, s>>>(a)));
   HISA_LAUNCH(kKDenseScan, s, (k_dense_scan<K><<<1, 1024, 0, s>>>(a)));
   HISA_LAUNCH(kKDenseEmit, s, (k_dense_emit<K><<<g.sms * kDenseCtasPerSm, kDenseThreads, 0, s>>>(a)));
