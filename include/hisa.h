@@ -85,6 +85,14 @@ typedef void (*hisa_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
  * is indexed directly: first position of every key, the run of key k being
  * [first[k], first[k+1]) -- one probe instead of a slot walk. */
 #define HISA_FLAG_HASH_INDEX 16u
+/* Never gather Tmp grouped by its kept column.  By default, a two-step rule
+ * variant H(x, y) <- A(x, a), delta(a, c), B(c, y) whose second step is a
+ * grouped bitmap join (SG's recursive rule) builds its Tmp relation by
+ * counting, per tuple of A in x order, the delta run it meets, and copying
+ * those runs to their offsets: Tmp comes out grouped by x with no join
+ * partition pass and no radix sort.  Same results; domain of at most 2^20
+ * values, not in batched runs. */
+#define HISA_FLAG_NO_CHAIN 32u
 
 typedef struct {
   hisa_alloc_fn alloc;      /* NULL: cudaMallocAsync from a private pool */

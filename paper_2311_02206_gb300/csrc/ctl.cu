@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
   const uint64_t* first = static_cast<const uint64_t*>(st->buf[a.in_buf].ptr);
+  const uint64_t* vals = a.indirect ? static_cast<const uint64_t*>(st->buf[a.vals_buf].ptr) : nullptr;
+  auto F = [&](uint64_t g) { return vals ? vals[first[g]] : first[g]; };
   uint64_t* out = static_cast<uint64_t*>(st->buf[a.out_buf].ptr);
   const uint64_t ocap = st->buf[a.out_buf].cap;
   const uint64_t nk = 1ull << bits;
@@ -161,8 +163,8 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
 #pragma unroll
     for (int i = 0; i < kB; ++i) {
       const uint64_t g = base + uint64_t(i) * 32 + lane;
-      f0[i] = g < w1 ? first[g] : 0;
-      f1[i] = g < w1 ? first[g + 1] : 0;
+      f0[i] = g < w1 ? F(g) : 0;
+      f1[i] = g < w1 ? F(g + 1) : 0;
     }
 #pragma unroll
     for (int i = 0; i < kB; ++i)
@@ -209,8 +211,8 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
 #pragma unroll
     for (int i = 0; i < kB; ++i) {
       const uint64_t g = base + uint64_t(i) * 32 + lane;
-      f0[i] = g < w1 ? first[g] : 0;
-      f1[i] = g < w1 ? first[g + 1] : 0;
+      f0[i] = g < w1 ? F(g) : 0;
+      f1[i] = g < w1 ? F(g + 1) : 0;
     }
 #pragma unroll
     for (int i = 0; i < kB; ++i) {
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
     const uint64_t carry = s_gm[32] & 0xFFFFFFFFull, mcarry = s_gm[32] >> 32, nu_tot = s_nu[32];
     st->cnt[a.out_cnt] = carry;
     bool over = false;
-    if (carry + 1 <= ocap) out[carry] = first[nk];
+    if (carry + 1 <= ocap) out[carry] = F(nk);
     else {
       atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)(carry + 1));
       over = true;
@@ -277,7 +279,7 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
 
 const char* const kKernelNames[kKindCount] = {
     "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
-    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level"};
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level", "chain_len", "chain_scan", "chain_gather"};
 
 thread_local KernelTimer* g_timer = nullptr;
 thread_local uint64_t g_launches = 0;

@@ -35,7 +35,93 @@ struct GroupArgs {
   // per group (see DenseArgs), computed in the same pass
   int units_buf, done_buf, mslot_buf, unit_size;
   int bmm_buf, bm_words;   // multi-unit bitmaps: capacity checked here, bm_words per group
+  // k_group_compact: with indirect, first[g] is read as vals[in[g]] (a
+  // gathered Tmp's starts: vals = offsets per inner tuple, in = the inner's
+  // direct index by the kept value)
+  int indirect, vals_buf;
 };
+
+// A two-step rule variant H(x, y) <- A(x, a), delta(a, c), B(c, y) -- delta
+// joined on its first stored column with the inner atom A, the Tmp relation
+// keeping A's other column x first and delta's second column c -- gathered
+// straight into Tmp grouped by x, in place of the join and the sort of Tmp
+// by x that the dense join needs (Section 4.1's join of delta with an inner
+// relation, its results grouped by the kept column):
+//   len:    per tuple (x, a) of A (sorted by x): |delta(a, .)| -> pre
+//   scan:   pre -> exclusive offsets, the total is |Tmp| (capacity check)
+//   gather: delta(a, .)'s second column, x prepended, copied to Tmp at pre
+// Tmp's group starts are then pre[first_A(x)] (k_group_compact, indirect).
+struct ChainArgs {
+  DevState* st;
+  int a_buf, a_cnt;           // A's codes sorted by x: x in the high half, a in the low half
+  int delta_buf, delta_cnt;   // delta sorted by its first stored column
+  int dfirst_buf;             // direct index of delta by its high half (2^b + 1 entries)
+  int pre_buf;                // u64 [|A| + 1]
+  int tmp_buf, tmp_cnt;
+  int b;
+  int skip_mask, stage_bit;
+};
+
+template <typename K>
+__global__ void k_chain_len(ChainArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t na = st->cnt[a.a_cnt];
+  if (st->buf[a.pre_buf].cap < na + 1) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicMax((unsigned long long*)&st->need[a.pre_buf], (unsigned long long)(na + 1));
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+    return;
+  }
+  const K* A = static_cast<const K*>(st->buf[a.a_buf].ptr);
+  const uint64_t* df = static_cast<const uint64_t*>(st->buf[a.dfirst_buf].ptr);
+  uint64_t* pre = static_cast<uint64_t*>(st->buf[a.pre_buf].ptr);
+  for (uint64_t j = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; j < na; j += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t av = colv(A[j], 1, a.b);
+    pre[j] = df[av + 1] - df[av];
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(1024) k_chain_scan(ChainArgs a) {
+  __shared__ uint64_t s_scan[33];
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t na = st->cnt[a.a_cnt];
+  uint64_t* pre = static_cast<uint64_t*>(st->buf[a.pre_buf].ptr);
+  const uint64_t total = cta_scan_inplace(pre, na, s_scan);
+  if (threadIdx.x == 0) {
+    pre[na] = total;
+    st->cnt[a.tmp_cnt] = total;
+    if (total > st->buf[a.tmp_buf].cap) {
+      atomicMax((unsigned long long*)&st->need[a.tmp_buf], (unsigned long long)total);
+      atomicOr(&st->overflow, 1u << a.stage_bit);
+    }
+  }
+}
+
+// A warp per tuple of A: its delta run copied (coalesced) behind pre[j].
+template <typename K>
+__global__ void k_chain_gather(ChainArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t na = st->cnt[a.a_cnt];
+  const K* A = static_cast<const K*>(st->buf[a.a_buf].ptr);
+  const K* delta = static_cast<const K*>(st->buf[a.delta_buf].ptr);
+  const uint64_t* df = static_cast<const uint64_t*>(st->buf[a.dfirst_buf].ptr);
+  const uint64_t* pre = static_cast<const uint64_t*>(st->buf[a.pre_buf].ptr);
+  K* tmp = static_cast<K*>(st->buf[a.tmp_buf].ptr);
+  const int lane = threadIdx.x & 31;
+  const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t j = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5; j < na; j += nw) {
+    const K code = A[j];
+    const uint32_t av = colv(code, 1, a.b);
+    const uint64_t hi = uint64_t(colv(code, 0, a.b)) << a.b;
+    const uint64_t d0 = df[av], n = df[av + 1] - d0, o = pre[j];
+    for (uint64_t i = lane; i < n; i += 32) tmp[o + i] = K(hi | colv(delta[d0 + i], 1, a.b));
+  }
+}
 
 struct DenseArgs {
   DevState* st;

@@ -167,6 +167,8 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.dense_done = new_slot(4);
   sc.dense_mslot = new_slot(4);
   sc.dense_bmm = new_slot(4);
+  sc.chain_dfirst = new_slot(8);
+  sc.chain_pre = new_slot(8);
   sc.group_cnt = nslots++;
   sc.raw_cnt = nslots++;
   slot_zero[sc.radix_status] = slot_zero[sc.setop_status] = slot_zero[sc.join_status] = true;
@@ -593,6 +595,28 @@ hisa_status Engine::compile() {
       sp.dense = true;
       sp.resort = !tmp && sp.outer_kcol == 0;
     }
+  // a two-step variant whose first step joins a delta on its first stored
+  // column and keeps the inner's other column x first and delta's second
+  // column, and whose second step is dense: Tmp is gathered grouped by x
+  // (ChainArgs) instead of joined and sorted.  The inner must be stored x
+  // first: an EDB relation builds that copy, an IDB one must keep it anyway.
+  for (auto& v : planN)
+    for (auto& sp : v) sp.chain = false;
+  if (dense_on && !(cfg.flags & HISA_FLAG_NO_CHAIN) && inst_bits == 0 && b <= kDirectMaxBits)
+    for (auto& v : planN) {
+      if (v.size() != 2 || !v[1].dense || v[1].outer_slot != sc.tmp_a) continue;
+      StepPlan& s1 = v[0];
+      bool delta_outer = false;
+      for (int r : idb) delta_outer = delta_outer || s1.outer_slot == rels[r].delta;
+      if (!delta_outer || !s1.has_inner || s1.nfilt || s1.outer_kcol != 0 || s1.proj0 != kSrcOther ||
+          s1.proj1 != kSrcOuter1)
+        continue;
+      Relation& A = rels[s1.inner_rel];
+      const int xcol = 1 - s1.inner_col;
+      if (A.idb && !A.need_idx[xcol]) continue;
+      s1.chain = true;
+      A.need_idx[xcol] = true;
+    }
   // log-structured full where nothing probes full (it is only differenced
   // and merged): REACH and SG, not CSPA's inner IDB atoms nor batched runs
   for (int r : idb) {
@@ -758,13 +782,43 @@ void Engine::emit_idb_index(std::vector<Op>& ops) {
   }
 }
 
-void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp) {
+// Tmp of a two-step variant gathered grouped by its kept column x: delta's
+// direct index by its first stored column (the join value), the inner's
+// direct index by x (into dense_first, read by the dense join's group
+// compaction through chain_pre), then len + scan + gather (ChainArgs).
+void Engine::emit_chain(std::vector<Op>& ops, const StepPlan& sp) {
+  const Relation& A = rels[sp.inner_rel];
+  const int abuf = sp.inner_col == 1 ? A.base : A.rev;   // stored x first
+  Op x{};
+  x.kind = Op::INDEX;
+  x.index = IndexArgs{dst, sp.outer_slot, sp.outer_cnt, sc.chain_dfirst, b, -1, 1, b};
+  ops.push_back(x);
+  Op y{};
+  y.kind = Op::INDEX;
+  y.index = IndexArgs{dst, abuf, abuf, sc.dense_first, b, -1, 1, b};
+  ops.push_back(y);
+  Op c{};
+  c.kind = Op::CHAIN;
+  c.chain = ChainArgs{dst, abuf, abuf, sp.outer_slot, sp.outer_cnt, sc.chain_dfirst, sc.chain_pre, sc.tmp_a,
+                      sc.tmp_cnt, b, 1, 0};
+  ops.push_back(c);
+}
+
+void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_groups) {
   const Relation& ir = rels[sp.inner_rel];
   const Relation& hr = rels[sp.out_rel];
   // group starts: a direct index of delta by the kept column, compacted to
   // the non-empty groups; one pass over delta when instance ids make the key
-  // space too large for a direct index
-  if (b + inst_bits <= kDirectMaxBits) {
+  // space too large for a direct index; for a gathered Tmp, its offsets at
+  // the inner's direct index (emit_chain)
+  if (chain_groups) {
+    Op g{};
+    g.kind = Op::GCOMPACT;
+    g.groups = GroupArgs{dst, sc.dense_first, sp.outer_cnt, b, sc.groups, sc.group_cnt, sc.join_status, 3, 1, 0};
+    g.groups.indirect = 1;
+    g.groups.vals_buf = sc.chain_pre;
+    ops.push_back(g);
+  } else if (b + inst_bits <= kDirectMaxBits) {
     Op x{};
     x.kind = Op::INDEX;
     x.index = IndexArgs{dst, sp.outer_slot, sp.outer_cnt, sc.dense_first, b, -1, 1, b + inst_bits};
@@ -831,17 +885,22 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
   if (idb_inner) emit_idb_index(ops);
   for (auto& v : plans) {
     const bool tmp_dense = v.size() > 1 && v.back().dense;
+    const bool chain = v.size() > 1 && v[0].chain;
     if (v.size() > 1) {
       Op t{};
       t.kind = Op::CTL;
       t.ctl.st = dst;
       t.ctl.skip_mask = 1;
       t.ctl.cmd[t.ctl.n++] = {kCtlSetCnt, sc.tmp_cnt, 0};
-      if (tmp_dense) t.ctl.cmd[t.ctl.n++] = {kCtlZeroSmall, sc.tmp_hist, 8 * 256};
+      if (tmp_dense && !chain) t.ctl.cmd[t.ctl.n++] = {kCtlZeroSmall, sc.tmp_hist, 8 * 256};
       ops.push_back(t);
     }
     for (auto& sp : v) {
-      if (sp.dense && sp.outer_slot == sc.tmp_a) {
+      if (sp.chain) {
+        emit_chain(ops, sp);
+      } else if (sp.dense && sp.outer_slot == sc.tmp_a && chain) {
+        emit_dense(ops, sp, true);   // Tmp gathered grouped by its kept column
+      } else if (sp.dense && sp.outer_slot == sc.tmp_a) {
         // Tmp sorted (kept column first) so its groups are contiguous
         emit_sort(ops, sc.tmp_a, sc.tmp_b, sc.tmp_cnt, sc.tmp_hist, 1, 0);
         StepPlan d = sp;
@@ -1140,6 +1199,7 @@ hisa_status Engine::exec_t(const std::vector<Op>& ops) {
       case Op::APPEND: launch_append<K>(o.append, grid, stream); break;
       case Op::GROUPS: launch_group_starts<K>(o.groups, grid, stream); break;
       case Op::DENSE: launch_join_dense<K>(o.dense, grid, stream); break;
+      case Op::CHAIN: launch_chain<K>(o.chain, grid, stream); break;
     }
   }
   return check_launch("kernel launch");
@@ -1434,6 +1494,10 @@ hisa_status Engine::init_run_state() {
   hs.cnt[sc.tmp_cnt] = 0;
   hs.cnt[sc.raw_cnt] = hs.cnt[sc.group_cnt] = 0;
   if (b + inst_bits <= kDirectMaxBits && (s = ensure(sc.dense_first, (1ull << (b + inst_bits)) + 2))) return s;
+  bool any_chain = false;
+  for (auto& v : planN) any_chain = any_chain || (!v.empty() && v[0].chain);
+  if (any_chain && ((s = ensure(sc.chain_dfirst, (1ull << b) + 2)) || (s = ensure(sc.chain_pre, 4 * nedb + 2))))
+    return s;
   if ((s = ensure(sc.tmp_hist, 8 * 256)) || (s = ensure(sc.tmp_b, 4 * nedb))) return s;
   if ((s = ensure(sc.groups, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
       (s = ensure(sc.dense_status, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
@@ -1515,12 +1579,25 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
           const double nn = double(hs.cnt[R.fresh]), nd = double(hs.cnt[R.delta]);
           const double m = double(m_prev[i]), dp = double(d_prev[i]);
           bool dense = false, via_tmp = false;
+          const StepPlan* chain = nullptr;
           for (auto& v : planN)
             if (!first && !v.empty() && v.back().dense && v.back().out_rel == idb[i]) {
               dense = true;
               via_tmp = v.size() > 1;
+              if (v[0].chain) chain = &v[0];
             }
-          if (via_tmp) {   // first join into Tmp, Tmp sorted by its kept column
+          if (chain) {
+            // Tmp gathered: delta's index; per inner tuple read it and two
+            // index entries, write its offset; scan; gather reads the inner
+            // tuple, its index entries and offset, the delta run, writes Tmp
+            const double tm = double(hs.cnt[sc.tmp_cnt]);
+            const Relation& A = rels[chain->inner_rel];
+            const double na = double(hs.cnt[chain->inner_col == 1 ? A.base : A.rev]);
+            kstat[kKIndex].bytes += 8.0 * double((1u << b) + 1) * 2.0;
+            kstat[kKChainLen].bytes += na * (kb + 16.0 + 8.0);
+            kstat[kKChainScan].bytes += 16.0 * na;
+            kstat[kKChainGather].bytes += na * (kb + 24.0) + 2.0 * tm * kb;
+          } else if (via_tmp) {   // first join into Tmp, Tmp sorted by its kept column
             const double tm = double(hs.cnt[sc.tmp_cnt]);
             kstat[kKJoinWrite].bytes += 2.0 * tm * kb + dp * (kb + 8.0);
             kstat[kKJoinCount].bytes += dp * (kb + 8.0 + 16.0);

@@ -63,10 +63,11 @@ struct StepPlan {
   int out_rel;
   bool dense;   // grouped join with bitmap deduplication (dense.cuh)
   bool resort;  // its outer (a delta stored join column first) is exchanged and sorted by the kept column first
+  bool chain;   // a first step whose Tmp is gathered grouped by its kept column (ChainArgs)
 };
 
 struct Op {
-  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT, APPEND, GROUPS } kind;
+  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT, APPEND, GROUPS, CHAIN } kind;
   CtlArgs ctl;
   JoinArgs join;
   RadixPassArgs pass;
@@ -81,6 +82,7 @@ struct Op {
   GroupArgs groups;
   AppendArgs append;
   DenseArgs dense;
+  ChainArgs chain;
 };
 
 struct Scratch {
@@ -93,6 +95,7 @@ struct Scratch {
   int dense_first;            // direct index of a delta by its kept column (group starts)
   int dense_units, dense_done;  // the dense join's first unit per group and finished-unit counters
   int dense_mslot, dense_bmm;   // multi-unit groups' bitmap slot and those bitmaps (kept zeroed)
+  int chain_dfirst, chain_pre;  // a gathered Tmp: delta's direct index, offsets per inner tuple
 
   int group_cnt, raw_cnt;     // count-only slots
 };
@@ -153,7 +156,8 @@ class Engine {
   hisa_status compile();
   hisa_status plan_variant(const hisa_rule& R, int delta_atom, std::vector<StepPlan>& out);
   void emit_join(std::vector<Op>& ops, const StepPlan& sp);
-  void emit_dense(std::vector<Op>& ops, const StepPlan& sp);
+  void emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_groups = false);
+  void emit_chain(std::vector<Op>& ops, const StepPlan& sp);
   hisa_status plan_all();
   void emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepPlan>>& plans, bool idb_inner);
   void emit_idb_index(std::vector<Op>& ops);

@@ -129,7 +129,7 @@ struct SwapArgs {
 
 enum KernelKind : int {
   kKEncode, kKDecode, kKRuns, kKHist, kKRadixPass, kKSetopPartition, kKSetop, kKIndex,
-  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKAppend, kKindCount
+  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKAppend, kKChainLen, kKChainScan, kKChainGather, kKindCount
 };
 extern const char* const kKernelNames[kKindCount];
 
@@ -184,6 +184,7 @@ void launch_group_compact(const GroupArgs& a, int bits, cudaStream_t s);
 template <typename K> void launch_group_starts(const GroupArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_append(const AppendArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_chain(const ChainArgs& a, const Grid& g, cudaStream_t s);   // len + scan + gather
 template <typename K> void launch_inst_hist(const InstArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_bounds(const InstArgs& a, const Grid& g, cudaStream_t s);
 void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStream_t s);

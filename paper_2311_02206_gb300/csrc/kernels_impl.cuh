@@ -162,6 +162,12 @@ void launch_group_starts(const GroupArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKGroups, s, (k_group_starts<K><<<g.setop, kGroupThreads, 0, s>>>(a)));
 }
 template <typename K>
+void launch_chain(const ChainArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKChainLen, s, (k_chain_len<K><<<g.small * 2, 256, 0, s>>>(a)));
+  HISA_LAUNCH(kKChainScan, s, (k_chain_scan<K><<<1, 1024, 0, s>>>(a)));
+  HISA_LAUNCH(kKChainGather, s, (k_chain_gather<K><<<g.join, 256, 0, s>>>(a)));
+}
+template <typename K>
 void launch_append(const AppendArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKAppend, s, (k_append<K><<<g.small * 2, 256, 0, s>>>(a)));
 }
@@ -290,6 +296,7 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_append<K>(const AppendArgs&, const Grid&, cudaStream_t);          \
   template void launch_group_starts<K>(const GroupArgs&, const Grid&, cudaStream_t);     \
   template void launch_join_dense<K>(const DenseArgs&, const Grid&, cudaStream_t);       \
+  template void launch_chain<K>(const ChainArgs&, const Grid&, cudaStream_t);            \
   template void launch_radix_hist<K>(const RadixHistArgs&, const Grid&, cudaStream_t);   \
   template void launch_radix_pass<K>(const RadixPassArgs&, const Grid&, cudaStream_t);   \
   template void launch_setop<K>(const SetopArgs&, const Grid&, cudaStream_t);            \

@@ -24,10 +24,12 @@ def _lib():
 
 def modes():
     """host-driven, graph-captured, both with the log-structured full,
-    graph-captured without the grouped bitmap join, and with hashed indexes"""
+    graph-captured without the grouped bitmap join, and with hashed indexes,
+    and with Tmp joined and sorted instead of gathered"""
     from paper_2311_02206_gb300 import hisa
     return [0, hisa.FLAG_GRAPH, hisa.FLAG_LOG_FULL, hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL,
-            hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE, hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE | hisa.FLAG_HASH_INDEX]
+            hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE, hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE | hisa.FLAG_HASH_INDEX,
+            hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_CHAIN]
 
 
 @pytest.mark.parametrize("seed", range(40))
@@ -182,8 +184,9 @@ def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense):
         assert np.array_equal(g0, ref.relations["Reach"][0]) and np.array_equal(g1, ref.relations["Reach"][1])
 
 
-@pytest.mark.parametrize("literal,log_full", [(False, False), (True, False), (False, True)])
-def test_sg_dag_full_size_golden(literal, log_full):
+@pytest.mark.parametrize("literal,log_full,no_chain",
+                         [(False, False, False), (True, False, False), (False, True, False), (False, True, True)])
+def test_sg_dag_full_size_golden(literal, log_full, no_chain):
     """SG on the 20,000-node DAG (x != y on both rules, or on rule 1 only as
     the workload description prints it): size, every delta count and the
     fingerprint of the whole relation against the oracle's stored values."""
@@ -193,7 +196,8 @@ def test_sg_dag_full_size_golden(literal, log_full):
     g = json.load(open(path))
     from paper_2311_02206_gb300 import hisa
     s, d = workloads.config_sg_dag()
-    with hisa.Context(flags=hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0)) as ctx:
+    flags = hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0) | (hisa.FLAG_NO_CHAIN if no_chain else 0)
+    with hisa.Context(flags=flags) as ctx:
         ctx.program(*(oracle.SG_LITERAL if literal else oracle.SG))
         ctx.load_tuples("Edge", s, d)
         ctx.run()
@@ -203,8 +207,8 @@ def test_sg_dag_full_size_golden(literal, log_full):
         assert fingerprint_device(c0, c1) == int(g["fingerprint"])
 
 
-@pytest.mark.parametrize("div,window", [(500, 32), (250, 128)])
-def test_cspa_golden(div, window):
+@pytest.mark.parametrize("div,window,no_chain", [(500, 32, False), (250, 128, False), (500, 32, True)])
+def test_cspa_golden(div, window, no_chain):
     """The points-to program on the skewed inputs divided by `div`: sizes,
     delta counts and fingerprints of the three IDB relations against the
     oracle's stored values (1/250 derives ~4.6e9 raw tuples on the GPU)."""
@@ -214,7 +218,8 @@ def test_cspa_golden(div, window):
     g = json.load(open(path))
     from paper_2311_02206_gb300 import hisa
     edb = workloads.config_cspa(div, window)
-    with hisa.Context() as ctx:
+    flags = hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | (hisa.FLAG_NO_CHAIN if no_chain else 0)
+    with hisa.Context(flags=flags) as ctx:
         ctx.program(*oracle.CSPA)
         for name, (c0, c1) in edb.items():
             ctx.load_tuples(name, c0, c1)

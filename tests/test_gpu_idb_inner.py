@@ -22,9 +22,10 @@ def _lib():
 
 
 def modes():
-    """host-driven and graph-captured; graph-captured with hashed indexes"""
+    """host-driven and graph-captured; graph-captured with hashed indexes, and
+    with Tmp joined and sorted instead of gathered"""
     from paper_2311_02206_gb300 import hisa
-    return [0, hisa.FLAG_GRAPH, hisa.FLAG_GRAPH | hisa.FLAG_HASH_INDEX]
+    return [0, hisa.FLAG_GRAPH, hisa.FLAG_GRAPH | hisa.FLAG_HASH_INDEX, hisa.FLAG_GRAPH | hisa.FLAG_NO_CHAIN]
 
 
 def random_graph(seed, nmax=60, dmax=4):
