@@ -556,4 +556,121 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_emit(DenseArgs a) {
   }
 }
 
+// Reading an append-only full (one sorted level per iteration, every level
+// keeping the group column first, levels disjoint) in lexicographic order
+// without sorting it: a CTA per group value g marks the group's runs of all
+// levels in a shared bitmap and writes its set bits in order, decoded into
+// the two output columns, at the group's offset sum over levels of
+// lvidx[lv][g] - lvidx[lv][0].  Reads full once and writes the output once
+// (coalesced), so a read into page-locked host columns runs at the host
+// link's rate.
+struct LevelsReadArgs {
+  DevState* st;
+  int full_buf, lvidx_buf, nlv_cnt;
+  int b;
+  uint32_t* out0;   // device or host-mapped; |full| entries each
+  uint32_t* out1;
+};
+constexpr int kLevelsChunk = kDenseThreads;   // levels whose run bounds are staged at once
+
+template <typename K>
+__global__ void __launch_bounds__(kDenseThreads) k_levels_read(LevelsReadArgs a) {
+  constexpr int nwarps = kDenseThreads / 32;
+  extern __shared__ __align__(16) uint32_t s_dyn[];   // bitmap (2^b bits), then the warps' staging
+  __shared__ uint64_t s_r0[kLevelsChunk], s_r1[kLevelsChunk];
+  __shared__ unsigned long long s_off, s_cnt;
+  __shared__ uint32_t s_wtot[nwarps];
+  DevState* st = a.st;
+  const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
+  uint32_t* s_bm = s_dyn;
+  uint32_t* s_stage = s_dyn + nwords;   // [nwarps][1024]
+  const uint64_t nk1 = (1ull << a.b) + 1, ng = 1ull << a.b;
+  const uint64_t nlv = st->cnt[a.nlv_cnt];
+  const uint64_t* lvidx = static_cast<const uint64_t*>(st->buf[a.lvidx_buf].ptr);
+  const K* fl = static_cast<const K*>(st->buf[a.full_buf].ptr);
+  const uint32_t vmask = a.b >= 32 ? 0xFFFFFFFFu : ((1u << a.b) - 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = tid; j < nwords; j += kDenseThreads) s_bm[j] = 0;
+  if (tid == 0) s_off = s_cnt = 0;
+  __syncthreads();
+  for (uint64_t g = blockIdx.x; g < ng; g += gridDim.x) {
+    // mark every level's run of g (levels staged kLevelsChunk at a time)
+    for (uint64_t l0 = 0; l0 < nlv; l0 += kLevelsChunk) {
+      const uint64_t lv = l0 + tid;
+      unsigned long long off = 0, cnt = 0;
+      if (lv < nlv) {
+        const uint64_t r0 = lvidx[lv * nk1 + g], r1 = lvidx[lv * nk1 + g + 1];
+        s_r0[tid] = r0;
+        s_r1[tid] = r1;
+        off = r0 - lvidx[lv * nk1];
+        cnt = r1 - r0;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+      }
+      if (lane == 0 && (off || cnt)) {
+        atomicAdd(&s_off, off);
+        atomicAdd(&s_cnt, cnt);
+      }
+      __syncthreads();
+      const int nl = int(min(uint64_t(kLevelsChunk), nlv - l0));
+      for (int l = 0; l < nl; ++l)
+        for (uint64_t i = s_r0[l] + tid; i < s_r1[l]; i += kDenseThreads) {
+          const uint32_t v = uint32_t(fl[i]) & vmask;
+          atomicOr(&s_bm[v >> 5], 1u << (v & 31));
+        }
+      __syncthreads();
+    }
+    const uint64_t base0 = s_off, total = s_cnt;
+    if (total) {
+      // emit: each warp owns a contiguous part of the bitmap; count, then
+      // 32 words per step staged and written coalesced; words cleared
+      const int wrange = (nwords + nwarps - 1) / nwarps;
+      const int w0 = min(nwords, warp * wrange), w1 = min(nwords, w0 + wrange);
+      uint32_t c = 0;
+      for (int j = w0 + lane; j < w1; j += 32) c += __popc(s_bm[j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if (lane == 0) s_wtot[warp] = c;
+      __syncthreads();
+      uint64_t base = base0;
+      for (int w = 0; w < warp; ++w) base += s_wtot[w];
+      uint32_t* stage = s_stage + warp * 1024;
+      for (int j0 = w0; j0 < w1; j0 += 32) {
+        const int j = j0 + lane;
+        const uint32_t bits = j < w1 ? s_bm[j] : 0u;
+        if (j < w1) s_bm[j] = 0;
+        const uint32_t pc = __popc(bits);
+        uint32_t incl = pc;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += y;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (tot == 0) continue;
+        uint32_t pos = incl - pc;
+        uint32_t rest = bits;
+        while (rest) {
+          const int t = __ffs(rest) - 1;
+          rest &= rest - 1;
+          stage[pos++] = uint32_t(j) * 32u + uint32_t(t);
+        }
+        __syncwarp();
+        for (uint32_t i = lane; i < tot; i += 32) {
+          a.out0[base + i] = uint32_t(g);
+          a.out1[base + i] = stage[i];
+        }
+        __syncwarp();
+        base += tot;
+      }
+    }
+    __syncthreads();   // s_wtot, s_off, s_cnt reused by the next group
+    if (tid == 0) s_off = s_cnt = 0;
+    __syncthreads();
+  }
+}
+
 }  // namespace hisa

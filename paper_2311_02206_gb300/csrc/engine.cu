@@ -1953,7 +1953,10 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
   void *t0 = nullptr, *t1 = nullptr;
   hisa_status s;
   int src = r.idb ? r.full : r.base;
-  if (r.idb && (r.order == 1 || r.append)) {
+  // an append-only full stored in declared order: its levels merged by
+  // group straight into the columns (k_levels_read), no sort
+  const bool levels = r.idb && r.append && r.order == 0;
+  if (r.idb && (r.order == 1 || r.append) && !levels) {
     // stored (c1, c0), or as unmerged levels: (exchange the columns and) sort,
     // so the caller gets the lexicographic order of the declared columns
     const int kt = wide ? radix_tile<uint64_t>() : radix_tile<uint32_t>();
@@ -2009,9 +2012,15 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
       d1 = static_cast<uint32_t*>(t1);
     }
   }
-  DecodeArgs a{dst, src, 0, d0, d1, b, 0, 0, size};
-  if (wide) launch_decode<uint64_t>(a, grid, stream);
-  else launch_decode<uint32_t>(a, grid, stream);
+  if (levels) {
+    LevelsReadArgs la{dst, r.full, r.lvidx, r.nlv, b, d0, d1};
+    if (wide) launch_levels_read<uint64_t>(la, grid, stream);
+    else launch_levels_read<uint32_t>(la, grid, stream);
+  } else {
+    DecodeArgs a{dst, src, 0, d0, d1, b, 0, 0, size};
+    if (wide) launch_decode<uint64_t>(a, grid, stream);
+    else launch_decode<uint32_t>(a, grid, stream);
+  }
   if ((s = check_launch("decode"))) return s;
   if (!on_device && !mapped) {
     CU(cudaMemcpyAsync(cols[0], d0, size * 4, cudaMemcpyDeviceToHost, stream));

@@ -168,6 +168,14 @@ void launch_chain(const ChainArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKChainGather, s, (k_chain_gather<K><<<g.join, 256, 0, s>>>(a)));
 }
 template <typename K>
+void launch_levels_read(const LevelsReadArgs& a, const Grid& g, cudaStream_t s) {
+  const size_t nwords = a.b >= 5 ? (size_t(1) << (a.b - 5)) : 1;
+  const size_t smem = (nwords + (kDenseThreads / 32) * 1024) * 4;
+  // the bitmap of an 18-bit domain and the staging exceed the default 48 KB
+  cudaFuncSetAttribute(k_levels_read<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  HISA_LAUNCH(kKDecode, s, (k_levels_read<K><<<g.sms * 8, kDenseThreads, smem, s>>>(a)));
+}
+template <typename K>
 void launch_append(const AppendArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKAppend, s, (k_append<K><<<g.small * 2, 256, 0, s>>>(a)));
 }
@@ -297,6 +305,7 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_group_starts<K>(const GroupArgs&, const Grid&, cudaStream_t);     \
   template void launch_join_dense<K>(const DenseArgs&, const Grid&, cudaStream_t);       \
   template void launch_chain<K>(const ChainArgs&, const Grid&, cudaStream_t);            \
+  template void launch_levels_read<K>(const LevelsReadArgs&, const Grid&, cudaStream_t);  \
   template void launch_radix_hist<K>(const RadixHistArgs&, const Grid&, cudaStream_t);   \
   template void launch_radix_pass<K>(const RadixPassArgs&, const Grid&, cudaStream_t);   \
   template void launch_setop<K>(const SetopArgs&, const Grid&, cudaStream_t);            \
