@@ -376,13 +376,13 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
       const uint32_t excl = incl - len;
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
       if (lane == 0) raw += total;
-      // two elements per lane per step: both loads are in flight before
-      // either is marked
-      for (uint32_t q0 = 0; q0 < total; q0 += 64) {
-        uint32_t v[2];
-        bool ok[2];
+      // four elements per lane per step: all four loads are in flight
+      // before any is marked
+      for (uint32_t q0 = 0; q0 < total; q0 += 128) {
+        uint32_t v[4];
+        bool ok[4];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < 4; ++u) {
           const uint32_t q = q0 + uint32_t(u) * 32 + lane;
           int owner = 0;   // lanes whose inclusive prefix is <= q
 #pragma unroll
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
           v[u] = ok[u] ? uint32_t(inner[ob_begin + (q - ob_excl)]) & vmask : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < 4; ++u) {
           if (!ok[u]) continue;
           const uint32_t bit = 1u << (v[u] & 31);
           // most values are marked already (many outer tuples share inner
