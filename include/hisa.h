@@ -90,8 +90,12 @@ typedef void (*hisa_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
  * grouped bitmap join (SG's recursive rule) builds its Tmp relation by
  * counting, per tuple of A in x order, the delta run it meets, and copying
  * those runs to their offsets: Tmp comes out grouped by x with no join
- * partition pass and no radix sort.  Same results; domain of at most 2^20
- * values, not in batched runs. */
+ * partition pass and no radix sort.  Also never run a one-step variant
+ * H(x, y) <- A(x, z), delta(z, y) as an inverted grouped bitmap join (A
+ * sorted by x the grouped outer, delta directly indexed by z the probed
+ * side; domains of at most 2^14 values), which by default replaces its
+ * raw results and their sort (CSPA's ValueFlow and ValueAlias rules).  Same
+ * results; domain of at most 2^20 values, not in batched runs. */
 #define HISA_FLAG_NO_CHAIN 32u
 
 typedef struct {

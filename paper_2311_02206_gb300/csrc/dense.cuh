@@ -60,7 +60,23 @@ struct ChainArgs {
   int tmp_buf, tmp_cnt;
   int b;
   int skip_mask, stage_bit;
+  // optional (tfirst_buf >= 0): Tmp's direct index by x, tfirst[x] =
+  // pre[afirst[x]] (afirst: A's direct index by x), for a next step that
+  // probes Tmp by x (an inverted dense join)
+  int afirst_buf, tfirst_buf;
 };
+
+template <typename K>
+__global__ void k_chain_first(ChainArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t* af = static_cast<const uint64_t*>(st->buf[a.afirst_buf].ptr);
+  const uint64_t* pre = static_cast<const uint64_t*>(st->buf[a.pre_buf].ptr);
+  uint64_t* tf = static_cast<uint64_t*>(st->buf[a.tfirst_buf].ptr);
+  const uint64_t nk = 1ull << a.b;
+  for (uint64_t k = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; k <= nk; k += uint64_t(gridDim.x) * blockDim.x)
+    tf[k] = pre[af[k]];
+}
 
 template <typename K>
 __global__ void k_chain_len(ChainArgs a) {
@@ -157,6 +173,9 @@ struct DenseArgs {
 constexpr int kDenseThreads = 128;
 constexpr int kDenseCtasPerSm = 16;   // latency-bound (L2 probes and run reads): full occupancy
 constexpr int kDenseMaxBits = 18;   // bitmap of 2^18 bits = 32 KB of shared memory
+// an inverted dense join reads all of its inner relation every iteration:
+// only over domains of at most 2^14 values (inner relations of <= 2^28 tuples)
+constexpr int kInvertMaxBits = 14;
 
 // Group starts by one pass over a sorted array (heads of runs of equal
 // g = code >> b, compacted in order by a decoupled look-back over tiles): for

@@ -169,6 +169,7 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.dense_bmm = new_slot(4);
   sc.chain_dfirst = new_slot(8);
   sc.chain_pre = new_slot(8);
+  sc.chain_tfirst = new_slot(8);
   sc.group_cnt = nslots++;
   sc.raw_cnt = nslots++;
   slot_zero[sc.radix_status] = slot_zero[sc.setop_status] = slot_zero[sc.join_status] = true;
@@ -600,11 +601,32 @@ hisa_status Engine::compile() {
   // column, and whose second step is dense: Tmp is gathered grouped by x
   // (ChainArgs) instead of joined and sorted.  The inner must be stored x
   // first: an EDB relation builds that copy, an IDB one must keep it anyway.
+  //
+  // A one-step variant H(x, y) <- A(x, z), delta(z, y) (the head keeps the
+  // inner's other column first and delta's second column) joins densely the
+  // other way round: A sorted by x is the grouped outer and delta, directly
+  // indexed by z, the probed side (StepPlan::invert); so does a second step
+  // of that shape over a gathered Tmp.  Each iteration reads all of A, so
+  // only over small domains (|A| <= 2^(2 * kInvertMaxBits)).
+  auto invertible = [&](const StepPlan& sp) {
+    if (sp.dense || sp.to_tmp || !sp.has_inner || sp.out_rel < 0 || rels[sp.out_rel].append) return false;
+    if (sp.outer_kcol != 0 || sp.proj0 != kSrcOther || sp.proj1 != kSrcOuter1) return false;
+    const bool filt_ok = sp.nfilt == 0 ||
+                         (sp.nfilt == 1 && sp.fop[0] == kFiltNeq &&
+                          ((sp.fa[0] == kSrcOther && sp.fb[0] == kSrcOuter1) ||
+                           (sp.fa[0] == kSrcOuter1 && sp.fb[0] == kSrcOther)));
+    const Relation& A = rels[sp.inner_rel];
+    return filt_ok && !(A.idb && sp.inner_col == 0 && !A.need_idx[1]);   // x second: its (c1, c0) order kept
+  };
+  const bool gather_on = dense_on && !(cfg.flags & HISA_FLAG_NO_CHAIN) && inst_bits == 0 && b <= kDirectMaxBits;
+  const bool invert_on = gather_on && b <= kInvertMaxBits;
   for (auto& v : planN)
-    for (auto& sp : v) sp.chain = false;
-  if (dense_on && !(cfg.flags & HISA_FLAG_NO_CHAIN) && inst_bits == 0 && b <= kDirectMaxBits)
+    for (auto& sp : v) sp.chain = sp.invert = false;
+  if (gather_on)
     for (auto& v : planN) {
-      if (v.size() != 2 || !v[1].dense || v[1].outer_slot != sc.tmp_a) continue;
+      if (v.size() != 2 || v[1].outer_slot != sc.tmp_a) continue;
+      const bool inv2 = !v[1].dense && invert_on && invertible(v[1]);
+      if (!v[1].dense && !inv2) continue;
       StepPlan& s1 = v[0];
       bool delta_outer = false;
       for (int r : idb) delta_outer = delta_outer || s1.outer_slot == rels[r].delta;
@@ -616,6 +638,22 @@ hisa_status Engine::compile() {
       if (A.idb && !A.need_idx[xcol]) continue;
       s1.chain = true;
       A.need_idx[xcol] = true;
+      if (inv2) {
+        v[1].invert = v[1].dense = true;
+        Relation& A2 = rels[v[1].inner_rel];
+        if (!A2.idb && v[1].inner_col == 0) A2.need_idx[1] = true;   // an EDB relation builds its (c1, c0) copy
+      }
+    }
+  if (invert_on)
+    for (auto& v : planN) {
+      if (v.size() != 1) continue;
+      StepPlan& sp = v[0];
+      bool delta_outer = false;
+      for (int r : idb) delta_outer = delta_outer || sp.outer_slot == rels[r].delta;
+      if (!delta_outer || !invertible(sp)) continue;
+      sp.invert = sp.dense = true;
+      Relation& A = rels[sp.inner_rel];
+      if (!A.idb && sp.inner_col == 0) A.need_idx[1] = true;   // an EDB relation builds its (c1, c0) copy
     }
   // log-structured full where nothing probes full (it is only differenced
   // and merged): REACH and SG, not CSPA's inner IDB atoms nor batched runs
@@ -786,9 +824,8 @@ void Engine::emit_idb_index(std::vector<Op>& ops) {
 // direct index by its first stored column (the join value), the inner's
 // direct index by x (into dense_first, read by the dense join's group
 // compaction through chain_pre), then len + scan + gather (ChainArgs).
-void Engine::emit_chain(std::vector<Op>& ops, const StepPlan& sp) {
-  const Relation& A = rels[sp.inner_rel];
-  const int abuf = sp.inner_col == 1 ? A.base : A.rev;   // stored x first
+void Engine::emit_chain(std::vector<Op>& ops, const StepPlan& sp, bool tmp_index) {
+  const int abuf = sorted_by_other(sp);   // stored x first
   Op x{};
   x.kind = Op::INDEX;
   x.index = IndexArgs{dst, sp.outer_slot, sp.outer_cnt, sc.chain_dfirst, b, -1, 1, b};
@@ -800,11 +837,36 @@ void Engine::emit_chain(std::vector<Op>& ops, const StepPlan& sp) {
   Op c{};
   c.kind = Op::CHAIN;
   c.chain = ChainArgs{dst, abuf, abuf, sp.outer_slot, sp.outer_cnt, sc.chain_dfirst, sc.chain_pre, sc.tmp_a,
-                      sc.tmp_cnt, b, 1, 0};
+                      sc.tmp_cnt, b, 1, 0, sc.dense_first, tmp_index ? sc.chain_tfirst : -1};
   ops.push_back(c);
 }
 
-void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_groups) {
+// The slot of a step's inner relation sorted by its other (non-join) column.
+int Engine::sorted_by_other(const StepPlan& sp) const {
+  const Relation& A = rels[sp.inner_rel];
+  return sp.inner_col == 1 ? A.base : A.rev;
+}
+
+// An inverted dense join (StepPlan::invert): delta's direct index by its
+// first stored column (the join value), then the grouped bitmap join with
+// the inner sorted by its other column as the outer and delta as the inner.
+void Engine::emit_invert(std::vector<Op>& ops, const StepPlan& sp, bool tmp_probe) {
+  // a gathered Tmp comes with its direct index (emit_chain); a delta is indexed here
+  if (!tmp_probe) {
+    Op x{};
+    x.kind = Op::INDEX;
+    x.index = IndexArgs{dst, sp.outer_slot, sp.outer_cnt, sc.chain_dfirst, b, -1, 1, b};
+    ops.push_back(x);
+  }
+  StepPlan d = sp;
+  d.outer_slot = d.outer_cnt = sorted_by_other(sp);
+  d.outer_kcol = 1;
+  d.proj0 = kSrcOuter0;
+  emit_dense(ops, d, false, sp.outer_slot, tmp_probe ? sc.chain_tfirst : sc.chain_dfirst);
+}
+
+void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_groups, int inner_buf,
+                        int table_buf) {
   const Relation& ir = rels[sp.inner_rel];
   const Relation& hr = rels[sp.out_rel];
   // group starts: a direct index of delta by the kept column, compacted to
@@ -850,9 +912,10 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
   Op d{};
   d.kind = Op::DENSE;
   d.dense = DenseArgs{dst, sp.outer_slot, sp.outer_cnt, sc.groups, sc.group_cnt,
-                      sp.inner_col == 0 ? ir.base : ir.rev, ir.table[sp.inner_col], b,
+                      inner_buf >= 0 ? inner_buf : sp.inner_col == 0 ? ir.base : ir.rev,
+                      table_buf >= 0 ? table_buf : ir.table[sp.inner_col], b,
                       out, out, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0,
-                      direct_bits > 0, hr.append ? hr.full : -1, hr.lvidx, hr.nlv, sp.nfilt > 0,
+                      inner_buf >= 0 || direct_bits > 0, hr.append ? hr.full : -1, hr.lvidx, hr.nlv, sp.nfilt > 0,
                       sc.dense_units, sc.dense_done, unit_size, sc.dense_mslot, sc.dense_bmm, units_ready};
   ops.push_back(d);
   if (hr.append) {   // no unique pass in the tail; |new| (statistics) = |delta|
@@ -897,7 +960,9 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
     }
     for (auto& sp : v) {
       if (sp.chain) {
-        emit_chain(ops, sp);
+        emit_chain(ops, sp, v.size() > 1 && v[1].invert);
+      } else if (sp.invert) {
+        emit_invert(ops, sp, chain);
       } else if (sp.dense && sp.outer_slot == sc.tmp_a && chain) {
         emit_dense(ops, sp, true);   // Tmp gathered grouped by its kept column
       } else if (sp.dense && sp.outer_slot == sc.tmp_a) {
@@ -1495,8 +1560,9 @@ hisa_status Engine::init_run_state() {
   hs.cnt[sc.raw_cnt] = hs.cnt[sc.group_cnt] = 0;
   if (b + inst_bits <= kDirectMaxBits && (s = ensure(sc.dense_first, (1ull << (b + inst_bits)) + 2))) return s;
   bool any_chain = false;
-  for (auto& v : planN) any_chain = any_chain || (!v.empty() && v[0].chain);
-  if (any_chain && ((s = ensure(sc.chain_dfirst, (1ull << b) + 2)) || (s = ensure(sc.chain_pre, 4 * nedb + 2))))
+  for (auto& v : planN) any_chain = any_chain || (!v.empty() && (v[0].chain || v[0].invert));
+  if (any_chain && ((s = ensure(sc.chain_dfirst, (1ull << b) + 2)) || (s = ensure(sc.chain_pre, 4 * nedb + 2)) ||
+                    (s = ensure(sc.chain_tfirst, (1ull << b) + 2))))
     return s;
   if ((s = ensure(sc.tmp_hist, 8 * 256)) || (s = ensure(sc.tmp_b, 4 * nedb))) return s;
   if ((s = ensure(sc.groups, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||

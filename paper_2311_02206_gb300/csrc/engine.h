@@ -64,6 +64,8 @@ struct StepPlan {
   bool dense;   // grouped join with bitmap deduplication (dense.cuh)
   bool resort;  // its outer (a delta stored join column first) is exchanged and sorted by the kept column first
   bool chain;   // a first step whose Tmp is gathered grouped by its kept column (ChainArgs)
+  bool invert;  // a dense join run the other way round: the inner (sorted by the kept column) is
+                // the grouped outer, delta (directly indexed by the join column) the probed side
 };
 
 struct Op {
@@ -96,6 +98,7 @@ struct Scratch {
   int dense_units, dense_done;  // the dense join's first unit per group and finished-unit counters
   int dense_mslot, dense_bmm;   // multi-unit groups' bitmap slot and those bitmaps (kept zeroed)
   int chain_dfirst, chain_pre;  // a gathered Tmp: delta's direct index, offsets per inner tuple
+  int chain_tfirst;             // a gathered Tmp's direct index by its kept column
 
   int group_cnt, raw_cnt;     // count-only slots
 };
@@ -156,8 +159,11 @@ class Engine {
   hisa_status compile();
   hisa_status plan_variant(const hisa_rule& R, int delta_atom, std::vector<StepPlan>& out);
   void emit_join(std::vector<Op>& ops, const StepPlan& sp);
-  void emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_groups = false);
-  void emit_chain(std::vector<Op>& ops, const StepPlan& sp);
+  void emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_groups = false, int inner_buf = -1,
+                  int table_buf = -1);
+  void emit_invert(std::vector<Op>& ops, const StepPlan& sp, bool tmp_probe);
+  int sorted_by_other(const StepPlan& sp) const;
+  void emit_chain(std::vector<Op>& ops, const StepPlan& sp, bool tmp_index);
   hisa_status plan_all();
   void emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepPlan>>& plans, bool idb_inner);
   void emit_idb_index(std::vector<Op>& ops);

@@ -166,6 +166,7 @@ void launch_chain(const ChainArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKChainLen, s, (k_chain_len<K><<<g.small * 2, 256, 0, s>>>(a)));
   HISA_LAUNCH(kKChainScan, s, (k_chain_scan<K><<<1, 1024, 0, s>>>(a)));
   HISA_LAUNCH(kKChainGather, s, (k_chain_gather<K><<<g.join, 256, 0, s>>>(a)));
+  if (a.tfirst_buf >= 0) HISA_LAUNCH(kKChainScan, s, (k_chain_first<K><<<g.small, 256, 0, s>>>(a)));
 }
 template <typename K>
 void launch_levels_read(const LevelsReadArgs& a, const Grid& g, cudaStream_t s) {
