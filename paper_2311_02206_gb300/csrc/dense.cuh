@@ -386,6 +386,32 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
         const uint32_t key = join_key(inst_of(code, a.b), colv(code, 1, a.b), a.b);
         if (!probe_run(table, tmask, a.index_direct, key, &begin, &len, &st->error)) len = 0;
       }
+      // runs of at least 32 values are walked by the whole warp one after
+      // another: coalesced, no per-value search for the run, and a sorted
+      // run's neighbouring values mostly share a bitmap word
+      for (uint32_t lm = __ballot_sync(0xffffffffu, len >= 32); lm; lm &= lm - 1) {
+        const int l = __ffs(lm) - 1;
+        const uint64_t rb = __shfl_sync(0xffffffffu, begin, l);
+        const uint32_t rn = __shfl_sync(0xffffffffu, len, l);
+        if (lane == 0) raw += rn;
+        for (uint32_t i0 = 0; i0 < rn; i0 += 128) {
+          uint32_t v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t i = i0 + uint32_t(u) * 32 + lane;
+            v[u] = i < rn ? uint32_t(inner[rb + i]) & vmask : 0xFFFFFFFFu;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (v[u] == 0xFFFFFFFFu) continue;
+            const uint32_t bit = 1u << (v[u] & 31);
+            if (!(s_bm[v[u] >> 5] & bit)) atomicOr(&s_bm[v[u] >> 5], bit);
+          }
+        }
+      }
+      if (len >= 32) len = 0;
+      // the short runs concatenated: each value finds its run by a binary
+      // search over the warp's inclusive run-length prefix
       uint32_t incl = len;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
