@@ -491,10 +491,28 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
       const uint64_t g = uint64_t(outer[gs[gi]]) >> a.b;
       for (uint64_t lv = 0; lv < nlv; ++lv) {
         const uint64_t r0 = lvidx[lv * nk + g], r1 = lvidx[lv * nk + g + 1];
-        for (uint64_t i = r0 + tid; i < r1; i += kDenseThreads) {
-          const uint32_t v = uint32_t(fl[i]) & vmask;
-          const uint32_t bit = 1u << (v & 31);
-          if (s_bm[v >> 5] & bit) atomicAnd(&s_bm[v >> 5], ~bit);
+        if (r1 - r0 <= 4 * kDenseThreads) {   // a short run: one pass
+          for (uint64_t i = r0 + tid; i < r1; i += kDenseThreads) {
+            const uint32_t v = uint32_t(fl[i]) & vmask;
+            const uint32_t bit = 1u << (v & 31);
+            if (s_bm[v >> 5] & bit) atomicAnd(&s_bm[v >> 5], ~bit);
+          }
+          continue;
+        }
+        // eight loads in flight per thread: the level runs come from HBM
+        for (uint64_t i0 = r0 + tid; i0 < r1; i0 += 8 * kDenseThreads) {
+          uint32_t v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const uint64_t i = i0 + uint64_t(u) * kDenseThreads;
+            v[u] = i < r1 ? uint32_t(fl[i]) & vmask : 0xFFFFFFFFu;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (v[u] == 0xFFFFFFFFu) continue;
+            const uint32_t bit = 1u << (v[u] & 31);
+            if (s_bm[v[u] >> 5] & bit) atomicAnd(&s_bm[v[u] >> 5], ~bit);
+          }
         }
       }
     }
