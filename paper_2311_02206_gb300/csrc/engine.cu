@@ -170,6 +170,8 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.chain_dfirst = new_slot(8);
   sc.chain_pre = new_slot(8);
   sc.chain_tfirst = new_slot(8);
+  sc.read_m = new_slot(4);
+  sc.read_rows = new_slot(8);
   sc.group_cnt = nslots++;
   sc.raw_cnt = nslots++;
   slot_zero[sc.radix_status] = slot_zero[sc.setop_status] = slot_zero[sc.join_status] = true;
@@ -2022,7 +2024,12 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
   // an append-only full stored in declared order: its levels merged by
   // group straight into the columns (k_levels_read), no sort
   const bool levels = r.idb && r.append && r.order == 0;
-  if (r.idb && (r.order == 1 || r.append) && !levels) {
+  // stored column-swapped: transposed through a bit matrix over the domain
+  // (k_levels_transpose; 2^(2b) bits), no sort
+  const bool transposed = r.idb && r.append && r.order == 1 && b >= 8 && b <= 16;
+  if (transposed && ((s = ensure(sc.read_m, (1ull << (2 * b)) / 32)) || (s = ensure(sc.read_rows, (1ull << b) + 1))))
+    return s;
+  if (r.idb && (r.order == 1 || r.append) && !levels && !transposed) {
     // stored (c1, c0), or as unmerged levels: (exchange the columns and) sort,
     // so the caller gets the lexicographic order of the declared columns
     const int kt = wide ? radix_tile<uint64_t>() : radix_tile<uint32_t>();
@@ -2068,9 +2075,19 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
     if (cudaPointerGetAttributes(&pa0, cols[0]) == cudaSuccess &&
         cudaPointerGetAttributes(&pa1, cols[1]) == cudaSuccess && pa0.type == cudaMemoryTypeHost &&
         pa1.type == cudaMemoryTypeHost && pa0.devicePointer && pa1.devicePointer) {
-      d0 = static_cast<uint32_t*>(pa0.devicePointer);
-      d1 = static_cast<uint32_t*>(pa1.devicePointer);
-      mapped = true;
+      // the row emit of a transposed read writes the host link slower than
+      // the copy engine does: stage in device memory when it fits
+      if (transposed && dev_alloc(size * 4, &t0) == HISA_OK && dev_alloc(size * 4, &t1) == HISA_OK) {
+        d0 = static_cast<uint32_t*>(t0);
+        d1 = static_cast<uint32_t*>(t1);
+      } else {
+        if (t0) dev_free(t0);
+        t0 = nullptr;
+        last_error.clear();
+        d0 = static_cast<uint32_t*>(pa0.devicePointer);
+        d1 = static_cast<uint32_t*>(pa1.devicePointer);
+        mapped = true;
+      }
     } else {
       cudaGetLastError();
       if ((s = dev_alloc(size * 4, &t0)) || (s = dev_alloc(size * 4, &t1))) return s;
@@ -2078,7 +2095,12 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
       d1 = static_cast<uint32_t*>(t1);
     }
   }
-  if (levels) {
+  if (transposed) {
+    LevelsTransposeArgs ta{dst, r.full, r.lvidx, r.nlv, b, static_cast<uint32_t*>(hs.buf[sc.read_m].ptr),
+                           static_cast<uint64_t*>(hs.buf[sc.read_rows].ptr), d0, d1};
+    if (wide) launch_levels_transpose<uint64_t>(ta, grid, stream);
+    else launch_levels_transpose<uint32_t>(ta, grid, stream);
+  } else if (levels) {
     LevelsReadArgs la{dst, r.full, r.lvidx, r.nlv, b, d0, d1};
     if (wide) launch_levels_read<uint64_t>(la, grid, stream);
     else launch_levels_read<uint32_t>(la, grid, stream);

@@ -99,6 +99,7 @@ struct Scratch {
   int dense_mslot, dense_bmm;   // multi-unit groups' bitmap slot and those bitmaps (kept zeroed)
   int chain_dfirst, chain_pre;  // a gathered Tmp: delta's direct index, offsets per inner tuple
   int chain_tfirst;             // a gathered Tmp's direct index by its kept column
+  int read_m, read_rows;        // reading a column-swapped append-only full: its bit matrix, row offsets
 
   int group_cnt, raw_cnt;     // count-only slots
 };

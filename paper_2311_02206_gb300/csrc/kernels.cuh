@@ -186,6 +186,7 @@ template <typename K> void launch_append(const AppendArgs& a, const Grid& g, cud
 template <typename K> void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_chain(const ChainArgs& a, const Grid& g, cudaStream_t s);   // len + scan + gather
 template <typename K> void launch_levels_read(const LevelsReadArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_levels_transpose(const LevelsTransposeArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_hist(const InstArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_bounds(const InstArgs& a, const Grid& g, cudaStream_t s);
 void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStream_t s);

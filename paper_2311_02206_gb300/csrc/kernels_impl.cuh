@@ -177,6 +177,15 @@ void launch_levels_read(const LevelsReadArgs& a, const Grid& g, cudaStream_t s) 
   HISA_LAUNCH(kKDecode, s, (k_levels_read<K><<<g.sms * 8, kDenseThreads, smem, s>>>(a)));
 }
 template <typename K>
+void launch_levels_transpose(const LevelsTransposeArgs& a, const Grid& g, cudaStream_t s) {
+  const size_t tile = (size_t(1) << a.b) * 2;   // 2^b 16-bit columns
+  cudaFuncSetAttribute(k_levels_transpose<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tile));
+  HISA_LAUNCH(kKDecode, s, (k_levels_transpose<K><<<g.sms, 1024, tile, s>>>(a)));
+  HISA_LAUNCH(kKDecode, s, (k_rows_count<K><<<g.small, 256, 0, s>>>(a)));
+  HISA_LAUNCH(kKDecode, s, (k_rows_scan<K><<<1, 1024, 0, s>>>(a)));
+  HISA_LAUNCH(kKDecode, s, (k_rows_emit<K><<<g.sms * 8, kDenseThreads, 0, s>>>(a)));
+}
+template <typename K>
 void launch_append(const AppendArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKAppend, s, (k_append<K><<<g.small * 2, 256, 0, s>>>(a)));
 }
@@ -307,6 +316,7 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_join_dense<K>(const DenseArgs&, const Grid&, cudaStream_t);       \
   template void launch_chain<K>(const ChainArgs&, const Grid&, cudaStream_t);            \
   template void launch_levels_read<K>(const LevelsReadArgs&, const Grid&, cudaStream_t);  \
+  template void launch_levels_transpose<K>(const LevelsTransposeArgs&, const Grid&, cudaStream_t); \
   template void launch_radix_hist<K>(const RadixHistArgs&, const Grid&, cudaStream_t);   \
   template void launch_radix_pass<K>(const RadixPassArgs&, const Grid&, cudaStream_t);   \
   template void launch_setop<K>(const SetopArgs&, const Grid&, cudaStream_t);            \

@@ -17,9 +17,20 @@ MUTUAL = ({"A": "edb", "B": "edb", "P": "idb", "Q": "idb"}, [
     (("Q", ("x", "x")), [("P", ("x", "w")), ("Q", ("w", "v"))], []),
 ])
 
+# a recursive rule whose head keeps the inner atom's other column first and
+# filters x != y (the engine runs it as an inverted grouped bitmap join with
+# its filter over small domains), and a rule reading R's delta on its second
+# column
+INVERTED = ({"E": "edb", "R": "idb", "S": "idb"}, [
+    (("R", ("x", "y")), [("E", ("x", "y"))], []),
+    (("R", ("x", "y")), [("E", ("x", "z")), ("R", ("z", "y"))], [("x", "y")]),
+    (("S", ("x", "y")), [("R", ("x", "z")), ("E", ("z", "y"))], []),
+])
+
 PROGRAMS = {
     "reach": oracle.REACH,
     "sg": oracle.SG,
     "tc_nonlinear": TC_NONLINEAR,
     "mutual": MUTUAL,
+    "inverted": INVERTED,
 }

@@ -72,6 +72,38 @@ def test_reach_er_1000():
     assert ref.size("Reach") == 889_271
 
 
+@pytest.mark.parametrize("prog", ["reach", "sg", "cspa"])
+def test_read_relation_destinations(prog):
+    """Each read path -- a column-swapped append-only full through the bit-matrix
+    transpose (REACH), one in declared order through the level merge (SG), a
+    single sorted full (the points-to program) -- gives the oracle's tuples in
+    lexicographic order into page-locked host columns (staged or written over
+    the host link), into pageable numpy arrays and into device tensors."""
+    from paper_2311_02206_gb300 import hisa
+    if prog == "reach":
+        program, edb = oracle.REACH, {"Edge": workloads.config_reach_er()}
+    elif prog == "sg":
+        program, edb = oracle.SG, {"Edge": workloads.dag_graph(400, 900, 16, 3)}
+    else:
+        program, edb = oracle.CSPA, workloads.config_cspa(1000, 32)
+    ref = oracle.reach(*edb["Edge"]) if prog == "reach" else oracle.seminaive(*program, edb)
+    with hisa.Context() as ctx:
+        ctx.program(*program)
+        for k, (c0, c1) in edb.items():
+            ctx.load_tuples(k, c0, c1)
+        ctx.run()
+        for name, (r0, r1) in ref.relations.items():
+            n = ctx.relation_size(name)
+            assert n == len(r0), name
+            h0 = torch.empty(max(n, 1), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+            h1 = torch.empty(max(n, 1), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+            p0, p1 = ctx.read_relation(name, out=(h0, h1))
+            a0, a1 = ctx.read_relation(name)
+            d0, d1 = ctx.read_relation(name, device=True)
+            for g0, g1 in ((p0, p1), (a0, a1), (d0.cpu().numpy().view(np.uint32), d1.cpu().numpy().view(np.uint32))):
+                assert np.array_equal(g0, r0) and np.array_equal(g1, r1), name
+
+
 def test_reach_wide_codes():
     """Node ids spread over the full uint32 range (64-bit codes, b = 32)."""
     rng = np.random.default_rng(11)

@@ -8,7 +8,7 @@ import pytest
 import oracle
 from paper_2311_02206_gb300 import workloads
 from hisa_testutil import assert_same, gpu_eval
-from programs import MUTUAL, TC_NONLINEAR
+from programs import INVERTED, MUTUAL, TC_NONLINEAR
 
 pytestmark = pytest.mark.gpu
 
@@ -73,6 +73,17 @@ def test_mutual_random(seed):
     ref = oracle.seminaive(*MUTUAL, edb)
     for flags in modes():
         rels, counts, _ = gpu_eval(*MUTUAL, edb, flags=flags)
+        assert_same(rels, counts, ref)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_inverted_filter_random(seed):
+    """x != y in a rule run as an inverted grouped bitmap join by default, and
+    as a join + sort with HISA_FLAG_NO_CHAIN (one of the modes)."""
+    edb = {"E": random_graph(3 * seed + 1, 50, 3)}
+    ref = oracle.seminaive(*INVERTED, edb)
+    for flags in modes():
+        rels, counts, _ = gpu_eval(*INVERTED, edb, flags=flags)
         assert_same(rels, counts, ref)
 
 
