@@ -7,6 +7,7 @@
 #include "radix.cuh"
 #include "setops.cuh"
 #include "dense.cuh"
+#include "read.cuh"
 #include <vector>
 
 namespace hisa {
