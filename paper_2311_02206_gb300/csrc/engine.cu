@@ -2026,9 +2026,11 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
   const bool levels = r.idb && r.append && r.order == 0;
   // stored column-swapped: transposed through a bit matrix over the domain
   // (k_levels_transpose; 2^(2b) bits), no sort
-  const bool transposed = r.idb && r.append && r.order == 1 && b >= 8 && b <= 16;
-  if (transposed && ((s = ensure(sc.read_m, (1ull << (2 * b)) / 32)) || (s = ensure(sc.read_rows, (1ull << b) + 1))))
-    return s;
+  bool transposed = r.idb && r.append && r.order == 1 && b >= 8 && b <= 16;
+  if (transposed && (ensure(sc.read_m, (1ull << (2 * b)) / 32) || ensure(sc.read_rows, (1ull << b) + 1))) {
+    transposed = false;   // the matrix does not fit (budget): sort instead
+    last_error.clear();
+  }
   if (r.idb && (r.order == 1 || r.append) && !levels && !transposed) {
     // stored (c1, c0), or as unmerged levels: (exchange the columns and) sort,
     // so the caller gets the lexicographic order of the declared columns
