@@ -154,24 +154,25 @@ def _barrier(world):
         dist.barrier()
 
 
-def _max_over_ranks(x, world):
+def _reduce_over_ranks(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"   # gloo (the CPU tests) reduces host tensors
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def _max_over_ranks(x, world):
+    import torch.distributed as dist
+    return _reduce_over_ranks(x, world, dist.ReduceOp.MAX)
 
 
 def _sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce_over_ranks(x, world, dist.ReduceOp.SUM)
 
 
 # ---- clocks ---------------------------------------------------------------------------------
