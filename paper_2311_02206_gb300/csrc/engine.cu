@@ -172,6 +172,8 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.chain_tfirst = new_slot(8);
   sc.read_m = new_slot(4);
   sc.read_rows = new_slot(8);
+  sc.read_s0 = new_slot(4);
+  sc.read_s1 = new_slot(4);
   sc.group_cnt = nslots++;
   sc.raw_cnt = nslots++;
   slot_zero[sc.radix_status] = slot_zero[sc.setop_status] = slot_zero[sc.join_status] = true;
@@ -2078,13 +2080,12 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
         cudaPointerGetAttributes(&pa1, cols[1]) == cudaSuccess && pa0.type == cudaMemoryTypeHost &&
         pa1.type == cudaMemoryTypeHost && pa0.devicePointer && pa1.devicePointer) {
       // the row emit of a transposed read writes the host link slower than
-      // the copy engine does: stage in device memory when it fits
-      if (transposed && dev_alloc(size * 4, &t0) == HISA_OK && dev_alloc(size * 4, &t1) == HISA_OK) {
-        d0 = static_cast<uint32_t*>(t0);
-        d1 = static_cast<uint32_t*>(t1);
+      // the copy engine does: stage in device memory (kept for the next
+      // read) when it fits
+      if (transposed && ensure(sc.read_s0, size) == HISA_OK && ensure(sc.read_s1, size) == HISA_OK) {
+        d0 = static_cast<uint32_t*>(hs.buf[sc.read_s0].ptr);
+        d1 = static_cast<uint32_t*>(hs.buf[sc.read_s1].ptr);
       } else {
-        if (t0) dev_free(t0);
-        t0 = nullptr;
         last_error.clear();
         d0 = static_cast<uint32_t*>(pa0.devicePointer);
         d1 = static_cast<uint32_t*>(pa1.devicePointer);

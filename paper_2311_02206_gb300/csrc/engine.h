@@ -100,6 +100,7 @@ struct Scratch {
   int chain_dfirst, chain_pre;  // a gathered Tmp: delta's direct index, offsets per inner tuple
   int chain_tfirst;             // a gathered Tmp's direct index by its kept column
   int read_m, read_rows;        // reading a column-swapped append-only full: its bit matrix, row offsets
+  int read_s0, read_s1;         // and its device staging columns (kept across reads)
 
   int group_cnt, raw_cnt;     // count-only slots
 };
