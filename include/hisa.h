@@ -191,8 +191,16 @@ hisa_status hisa_relation_size(hisa_ctx* ctx, uint32_t rel_id, uint64_t* n);
 
 /* Copies relation rel_id in ascending lexicographic order of (c0, c1) into
  * cols[0], cols[1] (each with room for `cap` values; device pointers if
- * cols_on_device).  *n receives the size.  Errors: CAPACITY (cap < size; *n is
- * still set), INVALID_ARG, CUDA. */
+ * cols_on_device).  *n receives the size.  Host columns that are page-locked
+ * (cudaHostAlloc / pinned) are written over the host link by the device or,
+ * for an IDB relation stored column-swapped as append-only levels over a
+ * domain of at most 2^16 values, staged in library-owned device memory and
+ * copied by the copy engine; other host columns are staged and copied.  Such
+ * a column-swapped relation is read through a library-owned bit matrix of
+ * 2^(2b) bits (512 MB at b = 16); the matrix and the staging columns stay
+ * allocated for later reads and count against hbm_budget_bytes (where they do
+ * not fit, the relation is sorted instead).  Errors: CAPACITY (cap < size; *n
+ * is still set), INVALID_ARG, OOM, CUDA. */
 hisa_status hisa_read_relation(hisa_ctx* ctx, uint32_t rel_id, uint32_t* const* cols, uint64_t cap,
                                uint64_t* n, int cols_on_device);
 
