@@ -198,8 +198,9 @@ hisa_status hisa_relation_size(hisa_ctx* ctx, uint32_t rel_id, uint64_t* n);
  * copied by the copy engine; other host columns are staged and copied.  Such
  * a column-swapped relation is read through a library-owned bit matrix of
  * 2^(2b) bits (512 MB at b = 16); the matrix and the staging columns stay
- * allocated for later reads and count against hbm_budget_bytes (where they do
- * not fit, the relation is sorted instead).  Errors: CAPACITY (cap < size; *n
+ * allocated for later reads and count against hbm_budget_bytes (where the
+ * matrix does not fit, the relation is sorted instead; where the staging does
+ * not fit, the device writes the page-locked columns directly).  Errors: CAPACITY (cap < size; *n
  * is still set), INVALID_ARG, OOM, CUDA. */
 hisa_status hisa_read_relation(hisa_ctx* ctx, uint32_t rel_id, uint32_t* const* cols, uint64_t cap,
                                uint64_t* n, int cols_on_device);
