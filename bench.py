@@ -65,7 +65,9 @@ def _args():
     ap.add_argument("--no-dense", action="store_true",
                     help="sort raw join results instead of the grouped bitmap join (HISA_FLAG_NO_DENSE)")
     ap.add_argument("--load-factor", type=float, default=0.0, help="hash-index load factor (0: the library default)")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-sub", action="store_true",
+                    help="rmat16: skip the compact sg20k / cspa / batch5 records of the default line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--micro", choices=["sort", "merge", "join"], default=None,
@@ -95,11 +97,9 @@ def _workload(name):
 def _program_workload(name):
     """(program, EDB columns, description, CPU-sample function) of the
     non-REACH workloads.  The CPU sample runs the oracle as it stands."""
-    import numpy as np
-    import oracle
-    from paper_2311_02206_gb300 import workloads
+    from paper_2311_02206_gb300 import programs, workloads
     if name.startswith("sg20k"):
-        prog = oracle.SG_LITERAL if name.endswith("literal") else oracle.SG
+        prog = programs.SG_LITERAL if name.endswith("literal") else programs.SG
         s, d = workloads.config_sg_dag()
         desc = ("SG (%s) on a random DAG: 20,000 nodes, 40,000 distinct edges u<v, v-u in [1,256], seed 1"
                 % ("x != y on rule 1 only" if name.endswith("literal") else "x != y on both rules"))
@@ -108,6 +108,7 @@ def _program_workload(name):
             # edges point to larger ids, so every derivation of SG(x, y) with
             # x, y < N uses nodes < N only: SG of the induced subgraph on
             # [0, N) is exactly SG restricted to [0, N)^2
+            import oracle
             keep = (s < nodes) & (d < nodes)
             t0 = time.perf_counter()
             r = oracle.seminaive(*prog, {"Edge": (s[keep], d[keep])})
@@ -122,13 +123,14 @@ def _program_workload(name):
                 "aligned windows of 128 ids, seed 2" % (len(edb["Assign"][0]), len(edb["Dereference"][0])))
 
         def sample():
+            import oracle
             small = workloads.config_cspa(1000, 32)
             t0 = time.perf_counter()
             r = oracle.seminaive(*oracle.CSPA, small)
             el = time.perf_counter() - t0
             n = sum(r.size(k) for k in ("ValueFlow", "MemoryAlias", "ValueAlias"))
             return n, el, "the same program and generator divided by 1,000 (windows of 32 ids)"
-        return oracle.CSPA, edb, desc, sample
+        return programs.CSPA, edb, desc, sample
     raise ValueError(name)
 
 
@@ -254,23 +256,39 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken on the current sources (profiles/<kernel>_<workload>.md carries a
-    machine-readable line 'traffic_bytes_per_launch: X source_hash: H')."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
-    try:
-        for line in open(path):
-            if line.startswith("traffic_bytes_per_launch:"):
-                parts = line.split()
-                val, src = float(parts[1]), parts[3]
-                return val if src == kernel_source_hash(kernel) else None
-    except (OSError, IndexError, ValueError):
-        pass
-    return None
-
-
 # ---- CPU oracle baseline ----------------------------------------------------------------------
+
+def host_description():
+    """CPU model, logical CPUs and RAM of the machine the CPU baseline ran on."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":", 1)[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    ram_gb = None
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemTotal:"):
+                ram_gb = round(int(line.split()[1]) / (1 << 20), 1)
+                break
+    except (OSError, ValueError, IndexError):
+        pass
+    return {"cpu_model": model or platform.processor() or "unknown", "arch": platform.machine(),
+            "nproc": os.cpu_count(), "ram_gb": ram_gb}
+
 
 def cpu_baseline(s, d, nodes, targets=64, seed=7):
     """The oracle as it stands (single-threaded std::set semi-naive), on REACH
@@ -282,7 +300,7 @@ def cpu_baseline(s, d, nodes, targets=64, seed=7):
     r = oracle.reach_targets(s, d, T)
     el = time.perf_counter() - t0
     n = r.size("Reach")
-    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_description(),
             "sample": f"REACH restricted to {len(T)} of {nodes} target columns "
                       f"({n} tuples, {el:.1f} s; the recursive rule keeps the target column, so "
                       f"this is exactly Reach on V x T)"}
@@ -290,12 +308,188 @@ def cpu_baseline(s, d, nodes, targets=64, seed=7):
 
 # ---- the GPU arm --------------------------------------------------------------------------------
 
+def _profile_lines(kernel, workload):
+    """Machine-readable lines of the committed ncu summary of `kernel` on
+    `workload` (profiles/<kernel>_<workload>.md), if it was taken on the
+    current sources: {'traffic': DRAM bytes per launch, 'limiter': text}."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    out = {}
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch:"):
+                parts = line.split()
+                if parts[3] != kernel_source_hash(kernel):
+                    return {}
+                out["traffic"] = float(parts[1])
+            elif line.startswith("limiter:"):
+                out["limiter"] = line.split(":", 1)[1].strip()
+    except (OSError, IndexError, ValueError):
+        return {}
+    return out
+
+
+def _timed_steps(ctx, dev_edb, steps, warmup, flush, kstats=None):
+    """`warmup` untimed steps, then `steps` steps timed with CUDA events on the
+    engine's stream (L2 flushed between steps, outside the events).  A step
+    reloads the EDB from device columns and runs to the fixpoint."""
+    import torch
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.reset_edb()
+        for k, (c0, c1) in dev_edb.items():
+            ctx.load_tuples(k, c0, c1)
+        return ctx.run()
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ms, launches, st = [], 0, None
+    for k in range(steps):
+        flush.fill_(k)
+        ev0.record(stream)
+        st = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+        launches += st.kernel_launches
+        if kstats is not None:
+            for e in ctx.kernel_stats():
+                acc = kstats.setdefault(e["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0})
+                acc["launches"] += e["launches"]
+                acc["ms"] += e["ms"]
+                acc["bytes"] += e["bytes"]
+    return ms, launches, st
+
+
+def _e2e(prog, edb, sizes, extra, load_factor, steps, local, world):
+    """The metric end to end through the C-ABI with page-locked host buffers:
+    each step copies the EDB in, runs to the fixpoint on the device (CUDA-graph
+    while loop) and reads every IDB relation back in lexicographic order.
+    Host timers around each part of each step explain the total."""
+    import numpy as np
+    import torch
+    from paper_2311_02206_gb300 import hisa
+
+    def pinned(x):
+        return torch.from_numpy(x.view(np.int32)).pin_memory().numpy().view(np.uint32)
+
+    idb_names = list(sizes)
+    host_edb = {k: (pinned(c0), pinned(c1)) for k, (c0, c1) in edb.items()}
+    outs = {k: (torch.empty(max(sizes[k], 1), dtype=torch.int32).pin_memory().numpy().view(np.uint32),
+                torch.empty(max(sizes[k], 1), dtype=torch.int32).pin_memory().numpy().view(np.uint32))
+            for k in idb_names}
+    edb_bytes = sum(c0.nbytes + c1.nbytes for c0, c1 in edb.values())
+    n_all = sum(sizes.values())
+    ectx = hisa.Context(device=local, flags=hisa.FLAG_GRAPH | extra, load_factor=load_factor)
+    ectx.program(*prog)
+
+    def estep():
+        t0 = time.perf_counter()
+        ectx.reset_edb()
+        for k, (c0, c1) in host_edb.items():
+            ectx.load_tuples(k, c0, c1)
+        ectx.run()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        got = sum(len(ectx.read_relation(k, out=outs[k])[0]) for k in idb_names)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        return got, (t1 - t0) * 1e3, (t2 - t1) * 1e3
+
+    estep()   # first use: buffers grow and caching-allocator blocks are created
+    estep()
+    torch.cuda.synchronize()
+    tot, run_ms, read_ms = [], [], []
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        got, r, rd = estep()
+        tot.append(round(r + rd, 2))
+        run_ms.append(round(r, 2))
+        read_ms.append(round(rd, 2))
+        assert got == n_all
+    et = time.perf_counter() - t0
+    ectx.close()
+    ev = _sum_over_ranks(float(n_all) * steps, world) / _max_over_ranks(et, world)
+    return {"value": ev, "unit": UNIT, "h2d_bytes_per_step": int(edb_bytes), "d2h_bytes_per_step": int(8 * n_all),
+            "steps": steps, "step_ms": tot, "load_run_ms": run_ms, "read_ms": read_ms,
+            "loop": "CUDA graph while node (device-side termination test)"}
+
+
+def _roofline(kstats, workload):
+    peak, peak_kind = _peaks()
+    dname, dk = max(kstats.items(), key=lambda kv: kv[1]["ms"])
+    launches = max(dk["launches"], 1)
+    per_launch_bytes = dk["bytes"] / launches
+    avg_ms = dk["ms"] / launches
+    achieved = dk["bytes"] / (dk["ms"] / 1e3) / 1e9 if dk["ms"] > 0 else 0.0
+    prof = _profile_lines(dname, workload)
+    traffic = prof.get("traffic")
+    dram = traffic / (avg_ms / 1e3) / 1e9 if traffic and avg_ms > 0 else None
+    kernel_ms_total = sum(v["ms"] for v in kstats.values())
+    return {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+            "traffic": traffic, "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
+            "algorithmic_frac": round(achieved / peak, 4),
+            "dram_achieved": round(dram, 1) if dram else None,
+            "dram_frac": round(dram / peak, 4) if dram else None,
+            "limiter": prof.get("limiter"),
+            "note": ("achieved/frac: algorithmic bytes (what the step must move) per launch / launch time; "
+                     "dram_achieved/dram_frac: ncu DRAM bytes per launch (traffic, committed profile of the "
+                     "same sources) / launch time; limiter: what ncu shows bounds the kernel"),
+            "share_of_kernel_time": round(dk["ms"] / kernel_ms_total, 4) if kernel_ms_total else None,
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                            "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] else None}
+                        for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])}}
+
+
+def _sub_program(name, local, flush, cpu, steps=5, warmup=3):
+    """A compact record of a further workload: tuples/s of the device-resident
+    fixpoint (CUDA-graph while loop, the production path), the kernel shares
+    of one host-driven run with per-kernel events, the end-to-end number and
+    the oracle on a bounded sample."""
+    import numpy as np
+    import torch
+    from paper_2311_02206_gb300 import hisa
+    prog, edb, desc, sample = _program_workload(name)
+    idb_names = [k for k, v in prog[0].items() if v == "idb"]
+    dev_edb = {k: (torch.from_numpy(c0.view(np.int32)).cuda(), torch.from_numpy(c1.view(np.int32)).cuda())
+               for k, (c0, c1) in edb.items()}
+    ctx = hisa.Context(device=local, flags=hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL)
+    ctx.program(*prog)
+    ms, launches, st = _timed_steps(ctx, dev_edb, steps, warmup, flush)
+    sizes = {k: ctx.relation_size(k) for k in idb_names}
+    ctx.close()
+    kstats = {}
+    kctx = hisa.Context(device=local, flags=hisa.FLAG_PHASE_TIMES | hisa.FLAG_LOG_FULL)
+    kctx.program(*prog)
+    _timed_steps(kctx, dev_edb, 1, 1, flush, kstats)
+    kctx.close()
+    torch.cuda.empty_cache()
+    n_all = sum(sizes.values())
+    tot_ms = sum(v["ms"] for v in kstats.values())
+    top = [{"kernel": k, "ms_per_run": round(v["ms"], 3), "share": round(v["ms"] / tot_ms, 4)}
+           for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])[:4]]
+    rec = {"workload": desc, "value": n_all * steps / (sum(ms) / 1e3), "unit": UNIT,
+           "ms_per_step": sum(ms) / steps, "step_ms": [round(x, 3) for x in ms], "steps": steps, "warmup": warmup,
+           "idb_tuples": sizes, "iterations": st.iterations, "gpu_launches": launches,
+           "loop": "CUDA graph while node", "kernels_host_driven_run": top,
+           "e2e": _e2e(prog, edb, sizes, hisa.FLAG_LOG_FULL, 0.0, 3, local, 1)}
+    torch.cuda.empty_cache()
+    if cpu:
+        n_s, el, what = sample()
+        rec["cpu_baseline"] = {"value": n_s / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{what}: {n_s} tuples in {el:.1f} s"}
+    return rec
+
+
 def run_hisa(a):
     import numpy as np
     import torch
 
-    import oracle
-    from paper_2311_02206_gb300 import build, hisa
+    from paper_2311_02206_gb300 import build, hisa, programs
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -304,127 +498,52 @@ def run_hisa(a):
     reach = a.workload in ("rmat16", "rmat15", "rmat13", "er1000")
     if reach:
         s, d, desc, nodes = _workload(a.workload)
-        prog, edb, sample = oracle.REACH, {"Edge": (s, d)}, None
+        prog, edb, sample = programs.REACH, {"Edge": (s, d)}, None
     else:
         prog, edb, desc, sample = _program_workload(a.workload)
     idb_names = [k for k, v in prog[0].items() if v == "idb"]
     dev_edb = {k: (torch.from_numpy(c0.view(np.int32)).cuda(), torch.from_numpy(c1.view(np.int32)).cuda())
                for k, (c0, c1) in edb.items()}
-    edb_bytes = sum(c0.nbytes + c1.nbytes for c0, c1 in edb.values())
-    stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 18, dtype=torch.int32, device="cuda")   # 512 MiB > 129 MB L2
 
     extra = (0 if a.single_full else hisa.FLAG_LOG_FULL) | (hisa.FLAG_NO_DENSE if a.no_dense else 0)
     ctx = hisa.Context(device=local, flags=hisa.FLAG_PHASE_TIMES | extra, load_factor=a.load_factor)
     ctx.program(*prog)
-
-    def step():
+    uuid = str(torch.cuda.get_device_properties(local).uuid) if hasattr(
+        torch.cuda.get_device_properties(local), "uuid") else ""
+    kstats = {}
+    for _ in range(a.warmup):          # warm-up outside the clock sampling
         ctx.reset_edb()
         for k, (c0, c1) in dev_edb.items():
             ctx.load_tuples(k, c0, c1)
-        return ctx.run()
-
-    for _ in range(a.warmup):
-        step()
-    torch.cuda.synchronize()
-    kstats = {}
-    launches = 0
-    ms = []
-    uuid = str(torch.cuda.get_device_properties(local).uuid) if hasattr(
-        torch.cuda.get_device_properties(local), "uuid") else ""
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+        ctx.run()
     _barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     gc.disable()   # no collector pause between a step's host-driven iterations
     torch.cuda.nvtx.range_push("timed")   # profilers can keep to the timed steps (ncu --nvtx-include timed/)
     with ClockSampler(uuid) as clk:
-        for k in range(a.steps):
-            flush.fill_(k)
-            ev0.record(stream)
-            st = step()
-            ev1.record(stream)
-            ev1.synchronize()
-            ms.append(ev0.elapsed_time(ev1))
-            launches += st.kernel_launches
-            for e in ctx.kernel_stats():
-                acc = kstats.setdefault(e["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0})
-                acc["launches"] += e["launches"]
-                acc["ms"] += e["ms"]
-                acc["bytes"] += e["bytes"]
+        ms, launches, st = _timed_steps(ctx, dev_edb, a.steps, 0, flush, kstats)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     gc.enable()
     _barrier(world)
     wall = time.perf_counter() - wall0
-    n_reach = sum(ctx.relation_size(k) for k in idb_names)
     sizes = {k: ctx.relation_size(k) for k in idb_names}
+    n_reach = sum(sizes.values())
     iters = st.iterations
     total_s = sum(ms) / 1e3
     slowest = _max_over_ranks(total_s, world)
     tuples_all = _sum_over_ranks(float(n_reach) * a.steps, world)
     value = tuples_all / slowest
-
-    # roofline of the dominant kernel (largest share of device time)
-    peak, peak_kind = _peaks()
-    dom = max(kstats.items(), key=lambda kv: kv[1]["ms"])
-    dname, dk = dom
-    per_launch_bytes = dk["bytes"] / max(dk["launches"], 1)
-    achieved = dk["bytes"] / (dk["ms"] / 1e3) / 1e9 if dk["ms"] > 0 else 0.0
-    traffic = _ncu_traffic(dname, a.workload)
-    kernel_ms_total = sum(v["ms"] for v in kstats.values())
-    roofline = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": traffic, "algorithmic_bytes_per_launch": per_launch_bytes,
-                "avg_launch_ms": dk["ms"] / max(dk["launches"], 1),
-                "share_of_kernel_time": round(dk["ms"] / kernel_ms_total, 4) if kernel_ms_total else None,
-                "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                                "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] else None}
-                            for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])}}
-
+    roofline = _roofline(kstats, a.workload)
     ctx.close()   # release its buffers before the end-to-end context allocates its own
     torch.cuda.empty_cache()
 
-    # end to end through the C-ABI with host buffers (pinned), copies inside the timing
     e2e = None
     if not a.no_e2e:
-        def pinned(x):
-            return torch.from_numpy(x.view(np.int32)).pin_memory().numpy().view(np.uint32)
-
-        host_edb = {k: (pinned(c0), pinned(c1)) for k, (c0, c1) in edb.items()}
-        outs = {k: (torch.empty(sizes[k], dtype=torch.int32).pin_memory().numpy().view(np.uint32),
-                    torch.empty(sizes[k], dtype=torch.int32).pin_memory().numpy().view(np.uint32))
-                for k in idb_names}
-        ectx = hisa.Context(device=local, flags=hisa.FLAG_GRAPH | extra,   # device-side loop in a CUDA graph
-                            load_factor=a.load_factor)
-        ectx.program(*prog)
-
-        def estep():
-            ectx.reset_edb()
-            for k, (c0, c1) in host_edb.items():
-                ectx.load_tuples(k, c0, c1)
-            ectx.run()
-            return sum(len(ectx.read_relation(k, out=outs[k])[0]) for k in idb_names)
-
-        estep()   # first use: buffers grow and caching-allocator blocks are created
-        estep()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e_ms = []
-        for _ in range(a.e2e_steps):
-            ts = time.perf_counter()
-            got = estep()
-            torch.cuda.synchronize()
-            e_ms.append(round((time.perf_counter() - ts) * 1e3, 2))
-        torch.cuda.synchronize()
-        et = time.perf_counter() - t0
-        assert got == n_reach
-        ev = _sum_over_ranks(float(n_reach) * a.e2e_steps, world) / _max_over_ranks(et, world)
-        e2e = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": int(edb_bytes),
-               "d2h_bytes_per_step": int(8 * n_reach), "steps": a.e2e_steps, "step_ms": e_ms,
-               "loop": "CUDA graph while node (device-side termination test)"}
-        ectx.close()
+        e2e = _e2e(prog, edb, sizes, extra, a.load_factor, a.e2e_steps, local, world)
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -432,8 +551,18 @@ def run_hisa(a):
             cpu = cpu_baseline(s, d, nodes)
         else:
             n_s, el, what = sample()
-            cpu = {"value": n_s / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            cpu = {"value": n_s / el, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_description(),
                    "sample": f"{what}: {n_s} tuples in {el:.1f} s"}
+
+    # the other workloads, compactly, on the default run at N = 1
+    subs = None
+    if world == 1 and a.workload == "rmat16" and not a.no_sub:
+        subs = {}
+        for name in ("sg20k", "cspa"):
+            subs[name] = _sub_program(name, local, flush, cpu=not a.no_cpu_baseline)
+        del flush
+        torch.cuda.empty_cache()
+        subs["batch5"] = batch5_record(a, cpu=not a.no_cpu_baseline)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -455,6 +584,8 @@ def run_hisa(a):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    if subs is not None:
+        line["workloads"] = subs
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -532,24 +663,30 @@ def run_reference_program(a):
 
 # ---- batched / served REACH (many independent instances) ------------------------------------------
 
-def run_batch5(a):
+def batch5_record(a, cpu=True):
     """Independent REACH instances (n log-uniform in [64, 8192], mean out-degree
     uniform in [1.5, 4], ER edges, seed 4) served three ways on one GPU:
     one by one (a run per instance), and through the serving loop with Poisson
     arrivals at 0.5x and 2x the one-by-one service rate (continuous batching:
     admission at iteration boundaries by free slots and memory budget,
-    retirement on convergence).  Latency = arrival -> result on the host."""
+    retirement on convergence), and all at once.  Latency = arrival -> result
+    on the host.  Every served instance is compared with its one-by-one run;
+    the CPU leg runs the oracle on instances drawn at random and compares
+    those with the one-by-one results too."""
     import numpy as np
     import torch
 
-    import oracle
-    from paper_2311_02206_gb300 import build, hisa, workloads
+    from paper_2311_02206_gb300 import build, hisa, programs, workloads
 
-    torch.cuda.set_device(0)
     build.build()
     specs = workloads.batch_instances(a.instances, 4)
     graphs = [workloads.er_graph(n, m, sd) for n, m, sd in specs]
     nmax = max(n for n, _, _ in specs)
+    rng_pick = np.random.default_rng(12)
+    order = rng_pick.permutation(len(graphs))
+    cpu_pick = [int(i) for i in order if specs[i][0] <= 2048][:24]
+    cpu_keep = set(cpu_pick)
+    kept = {}
 
     def dev_fp(c0, c1):
         """Order-independent hash of a relation held in two int32 CUDA tensors."""
@@ -561,7 +698,7 @@ def run_batch5(a):
 
     # one by one
     ctx = hisa.Context(flags=hisa.FLAG_GRAPH)
-    ctx.program(*oracle.REACH)
+    ctx.program(*programs.REACH)
     alone = {}
     lat1 = []
     for i in range(min(3, len(graphs))):   # warm-up
@@ -578,6 +715,8 @@ def run_batch5(a):
         torch.cuda.synchronize()
         lat1.append(time.perf_counter() - t0)
         alone[i] = (c0.numel(), ctx.delta_counts("Reach"), dev_fp(c0, c1))
+        if i in cpu_keep:
+            kept[i] = (c0.cpu().numpy().view(np.uint32), c1.cpu().numpy().view(np.uint32), alone[i][1])
     t1 = time.perf_counter() - t_all
     ctx.close()
     torch.cuda.empty_cache()
@@ -588,7 +727,7 @@ def run_batch5(a):
         rng = np.random.default_rng(seed)
         arrivals = np.cumsum(rng.exponential(1.0 / lam, len(graphs))) if lam else np.zeros(len(graphs))
         sctx = hisa.Context()
-        sctx.program(*oracle.REACH)
+        sctx.program(*programs.REACH)
         slots = 1
         while slots < min(len(graphs), 4096):
             slots *= 2
@@ -636,7 +775,35 @@ def run_batch5(a):
         "served_2x": served(2.0 * rate1, 3),
         "exact": "every served instance equals its one-by-one run (size, delta counts, device hash of the tuples)",
     }
-    print(json.dumps(res), flush=True)
+    res["served_2x_vs_one_by_one"] = res["served_2x"]["instances_per_s"] / rate1
+    if cpu:
+        import oracle
+        budget_s, n_done, n_tup, el, mism = 15.0, 0, 0, 0.0, 0
+        for i in cpu_pick:
+            if el > budget_s:
+                break
+            t0 = time.perf_counter()
+            r = oracle.reach(*graphs[i])
+            el += time.perf_counter() - t0
+            w0, w1 = r.relations["Reach"]
+            g0, g1, gdc = kept[i]
+            if not (np.array_equal(w0, g0) and np.array_equal(w1, g1) and gdc == r.delta_counts["Reach"]):
+                mism += 1
+            n_done += 1
+            n_tup += len(w0)
+        res["cpu_baseline"] = {"value": n_done / el, "unit": "instances/s", "tuples_per_s": n_tup / el, "cores": 1,
+                               "kind": "oracle", "sample": f"{n_done} instances of at most 2,048 nodes drawn at "
+                                                           f"random ({n_tup} tuples, {el:.1f} s)",
+                               "oracle_equal_one_by_one": f"{n_done - mism} of {n_done}"}
+        if mism:
+            raise RuntimeError(f"{mism} sampled instances differ from the oracle")
+    return res
+
+
+def run_batch5(a):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(batch5_record(a, cpu=not a.no_cpu_baseline)), flush=True)
 
 
 # ---- sort / merge microbenchmark ----------------------------------------------------------------

@@ -97,6 +97,18 @@ typedef void (*hisa_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
  * raw results and their sort (CSPA's ValueFlow and ValueAlias rules).  Same
  * results; domain of at most 2^20 values, not in batched runs. */
 #define HISA_FLAG_NO_CHAIN 32u
+/* Never work a group of the grouped bitmap join in pull mode.  By default,
+ * for an IDB relation written only by a one-step grouped bitmap join of its
+ * delta with an EDB relation (REACH's recursive rule; domains of at most 2^16
+ * values, not in batched runs), each group chooses per iteration between
+ * marking the inner runs of its delta values (Algorithm 3's range probes,
+ * "push") and "pull": every value o not yet derived for the group that has
+ * inner tuples scans them, in the inner relation sorted by its other column,
+ * until one joins a delta value -- the direction-optimizing traversal of
+ * Beamer et al. (2012) applied per group.  A group pulls when the inner runs
+ * its next delta would mark outnumber, several times over, the values it
+ * could still derive.  Same results. */
+#define HISA_FLAG_NO_PULL 64u
 
 typedef struct {
   hisa_alloc_fn alloc;      /* NULL: cudaMallocAsync from a private pool */
@@ -109,6 +121,9 @@ typedef struct {
   uint32_t max_iters;       /* iteration cap; 0 = 1,000,000 */
   uint32_t flags;           /* HISA_FLAG_*; default HISA_FLAG_LOG_FULL */
   int32_t device;           /* CUDA device ordinal; -1 = the current device */
+  float pull_ratio;         /* pull mode switch point (HISA_FLAG_NO_PULL): a group pulls when the
+                               inner runs its next delta would mark exceed pull_ratio times the
+                               values it could still derive (plus the delta's size); 0 = 4 */
 } hisa_config;
 
 typedef struct hisa_ctx hisa_ctx;
@@ -198,10 +213,12 @@ hisa_status hisa_relation_size(hisa_ctx* ctx, uint32_t rel_id, uint64_t* n);
  * copied by the copy engine; other host columns are staged and copied.  Such
  * a column-swapped relation is read through a library-owned bit matrix of
  * 2^(2b) bits (512 MB at b = 16); the matrix and the staging columns stay
- * allocated for later reads and count against hbm_budget_bytes (where the
- * matrix does not fit, the relation is sorted instead; where the staging does
- * not fit, the device writes the page-locked columns directly).  Errors: CAPACITY (cap < size; *n
- * is still set), INVALID_ARG, OOM, CUDA. */
+ * allocated for later reads and count against hbm_budget_bytes, and any later
+ * allocation that would pass the budget, or that the allocator refuses,
+ * releases them first.  Where the matrix does not fit, the relation is sorted
+ * instead; where the staging does not fit, the device writes the page-locked
+ * columns directly.  Errors: CAPACITY (cap < size; *n is still set),
+ * INVALID_ARG, OOM, CUDA. */
 hisa_status hisa_read_relation(hisa_ctx* ctx, uint32_t rel_id, uint32_t* const* cols, uint64_t cap,
                                uint64_t* n, int cols_on_device);
 

@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
 and the cpu-baseline / reference legs of ``bench.py``.  Nothing in the product
 package imports it, and it imports nothing from the product package (only the
-seeded input generators in ``paper_2311_02206_gb300.workloads``, which hold no
+seeded input generators in ``paper_2311_02206_gb300.workloads`` and the
+program texts in ``paper_2311_02206_gb300.programs``, which hold no
 evaluation arithmetic).
 
 * ``seminaive``  -- C++ std::set semi-naive evaluator (``seminaive.cpp``):
@@ -137,60 +138,11 @@ def seminaive(relations: dict, rules: list, edb: dict, max_iters: int = 1 << 20)
         lib.oracle_free(h)
 
 
-# ---- programs used throughout (rules as printed in the paper) -------------------------
-
-# REACH, Section 1: Reach(from,to) <- Edge(from,to); Reach(from,to) <- Edge(from,mid), Reach(mid,to).
-REACH = (
-    {"Edge": "edb", "Reach": "idb"},
-    [
-        (("Reach", ("f", "t")), [("Edge", ("f", "t"))], []),
-        (("Reach", ("f", "t")), [("Edge", ("f", "m")), ("Reach", ("m", "t"))], []),
-    ],
-)
-
-# SG, Section 2: both rules carry x != y.
-SG = (
-    {"Edge": "edb", "SG": "idb"},
-    [
-        (("SG", ("x", "y")), [("Edge", ("p", "x")), ("Edge", ("p", "y"))], [("x", "y")]),
-        (("SG", ("x", "y")), [("Edge", ("a", "x")), ("SG", ("a", "b")), ("Edge", ("b", "y"))], [("x", "y")]),
-    ],
-)
-
-# SG as the workload description prints it: the filter on the first rule only
-# (on a DAG whose nodes have several parents, rule 2 then also derives SG(x,x)).
-SG_LITERAL = (
-    {"Edge": "edb", "SG": "idb"},
-    [
-        (("SG", ("x", "y")), [("Edge", ("p", "x")), ("Edge", ("p", "y"))], [("x", "y")]),
-        (("SG", ("x", "y")), [("Edge", ("a", "x")), ("SG", ("a", "b")), ("Edge", ("b", "y"))], []),
-    ],
-)
-
-
-# A context-sensitive points-to style program over Assign / Dereference (written
-# for this project; the paper elides its CSPA query, stating only that five rules
-# initialise and five mutually recursive rules propagate, that the first
-# recursive rule makes ValueFlow transitive and that the second makes two values
-# flowing into the same variable aliases).  ValueFlow(a, b): the value of b flows
-# into a; Assign(a, b): a = b; Dereference(a, b): a is the dereference of b.
-CSPA = (
-    {"Assign": "edb", "Dereference": "edb", "ValueFlow": "idb", "MemoryAlias": "idb", "ValueAlias": "idb"},
-    [
-        (("ValueFlow", ("y", "x")), [("Assign", ("y", "x"))], []),
-        (("ValueFlow", ("x", "x")), [("Assign", ("x", "y"))], []),
-        (("ValueFlow", ("x", "x")), [("Assign", ("y", "x"))], []),
-        (("MemoryAlias", ("x", "x")), [("Assign", ("y", "x"))], []),
-        (("MemoryAlias", ("x", "x")), [("Assign", ("x", "y"))], []),
-        (("ValueFlow", ("x", "y")), [("ValueFlow", ("x", "z")), ("ValueFlow", ("z", "y"))], []),
-        (("ValueAlias", ("x", "y")), [("ValueFlow", ("z", "x")), ("ValueFlow", ("z", "y"))], []),
-        (("ValueFlow", ("x", "y")), [("Assign", ("x", "z")), ("MemoryAlias", ("z", "y"))], []),
-        (("MemoryAlias", ("x", "w")), [("Dereference", ("y", "x")), ("ValueAlias", ("y", "z")),
-                                       ("Dereference", ("z", "w"))], []),
-        (("ValueAlias", ("x", "y")), [("ValueFlow", ("z", "x")), ("MemoryAlias", ("z", "w")),
-                                      ("ValueFlow", ("w", "y"))], []),
-    ],
-)
+# ---- programs used throughout ---------------------------------------------------------
+# The Datalog programs are inputs, like the seeded EDB generators: plain data
+# (relation kinds and rules) kept in a module of their own that both the
+# oracle and the engine's callers read; it holds no evaluation arithmetic.
+from paper_2311_02206_gb300.programs import CSPA, REACH, SG, SG_LITERAL  # noqa: E402,F401
 
 
 def fingerprint(c0, c1) -> int:

@@ -71,14 +71,16 @@ __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
 
 // Polls allowed while waiting on a predecessor tile before the kernel gives up,
 // records kDevTimeout and continues with a zero contribution (results are then
-// invalid and the host reports HISA_ERR_DEVICE_TIMEOUT).
+// invalid and the host reports HISA_ERR_DEVICE_TIMEOUT).  The look-back
+// routines take the limit as an argument (this value by default), so that a
+// check can make a wait run out after a few polls.
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Warp-cooperative decoupled look-back (Merrill & Garland, "Single-pass
 // parallel prefix scan with decoupled look-back", 2016).  Called by one full
 // warp; returns the exclusive prefix of `tile` and publishes its inclusive one.
 __device__ __forceinline__ uint64_t lookback_warp(uint64_t* status, uint64_t tile, uint64_t local,
-                                                  uint32_t epoch, uint32_t* err) {
+                                                  uint32_t epoch, uint32_t* err, uint32_t spin_limit = kSpinLimit) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) {
     if (lane == 0) st_release(&status[0], lb_pack(epoch, kFlagIncl, local));
@@ -97,7 +99,7 @@ __device__ __forceinline__ uint64_t lookback_warp(uint64_t* status, uint64_t til
       v = lb_value(w);
     }
     if (__any_sync(0xffffffffu, f == 0)) {
-      if (++spins > kSpinLimit) {
+      if (++spins > spin_limit) {
         if (lane == 0) atomicExch(err, kDevTimeout);
         break;
       }
@@ -123,14 +125,15 @@ __device__ __forceinline__ void lookback_publish(uint64_t* status, uint64_t tile
   st_release(&status[tile * stride], lb_pack(epoch, tile == 0 ? kFlagIncl : kFlagAgg, local));
 }
 __device__ __forceinline__ uint64_t lookback_resolve(uint64_t* status, uint64_t tile, uint64_t stride, uint64_t local,
-                                                     uint32_t epoch, uint32_t* err);
+                                                     uint32_t epoch, uint32_t* err, uint32_t spin_limit = kSpinLimit);
 
 // Single-thread look-back for per-digit chains (radix sort: one thread per
 // digit).  Eight predecessor words are read per round trip, so a walk over
 // tiles that only published their aggregate costs 1/8 of the latency.
 constexpr int kLookbackBatch = 8;
 __device__ __forceinline__ uint64_t lookback_thread(uint64_t* status, uint64_t tile, uint64_t stride,
-                                                    uint64_t local, uint32_t epoch, uint32_t* err) {
+                                                    uint64_t local, uint32_t epoch, uint32_t* err,
+                                                    uint32_t spin_limit = kSpinLimit) {
   if (tile == 0) {
     st_release(&status[0], lb_pack(epoch, kFlagIncl, local));
     return 0;
@@ -158,7 +161,7 @@ __device__ __forceinline__ uint64_t lookback_thread(uint64_t* status, uint64_t t
     if (done) break;
     j -= used;
     if (used == 0) {
-      if (++spins > kSpinLimit) {
+      if (++spins > spin_limit) {
         atomicExch(err, kDevTimeout);
         break;
       }
@@ -170,7 +173,7 @@ __device__ __forceinline__ uint64_t lookback_thread(uint64_t* status, uint64_t t
 }
 
 __device__ __forceinline__ uint64_t lookback_resolve(uint64_t* status, uint64_t tile, uint64_t stride, uint64_t local,
-                                                     uint32_t epoch, uint32_t* err) {
+                                                     uint32_t epoch, uint32_t* err, uint32_t spin_limit) {
   if (tile == 0) return 0;
   uint64_t excl = 0;
   int64_t j = int64_t(tile) - 1;
@@ -194,7 +197,7 @@ __device__ __forceinline__ uint64_t lookback_resolve(uint64_t* status, uint64_t 
     if (done) break;
     j -= used;
     if (used == 0) {
-      if (++spins > kSpinLimit) {
+      if (++spins > spin_limit) {
         atomicExch(err, kDevTimeout);
         break;
       }

@@ -153,6 +153,10 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
   uint32_t* mslot = units_on ? static_cast<uint32_t*>(st->buf[a.mslot_buf].ptr) : nullptr;
   const uint64_t ucap = units_on ? min(st->buf[a.units_buf].cap, min(st->buf[a.done_buf].cap, st->buf[a.mslot_buf].cap))
                                  : 0;
+  // pulled groups (dense.cuh, pull mode) are one unit each
+  const uint32_t* pbm = units_on && a.pull_bm_buf >= 0 ? static_cast<const uint32_t*>(st->buf[a.pull_bm_buf].ptr)
+                                                       : nullptr;
+  auto pulled = [&](uint64_t g) { return pbm && ((pbm[g >> 5] >> (g & 31)) & 1u); };
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint64_t wper = (((nk + nw - 1) / nw) + 31) & ~31ull;
   const uint64_t w0 = min(nk, uint64_t(warp) * wper), w1 = min(nk, w0 + wper);
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
 #pragma unroll
     for (int i = 0; i < kB; ++i)
       if (f1[i] > f0[i]) {
-        const uint64_t nu = (f1[i] - f0[i] + usz - 1) / usz;
+        const uint64_t nu = pulled(base + uint64_t(i) * 32 + lane) ? 1 : (f1[i] - f0[i] + usz - 1) / usz;
         gm += 1 + (uint64_t(nu > 1) << 32);
         nus += nu;
       }
@@ -221,7 +225,8 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
       const uint64_t pos = c + __popc(hb & lt);
       if (head && pos < ocap) out[pos] = f0[i];
       if (units_on) {
-        const uint64_t nu = head ? (f1[i] - f0[i] + usz - 1) / usz : 0;
+        const bool pg = head && pulled(base + uint64_t(i) * 32 + lane);
+        const uint64_t nu = !head ? 0 : pg ? 1 : (f1[i] - f0[i] + usz - 1) / usz;
         const uint32_t mb = __ballot_sync(0xffffffffu, nu > 1);
         uint64_t incl = nu;
 #pragma unroll
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
         if (head && pos + 1 < ucap) {
           units[pos] = u + incl - nu;
           done[pos] = 0;
-          mslot[pos] = uint32_t(m + __popc(mb & lt));
+          mslot[pos] = pg ? kPullMark : uint32_t(m + __popc(mb & lt));
         }
         u += __shfl_sync(0xffffffffu, incl, 31);
         m += __popc(mb);
@@ -268,6 +273,31 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
   }
 }
 
+// dense.cuh, pull mode: the bitmap of values with inner tuples and their count
+__global__ void k_pull_out(PullOutArgs a) {
+  DevState* st = a.st;
+  const uint64_t* first = static_cast<const uint64_t*>(st->buf[a.index_buf].ptr);
+  uint32_t* out = static_cast<uint32_t*>(st->buf[a.out_buf].ptr);
+  const uint64_t nwords = a.b >= 5 ? (1ull << (a.b - 5)) : 1;
+  const uint64_t nk = 1ull << a.b;
+  unsigned long long cnt = 0;
+  for (uint64_t w = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; w < nwords;
+       w += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t bits = 0;
+    for (uint32_t i = 0; i < 32; ++i) {
+      const uint64_t o = w * 32 + i;
+      if (o < nk && first[o + 1] > first[o]) bits |= 1u << i;
+    }
+    out[w] = bits;
+    cnt += __popc(bits);
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd((unsigned long long*)&st->cnt[a.nout_cnt], cnt);
+}
+
+void launch_pull_out(const PullOutArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKIndex, s, (k_pull_out<<<g.small, 256, 0, s>>>(a)));
+}
 void launch_ctl(const CtlArgs& a, cudaStream_t s) { HISA_LAUNCH(kKCtl, s, (k_ctl<<<1, 256, 0, s>>>(a))); }
 void launch_group_compact(const GroupArgs& a, int bits, cudaStream_t s) {
   HISA_LAUNCH(kKGroups, s, (k_group_compact<<<1, 1024, 0, s>>>(a, bits)));

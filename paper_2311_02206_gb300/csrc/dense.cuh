@@ -20,6 +20,9 @@
 
 namespace hisa {
 
+// a group marked in the units' multi-unit slot array as pulled (one unit)
+constexpr uint32_t kPullMark = 0xFFFFFFFFu;
+
 // Start position of every run of equal g = code >> b in a sorted code array,
 // compacted in order; cnt[out_cnt] = number of groups and out[groups] = n
 // (k_group_compact, from a direct index of the array by g).
@@ -39,6 +42,9 @@ struct GroupArgs {
   // gathered Tmp's starts: vals = offsets per inner tuple, in = the inner's
   // direct index by the kept value)
   int indirect, vals_buf;
+  // k_group_compact with units: bit g of this u32 bitmap set = group g is
+  // pulled (one unit, marked kPullMark in its multi-unit slot); -1: none
+  int pull_bm_buf = -1;
 };
 
 // A two-step rule variant H(x, y) <- A(x, a), delta(a, c), B(c, y) -- delta
@@ -168,6 +174,40 @@ struct DenseArgs {
   int unit_size;
   int mslot_buf, bmm_buf;
   int units_ready;              // computed by the group compaction (else k_dense_units runs)
+  // pull mode (pull_inner_buf >= 0; a direct inner index, b <= kPullMaxBits):
+  // a group whose units entry is marked kPullMark is one unit worked the
+  // other way round.  Its delta values k go into a frontier bitmap F, full's
+  // tuples of the group into a bitmap V, and every candidate o (a value with
+  // inner tuples, not in V) walks its inner tuples (o, k') -- the inner
+  // relation sorted by its other column, with a direct index by it -- until
+  // one k' is in F: o is then new.  Same results as marking the inner runs of
+  // the delta values (the direction-optimizing traversal of Beamer et al.,
+  // 2012, applied per group).  Each group's finish chooses the next
+  // iteration's mode: pull when the inner runs the next delta would mark
+  // (sum of their lengths) exceed pull_k16 / 16 times the candidates left
+  // (|other values| - |full_g| - |next delta|) plus the next delta's size.
+  int pull_inner_buf = -1, pull_index_buf = -1;   // inner codes (o, k) sorted; direct index by o
+  int pull_out_buf = -1;                // u32 [2^b / 32]: values o with inner tuples
+  int pull_bm_buf = -1;                 // u32 [2^b / 32]: bit g = group g pulls next iteration
+  int fcnt_buf = -1;                    // u32 [2^b]: |full_g| (kept by the append of each level)
+  int nout_cnt = -1;                    // cnt slot: number of values o with inner tuples
+  uint32_t pull_k16 = 64;
+};
+
+// two bitmaps (frontier and full) of 2^b bits in shared memory
+constexpr int kPullMaxBits = 16;
+// default switch point, x16: a group pulls when the inner runs its next delta
+// would mark exceed 4x its candidates plus the delta's size
+constexpr uint32_t kPullK16 = 64;
+
+// Values o with inner tuples (a non-empty run in the direct index by o), as a
+// bitmap, and their number (added to cnt[nout_cnt]).
+struct PullOutArgs {
+  DevState* st;
+  int index_buf;   // u64 [2^b + 1] direct index by o
+  int b;
+  int out_buf;     // u32 [2^b / 32]
+  int nout_cnt;
 };
 
 constexpr int kDenseThreads = 128;
@@ -322,11 +362,14 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
   __shared__ uint64_t s_unit[3];   // the unit's outer range [start, end) and its group
   __shared__ uint32_t s_nu;        // units in that group
   __shared__ int s_last;
+  __shared__ int s_pull;           // the unit is a whole group worked in pull mode
+  __shared__ unsigned long long s_td;
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
   const uint64_t ngroups = st->cnt[a.groups_cnt];
   if (ngroups == 0) return;
   const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
+  const bool pull_on = a.pull_inner_buf >= 0;
   // (the multi-unit bitmaps' capacity is checked where the units are made)
   if (st->buf[a.bm_buf].cap < ngroups * uint64_t(nwords) || st->buf[a.offs_buf].cap < ngroups + 1) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -346,8 +389,11 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nwarps = kDenseThreads / 32;
   const uint32_t vmask = a.b >= 32 ? 0xFFFFFFFFu : ((1u << a.b) - 1);
-  for (int j = tid; j < nwords; j += kDenseThreads) s_bm[j] = 0;
-  if (tid == 0) s_cnt = 0;
+  for (int j = tid; j < (pull_on ? 2 : 1) * nwords; j += kDenseThreads) s_bm[j] = 0;
+  if (tid == 0) {
+    s_cnt = 0;
+    s_td = 0;
+  }
   unsigned long long raw = 0;
   while (true) {
     // one thread finds the unit (its group: the last g with units[g] <= ui)
@@ -369,11 +415,90 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
         s_unit[0] = s;
         s_unit[1] = min(gs[gi + 1], s + uint64_t(a.unit_size));
         s_nu = uint32_t(units[gi + 1] - units[gi]);
+        s_pull = pull_on && static_cast<const uint32_t*>(st->buf[a.mslot_buf].ptr)[gi] == kPullMark;
+        if (s_pull) s_unit[1] = gs[gi + 1];   // a pulled group is one unit
       }
       s_unit[2] = gi;
     }
     __syncthreads();
     if (s_unit[2] == ~0ull) break;
+    const bool pull = s_pull;
+    uint32_t* res = pull ? s_bm + nwords : s_bm;   // the group's result bitmap at the finish
+    const uint64_t gi = s_unit[2];
+    uint32_t* gbm = bm + gi * uint64_t(nwords);
+    if (pull) {
+      // pull: frontier F (the group's delta values) and full's tuples V
+      uint32_t* F = s_bm;
+      uint32_t* V = s_bm + nwords;
+      const K* pin = static_cast<const K*>(st->buf[a.pull_inner_buf].ptr);
+      const uint64_t* pidx = static_cast<const uint64_t*>(st->buf[a.pull_index_buf].ptr);
+      const uint32_t* outbm = static_cast<const uint32_t*>(st->buf[a.pull_out_buf].ptr);
+      for (uint64_t i = s_unit[0] + tid; i < s_unit[1]; i += kDenseThreads) {
+        const uint32_t v = uint32_t(outer[i]) & vmask;
+        const uint32_t bit = 1u << (v & 31);
+        if (!(F[v >> 5] & bit)) atomicOr(&F[v >> 5], bit);
+      }
+      if (a.full_buf >= 0) {
+        const uint64_t nlv = st->cnt[a.nlv_cnt], nk = (1ull << a.b) + 1;
+        const uint64_t* lvidx = static_cast<const uint64_t*>(st->buf[a.lvidx_buf].ptr);
+        const K* fl = static_cast<const K*>(st->buf[a.full_buf].ptr);
+        const uint64_t g = uint64_t(outer[s_unit[0]]) >> a.b;
+        for (uint64_t lv = 0; lv < nlv; ++lv) {
+          const uint64_t r0 = lvidx[lv * nk + g], r1 = lvidx[lv * nk + g + 1];
+          for (uint64_t i0 = r0 + tid; i0 < r1; i0 += 8 * kDenseThreads) {
+            uint32_t v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const uint64_t i = i0 + uint64_t(u) * kDenseThreads;
+              v[u] = i < r1 ? uint32_t(fl[i]) & vmask : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (v[u] != 0xFFFFFFFFu) atomicOr(&V[v[u] >> 5], 1u << (v[u] & 31));
+          }
+        }
+      }
+      __syncthreads();
+      // each lane owns one word of candidates (values with inner tuples, not
+      // in full) and walks their inner runs four tuples at a time until one
+      // reaches the frontier; a lane that finishes a candidate takes its
+      // word's next one at once
+      for (int base = warp * 32; base < nwords; base += nwarps * 32) {
+        const int w = base + lane;
+        uint32_t cm = w < nwords ? (outbm[w] & ~V[w]) : 0u;
+        uint32_t r = 0, o = 0;
+        uint64_t p = 0, pe = 0;
+        bool act = false;
+        while (__any_sync(0xffffffffu, act || cm != 0)) {
+          if (!act && cm) {
+            const int bit = __ffs(cm) - 1;
+            cm &= cm - 1;
+            o = uint32_t(w) * 32 + uint32_t(bit);
+            p = pidx[o];
+            pe = pidx[o + 1];
+            act = p < pe;
+          }
+          if (act) {
+            uint32_t k[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k[u] = p + u < pe ? uint32_t(pin[p + u]) & vmask : 0xFFFFFFFFu;
+            bool hit = false;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) hit = hit || (k[u] != 0xFFFFFFFFu && ((F[k[u] >> 5] >> (k[u] & 31)) & 1u));
+            raw += 4;
+            if (hit) {
+              r |= 1u << (o & 31);
+              act = false;
+            } else {
+              p += 4;
+              act = p < pe;
+            }
+          }
+        }
+        if (w < nwords) V[w] = r;
+      }
+      __syncthreads();
+    } else {
     // a unit spans at most unit_size (< 2^31) outer tuples: 32-bit offsets
     const K* uo = outer + s_unit[0];
     const uint32_t un = uint32_t(s_unit[1] - s_unit[0]);
@@ -451,8 +576,6 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
       }
     }
     __syncthreads();
-    const uint64_t gi = s_unit[2];
-    uint32_t* gbm = bm + gi * uint64_t(nwords);
     if (s_nu > 1) {
       // this unit's marks into the group's multi-unit bitmap; the last unit
       // takes it back (leaving it zeroed) and finishes the group
@@ -516,24 +639,57 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
         }
       }
     }
+    }   // top-down
+    if (pull && a.drop_self && tid == 0) {
+      const uint32_t g = uint32_t(uint64_t(outer[gs[gi]]) >> a.b) & vmask;
+      res[g >> 5] &= ~(1u << (g & 31));
+    }
     __syncthreads();
-    // store the bitmap (coalesced) and clear it; count its bits
+    // store the bitmap (coalesced) and clear it; count its bits.  With pull
+    // mode on, also sum the inner run lengths of the group's next delta (the
+    // raw results a top-down pass would mark next iteration) and choose the
+    // group's next mode.
+    const uint64_t* tfirst = static_cast<const uint64_t*>(static_cast<const void*>(table));
     uint32_t mine = 0;
+    unsigned long long td = 0;
     for (int j = tid; j < nwords; j += kDenseThreads) {
-      const uint32_t w = s_bm[j];
+      const uint32_t w = res[j];
       gbm[j] = w;
       mine += __popc(w);
-      s_bm[j] = 0;
+      res[j] = 0;
+      if (pull) s_bm[j] = 0;
+      if (pull_on)
+        for (uint32_t x = w; x; x &= x - 1) {
+          const uint32_t o = uint32_t(j) * 32 + uint32_t(__ffs(x) - 1);
+          td += tfirst[o + 1] - tfirst[o];
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      mine += __shfl_xor_sync(0xffffffffu, mine, o);
+      td += __shfl_xor_sync(0xffffffffu, td, o);
+    }
     if (lane == 0 && mine) atomicAdd(&s_cnt, (unsigned long long)mine);
+    if (lane == 0 && td) atomicAdd(&s_td, td);
     __syncthreads();
     if (tid == 0) {
       counts[gi] = s_cnt;
+      if (pull_on) {
+        const uint32_t g = uint32_t(uint64_t(outer[gs[gi]]) >> a.b) & vmask;
+        const uint64_t nout = st->cnt[a.nout_cnt];
+        const uint64_t full_after = uint64_t(static_cast<const uint32_t*>(st->buf[a.fcnt_buf].ptr)[g]) + s_cnt;
+        const uint64_t cand = nout > full_after ? nout - full_after : 0;
+        const bool pull_next = 16ull * s_td > uint64_t(a.pull_k16) * cand + 16ull * s_cnt;
+        uint32_t* pbm = static_cast<uint32_t*>(st->buf[a.pull_bm_buf].ptr);
+        if (pull_next) atomicOr(&pbm[g >> 5], 1u << (g & 31));
+        else atomicAnd(&pbm[g >> 5], ~(1u << (g & 31)));
+      }
       s_cnt = 0;   // read again only after the next group's first barrier
+      s_td = 0;
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) raw += __shfl_xor_sync(0xffffffffu, raw, o);
   if (lane == 0 && raw) atomicAdd((unsigned long long*)&st->cnt[a.raw_cnt], raw);
 }
 

@@ -34,17 +34,23 @@ hisa_status Engine::dev_alloc(size_t bytes, void** out) {
   *out = nullptr;
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
-  if (cfg.hbm_budget_bytes && bytes_in_use + bytes > cfg.hbm_budget_bytes)
+  if (cfg.hbm_budget_bytes && bytes_in_use + bytes > cfg.hbm_budget_bytes &&
+      (!release_read_scratch() || bytes_in_use + bytes > cfg.hbm_budget_bytes))
     return ctx_fail(HISA_ERR_OOM, "HBM budget exceeded", nullptr);
   void* p = nullptr;
-  if (cfg.alloc) {
-    p = cfg.alloc(bytes, stream, cfg.user);
-    if (!p) return ctx_fail(HISA_ERR_OOM, "allocator hook returned NULL", nullptr);
-  } else {
-    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return ctx_fail(HISA_ERR_OOM, "cudaMallocFromPoolAsync", cudaGetErrorString(e));
+  for (int attempt = 0; !p; ++attempt) {
+    if (cfg.alloc) {
+      p = cfg.alloc(bytes, stream, cfg.user);
+      if (!p && (attempt || !release_read_scratch()))
+        return ctx_fail(HISA_ERR_OOM, "allocator hook returned NULL", nullptr);
+    } else {
+      cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        if (attempt || !release_read_scratch())
+          return ctx_fail(HISA_ERR_OOM, "cudaMallocFromPoolAsync", cudaGetErrorString(e));
+      }
     }
   }
   allocs[p] = bytes;
@@ -62,6 +68,18 @@ void Engine::dev_free(void* p) {
   else cudaFreeAsync(p, stream);
   bytes_in_use -= it->second;
   allocs.erase(it);
+}
+
+bool Engine::release_read_scratch() {
+  if (reading) return false;
+  bool freed = false;
+  for (int id : {sc.read_m, sc.read_rows, sc.read_s0, sc.read_s1}) {
+    if (id < 0 || !hs.buf[id].ptr) continue;
+    dev_free(hs.buf[id].ptr);
+    hs.buf[id] = {nullptr, 0};
+    freed = true;
+  }
+  return freed;
 }
 
 int Engine::new_slot(int elem_bytes) {
@@ -117,6 +135,7 @@ hisa_status Engine::init(const hisa_config& c) {
   if (cfg.load_factor <= 0.f || cfg.load_factor > 0.95f) cfg.load_factor = 0.8f;
   if (cfg.ebm_k <= 0.f) cfg.ebm_k = 2.f;
   if (cfg.max_iters == 0) cfg.max_iters = 1000000;
+  if (!(cfg.pull_ratio > 0.f) || cfg.pull_ratio > 4096.f) cfg.pull_ratio = float(kPullK16) / 16.f;
   if (cfg.device >= 0) CU(cudaSetDevice(cfg.device));
   CU(cudaGetDevice(&device));
   stream = static_cast<cudaStream_t>(cfg.cuda_stream);
@@ -659,6 +678,33 @@ hisa_status Engine::compile() {
       Relation& A = rels[sp.inner_rel];
       if (!A.idb && sp.inner_col == 0) A.need_idx[1] = true;   // an EDB relation builds its (c1, c0) copy
     }
+  // pull mode (dense.cuh) for a relation written only by a one-step grouped
+  // bitmap join of its delta with an EDB relation (REACH's recursive rule):
+  // the inner relation is also sorted and directly indexed by its other column
+  const bool pull_on = dense_on && !(cfg.flags & HISA_FLAG_NO_PULL) && !batched && inst_bits == 0 &&
+                       direct_bits > 0 && b <= kPullMaxBits;
+  for (int r : idb) {
+    Relation& R = rels[r];
+    R.pull = false;
+    if (!pull_on || !R.append) continue;
+    auto w = writers(r);
+    if (w.size() != 1 || w[0]->size() != 1) continue;
+    const StepPlan& sp = (*w[0])[0];
+    if (!sp.dense || sp.invert || sp.chain || sp.outer_slot != R.delta || !sp.has_inner || rels[sp.inner_rel].idb)
+      continue;
+    Relation& I = rels[sp.inner_rel];
+    const int ocol = 1 - sp.inner_col;
+    I.need_idx[ocol] = true;
+    R.pull = true;
+    R.pull_inner = ocol == 0 ? I.base : I.rev;
+    R.pull_index = I.table[ocol];
+    if (R.pull_out < 0) {
+      R.pull_out = new_slot(4);
+      R.pull_bm = new_slot(4);
+      R.fcnt = new_slot(4);
+      R.nout = nslots++;
+    }
+  }
   // log-structured full where nothing probes full (it is only differenced
   // and merged): REACH and SG, not CSPA's inner IDB atoms nor batched runs
   for (int r : idb) {
@@ -904,6 +950,7 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
   // a unit holds enough outer tuples to outweigh its bitmap
   const int unit_size = int(std::max<uint64_t>(256, std::min<uint64_t>(32768, 16ull << (b >= 5 ? b - 5 : 0))));
   const bool units_ready = b + inst_bits <= kDirectMaxBits;
+  const bool pull = hr.pull && !chain_groups && inner_buf < 0 && units_ready;
   if (units_ready) {
     GroupArgs& ga = ops.back().groups;
     ga.units_buf = sc.dense_units;
@@ -912,6 +959,7 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
     ga.unit_size = unit_size;
     ga.bmm_buf = sc.dense_bmm;
     ga.bm_words = b >= 5 ? 1 << (b - 5) : 1;
+    if (pull) ga.pull_bm_buf = hr.pull_bm;
   }
   Op d{};
   d.kind = Op::DENSE;
@@ -921,6 +969,16 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
                       out, out, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0,
                       inner_buf >= 0 || direct_bits > 0, hr.append ? hr.full : -1, hr.lvidx, hr.nlv, sp.nfilt > 0,
                       sc.dense_units, sc.dense_done, unit_size, sc.dense_mslot, sc.dense_bmm, units_ready};
+  if (pull) {
+    DenseArgs& da = d.dense;
+    da.pull_inner_buf = hr.pull_inner;
+    da.pull_index_buf = hr.pull_index;
+    da.pull_out_buf = hr.pull_out;
+    da.pull_bm_buf = hr.pull_bm;
+    da.fcnt_buf = hr.fcnt;
+    da.nout_cnt = hr.nout;
+    da.pull_k16 = uint32_t(cfg.pull_ratio * 16.f + 0.5f);
+  }
   ops.push_back(d);
   if (hr.append) {   // no unique pass in the tail; |new| (statistics) = |delta|
     Op f{};
@@ -1154,6 +1212,7 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
       Op p{};
       p.kind = Op::APPEND;
       p.append = AppendArgs{dst, R.delta_next, R.delta_next, R.full, R.full, R.lvidx, R.nlv, b, b, 3, 1};
+      if (R.pull) p.append.fcnt_buf = R.fcnt;
       ops.push_back(p);
       continue;
     }
@@ -1354,6 +1413,12 @@ hisa_status Engine::prepare_rel_t(Relation& r, int order, int slot) {
 
 hisa_status Engine::prepare_edb() {
   hisa_status s;
+  // a run that failed (an allocation refused during a regrow, say) leaves its
+  // overflow bits, needs and error code in the host mirror of the device
+  // state; uploaded again, they would make every kernel here skip its work
+  hs.overflow = 0;
+  hs.error = 0;
+  std::memset(hs.need, 0, sizeof hs.need);
   for (auto& r : rels) {
     if (r.idb) continue;
     for (int order = 0; order < 2; ++order) {
@@ -1595,7 +1660,24 @@ hisa_status Engine::init_run_state() {
   hs.aux[1] = 0;
   std::memset(hs.need, 0, sizeof hs.need);
   inst_hist.assign(idb.size(), {});
-  return upload();
+  for (int r : idb) {
+    Relation& R = rels[r];
+    if (!R.pull) continue;
+    const uint64_t nw = b >= 5 ? (1ull << (b - 5)) : 1;
+    if ((s = ensure(R.fcnt, 1ull << b)) || (s = ensure(R.pull_bm, nw)) || (s = ensure(R.pull_out, nw))) return s;
+    CU(cudaMemsetAsync(hs.buf[R.fcnt].ptr, 0, (1ull << b) * 4, stream));
+    CU(cudaMemsetAsync(hs.buf[R.pull_bm].ptr, 0, nw * 4, stream));   // iteration 2 marks (push)
+    hs.cnt[R.nout] = 0;
+  }
+  if ((s = upload())) return s;
+  for (int r : idb) {
+    const Relation& R = rels[r];
+    if (!R.pull) continue;
+    PullOutArgs pa{dst, R.pull_index, b, R.pull_out, R.nout};
+    launch_pull_out(pa, grid, stream);
+    if ((s = check_launch("pull out"))) return s;
+  }
+  return HISA_OK;
 }
 
 hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::time_point t0) {
@@ -2018,6 +2100,11 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
   *n = size;
   if (cap < size) return ctx_fail(HISA_ERR_CAPACITY, "read_relation: buffer too small", nullptr);
   if (size == 0) return HISA_OK;
+  struct ReadGuard {   // the read scratch is in use until this call returns
+    bool& f;
+    explicit ReadGuard(bool& x) : f(x) { f = true; }
+    ~ReadGuard() { f = false; }
+  } guard(reading);
   uint32_t* d0 = cols[0];
   uint32_t* d1 = cols[1];
   void *t0 = nullptr, *t1 = nullptr;

@@ -50,6 +50,13 @@ struct Relation {
   int bigf = -1, smallf = -1;   // this iteration merges new straight into full / probes it
   int history = -1;                 // |delta_k| per iteration
   std::vector<uint64_t> delta_counts;
+  // pull mode of its grouped bitmap join (dense.cuh): the inner relation
+  // sorted by its other column and that order's direct index; the values with
+  // inner tuples (bitmap, and their number in cnt[nout]); the groups that pull
+  // next iteration (bitmap); |full_g| per kept value g
+  bool pull = false;
+  int pull_inner = -1, pull_index = -1;
+  int pull_out = -1, nout = -1, pull_bm = -1, fcnt = -1;
 };
 
 // One binary join (or a one-atom projection) of a compiled rule variant.
@@ -99,8 +106,8 @@ struct Scratch {
   int dense_mslot, dense_bmm;   // multi-unit groups' bitmap slot and those bitmaps (kept zeroed)
   int chain_dfirst, chain_pre;  // a gathered Tmp: delta's direct index, offsets per inner tuple
   int chain_tfirst;             // a gathered Tmp's direct index by its kept column
-  int read_m, read_rows;        // reading a column-swapped append-only full: its bit matrix, row offsets
-  int read_s0, read_s1;         // and its device staging columns (kept across reads)
+  int read_m = -1, read_rows = -1;  // reading a column-swapped append-only full: its bit matrix, row offsets
+  int read_s0 = -1, read_s1 = -1;   // and its device staging columns (kept across reads)
 
   int group_cnt, raw_cnt;     // count-only slots
 };
@@ -152,6 +159,11 @@ class Engine {
  private:
   hisa_status dev_alloc(size_t bytes, void** out);
   void dev_free(void* p);
+  // The read scratch (bit matrix, row offsets, staging columns) stays
+  // allocated between reads; an allocation that would exceed the budget, or
+  // that the allocator refuses, first releases it (never during a read).
+  bool release_read_scratch();
+  bool reading = false;
   int new_slot(int elem_bytes);
   hisa_status ensure(int id, uint64_t cap);
   hisa_status upload();

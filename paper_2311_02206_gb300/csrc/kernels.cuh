@@ -71,6 +71,7 @@ struct AppendArgs {
   int lvidx_buf, nlv_cnt;   // u64 [levels][2^bits + 1]
   int b, bits;
   int skip_mask, stage_bit;
+  int fcnt_buf = -1;        // u32 [2^bits]: tuples of full per kept value, grown by the new level's runs
 };
 
 struct EncodeArgs {
@@ -182,6 +183,7 @@ template <typename K> void launch_count_runs(const RunsArgs& a, const Grid& g, c
 template <typename K> void launch_swap(const SwapArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_diff(const DiffArgs& a, const Grid& g, cudaStream_t s);
 void launch_group_compact(const GroupArgs& a, int bits, cudaStream_t s);
+void launch_pull_out(const PullOutArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_group_starts(const GroupArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_append(const AppendArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s);

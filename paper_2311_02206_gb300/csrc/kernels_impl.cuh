@@ -139,14 +139,20 @@ __global__ void k_append(AppendArgs a) {
   uint64_t* idx = static_cast<uint64_t*>(st->buf[a.lvidx_buf].ptr) + lv * nk;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += stride) full[i] = src[i];
-  for (uint64_t k = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; k < nk; k += stride) {
+  uint32_t* fcnt = a.fcnt_buf >= 0 ? static_cast<uint32_t*>(st->buf[a.fcnt_buf].ptr) : nullptr;
+  auto lower = [&](uint64_t k) {
     uint64_t lo = 0, hi = n;
     while (lo < hi) {
       const uint64_t m = (lo + hi) >> 1;
       if ((uint64_t(src[m]) >> a.b) < k) lo = m + 1;
       else hi = m;
     }
+    return lo;
+  };
+  for (uint64_t k = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; k < nk; k += stride) {
+    const uint64_t lo = lower(k);
     idx[k] = base + lo;
+    if (fcnt && k + 1 < nk) fcnt[k] += uint32_t(lower(k + 1) - lo);
   }
 }
 
@@ -258,7 +264,8 @@ void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s) {
   c.cmd[0] = {kCtlEpoch, 0, 0};
   c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
   launch_ctl(c, s);
-  const size_t smem = size_t(a.b >= 5 ? (1u << (a.b - 5)) : 1u) * 4;
+  // one bitmap of 2^b bits; two (frontier and full) when groups may pull
+  const size_t smem = size_t(a.b >= 5 ? (1u << (a.b - 5)) : 1u) * 4 * (a.pull_inner_buf >= 0 ? 2 : 1);
   if (!a.units_ready) HISA_LAUNCH(kKDenseScan, s, (k_dense_units<K><<<1, 1024, 0, s>>>(a)));
   HISA_LAUNCH(kKJoinDense, s, (k_dense_mark<K><<<g.sms * kDenseCtasPerSm, kDenseThreads, smem, s>>>(a)));
   HISA_LAUNCH(kKDenseScan, s, (k_dense_scan<K><<<1, 1024, 0, s>>>(a)));

@@ -2,14 +2,16 @@
 // that must not allocate device memory.
 //
 // Who needs it: code that runs where cudaMalloc / cudaMallocAsync (or any
-// allocating library call) is not allowed or not safe -- for example inside a
-// region being captured into a CUDA graph under a relaxed/global capture mode
-// that forbids allocation calls, a real-time or signal-safe path that must not
-// enter the allocator, or a host that runs under a fixed device-memory budget
-// handed out up front.  Such a caller still passes its own input and output
-// buffers; only the kernels' scratch (the merge-path tile splits, the
-// look-back words and the kernels' control block) has to come from somewhere,
-// and here it comes from one array reserved when the library is loaded.
+// allocating library call) is not allowed or not safe -- a host framework that
+// owns all device memory and lends this library only the inputs and outputs, a
+// real-time path that must not enter an allocator (an allocation can wait on
+// other work or fail when memory is fragmented), or a program that runs under
+// a device-memory budget handed out up front.  Such a caller still passes its
+// own input and output buffers; only the kernels' scratch (the merge-path tile
+// splits, the look-back words and the kernels' control block) has to come from
+// somewhere, and here it comes from one array reserved when the library is
+// loaded.  The call reads the delta size back to the host, so it synchronises
+// the caller's stream before it returns.
 //
 // The scratch is the file-scope array below (1 MiB).  Every GPU that loads the
 // library holds that array until the process exits.  All calls share it and it

@@ -244,6 +244,157 @@ hisa_status join_t(const void* outer, uint64_t no, const void* inner, uint64_t n
   return P.download();
 }
 
+// ---- hash partitioning (multi-GPU scheme) ------------------------------------------------
+
+template <typename K>
+__global__ void k_encode_pairs(const uint32_t* c0, const uint32_t* c1, uint64_t n, int b, K* out) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
+    out[i] = (K(c0[i]) << b) | K(c1[i]);
+}
+
+template <typename K>
+__global__ void k_decode_pairs(const K* in, uint64_t n, int b, uint32_t* c0, uint32_t* c1) {
+  const K mask = b >= int(sizeof(K) * 8) ? ~K(0) : ((K(1) << b) - 1);
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+    const K c = in[i];
+    c0[i] = uint32_t(c >> b);
+    c1[i] = uint32_t(c & mask);
+  }
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t part_owner(K code, int b, int key_col, uint32_t nparts) {
+  const K mask = (K(1) << b) - 1;
+  const uint32_t key = key_col == 0 ? uint32_t(code >> b) : uint32_t(code & mask);
+  return fmix32(key) % nparts;
+}
+
+// Counts per part of block `blockIdx.x`'s contiguous chunk of the codes.
+template <typename K>
+__global__ void k_part_count(const K* in, uint64_t n, uint64_t chunk, int b, int key_col, uint32_t nparts,
+                             uint32_t* bcount) {
+  extern __shared__ uint32_t s_pc[];
+  for (uint32_t p = threadIdx.x; p < nparts; p += blockDim.x) s_pc[p] = 0;
+  __syncthreads();
+  const uint64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&s_pc[part_owner(in[i], b, key_col, nparts)], 1u);
+  __syncthreads();
+  for (uint32_t p = threadIdx.x; p < nparts; p += blockDim.x) bcount[uint64_t(blockIdx.x) * nparts + p] = s_pc[p];
+}
+
+// One CTA: each block's first output position per part (parts in order,
+// blocks in order within a part) and each part's total.
+__global__ void k_part_offsets(const uint32_t* bcount, uint32_t nblocks, uint32_t nparts, uint64_t* off,
+                               uint64_t* totals) {
+  __shared__ uint64_t s_scan[33];
+  __shared__ uint64_t s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t p0 = 0; p0 < nparts; p0 += blockDim.x) {
+    const uint32_t p = p0 + threadIdx.x;
+    uint64_t run = 0;
+    if (p < nparts)
+      for (uint32_t k = 0; k < nblocks; ++k) {
+        off[uint64_t(k) * nparts + p] = run;
+        run += bcount[uint64_t(k) * nparts + p];
+      }
+    uint64_t tot;
+    const uint64_t base = s_carry + block_exclusive_sum<uint64_t>(run, s_scan, &tot);
+    if (p < nparts) {
+      totals[p] = run;
+      for (uint32_t k = 0; k < nblocks; ++k) off[uint64_t(k) * nparts + p] += base;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += tot;
+    __syncthreads();
+  }
+}
+
+// Each block scatters its chunk to its positions (order within a part and a
+// block unspecified: the receiver sorts).
+template <typename K>
+__global__ void k_part_scatter(const K* in, uint64_t n, uint64_t chunk, int b, int key_col, uint32_t nparts,
+                               const uint64_t* off, K* out) {
+  extern __shared__ unsigned long long s_po[];
+  for (uint32_t p = threadIdx.x; p < nparts; p += blockDim.x) s_po[p] = off[uint64_t(blockIdx.x) * nparts + p];
+  __syncthreads();
+  const uint64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const K c = in[i];
+    out[atomicAdd(&s_po[part_owner(c, b, key_col, nparts)], 1ull)] = c;
+  }
+}
+
+template <typename K>
+hisa_status partition_t(const void* in, uint64_t n, int b, int key_col, uint32_t nparts, void* out, uint64_t* counts,
+                        cudaStream_t s) {
+  for (uint32_t p = 0; p < nparts; ++p) counts[p] = 0;
+  if (n == 0) return HISA_OK;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return HISA_ERR_CUDA;
+  const uint32_t nblocks = uint32_t(std::max(1, sms * 4));
+  const uint64_t chunk = (n + nblocks - 1) / nblocks;
+  uint32_t* bcount = nullptr;
+  uint64_t *off = nullptr, *totals = nullptr;
+  cudaError_t e = cudaMallocAsync(&bcount, size_t(nblocks) * nparts * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&off, size_t(nblocks) * nparts * 8, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&totals, size_t(nparts) * 8, s);
+  hisa_status rc = HISA_OK;
+  if (e != cudaSuccess) {
+    rc = e == cudaErrorMemoryAllocation ? HISA_ERR_OOM : HISA_ERR_CUDA;
+  } else {
+    k_part_count<K><<<nblocks, 256, nparts * 4, s>>>(static_cast<const K*>(in), n, chunk, b, key_col, nparts, bcount);
+    k_part_offsets<<<1, 256, 0, s>>>(bcount, nblocks, nparts, off, totals);
+    k_part_scatter<K><<<nblocks, 256, nparts * 8, s>>>(static_cast<const K*>(in), n, chunk, b, key_col, nparts, off,
+                                                      static_cast<K*>(out));
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(counts, totals, size_t(nparts) * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      rc = HISA_ERR_CUDA;
+  }
+  if (bcount) cudaFreeAsync(bcount, s);
+  if (off) cudaFreeAsync(off, s);
+  if (totals) cudaFreeAsync(totals, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) rc = HISA_ERR_CUDA;
+  return rc;
+}
+
+__global__ void k_column_max(const uint32_t* a, const uint32_t* b2, uint64_t n, uint32_t* out) {
+  uint32_t m = 0;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
+    m = max(m, max(a[i], b2[i]));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// ---- fault path of the bounded waits -------------------------------------------------
+
+// One of the library's bounded device-side waits, run on a word that nothing
+// publishes (or an mbarrier that nothing arrives on, with no copy in flight)
+// and a short limit: the wait must run out, record kDevTimeout and return.
+__global__ void k_check_bounded_wait(DevState* st, int which, uint32_t limit, uint64_t* status) {
+  __shared__ __align__(8) uint64_t mbar;
+  constexpr uint32_t epoch = 1;
+  constexpr uint64_t tile = 5;   // predecessors 0..4 are never published
+  if (which == 0) {
+    if (threadIdx.x < 32) lookback_warp(status, tile, 1, epoch, &st->error, limit);
+  } else if (which == 1) {
+    if (threadIdx.x == 0) {
+      lookback_publish(status, tile, 1, 1, epoch);
+      lookback_resolve(status, tile, 1, 1, epoch, &st->error, limit);
+    }
+  } else if (which == 2) {
+    if (threadIdx.x == 0) lookback_thread(status, tile, 1, 1, epoch, &st->error, limit);
+  } else {
+    if (threadIdx.x == 0) {
+      mbar_init(&mbar, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&mbar, 0, limit)) atomicExch(&st->error, kDevTimeout);
+  }
+}
+
 }  // namespace
 }  // namespace hisa
 
@@ -289,6 +440,74 @@ hisa_status hisa_join_codes(const void* outer, uint64_t n_outer, const void* inn
   if (key_bytes == 8)
     return join_t<uint64_t>(outer, n_outer, inner, n_inner, b, outer_col, proj0, proj1, neq, out, out_cap, n_out, stream);
   return HISA_ERR_INVALID_ARG;
+}
+
+hisa_status hisa_check_bounded_wait(int which, uint32_t spin_limit, void* stream) {
+  if (which < 0 || which > 3 || spin_limit < 1 || spin_limit > 65536) return HISA_ERR_INVALID_ARG;
+  Prim P(stream);
+  const int status = P.scratch(16, 8);
+  P.zero(status, 16 * 8);
+  hisa_status s = P.upload();
+  if (s) return s;
+  k_check_bounded_wait<<<1, 32, 0, P.s>>>(P.d, which, spin_limit, static_cast<uint64_t*>(P.h.buf[status].ptr));
+  return P.download();
+}
+
+hisa_status hisa_encode_codes(const uint32_t* c0, const uint32_t* c1, uint64_t n, int b, void* out, int key_bytes,
+                              void* stream) {
+  if (b < 1 || b > 32 || (key_bytes != 4 && key_bytes != 8) || (key_bytes == 4 && 2 * b > 32) ||
+      (n && (!c0 || !c1 || !out)))
+    return HISA_ERR_INVALID_ARG;
+  if (n == 0) return HISA_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned grid = unsigned(std::min<uint64_t>((n + 255) / 256, 152 * 8));
+  if (key_bytes == 4) k_encode_pairs<uint32_t><<<grid, 256, 0, s>>>(c0, c1, n, b, static_cast<uint32_t*>(out));
+  else k_encode_pairs<uint64_t><<<grid, 256, 0, s>>>(c0, c1, n, b, static_cast<uint64_t*>(out));
+  return cudaGetLastError() == cudaSuccess ? HISA_OK : HISA_ERR_CUDA;
+}
+
+hisa_status hisa_decode_codes(const void* in, uint64_t n, int b, uint32_t* c0, uint32_t* c1, int key_bytes,
+                              void* stream) {
+  if (b < 1 || b > 32 || (key_bytes != 4 && key_bytes != 8) || (key_bytes == 4 && 2 * b > 32) ||
+      (n && (!in || !c0 || !c1)))
+    return HISA_ERR_INVALID_ARG;
+  if (n == 0) return HISA_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned grid = unsigned(std::min<uint64_t>((n + 255) / 256, 152 * 8));
+  if (key_bytes == 4) k_decode_pairs<uint32_t><<<grid, 256, 0, s>>>(static_cast<const uint32_t*>(in), n, b, c0, c1);
+  else k_decode_pairs<uint64_t><<<grid, 256, 0, s>>>(static_cast<const uint64_t*>(in), n, b, c0, c1);
+  return cudaGetLastError() == cudaSuccess ? HISA_OK : HISA_ERR_CUDA;
+}
+
+hisa_status hisa_partition_codes(const void* in, uint64_t n, int key_bytes, int b, int key_col, uint32_t nparts,
+                                 void* out, uint64_t* counts, void* stream) {
+  if (!counts || nparts < 1 || nparts > 1024 || key_col < 0 || key_col > 1 || b < 1 || b > 32 ||
+      (key_bytes != 4 && key_bytes != 8) || (key_bytes == 4 && 2 * b > 32) || (n && (!in || !out)))
+    return HISA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (key_bytes == 4) return partition_t<uint32_t>(in, n, b, key_col, nparts, out, counts, s);
+  return partition_t<uint64_t>(in, n, b, key_col, nparts, out, counts, s);
+}
+
+hisa_status hisa_column_max(const uint32_t* c0, const uint32_t* c1, uint64_t n, uint32_t* out, void* stream) {
+  if (!out || (n && (!c0 || !c1))) return HISA_ERR_INVALID_ARG;
+  *out = 0;
+  if (n == 0) return HISA_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, 4, s);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? HISA_ERR_OOM : HISA_ERR_CUDA;
+  hisa_status rc = HISA_OK;
+  if (cudaMemsetAsync(d, 0, 4, s) != cudaSuccess) rc = HISA_ERR_CUDA;
+  if (!rc) {
+    const unsigned grid = unsigned(std::min<uint64_t>((n + 255) / 256, 152 * 8));
+    k_column_max<<<grid, 256, 0, s>>>(c0, c1, n, d);
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(out, d, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      rc = HISA_ERR_CUDA;
+  }
+  cudaFreeAsync(d, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) rc = HISA_ERR_CUDA;
+  return rc;
 }
 
 }  // extern "C"

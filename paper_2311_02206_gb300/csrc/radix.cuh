@@ -4,8 +4,8 @@
 //
 // One pass is a single "onesweep" kernel (Adinets & Merrill, "Onesweep: a
 // faster least significant digit radix sort for GPUs", 2022): each CTA takes
-// the next tile of keys, ranks them stably inside the tile with warp match
-// (one digit counter set per warp), learns the tile's global offset per digit
+// the next tile of keys, ranks them stably inside the tile with eight warp
+// ballots per key (one digit counter set per warp), learns the tile's global offset per digit
 // by decoupled look-back over the previous tiles, stages the tile in shared
 // memory in digit order and writes it out.  The digit histograms of all passes
 // come from one earlier read (or are fused into the kernel that produced the
@@ -104,8 +104,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 // Bounded wait for the mbarrier phase `parity`; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 26); ++i)
+constexpr uint32_t kMbarWaitLimit = 1u << 26;
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, uint32_t limit = kMbarWaitLimit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(m, parity)) return true;
   return false;
 }

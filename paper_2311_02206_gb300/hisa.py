@@ -24,6 +24,7 @@ FLAG_LOG_FULL = 4
 FLAG_NO_DENSE = 8
 FLAG_HASH_INDEX = 16
 FLAG_NO_CHAIN = 32
+FLAG_NO_PULL = 64
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -41,6 +42,7 @@ class Config(ctypes.Structure):
         ("max_iters", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
         ("device", ctypes.c_int32),
+        ("pull_ratio", ctypes.c_float),
     ]
 
 
@@ -134,6 +136,12 @@ SIGNATURES = {
     "hisa_difference_merge_noalloc": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, _P,
                                                        ctypes.c_uint64, _P, ctypes.c_uint64, _U64P, ctypes.c_int,
                                                        _P]),
+    "hisa_check_bounded_wait": (ctypes.c_int32, [ctypes.c_int, ctypes.c_uint32, _P]),
+    "hisa_column_max": (ctypes.c_int32, [_P, _P, ctypes.c_uint64, _U32P, _P]),
+    "hisa_encode_codes": (ctypes.c_int32, [_P, _P, ctypes.c_uint64, ctypes.c_int, _P, ctypes.c_int, _P]),
+    "hisa_decode_codes": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "hisa_partition_codes": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_uint32, _P, _U64P, _P]),
     "hisa_join_codes": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint64, _U64P,
                                          ctypes.c_int, _P]),
@@ -186,7 +194,10 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None, flags: int = FLAG_GRAPH | FLAG_LOG_FULL, max_iters: int = 0,
                  load_factor: float = 0.0, ebm_k: float = 0.0, hbm_budget_bytes: int = 0,
-                 torch_allocator: bool = True):
+                 torch_allocator: bool = True, allocator=None, pull_ratio: float = 0.0):
+        """``allocator``: optional pair (alloc, free) of Python callables,
+        alloc(nbytes, stream) -> device pointer or None, free(ptr, nbytes,
+        stream), used in place of torch's caching allocator."""
         lib = load_library()
         torch = _torch()
         self._lib = lib
@@ -203,7 +214,24 @@ class Context:
         cfg.load_factor = load_factor
         cfg.ebm_k = ebm_k
         cfg.hbm_budget_bytes = hbm_budget_bytes
-        if torch_allocator:
+        cfg.pull_ratio = pull_ratio
+        if allocator is not None:
+            user_alloc, user_free = allocator
+
+            def _alloc(nbytes, strm, user):
+                try:
+                    return user_alloc(int(nbytes), int(strm or 0))
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, strm, user):
+                user_free(int(ptr), int(nbytes), int(strm or 0))
+
+            self._alloc_cb = _ALLOC_FN(_alloc)
+            self._free_cb = _FREE_FN(_free)
+            cfg.alloc = self._alloc_cb
+            cfg.free = self._free_cb
+        elif torch_allocator:
             def _alloc(nbytes, strm, user):
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(strm or 0))
@@ -517,3 +545,51 @@ def join_codes(outer, inner, b: int, outer_col: int, proj0: int, proj1: int, neq
         _check(rc)
         return out[:n.value]
     raise HisaError(-9, "join output did not fit")
+
+
+def check_bounded_wait(which: int, spin_limit: int = 64, stream=None) -> int:
+    """hisa_check_bounded_wait: the status of one bounded device-side wait run
+    on a word that nothing publishes (HISA_ERR_DEVICE_TIMEOUT, -5, expected)."""
+    return int(load_library().hisa_check_bounded_wait(which, spin_limit, _stream_ptr(stream)))
+
+
+def encode_codes(c0, c1, b: int, wide: bool = False, stream=None):
+    """Two int32 CUDA tensors (uint32 bit patterns) -> codes (c0 << b) | c1
+    (int32, or int64 when ``wide``)."""
+    torch = _torch()
+    out = torch.empty(max(c0.numel(), 1), dtype=torch.int64 if wide else torch.int32, device=c0.device)
+    _check(load_library().hisa_encode_codes(c0.data_ptr() if c0.numel() else None,
+                                            c1.data_ptr() if c1.numel() else None, c0.numel(), b,
+                                            out.data_ptr(), 8 if wide else 4, _stream_ptr(stream)))
+    return out[:c0.numel()]
+
+
+def decode_codes(codes, b: int, stream=None):
+    """Codes -> (c0, c1) int32 CUDA tensors."""
+    torch = _torch()
+    n = codes.numel()
+    c0 = torch.empty(max(n, 1), dtype=torch.int32, device=codes.device)
+    c1 = torch.empty(max(n, 1), dtype=torch.int32, device=codes.device)
+    _check(load_library().hisa_decode_codes(codes.data_ptr() if n else None, n, b, c0.data_ptr(), c1.data_ptr(),
+                                            _kb(codes), _stream_ptr(stream)))
+    return c0[:n], c1[:n]
+
+
+def partition_codes(codes, b: int, key_col: int, nparts: int, stream=None):
+    """hisa_partition_codes: (codes grouped by owner, list of part sizes)."""
+    torch = _torch()
+    n = codes.numel()
+    out = torch.empty(max(n, 1), dtype=codes.dtype, device=codes.device)
+    counts = (ctypes.c_uint64 * nparts)()
+    _check(load_library().hisa_partition_codes(codes.data_ptr() if n else None, n, _kb(codes), b, key_col, nparts,
+                                               out.data_ptr(), counts, _stream_ptr(stream)))
+    return out[:n], [int(counts[i]) for i in range(nparts)]
+
+
+def column_max(c0, c1, stream=None) -> int:
+    """Largest uint32 value of two int32 CUDA tensors (uint32 bit patterns)."""
+    out = ctypes.c_uint32()
+    n = c0.numel()
+    _check(load_library().hisa_column_max(c0.data_ptr() if n else None, c1.data_ptr() if n else None, n,
+                                          ctypes.byref(out), _stream_ptr(stream)))
+    return int(out.value)

@@ -18,7 +18,10 @@ on the first rule only.
 
 ``cspa``: the ten-rule points-to program on the skewed Assign/Dereference
 inputs divided by ``--div`` (windows of ``--window`` ids, seed 2), evaluated
-in one piece.
+in one piece.  Beside the sizes, delta counts and fingerprints it stores the
+whole sorted relations (``cspa_d<div>_w<window>.npz``: per IDB relation the
+codes (c0 << 32) | c1 ascending, as uint64), so the GPU tests compare every
+tuple and its position.
 """
 from __future__ import annotations
 
@@ -110,10 +113,13 @@ def cspa(div: int, window: int):
         "iterations": r.iterations,
         "oracle_cpu_seconds": None,
     }
+    arrays = {}
     for name in ("ValueFlow", "MemoryAlias", "ValueAlias"):
         c0, c1 = r.relations[name]
         out[name] = {"size": int(r.size(name)), "delta_counts": r.delta_counts[name],
                      "fingerprint": str(oracle.fingerprint(c0, c1))}
+        arrays[name] = (c0.astype(np.uint64) << np.uint64(32)) | c1.astype(np.uint64)
+    np.savez_compressed(os.path.join(HERE, "cspa_d%d_w%d.npz" % (div, window)), **arrays)
     out["oracle_cpu_seconds"] = round(time.time() - t0, 1)
     with open(os.path.join(HERE, "cspa_d%d_w%d.json" % (div, window)), "w") as f:
         json.dump(out, f, indent=1)

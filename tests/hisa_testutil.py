@@ -44,3 +44,25 @@ def fingerprint_device(c0, c1, chunk=1 << 27) -> int:
         b = c1[s:s + chunk].cpu().numpy().view(np.uint32)
         total = (total + oracle.fingerprint(a, b)) % (1 << 64)
     return total
+
+
+def assert_strictly_increasing_device(c0, c1, chunk=1 << 28):
+    """The tuples (c0[i], c1[i]) of two int32 CUDA tensors (uint32 bit patterns)
+    are in strictly increasing lexicographic order: every read must return a
+    sorted set.  Checked on the device, chunk by chunk, over 64-bit codes."""
+    import torch
+    n = c0.numel()
+    assert c1.numel() == n
+    prev = None
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        code = ((c0[s:e].to(torch.int64) & 0xFFFFFFFF) << 32) | (c1[s:e].to(torch.int64) & 0xFFFFFFFF)
+        # codes are below 2**64 as unsigned; flip the sign bit so signed order is unsigned order
+        code = code ^ (-(1 << 63))
+        if code.numel() > 1:
+            assert bool((code[1:] > code[:-1]).all()), f"not strictly increasing in [{s}, {e})"
+        if prev is not None and code.numel():
+            assert int(code[0]) > prev, f"not strictly increasing at {s}"
+        if code.numel():
+            prev = int(code[-1])
+        del code

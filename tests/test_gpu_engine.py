@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2311_02206_gb300 import workloads
-from hisa_testutil import assert_same, fingerprint_device, gpu_eval
+from hisa_testutil import assert_same, assert_strictly_increasing_device, fingerprint_device, gpu_eval
 
 pytestmark = pytest.mark.gpu
 
@@ -25,11 +25,42 @@ def _lib():
 def modes():
     """host-driven, graph-captured, both with the log-structured full,
     graph-captured without the grouped bitmap join, and with hashed indexes,
-    and with Tmp joined and sorted instead of gathered"""
+    with Tmp joined and sorted instead of gathered, and without pull mode"""
     from paper_2311_02206_gb300 import hisa
     return [0, hisa.FLAG_GRAPH, hisa.FLAG_LOG_FULL, hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL,
             hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE, hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE | hisa.FLAG_HASH_INDEX,
-            hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_CHAIN]
+            hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_CHAIN,
+            hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_PULL]
+
+
+@pytest.mark.parametrize("ratio", [1 / 16, 4.0, 4096.0])
+@pytest.mark.parametrize("graph", ["er1000", "rmat10", "path", "cycle", "star"] + [f"random{i}" for i in range(8)])
+def test_reach_pull_switch_points(ratio, graph):
+    """Groups pulled almost always (ratio 1/16), by the default rule, and
+    never (4096): the same relation and delta counts as the oracle."""
+    from paper_2311_02206_gb300 import hisa
+    if graph == "er1000":
+        s, d = workloads.config_reach_er()
+    elif graph == "rmat10":
+        s, d = workloads.rmat_graph(10, 1 << 13, 5)
+    elif graph == "path":
+        s, d = workloads.path_graph(200)
+    elif graph == "cycle":
+        s, d = workloads.cycle_graph(100)
+    elif graph == "star":   # a hub with every edge in and out, plus a tail
+        n = 300
+        s = np.concatenate([np.arange(1, n), np.zeros(n - 1), np.arange(n, n + 50)]).astype(np.uint32)
+        d = np.concatenate([np.zeros(n - 1), np.arange(1, n), np.arange(n + 1, n + 51)]).astype(np.uint32)
+    else:
+        rng = np.random.default_rng(100 + int(graph[6:]))
+        n = int(rng.integers(2, 400))
+        m = int(rng.integers(1, 6 * n))
+        s = rng.integers(0, n, m).astype(np.uint32)
+        d = rng.integers(0, n, m).astype(np.uint32)
+    ref = oracle.reach(s, d)
+    for flags in (hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL, hisa.FLAG_LOG_FULL):
+        rels, counts, _ = gpu_eval(*oracle.REACH, {"Edge": (s, d)}, flags=flags, pull_ratio=ratio)
+        assert_same(rels, counts, ref)
 
 
 @pytest.mark.parametrize("seed", range(40))
@@ -188,8 +219,9 @@ def test_sg_random_dag(seed):
         assert_same(rels, counts, ref)
 
 
-@pytest.mark.parametrize("log_full,no_dense", [(False, True), (True, True), (True, False)])
-def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense):
+@pytest.mark.parametrize("log_full,no_dense,no_pull", [(False, True, False), (True, True, False), (True, False, False),
+                                                       (True, False, True)])
+def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense, no_pull):
     """REACH on R-MAT scale 16 / 2**19 edges, in the launch configuration the
     benchmark times: total size, delta counts and fingerprint against the
     oracle's stored values, and 16 sampled target columns element by element."""
@@ -199,7 +231,8 @@ def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense):
     g = json.load(open(path))
     from paper_2311_02206_gb300 import hisa
     s, d = workloads.config_reach_rmat()
-    flags = hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0) | (hisa.FLAG_NO_DENSE if no_dense else 0)
+    flags = hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0) | (hisa.FLAG_NO_DENSE if no_dense else 0) | \
+        (hisa.FLAG_NO_PULL if no_pull else 0)
     with hisa.Context(flags=flags) as ctx:
         ctx.program(*oracle.REACH)
         ctx.load_tuples("Edge", s, d)
@@ -208,6 +241,7 @@ def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense):
         assert ctx.relation_size("Reach") == g["reach_size"]
         c0, c1 = ctx.read_relation("Reach", device=True)
         assert fingerprint_device(c0, c1) == int(g["fingerprint"])
+        assert_strictly_increasing_device(c0, c1)
         targets = np.random.default_rng(2024).choice(1 << 16, 16, replace=False).astype(np.uint32)
         ref = oracle.reach_targets(s, d, targets)
         keep = torch.isin(c1, torch.from_numpy(targets.view(np.int32)).cuda())
@@ -216,12 +250,33 @@ def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense):
         assert np.array_equal(g0, ref.relations["Reach"][0]) and np.array_equal(g1, ref.relations["Reach"][1])
 
 
+_SG_SUB = {}
+
+
+def _sg_induced(literal, nodes):
+    """The oracle's SG on the subgraph of the 20,000-node DAG induced by the
+    nodes [0, nodes).  Edges point to larger ids, so every derivation of SG(x,
+    y) with x, y < nodes (rule 1 through a parent p < x, rule 2 through a, b <
+    x, y) uses nodes below `nodes` only: this is exactly SG restricted to
+    [0, nodes)^2."""
+    key = (literal, nodes)
+    if key not in _SG_SUB:
+        s, d = workloads.config_sg_dag()
+        keep = (s < nodes) & (d < nodes)
+        _SG_SUB[key] = oracle.seminaive(*(oracle.SG_LITERAL if literal else oracle.SG),
+                                        {"Edge": (s[keep], d[keep])}).relations["SG"]
+    return _SG_SUB[key]
+
+
 @pytest.mark.parametrize("literal,log_full,no_chain",
                          [(False, False, False), (True, False, False), (False, True, False), (False, True, True)])
 def test_sg_dag_full_size_golden(literal, log_full, no_chain):
     """SG on the 20,000-node DAG (x != y on both rules, or on rule 1 only as
     the workload description prints it): size, every delta count and the
-    fingerprint of the whole relation against the oracle's stored values."""
+    fingerprint of the whole relation against the oracle's stored values; the
+    whole relation in strictly increasing order; and, element by element and
+    position by position, its restriction to nodes [0, 3000) against the
+    oracle's SG of the induced subgraph (3.1 million tuples)."""
     path = os.path.join(GOLDEN, "sg_literal_dag_20k.json" if literal else "sg_dag_20k.json")
     if not os.path.exists(path):
         pytest.skip("golden values not generated")
@@ -237,17 +292,37 @@ def test_sg_dag_full_size_golden(literal, log_full, no_chain):
         assert ctx.relation_size("SG") == g["sg_size"]
         c0, c1 = ctx.read_relation("SG", device=True)
         assert fingerprint_device(c0, c1) == int(g["fingerprint"])
+        assert_strictly_increasing_device(c0, c1)
+        nodes = 3000
+        keep = (c0 >= 0) & (c0 < nodes) & (c1 >= 0) & (c1 < nodes)
+        g0 = c0[keep].cpu().numpy().view(np.uint32)
+        g1 = c1[keep].cpu().numpy().view(np.uint32)
+    w0, w1 = _sg_induced(literal, nodes)
+    assert len(w0) > 3_000_000
+    assert np.array_equal(g0, w0) and np.array_equal(g1, w1)
+
+
+def _cspa_arrays(div, window):
+    path = os.path.join(GOLDEN, "cspa_d%d_w%d.npz" % (div, window))
+    if not os.path.exists(path):
+        return None
+    z = np.load(path)
+    return {k: ((z[k] >> np.uint64(32)).astype(np.uint32), (z[k] & np.uint64(0xFFFFFFFF)).astype(np.uint32))
+            for k in z.files}
 
 
 @pytest.mark.parametrize("div,window,no_chain", [(500, 32, False), (250, 128, False), (500, 32, True)])
 def test_cspa_golden(div, window, no_chain):
     """The points-to program on the skewed inputs divided by `div`: sizes,
     delta counts and fingerprints of the three IDB relations against the
-    oracle's stored values (1/250 derives ~4.6e9 raw tuples on the GPU)."""
+    oracle's stored values, and every tuple of each relation, in order,
+    against the oracle's stored sorted relations (1/250 derives ~4.6e9 raw
+    tuples on the GPU)."""
     path = os.path.join(GOLDEN, "cspa_d%d_w%d.json" % (div, window))
     if not os.path.exists(path):
         pytest.skip("golden values not generated")
     g = json.load(open(path))
+    arrays = _cspa_arrays(div, window)
     from paper_2311_02206_gb300 import hisa
     edb = workloads.config_cspa(div, window)
     flags = hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | (hisa.FLAG_NO_CHAIN if no_chain else 0)
@@ -262,3 +337,9 @@ def test_cspa_golden(div, window, no_chain):
             assert ctx.delta_counts(name) == g[name]["delta_counts"], name
             c0, c1 = ctx.read_relation(name, device=True)
             assert fingerprint_device(c0, c1) == int(g[name]["fingerprint"]), name
+            assert_strictly_increasing_device(c0, c1)
+            if arrays is not None:
+                w0, w1 = arrays[name]
+                assert np.array_equal(c0.cpu().numpy().view(np.uint32), w0), name
+                assert np.array_equal(c1.cpu().numpy().view(np.uint32), w1), name
+    assert arrays is not None, "stored sorted relations missing (tests/golden/make_golden.py cspa)"
