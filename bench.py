@@ -66,6 +66,8 @@ def _args():
                     help="sort raw join results instead of the grouped bitmap join (HISA_FLAG_NO_DENSE)")
     ap.add_argument("--load-factor", type=float, default=0.0, help="hash-index load factor (0: the library default)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--partitioned", action="store_true",
+                    help="REACH hash-partitioned over the ranks (one all-to-all per iteration; strong scaling)")
     ap.add_argument("--no-sub", action="store_true",
                     help="rmat16: skip the compact sg20k / cspa / batch5 records of the default line")
     ap.add_argument("--no-e2e", action="store_true")
@@ -593,6 +595,71 @@ def run_hisa(a):
         dist.destroy_process_group()
 
 
+def run_partitioned(a):
+    """REACH hash-partitioned over the ranks (paper_2311_02206_gb300.partitioned):
+    rank r loads the r-th share of the edge list; every iteration joins locally,
+    sends each new tuple to the owner of its first column (NCCL all-to-all),
+    and the owners deduplicate, difference and merge; an all-reduce of |delta|
+    ends the loop.  value = |Reach| / the slowest rank's time (strong scaling:
+    the workload is fixed, N GPUs share it).  At N = 1 the exchange is local."""
+    import numpy as np
+    import torch
+
+    from paper_2311_02206_gb300 import build, partitioned
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    _init_pg(world)
+    build.build()
+    s, d, desc, _nodes = _workload(a.workload)
+    lo, hi = rank * len(s) // world, (rank + 1) * len(s) // world
+    edges = [(torch.from_numpy(s[lo:hi].view(np.int32).copy()).cuda(),
+              torch.from_numpy(d[lo:hi].view(np.int32).copy()).cuda())]
+    ops = partitioned.CudaPartOps()
+    ex = partitioned.TorchExchange() if world > 1 else partitioned.LocalExchange(1)
+    flush = torch.empty(512 << 18, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        full, b, counts = partitioned.reach_partitioned(edges, ops, ex)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    uuid = str(torch.cuda.get_device_properties(local).uuid) if hasattr(
+        torch.cuda.get_device_properties(local), "uuid") else ""
+    ms = []
+    _barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        for k in range(a.steps):
+            flush.fill_(k)
+            _barrier(world)
+            ev0.record(stream)
+            full, b, counts = partitioned.reach_partitioned(edges, ops, ex)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+    _barrier(world)
+    mine = sum(int(f.numel()) for f in full)
+    total = int(_sum_over_ranks(float(mine), world))
+    slowest = _max_over_ranks(sum(ms) / 1e3, world)
+    line = {
+        "metric": METRIC, "value": total * a.steps / slowest, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": slowest * 1e3 / a.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc + ", hash-partitioned over the GPUs by the first column",
+                   "idb_tuples": {"Reach": total}, "iterations": len(counts),
+                   "l2": "flushed by a 512 MiB write between steps (outside the timed events)",
+                   "loop": "host-driven; per iteration: join, hash partition, all-to-all, sort + unique, "
+                           "difference + merge, all-reduce of |delta|",
+                   "parallelism": f"hash partition over {world} GPU(s)",
+                   "step_ms": [round(x, 3) for x in ms]},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 # ---- the reference arm: the CPU oracle as it stands ---------------------------------------------
 
 def run_reference(a):
@@ -882,6 +949,8 @@ if __name__ == "__main__":
         run_micro(args)
     elif args.workload == "batch5" and args.impl == "hisa":
         run_batch5(args)
+    elif args.partitioned and args.impl == "hisa":
+        run_partitioned(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

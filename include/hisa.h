@@ -123,7 +123,7 @@ typedef struct {
   int32_t device;           /* CUDA device ordinal; -1 = the current device */
   float pull_ratio;         /* pull mode switch point (HISA_FLAG_NO_PULL): a group pulls when the
                                inner runs its next delta would mark exceed pull_ratio times the
-                               values it could still derive (plus the delta's size); 0 = 4 */
+                               values it could still derive (plus the delta's size); 0 = 8 */
 } hisa_config;
 
 typedef struct hisa_ctx hisa_ctx;

@@ -134,7 +134,7 @@ void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStr
 // keys, read coalesced with eight loads in flight per lane, counts it, and
 // after a scan over the warps' counts writes it.
 __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
-  __shared__ uint64_t s_gm[33], s_nu[33];
+  __shared__ uint64_t s_gm[33], s_nu[33], s_pl[33];
   constexpr int kB = 8;   // 32-key chunks loaded before any is used
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
@@ -157,11 +157,14 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
   const uint32_t* pbm = units_on && a.pull_bm_buf >= 0 ? static_cast<const uint32_t*>(st->buf[a.pull_bm_buf].ptr)
                                                        : nullptr;
   auto pulled = [&](uint64_t g) { return pbm && ((pbm[g >> 5] >> (g & 31)) & 1u); };
+  uint32_t* plist = pbm ? static_cast<uint32_t*>(st->buf[a.plist_buf].ptr) : nullptr;
+  const uint64_t pcap = pbm ? st->buf[a.plist_buf].cap : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint64_t wper = (((nk + nw - 1) / nw) + 31) & ~31ull;
   const uint64_t w0 = min(nk, uint64_t(warp) * wper), w1 = min(nk, w0 + wper);
-  // pass 1: groups and multi-unit groups (packed, each < 2^32), units
-  uint64_t gm = 0, nus = 0;
+  // pass 1: groups and multi-unit groups (packed, each < 2^32), units,
+  // pulled groups
+  uint64_t gm = 0, nus = 0, npl = 0;
   for (uint64_t base = w0; base < w1; base += 32 * kB) {
     uint64_t f0[kB], f1[kB];
 #pragma unroll
@@ -173,42 +176,50 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
 #pragma unroll
     for (int i = 0; i < kB; ++i)
       if (f1[i] > f0[i]) {
-        const uint64_t nu = pulled(base + uint64_t(i) * 32 + lane) ? 1 : (f1[i] - f0[i] + usz - 1) / usz;
+        const bool pg = pulled(base + uint64_t(i) * 32 + lane);
+        const uint64_t nu = pg ? 0 : (f1[i] - f0[i] + usz - 1) / usz;
         gm += 1 + (uint64_t(nu > 1) << 32);
         nus += nu;
+        npl += pg;
       }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     gm += __shfl_xor_sync(0xffffffffu, gm, o);
     nus += __shfl_xor_sync(0xffffffffu, nus, o);
+    npl += __shfl_xor_sync(0xffffffffu, npl, o);
   }
   if (lane == 0) {
     s_gm[warp] = gm;
     s_nu[warp] = nus;
+    s_pl[warp] = npl;
   }
   __syncthreads();
   if (warp == 0) {   // exclusive scan over the warps; totals in [32]
-    uint64_t x = lane < nw ? s_gm[lane] : 0, y = lane < nw ? s_nu[lane] : 0;
-    const uint64_t x0 = x, y0 = y;
+    uint64_t x = lane < nw ? s_gm[lane] : 0, y = lane < nw ? s_nu[lane] : 0, z = lane < nw ? s_pl[lane] : 0;
+    const uint64_t x0 = x, y0 = y, z0 = z;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t xs = __shfl_up_sync(0xffffffffu, x, o), ys = __shfl_up_sync(0xffffffffu, y, o);
+      const uint64_t xs = __shfl_up_sync(0xffffffffu, x, o), ys = __shfl_up_sync(0xffffffffu, y, o),
+                     zs = __shfl_up_sync(0xffffffffu, z, o);
       if (lane >= o) {
         x += xs;
         y += ys;
+        z += zs;
       }
     }
     s_gm[lane] = x - x0;
     s_nu[lane] = y - y0;
+    s_pl[lane] = z - z0;
     if (lane == 31) {
       s_gm[32] = x;
       s_nu[32] = y;
+      s_pl[32] = z;
     }
   }
   __syncthreads();
   // pass 2: write the groups' starts (and units) at their ranks
-  uint64_t c = s_gm[warp] & 0xFFFFFFFFull, m = s_gm[warp] >> 32, u = s_nu[warp];
+  uint64_t c = s_gm[warp] & 0xFFFFFFFFull, m = s_gm[warp] >> 32, u = s_nu[warp], pl = s_pl[warp];
   const uint32_t lt = (1u << lane) - 1;
   for (uint64_t base = w0; base < w1; base += 32 * kB) {
     uint64_t f0[kB], f1[kB];
@@ -226,7 +237,10 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
       if (head && pos < ocap) out[pos] = f0[i];
       if (units_on) {
         const bool pg = head && pulled(base + uint64_t(i) * 32 + lane);
-        const uint64_t nu = !head ? 0 : pg ? 1 : (f1[i] - f0[i] + usz - 1) / usz;
+        const uint64_t nu = !head || pg ? 0 : (f1[i] - f0[i] + usz - 1) / usz;
+        const uint32_t pb = __ballot_sync(0xffffffffu, pg);
+        if (pg && pl + __popc(pb & lt) < pcap) plist[pl + __popc(pb & lt)] = uint32_t(pos);
+        pl += __popc(pb);
         const uint32_t mb = __ballot_sync(0xffffffffu, nu > 1);
         uint64_t incl = nu;
 #pragma unroll
@@ -237,7 +251,7 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
         if (head && pos + 1 < ucap) {
           units[pos] = u + incl - nu;
           done[pos] = 0;
-          mslot[pos] = pg ? kPullMark : uint32_t(m + __popc(mb & lt));
+          mslot[pos] = uint32_t(m + __popc(mb & lt));
         }
         u += __shfl_sync(0xffffffffu, incl, 31);
         m += __popc(mb);
@@ -253,6 +267,13 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
     else {
       atomicMax((unsigned long long*)&st->need[a.out_buf], (unsigned long long)(carry + 1));
       over = true;
+    }
+    if (pbm) {
+      st->cnt[a.pull_cnt] = s_pl[32];
+      if (s_pl[32] > pcap) {
+        atomicMax((unsigned long long*)&st->need[a.plist_buf], (unsigned long long)s_pl[32]);
+        over = true;
+      }
     }
     if (units_on) {
       if (carry + 1 < ucap) {
@@ -277,16 +298,25 @@ __global__ void __launch_bounds__(1024) k_group_compact(GroupArgs a, int bits) {
 __global__ void k_pull_out(PullOutArgs a) {
   DevState* st = a.st;
   const uint64_t* first = static_cast<const uint64_t*>(st->buf[a.index_buf].ptr);
+  const uint64_t* tfirst = static_cast<const uint64_t*>(st->buf[a.top_index_buf].ptr);
+  const uint32_t* inner = static_cast<const uint32_t*>(st->buf[a.inner_buf].ptr);
   uint32_t* out = static_cast<uint32_t*>(st->buf[a.out_buf].ptr);
+  uint32_t* fk = static_cast<uint32_t*>(st->buf[a.first_buf].ptr);
+  uint32_t* tdeg = static_cast<uint32_t*>(st->buf[a.tdeg_buf].ptr);
   const uint64_t nwords = a.b >= 5 ? (1ull << (a.b - 5)) : 1;
   const uint64_t nk = 1ull << a.b;
+  const uint32_t mask = uint32_t(nk - 1);
   unsigned long long cnt = 0;
   for (uint64_t w = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; w < nwords;
        w += uint64_t(gridDim.x) * blockDim.x) {
     uint32_t bits = 0;
     for (uint32_t i = 0; i < 32; ++i) {
       const uint64_t o = w * 32 + i;
-      if (o < nk && first[o + 1] > first[o]) bits |= 1u << i;
+      if (o >= nk) break;
+      const uint64_t f0 = first[o], f1 = first[o + 1];
+      if (f1 > f0) bits |= 1u << i;
+      fk[o] = f1 > f0 ? inner[f0] & mask : 0xFFFFFFFFu;
+      tdeg[o] = uint32_t(tfirst[o + 1] - tfirst[o]);
     }
     out[w] = bits;
     cnt += __popc(bits);
@@ -309,7 +339,7 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
 
 const char* const kKernelNames[kKindCount] = {
     "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
-    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level", "chain_len", "chain_scan", "chain_gather"};
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level", "chain_len", "chain_scan", "chain_gather", "join_dense_pull"};
 
 thread_local KernelTimer* g_timer = nullptr;
 thread_local uint64_t g_launches = 0;

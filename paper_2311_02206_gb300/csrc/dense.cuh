@@ -20,9 +20,6 @@
 
 namespace hisa {
 
-// a group marked in the units' multi-unit slot array as pulled (one unit)
-constexpr uint32_t kPullMark = 0xFFFFFFFFu;
-
 // Start position of every run of equal g = code >> b in a sorted code array,
 // compacted in order; cnt[out_cnt] = number of groups and out[groups] = n
 // (k_group_compact, from a direct index of the array by g).
@@ -43,8 +40,8 @@ struct GroupArgs {
   // direct index by the kept value)
   int indirect, vals_buf;
   // k_group_compact with units: bit g of this u32 bitmap set = group g is
-  // pulled (one unit, marked kPullMark in its multi-unit slot); -1: none
-  int pull_bm_buf = -1;
+  // pulled: it gets no units; its index goes to plist (count in cnt[pull_cnt])
+  int pull_bm_buf = -1, plist_buf = -1, pull_cnt = -1;
 };
 
 // A two-step rule variant H(x, y) <- A(x, a), delta(a, c), B(c, y) -- delta
@@ -175,8 +172,8 @@ struct DenseArgs {
   int mslot_buf, bmm_buf;
   int units_ready;              // computed by the group compaction (else k_dense_units runs)
   // pull mode (pull_inner_buf >= 0; a direct inner index, b <= kPullMaxBits):
-  // a group whose units entry is marked kPullMark is one unit worked the
-  // other way round.  Its delta values k go into a frontier bitmap F, full's
+  // a group listed in plist is worked the other way round by k_dense_pull
+  // (one CTA per group; it has no units in k_dense_mark).  Its delta values k go into a frontier bitmap F, full's
   // tuples of the group into a bitmap V, and every candidate o (a value with
   // inner tuples, not in V) walks its inner tuples (o, k') -- the inner
   // relation sorted by its other column, with a direct index by it -- until
@@ -188,27 +185,74 @@ struct DenseArgs {
   // (|other values| - |full_g| - |next delta|) plus the next delta's size.
   int pull_inner_buf = -1, pull_index_buf = -1;   // inner codes (o, k) sorted; direct index by o
   int pull_out_buf = -1;                // u32 [2^b / 32]: values o with inner tuples
-  int pull_bm_buf = -1;                 // u32 [2^b / 32]: bit g = group g pulls next iteration
+  int pull_bm_buf = -1;                 // u32 [2^b / 32]: bit g = group g pulls (this and next iteration)
   int fcnt_buf = -1;                    // u32 [2^b]: |full_g| (kept by the append of each level)
   int nout_cnt = -1;                    // cnt slot: number of values o with inner tuples
+  int pull_first_buf = -1;              // u32 [2^b]: each o's first k (PullOutArgs)
+  int tdeg_buf = -1;                    // u32 [2^b]: each k's run length in the push-ordered inner
+  int plist_buf = -1, pull_cnt = -1;    // pulled groups (indices, written by the group compaction)
+  int pull_raw_cnt = -1;                // cnt slot: codes the pull kernel read (delta, full, inner tuples)
   uint32_t pull_k16 = 64;
 };
 
 // two bitmaps (frontier and full) of 2^b bits in shared memory
 constexpr int kPullMaxBits = 16;
 // default switch point, x16: a group pulls when the inner runs its next delta
-// would mark exceed 4x its candidates plus the delta's size
-constexpr uint32_t kPullK16 = 64;
+// would mark exceed 8x its candidates plus the delta's size (R-MAT 16: the
+// fastest of 1, 2, 4, 8, 16 by 0.2-3 ms per fixpoint)
+constexpr uint32_t kPullK16 = 128;
 
 // Values o with inner tuples (a non-empty run in the direct index by o), as a
 // bitmap, and their number (added to cnt[nout_cnt]).
+// (pull mode needs b <= 16, so the inner codes are 32-bit)
 struct PullOutArgs {
   DevState* st;
-  int index_buf;   // u64 [2^b + 1] direct index by o
+  int index_buf;       // u64 [2^b + 1] direct index of the pull-ordered inner by o
+  int inner_buf;       // u32 codes (o, k), sorted
+  int top_index_buf;   // u64 [2^b + 1] direct index of the push-ordered inner by k
   int b;
-  int out_buf;     // u32 [2^b / 32]
+  int out_buf;         // u32 [2^b / 32]: values o with inner tuples
+  int first_buf;       // u32 [2^b]: o's first (smallest) k, 0xFFFFFFFF when none
+  int tdeg_buf;        // u32 [2^b]: length of k's run in the push-ordered inner
   int nout_cnt;
 };
+
+// OR of `bits` into s[word] for the 32 lanes of a warp whose words do not
+// decrease from lane to lane (values taken in sorted order): lanes of one
+// word are combined first (a segmented OR by shuffles), so each distinct word
+// takes one shared-memory atomic instead of one per lane.
+__device__ __forceinline__ void seg_or_sorted(uint32_t* s, uint32_t word, uint32_t bits, bool valid) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t w = valid ? word : 0xFFFFFFFFu;
+  uint32_t acc = valid ? bits : 0u;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t ow = __shfl_down_sync(0xffffffffu, w, d);
+    const uint32_t oa = __shfl_down_sync(0xffffffffu, acc, d);
+    if (lane + d < 32 && ow == w) acc |= oa;
+  }
+  const uint32_t pw = __shfl_up_sync(0xffffffffu, w, 1);
+  if (valid && (lane == 0 || pw != w) && (acc & ~s[w])) atomicOr(&s[w], acc);
+}
+
+// The values (low b bits) of the sorted codes src[r0 .. r1) into the bitmap
+// `bm`, by the calling warp and the other warps of the CTA (warp of nwarps):
+// 256 codes per warp per step, eight loads in flight per lane.
+template <typename K>
+__device__ __forceinline__ void sorted_run_to_bitmap(uint32_t* bm, const K* src, uint64_t r0, uint64_t r1,
+                                                     uint32_t vmask, int warp, int nwarps) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t i0 = r0 + uint64_t(warp) * 256; i0 < r1; i0 += uint64_t(nwarps) * 256) {
+    uint32_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const uint64_t i = i0 + uint64_t(u) * 32 + lane;
+      v[u] = i < r1 ? uint32_t(src[i]) & vmask : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) seg_or_sorted(bm, v[u] >> 5, 1u << (v[u] & 31), i0 + uint64_t(u) * 32 + lane < r1);
+  }
+}
 
 constexpr int kDenseThreads = 128;
 constexpr int kDenseCtasPerSm = 16;   // latency-bound (L2 probes and run reads): full occupancy
@@ -293,6 +337,84 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_starts(GroupArgs a) {
   }
 }
 
+// The end of a group in either direction: its bitmap `res` (the group's new
+// delta) stored to its slot gbm (coalesced) and cleared, with `also` (null or
+// a second bitmap) cleared beside it, its size into counts[gi].  With pull
+// mode on, the inner-run lengths of the set bits are summed (what a push pass
+// would mark next iteration) and the group's next mode is chosen: pull when
+// that sum exceeds pull_k16 / 16 times its remaining candidates plus the
+// delta's size.  Called by every thread of the CTA (blockDim.x threads).
+template <typename K>
+__device__ __forceinline__ void dense_finish(const DenseArgs& a, DevState* st, uint32_t* res, uint32_t* also,
+                                             uint32_t* gbm, uint64_t gi, uint32_t g, int nwords,
+                                             unsigned long long* s_cnt, unsigned long long* s_td) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthreads = blockDim.x;
+  const bool pull_on = a.pull_inner_buf >= 0;
+  uint32_t mine = 0;
+  for (int j0 = warp * 32; j0 < nwords; j0 += nthreads) {   // warp-uniform
+    const int j = j0 + lane;
+    const uint32_t w = j < nwords ? res[j] : 0u;
+    if (j < nwords) gbm[j] = w;
+    mine += __popc(w);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if (lane == 0 && mine) atomicAdd(s_cnt, (unsigned long long)mine);
+  __syncthreads();
+  // the next delta's inner-run total, only where pulling could pay: the
+  // delta is at least 1/16 of the candidates left (a word at a time, a lane
+  // per bit, coalesced)
+  uint64_t cand = 0;
+  bool weigh = false;
+  if (pull_on) {
+    const uint64_t nout = st->cnt[a.nout_cnt];
+    const uint64_t full_after = uint64_t(static_cast<const uint32_t*>(st->buf[a.fcnt_buf].ptr)[g]) + *s_cnt;
+    cand = nout > full_after ? nout - full_after : 0;
+    weigh = 16ull * *s_cnt >= cand && *s_cnt > 0;
+  }
+  unsigned long long td = 0;
+  const uint32_t* tdeg = weigh ? static_cast<const uint32_t*>(st->buf[a.tdeg_buf].ptr) : nullptr;
+  for (int j0 = warp * 32; j0 < nwords; j0 += nthreads) {   // warp-uniform
+    const int j = j0 + lane;
+    const uint32_t w = j < nwords ? res[j] : 0u;
+    if (j < nwords) {
+      res[j] = 0;
+      if (also) also[j] = 0;
+    }
+    if (weigh)   // eight words' loads in flight
+      for (uint32_t any = __ballot_sync(0xffffffffu, w != 0u); any;) {
+        uint32_t t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int jl = any ? __ffs(any) - 1 : -1;
+          any = any ? any & (any - 1) : 0u;
+          const uint32_t ww = __shfl_sync(0xffffffffu, w, jl & 31);
+          t[u] = jl >= 0 && ((ww >> lane) & 1u) ? tdeg[uint32_t(j0 + jl) * 32 + uint32_t(lane)] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) td += t[u];
+      }
+  }
+  if (weigh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) td += __shfl_xor_sync(0xffffffffu, td, o);
+    if (lane == 0 && td) atomicAdd(s_td, td);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    static_cast<uint64_t*>(st->buf[a.offs_buf].ptr)[gi] = *s_cnt;
+    if (pull_on) {
+      const bool pull_next = weigh && 16ull * *s_td > uint64_t(a.pull_k16) * cand + 16ull * *s_cnt;
+      uint32_t* pbm = static_cast<uint32_t*>(st->buf[a.pull_bm_buf].ptr);
+      if (pull_next) atomicOr(&pbm[g >> 5], 1u << (g & 31));
+      else atomicAnd(&pbm[g >> 5], ~(1u << (g & 31)));
+    }
+    *s_cnt = 0;   // read again only after the next group's first barrier
+    *s_td = 0;
+  }
+}
+
 // Phase 0 (one CTA): units per group (ceil(size / unit_size)) -> first unit
 // of each group, total units in units[groups]; done counters cleared.
 template <typename K>
@@ -362,14 +484,12 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
   __shared__ uint64_t s_unit[3];   // the unit's outer range [start, end) and its group
   __shared__ uint32_t s_nu;        // units in that group
   __shared__ int s_last;
-  __shared__ int s_pull;           // the unit is a whole group worked in pull mode
   __shared__ unsigned long long s_td;
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
   const uint64_t ngroups = st->cnt[a.groups_cnt];
   if (ngroups == 0) return;
   const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
-  const bool pull_on = a.pull_inner_buf >= 0;
   // (the multi-unit bitmaps' capacity is checked where the units are made)
   if (st->buf[a.bm_buf].cap < ngroups * uint64_t(nwords) || st->buf[a.offs_buf].cap < ngroups + 1) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -385,11 +505,10 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
   const Slot* table = static_cast<const Slot*>(st->buf[a.table_buf].ptr);
   const uint64_t tmask = st->buf[a.table_buf].cap - 1;
   uint32_t* bm = static_cast<uint32_t*>(st->buf[a.bm_buf].ptr);
-  uint64_t* counts = static_cast<uint64_t*>(st->buf[a.offs_buf].ptr);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nwarps = kDenseThreads / 32;
   const uint32_t vmask = a.b >= 32 ? 0xFFFFFFFFu : ((1u << a.b) - 1);
-  for (int j = tid; j < (pull_on ? 2 : 1) * nwords; j += kDenseThreads) s_bm[j] = 0;
+  for (int j = tid; j < nwords; j += kDenseThreads) s_bm[j] = 0;
   if (tid == 0) {
     s_cnt = 0;
     s_td = 0;
@@ -415,90 +534,13 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
         s_unit[0] = s;
         s_unit[1] = min(gs[gi + 1], s + uint64_t(a.unit_size));
         s_nu = uint32_t(units[gi + 1] - units[gi]);
-        s_pull = pull_on && static_cast<const uint32_t*>(st->buf[a.mslot_buf].ptr)[gi] == kPullMark;
-        if (s_pull) s_unit[1] = gs[gi + 1];   // a pulled group is one unit
       }
       s_unit[2] = gi;
     }
     __syncthreads();
     if (s_unit[2] == ~0ull) break;
-    const bool pull = s_pull;
-    uint32_t* res = pull ? s_bm + nwords : s_bm;   // the group's result bitmap at the finish
     const uint64_t gi = s_unit[2];
     uint32_t* gbm = bm + gi * uint64_t(nwords);
-    if (pull) {
-      // pull: frontier F (the group's delta values) and full's tuples V
-      uint32_t* F = s_bm;
-      uint32_t* V = s_bm + nwords;
-      const K* pin = static_cast<const K*>(st->buf[a.pull_inner_buf].ptr);
-      const uint64_t* pidx = static_cast<const uint64_t*>(st->buf[a.pull_index_buf].ptr);
-      const uint32_t* outbm = static_cast<const uint32_t*>(st->buf[a.pull_out_buf].ptr);
-      for (uint64_t i = s_unit[0] + tid; i < s_unit[1]; i += kDenseThreads) {
-        const uint32_t v = uint32_t(outer[i]) & vmask;
-        const uint32_t bit = 1u << (v & 31);
-        if (!(F[v >> 5] & bit)) atomicOr(&F[v >> 5], bit);
-      }
-      if (a.full_buf >= 0) {
-        const uint64_t nlv = st->cnt[a.nlv_cnt], nk = (1ull << a.b) + 1;
-        const uint64_t* lvidx = static_cast<const uint64_t*>(st->buf[a.lvidx_buf].ptr);
-        const K* fl = static_cast<const K*>(st->buf[a.full_buf].ptr);
-        const uint64_t g = uint64_t(outer[s_unit[0]]) >> a.b;
-        for (uint64_t lv = 0; lv < nlv; ++lv) {
-          const uint64_t r0 = lvidx[lv * nk + g], r1 = lvidx[lv * nk + g + 1];
-          for (uint64_t i0 = r0 + tid; i0 < r1; i0 += 8 * kDenseThreads) {
-            uint32_t v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const uint64_t i = i0 + uint64_t(u) * kDenseThreads;
-              v[u] = i < r1 ? uint32_t(fl[i]) & vmask : 0xFFFFFFFFu;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (v[u] != 0xFFFFFFFFu) atomicOr(&V[v[u] >> 5], 1u << (v[u] & 31));
-          }
-        }
-      }
-      __syncthreads();
-      // each lane owns one word of candidates (values with inner tuples, not
-      // in full) and walks their inner runs four tuples at a time until one
-      // reaches the frontier; a lane that finishes a candidate takes its
-      // word's next one at once
-      for (int base = warp * 32; base < nwords; base += nwarps * 32) {
-        const int w = base + lane;
-        uint32_t cm = w < nwords ? (outbm[w] & ~V[w]) : 0u;
-        uint32_t r = 0, o = 0;
-        uint64_t p = 0, pe = 0;
-        bool act = false;
-        while (__any_sync(0xffffffffu, act || cm != 0)) {
-          if (!act && cm) {
-            const int bit = __ffs(cm) - 1;
-            cm &= cm - 1;
-            o = uint32_t(w) * 32 + uint32_t(bit);
-            p = pidx[o];
-            pe = pidx[o + 1];
-            act = p < pe;
-          }
-          if (act) {
-            uint32_t k[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) k[u] = p + u < pe ? uint32_t(pin[p + u]) & vmask : 0xFFFFFFFFu;
-            bool hit = false;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) hit = hit || (k[u] != 0xFFFFFFFFu && ((F[k[u] >> 5] >> (k[u] & 31)) & 1u));
-            raw += 4;
-            if (hit) {
-              r |= 1u << (o & 31);
-              act = false;
-            } else {
-              p += 4;
-              act = p < pe;
-            }
-          }
-        }
-        if (w < nwords) V[w] = r;
-      }
-      __syncthreads();
-    } else {
     // a unit spans at most unit_size (< 2^31) outer tuples: 32-bit offsets
     const K* uo = outer + s_unit[0];
     const uint32_t un = uint32_t(s_unit[1] - s_unit[0]);
@@ -639,58 +681,140 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
         }
       }
     }
-    }   // top-down
-    if (pull && a.drop_self && tid == 0) {
-      const uint32_t g = uint32_t(uint64_t(outer[gs[gi]]) >> a.b) & vmask;
-      res[g >> 5] &= ~(1u << (g & 31));
-    }
     __syncthreads();
-    // store the bitmap (coalesced) and clear it; count its bits.  With pull
-    // mode on, also sum the inner run lengths of the group's next delta (the
-    // raw results a top-down pass would mark next iteration) and choose the
-    // group's next mode.
-    const uint64_t* tfirst = static_cast<const uint64_t*>(static_cast<const void*>(table));
-    uint32_t mine = 0;
-    unsigned long long td = 0;
-    for (int j = tid; j < nwords; j += kDenseThreads) {
-      const uint32_t w = res[j];
-      gbm[j] = w;
-      mine += __popc(w);
-      res[j] = 0;
-      if (pull) s_bm[j] = 0;
-      if (pull_on)
-        for (uint32_t x = w; x; x &= x - 1) {
-          const uint32_t o = uint32_t(j) * 32 + uint32_t(__ffs(x) - 1);
-          td += tfirst[o + 1] - tfirst[o];
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mine += __shfl_xor_sync(0xffffffffu, mine, o);
-      td += __shfl_xor_sync(0xffffffffu, td, o);
-    }
-    if (lane == 0 && mine) atomicAdd(&s_cnt, (unsigned long long)mine);
-    if (lane == 0 && td) atomicAdd(&s_td, td);
-    __syncthreads();
-    if (tid == 0) {
-      counts[gi] = s_cnt;
-      if (pull_on) {
-        const uint32_t g = uint32_t(uint64_t(outer[gs[gi]]) >> a.b) & vmask;
-        const uint64_t nout = st->cnt[a.nout_cnt];
-        const uint64_t full_after = uint64_t(static_cast<const uint32_t*>(st->buf[a.fcnt_buf].ptr)[g]) + s_cnt;
-        const uint64_t cand = nout > full_after ? nout - full_after : 0;
-        const bool pull_next = 16ull * s_td > uint64_t(a.pull_k16) * cand + 16ull * s_cnt;
-        uint32_t* pbm = static_cast<uint32_t*>(st->buf[a.pull_bm_buf].ptr);
-        if (pull_next) atomicOr(&pbm[g >> 5], 1u << (g & 31));
-        else atomicAnd(&pbm[g >> 5], ~(1u << (g & 31)));
-      }
-      s_cnt = 0;   // read again only after the next group's first barrier
-      s_td = 0;
-    }
+    dense_finish<K>(a, st, s_bm, nullptr, gbm, gi, uint32_t(uint64_t(outer[gs[gi]]) >> a.b) & vmask, nwords, &s_cnt,
+                    &s_td);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) raw += __shfl_xor_sync(0xffffffffu, raw, o);
   if (lane == 0 && raw) atomicAdd((unsigned long long*)&st->cnt[a.raw_cnt], raw);
+}
+
+// Pull mode (see DenseArgs): one CTA per listed group.  The group's delta
+// values go into a frontier bitmap F and full's tuples of the group into V
+// (both sorted, so a warp combines the bits of one word before its atomic);
+// every candidate -- a value with inner tuples, not in V -- is new if one of
+// its inner tuples (o, k) has k in F.  A warp takes a candidate word at a time,
+// a lane per candidate: its first inner tuple (the smallest k, precomputed;
+// coalesced over the word) decides most of them, eight words in flight; then
+// each lane scans the rest of the runs of its own word's undecided candidates,
+// four tuples at a time until one k is in F, 32 words at once.
+constexpr int kPullCtasPerSm = 10;   // two bitmaps of up to 8 KB each; 48 registers
+template <typename K>
+__global__ void __launch_bounds__(kDenseThreads, kPullCtasPerSm) k_dense_pull(DenseArgs a) {
+  extern __shared__ __align__(16) uint32_t s_bm[];   // F, then V (2^b bits each)
+  __shared__ unsigned long long s_cnt, s_td;
+  __shared__ uint64_t s_gi;
+  DevState* st = a.st;
+  if ((st->overflow & a.skip_mask) || a.pull_inner_buf < 0) return;
+  const uint64_t ngroups = st->cnt[a.groups_cnt];
+  const uint64_t npull = st->cnt[a.pull_cnt];
+  const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
+  if (npull == 0 || st->buf[a.bm_buf].cap < ngroups * uint64_t(nwords) || st->buf[a.offs_buf].cap < ngroups + 1)
+    return;   // (k_dense_mark reports the capacities; this launch follows it)
+  const K* outer = static_cast<const K*>(st->buf[a.outer_buf].ptr);
+  const uint64_t* gs = static_cast<const uint64_t*>(st->buf[a.groups_buf].ptr);
+  const uint32_t* plist = static_cast<const uint32_t*>(st->buf[a.plist_buf].ptr);
+  const K* pin = static_cast<const K*>(st->buf[a.pull_inner_buf].ptr);
+  const uint64_t* pidx = static_cast<const uint64_t*>(st->buf[a.pull_index_buf].ptr);
+  const uint32_t* outbm = static_cast<const uint32_t*>(st->buf[a.pull_out_buf].ptr);
+  const uint32_t* firstk = static_cast<const uint32_t*>(st->buf[a.pull_first_buf].ptr);
+  uint32_t* bm = static_cast<uint32_t*>(st->buf[a.bm_buf].ptr);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nwarps = kDenseThreads / 32;
+  const uint32_t vmask = (1u << a.b) - 1;
+  uint32_t* F = s_bm;
+  uint32_t* V = s_bm + nwords;
+  for (int j = tid; j < 2 * nwords; j += kDenseThreads) s_bm[j] = 0;
+  if (tid == 0) {
+    s_cnt = 0;
+    s_td = 0;
+  }
+  unsigned long long raw = 0;
+  while (true) {
+    if (tid == 0) {
+      const uint64_t i = atomicAdd(&st->tile_ctr[a.ctr + 1], 1u);
+      s_gi = i < npull ? uint64_t(plist[i]) : ~0ull;
+    }
+    __syncthreads();
+    const uint64_t gi = s_gi;
+    if (gi == ~0ull) break;
+    const uint64_t o0 = gs[gi], o1 = gs[gi + 1];
+    const uint32_t g = uint32_t(uint64_t(outer[o0]) >> a.b) & vmask;
+    if (tid == 0) raw += o1 - o0;
+    sorted_run_to_bitmap<K>(F, outer, o0, o1, vmask, warp, nwarps);
+    if (a.full_buf >= 0) {
+      const uint64_t nlv = st->cnt[a.nlv_cnt], nk = (1ull << a.b) + 1;
+      const uint64_t* lvidx = static_cast<const uint64_t*>(st->buf[a.lvidx_buf].ptr);
+      const K* fl = static_cast<const K*>(st->buf[a.full_buf].ptr);
+      for (uint64_t lv = 0; lv < nlv; ++lv) {
+        const uint64_t r0 = lvidx[lv * nk + g], r1 = lvidx[lv * nk + g + 1];
+        if (tid == 0) raw += r1 - r0;
+        sorted_run_to_bitmap<K>(V, fl, r0, r1, vmask, warp, nwarps);
+      }
+    }
+    __syncthreads();
+    for (int base = warp * 32; base < nwords; base += nwarps * 32) {
+      const int wl = base + lane;
+      const uint32_t cm_l = wl < nwords ? (outbm[wl] & ~V[wl]) : 0u;
+      uint32_t any = __ballot_sync(0xffffffffu, cm_l != 0u);
+      uint32_t r_l = 0, m_l = 0;   // this lane's word: hits, and misses of the first tuple
+      // first tuples: a word at a time, a lane per candidate, eight words in flight
+      while (any) {
+        int jl[8];
+        uint32_t kf[8];
+        bool mine[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          jl[u] = any ? __ffs(any) - 1 : -1;
+          any = any ? any & (any - 1) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint32_t cm = __shfl_sync(0xffffffffu, cm_l, jl[u] & 31);
+          mine[u] = jl[u] >= 0 && ((cm >> lane) & 1u);
+          kf[u] = mine[u] ? firstk[uint32_t(base + jl[u]) * 32 + uint32_t(lane)] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const bool hit = mine[u] && ((F[kf[u] >> 5] >> (kf[u] & 31)) & 1u);
+          raw += mine[u];
+          const uint32_t hb = __ballot_sync(0xffffffffu, hit), mb = __ballot_sync(0xffffffffu, mine[u] && !hit);
+          if (lane == jl[u]) {
+            r_l = hb;
+            m_l = mb;
+          }
+        }
+      }
+      // the misses: every lane scans the rest of its own word's candidates'
+      // runs, four tuples at a time, the 32 words of the warp at once
+      for (uint32_t mm = m_l; mm; mm &= mm - 1) {
+        const uint32_t bit = uint32_t(__ffs(mm) - 1);
+        const uint32_t o = uint32_t(wl) * 32 + bit;
+        uint64_t p = pidx[o] + 1;
+        const uint64_t pe = pidx[o + 1];
+        bool hit = false;
+        while (p < pe && !hit) {
+          uint32_t k[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) k[q] = p + q < pe ? uint32_t(pin[p + q]) & vmask : 0xFFFFFFFFu;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) hit = hit || (k[q] != 0xFFFFFFFFu && ((F[k[q] >> 5] >> (k[q] & 31)) & 1u));
+          raw += min(uint64_t(4), pe - p);
+          p += 4;
+        }
+        if (hit) r_l |= 1u << bit;
+      }
+      if (wl < nwords) V[wl] = r_l;   // the results replace the word of V
+    }
+    __syncthreads();
+    if (a.drop_self && tid == 0) V[g >> 5] &= ~(1u << (g & 31));
+    __syncthreads();
+    dense_finish<K>(a, st, V, F, bm + gi * uint64_t(nwords), gi, g, nwords, &s_cnt, &s_td);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) raw += __shfl_xor_sync(0xffffffffu, raw, o);
+  if (lane == 0 && raw) atomicAdd((unsigned long long*)&st->cnt[a.pull_raw_cnt], raw);
 }
 
 // Phase 2 (one CTA): counts -> exclusive offsets; total and capacity check.

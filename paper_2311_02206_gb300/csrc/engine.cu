@@ -189,6 +189,9 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.chain_dfirst = new_slot(8);
   sc.chain_pre = new_slot(8);
   sc.chain_tfirst = new_slot(8);
+  sc.dense_plist = new_slot(4);
+  sc.pull_cnt = nslots++;
+  sc.pull_raw_cnt = nslots++;
   sc.read_m = new_slot(4);
   sc.read_rows = new_slot(8);
   sc.read_s0 = new_slot(4);
@@ -698,10 +701,13 @@ hisa_status Engine::compile() {
     R.pull = true;
     R.pull_inner = ocol == 0 ? I.base : I.rev;
     R.pull_index = I.table[ocol];
+    R.push_index = I.table[sp.inner_col];
     if (R.pull_out < 0) {
       R.pull_out = new_slot(4);
       R.pull_bm = new_slot(4);
       R.fcnt = new_slot(4);
+      R.pull_first = new_slot(4);
+      R.tdeg = new_slot(4);
       R.nout = nslots++;
     }
   }
@@ -959,7 +965,11 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
     ga.unit_size = unit_size;
     ga.bmm_buf = sc.dense_bmm;
     ga.bm_words = b >= 5 ? 1 << (b - 5) : 1;
-    if (pull) ga.pull_bm_buf = hr.pull_bm;
+    if (pull) {
+      ga.pull_bm_buf = hr.pull_bm;
+      ga.plist_buf = sc.dense_plist;
+      ga.pull_cnt = sc.pull_cnt;
+    }
   }
   Op d{};
   d.kind = Op::DENSE;
@@ -977,6 +987,11 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
     da.pull_bm_buf = hr.pull_bm;
     da.fcnt_buf = hr.fcnt;
     da.nout_cnt = hr.nout;
+    da.pull_first_buf = hr.pull_first;
+    da.tdeg_buf = hr.tdeg;
+    da.plist_buf = sc.dense_plist;
+    da.pull_cnt = sc.pull_cnt;
+    da.pull_raw_cnt = sc.pull_raw_cnt;
     da.pull_k16 = uint32_t(cfg.pull_ratio * 16.f + 0.5f);
   }
   ops.push_back(d);
@@ -997,15 +1012,23 @@ void Engine::emit_head(std::vector<Op>& ops, const std::vector<std::vector<StepP
   c.kind = Op::CTL;
   c.ctl.st = dst;
   c.ctl.skip_mask = 1;
+  auto cmd = [&](CtlCmd x) {   // a full command list goes out as its own launch
+    if (c.ctl.n == kMaxCtl) {
+      ops.push_back(c);
+      c.ctl.n = 0;
+    }
+    c.ctl.cmd[c.ctl.n++] = x;
+  };
   for (int r : idb) {
-    c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, rels[r].fresh, 0};
-    c.ctl.cmd[c.ctl.n++] = {kCtlZeroSmall, rels[r].hist, 8 * 256};
+    cmd({kCtlSetCnt, rels[r].fresh, 0});
+    cmd({kCtlZeroSmall, rels[r].hist, 8 * 256});
     if (rels[r].append) {
-      c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, rels[r].delta_next, 0};
-      c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, rels[r].sortf, 1};
+      cmd({kCtlSetCnt, rels[r].delta_next, 0});
+      cmd({kCtlSetCnt, rels[r].sortf, 1});
     }
   }
-  c.ctl.cmd[c.ctl.n++] = {kCtlSetCnt, sc.raw_cnt, 0};
+  cmd({kCtlSetCnt, sc.raw_cnt, 0});
+  cmd({kCtlSetCnt, sc.pull_raw_cnt, 0});
   ops.push_back(c);
   if (idb_inner) emit_idb_index(ops);
   for (auto& v : plans) {
@@ -1626,7 +1649,7 @@ hisa_status Engine::init_run_state() {
     }
   }
   hs.cnt[sc.tmp_cnt] = 0;
-  hs.cnt[sc.raw_cnt] = hs.cnt[sc.group_cnt] = 0;
+  hs.cnt[sc.raw_cnt] = hs.cnt[sc.group_cnt] = hs.cnt[sc.pull_raw_cnt] = 0;
   if (b + inst_bits <= kDirectMaxBits && (s = ensure(sc.dense_first, (1ull << (b + inst_bits)) + 2))) return s;
   bool any_chain = false;
   for (auto& v : planN) any_chain = any_chain || (!v.empty() && (v[0].chain || v[0].invert));
@@ -1640,6 +1663,9 @@ hisa_status Engine::init_run_state() {
       (s = ensure(sc.dense_done, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)) ||
       (s = ensure(sc.dense_mslot, std::min<uint64_t>(4 * nedb, 1ull << (b + inst_bits)) + 2)))
     return s;
+  bool any_pull = false;
+  for (int r : idb) any_pull = any_pull || rels[r].pull;
+  if (any_pull && (s = ensure(sc.dense_plist, std::min<uint64_t>(4 * nedb, 1ull << b) + 2))) return s;
   if ((s = ensure(sc.radix_status, (4 * nedb / kt + 2) * 256)) || (s = ensure(sc.offs, 4 * nedb + 1)) ||
       (s = ensure(sc.join_status, 4 * nedb / kJoinTile + 2)) || (s = ensure(sc.starts, 4 * nedb / kJoinChunk + 2)) ||
       (s = ensure(sc.split, 8 * nedb / 2048 + 2)) || (s = ensure(sc.setop_status, 8 * nedb / 2048 + 2)) ||
@@ -1664,7 +1690,9 @@ hisa_status Engine::init_run_state() {
     Relation& R = rels[r];
     if (!R.pull) continue;
     const uint64_t nw = b >= 5 ? (1ull << (b - 5)) : 1;
-    if ((s = ensure(R.fcnt, 1ull << b)) || (s = ensure(R.pull_bm, nw)) || (s = ensure(R.pull_out, nw))) return s;
+    if ((s = ensure(R.fcnt, 1ull << b)) || (s = ensure(R.pull_bm, nw)) || (s = ensure(R.pull_out, nw)) ||
+        (s = ensure(R.pull_first, 1ull << b)) || (s = ensure(R.tdeg, 1ull << b)))
+      return s;
     CU(cudaMemsetAsync(hs.buf[R.fcnt].ptr, 0, (1ull << b) * 4, stream));
     CU(cudaMemsetAsync(hs.buf[R.pull_bm].ptr, 0, nw * 4, stream));   // iteration 2 marks (push)
     hs.cnt[R.nout] = 0;
@@ -1673,7 +1701,7 @@ hisa_status Engine::init_run_state() {
   for (int r : idb) {
     const Relation& R = rels[r];
     if (!R.pull) continue;
-    PullOutArgs pa{dst, R.pull_index, b, R.pull_out, R.nout};
+    PullOutArgs pa{dst, R.pull_index, R.pull_inner, R.push_index, b, R.pull_out, R.pull_first, R.tdeg, R.nout};
     launch_pull_out(pa, grid, stream);
     if ((s = check_launch("pull out"))) return s;
   }
@@ -1765,6 +1793,9 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
             kstat[kKGroups].bytes += 16.0 * double(1u << b) + 8.0 * ng;
             // (+ the full levels' runs read for the set difference)
             kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + bmb + m * kb;
+            // pulled groups: their delta, full's runs and the inner tuples they
+            // scanned (the push term above still counts full for every group)
+            kstat[kKJoinPull].bytes += double(hs.cnt[sc.pull_raw_cnt]) * kb;
             kstat[kKDenseScan].bytes += 16.0 * ng;
             kstat[kKDenseEmit].bytes += bmb + nn * kb;
           } else {

@@ -57,6 +57,8 @@ struct Relation {
   bool pull = false;
   int pull_inner = -1, pull_index = -1;
   int pull_out = -1, nout = -1, pull_bm = -1, fcnt = -1;
+  int pull_first = -1, tdeg = -1;   // each o's first k; each k's push-run length
+  int push_index = -1;              // the push-ordered inner's direct index by k
 };
 
 // One binary join (or a one-atom projection) of a compiled rule variant.
@@ -106,6 +108,8 @@ struct Scratch {
   int dense_mslot, dense_bmm;   // multi-unit groups' bitmap slot and those bitmaps (kept zeroed)
   int chain_dfirst, chain_pre;  // a gathered Tmp: delta's direct index, offsets per inner tuple
   int chain_tfirst;             // a gathered Tmp's direct index by its kept column
+  int dense_plist = -1, pull_cnt = -1;   // pulled groups of the grouped bitmap join, and their count
+  int pull_raw_cnt = -1;                 // codes read by the pull kernel
   int read_m = -1, read_rows = -1;  // reading a column-swapped append-only full: its bit matrix, row offsets
   int read_s0 = -1, read_s1 = -1;   // and its device staging columns (kept across reads)
 

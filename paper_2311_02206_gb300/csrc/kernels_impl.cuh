@@ -260,14 +260,16 @@ void launch_join_dense(const DenseArgs& a, const Grid& g, cudaStream_t s) {
   CtlArgs c{};
   c.st = a.st;
   c.skip_mask = a.skip_mask;
-  c.n = 2;
+  c.n = 3;
   c.cmd[0] = {kCtlEpoch, 0, 0};
   c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
+  c.cmd[2] = {kCtlResetCtr, a.ctr + 1, 0};   // the pull kernel's group counter
   launch_ctl(c, s);
-  // one bitmap of 2^b bits; two (frontier and full) when groups may pull
-  const size_t smem = size_t(a.b >= 5 ? (1u << (a.b - 5)) : 1u) * 4 * (a.pull_inner_buf >= 0 ? 2 : 1);
+  const size_t smem = size_t(a.b >= 5 ? (1u << (a.b - 5)) : 1u) * 4;   // one bitmap of 2^b bits
   if (!a.units_ready) HISA_LAUNCH(kKDenseScan, s, (k_dense_units<K><<<1, 1024, 0, s>>>(a)));
   HISA_LAUNCH(kKJoinDense, s, (k_dense_mark<K><<<g.sms * kDenseCtasPerSm, kDenseThreads, smem, s>>>(a)));
+  if (a.pull_inner_buf >= 0)   // pulled groups: frontier and full bitmaps
+    HISA_LAUNCH(kKJoinPull, s, (k_dense_pull<K><<<g.sms * kPullCtasPerSm, kDenseThreads, 2 * smem, s>>>(a)));
   HISA_LAUNCH(kKDenseScan, s, (k_dense_scan<K><<<1, 1024, 0, s>>>(a)));
   HISA_LAUNCH(kKDenseEmit, s, (k_dense_emit<K><<<g.sms * kDenseCtasPerSm, kDenseThreads, 0, s>>>(a)));
   CtlArgs d{};
