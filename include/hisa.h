@@ -109,6 +109,14 @@ typedef void (*hisa_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
  * its next delta would mark outnumber, several times over, the values it
  * could still derive.  Same results. */
 #define HISA_FLAG_NO_PULL 64u
+/* Keep an append-only full as sorted levels.  By default, when the program
+ * has one IDB relation and it is written only by the grouped bitmap join
+ * (REACH, SG) over a domain of 2^8 .. 2^16 values, its full is a bit matrix of
+ * 2^(2b) bits (512 MB at b = 16), row = the kept column: the join's set
+ * difference is an AND-NOT of the group's row, each iteration's new tuples
+ * are ORed into it, and reads write its rows (transposed first when stored
+ * column-swapped) in order.  Same results. */
+#define HISA_FLAG_LEVELS 128u
 
 typedef struct {
   hisa_alloc_fn alloc;      /* NULL: cudaMallocAsync from a private pool */
@@ -123,7 +131,7 @@ typedef struct {
   int32_t device;           /* CUDA device ordinal; -1 = the current device */
   float pull_ratio;         /* pull mode switch point (HISA_FLAG_NO_PULL): a group pulls when the
                                inner runs its next delta would mark exceed pull_ratio times the
-                               values it could still derive (plus the delta's size); 0 = 8 */
+                               values it could still derive (plus the delta's size); 0 = 4 */
 } hisa_config;
 
 typedef struct hisa_ctx hisa_ctx;

@@ -18,7 +18,7 @@ hisa_status hisa_config_default(hisa_config* cfg) {
   cfg->max_iters = 1000000;
   cfg->flags = HISA_FLAG_LOG_FULL;
   cfg->device = -1;
-  cfg->pull_ratio = 8.0f;
+  cfg->pull_ratio = 4.0f;
   return HISA_OK;
 }
 

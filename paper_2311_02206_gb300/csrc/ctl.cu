@@ -83,7 +83,11 @@ __global__ void k_commit(CommitArgs a) {
   const uint32_t it = st->iter;
   for (int r = 0; r < a.nrel; ++r) {
     const uint64_t nd = st->cnt[a.delta_next[r]];
-    if (nd > 0 && a.append_nlv1[r] > 0) {
+    if (nd > 0 && a.add_full[r]) {
+      // delta was ORed into full's bit matrix
+      st->cnt[a.full[r]] += nd;
+      any = true;
+    } else if (nd > 0 && a.append_nlv1[r] > 0) {
       // delta was appended to full as a new level
       st->cnt[a.full[r]] += nd;
       const uint64_t lv = ++st->cnt[a.append_nlv1[r] - 1];
@@ -339,7 +343,7 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
 
 const char* const kKernelNames[kKindCount] = {
     "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
-    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level", "chain_len", "chain_scan", "chain_gather", "join_dense_pull"};
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level", "chain_len", "chain_scan", "chain_gather", "join_dense_pull", "matrix_merge"};
 
 thread_local KernelTimer* g_timer = nullptr;
 thread_local uint64_t g_launches = 0;

@@ -192,15 +192,21 @@ struct DenseArgs {
   int tdeg_buf = -1;                    // u32 [2^b]: each k's run length in the push-ordered inner
   int plist_buf = -1, pull_cnt = -1;    // pulled groups (indices, written by the group compaction)
   int pull_raw_cnt = -1;                // cnt slot: codes the pull kernel read (delta, full, inner tuples)
+  // full kept as a bit matrix (fbm_buf >= 0; b <= kMatrixMaxBits): row g holds
+  // bit o for every (g, o) in full, 2^b bits per row.  The difference against
+  // full is then one AND-NOT of the group's row; full_buf is -1.
+  int fbm_buf = -1;
   uint32_t pull_k16 = 64;
 };
 
 // two bitmaps (frontier and full) of 2^b bits in shared memory
 constexpr int kPullMaxBits = 16;
+// a full kept as a bit matrix: 2^(2b) bits (512 MB at b = 16)
+constexpr int kMatrixMaxBits = 16;
 // default switch point, x16: a group pulls when the inner runs its next delta
-// would mark exceed 8x its candidates plus the delta's size (R-MAT 16: the
-// fastest of 1, 2, 4, 8, 16 by 0.2-3 ms per fixpoint)
-constexpr uint32_t kPullK16 = 128;
+// would mark exceed 4x its candidates plus the delta's size (R-MAT 16 with
+// full as a bit matrix: 23.3 / 23.5 / 27.3 ms per fixpoint at 4 / 8 / 16)
+constexpr uint32_t kPullK16 = 64;
 
 // Values o with inner tuples (a non-empty run in the direct index by o), as a
 // bitmap, and their number (added to cnt[nout_cnt]).
@@ -217,40 +223,31 @@ struct PullOutArgs {
   int nout_cnt;
 };
 
-// OR of `bits` into s[word] for the 32 lanes of a warp whose words do not
-// decrease from lane to lane (values taken in sorted order): lanes of one
-// word are combined first (a segmented OR by shuffles), so each distinct word
-// takes one shared-memory atomic instead of one per lane.
-__device__ __forceinline__ void seg_or_sorted(uint32_t* s, uint32_t word, uint32_t bits, bool valid) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t w = valid ? word : 0xFFFFFFFFu;
-  uint32_t acc = valid ? bits : 0u;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t ow = __shfl_down_sync(0xffffffffu, w, d);
-    const uint32_t oa = __shfl_down_sync(0xffffffffu, acc, d);
-    if (lane + d < 32 && ow == w) acc |= oa;
-  }
-  const uint32_t pw = __shfl_up_sync(0xffffffffu, w, 1);
-  if (valid && (lane == 0 || pw != w) && (acc & ~s[w])) atomicOr(&s[w], acc);
-}
-
 // The values (low b bits) of the sorted codes src[r0 .. r1) into the bitmap
 // `bm`, by the calling warp and the other warps of the CTA (warp of nwarps):
-// 256 codes per warp per step, eight loads in flight per lane.
+// each lane takes eight consecutive codes (a warp reads 1 KB per step, all
+// eight loads in flight), ORs the bits of neighbours that share a word in
+// registers and issues one shared-memory atomic per distinct word.
 template <typename K>
 __device__ __forceinline__ void sorted_run_to_bitmap(uint32_t* bm, const K* src, uint64_t r0, uint64_t r1,
                                                      uint32_t vmask, int warp, int nwarps) {
   const int lane = threadIdx.x & 31;
-  for (uint64_t i0 = r0 + uint64_t(warp) * 256; i0 < r1; i0 += uint64_t(nwarps) * 256) {
+  for (uint64_t i = r0 + (uint64_t(warp) * 32 + lane) * 8; i < r1; i += uint64_t(nwarps) * 256) {
     uint32_t v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const uint64_t i = i0 + uint64_t(u) * 32 + lane;
-      v[u] = i < r1 ? uint32_t(src[i]) & vmask : 0u;
-    }
+    for (int u = 0; u < 8; ++u) v[u] = i + u < r1 ? uint32_t(src[i + u]) & vmask : 0xFFFFFFFFu;
+    uint32_t cw = v[0] >> 5, acc = 0;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) seg_or_sorted(bm, v[u] >> 5, 1u << (v[u] & 31), i0 + uint64_t(u) * 32 + lane < r1);
+    for (int u = 0; u < 8; ++u) {
+      if (v[u] == 0xFFFFFFFFu) break;
+      if ((v[u] >> 5) != cw) {
+        if (acc & ~bm[cw]) atomicOr(&bm[cw], acc);
+        cw = v[u] >> 5;
+        acc = 0;
+      }
+      acc |= 1u << (v[u] & 31);
+    }
+    if (acc && (acc & ~bm[cw])) atomicOr(&bm[cw], acc);
   }
 }
 
@@ -334,6 +331,68 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_starts(GroupArgs a) {
       }
     }
     __syncthreads();
+  }
+}
+
+// A full kept as a bit matrix takes a committed iteration's delta: each
+// group's bitmap (the grouped join's output, indexed by group) ORed into the
+// row of its kept value, and |full_g| recounted from the row.  Idempotent, so
+// a tail re-run after a buffer grew repeats it safely.  A warp per group.
+struct MatrixArgs {
+  DevState* st;
+  int groups_buf, groups_cnt;   // group starts into the outer relation
+  int outer_buf;                // the outer codes (kept value in the high half)
+  int bm_buf;                   // u32 [groups][2^b / 32]: each group's new tuples
+  int codes_buf, codes_cnt;     // k_matrix_codes: codes (kept value high) to add
+  int b;
+  int fbm_buf, fcnt_buf;
+  int skip_mask;
+  int gate1;                    // k_matrix_codes runs only when cnt[gate1 - 1] != 0 (0: always)
+};
+template <typename K>
+__global__ void k_matrix_merge(MatrixArgs a) {
+  DevState* st = a.st;
+  if (st->overflow & a.skip_mask) return;
+  const uint64_t ngroups = st->cnt[a.groups_cnt];
+  const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
+  const uint32_t vmask = (1u << a.b) - 1;
+  const K* outer = static_cast<const K*>(st->buf[a.outer_buf].ptr);
+  const uint64_t* gs = static_cast<const uint64_t*>(st->buf[a.groups_buf].ptr);
+  const uint32_t* bm = static_cast<const uint32_t*>(st->buf[a.bm_buf].ptr);
+  uint32_t* fbm = static_cast<uint32_t*>(st->buf[a.fbm_buf].ptr);
+  uint32_t* fcnt = static_cast<uint32_t*>(st->buf[a.fcnt_buf].ptr);
+  const int lane = threadIdx.x & 31;
+  for (uint64_t gi = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5; gi < ngroups;
+       gi += (uint64_t(gridDim.x) * blockDim.x) >> 5) {
+    const uint32_t g = uint32_t(uint64_t(outer[gs[gi]]) >> a.b) & vmask;
+    const uint32_t* src = bm + gi * uint64_t(nwords);
+    uint32_t* row = fbm + uint64_t(g) * nwords;
+    uint32_t c = 0;
+    for (int j = lane; j < nwords; j += 32) {
+      const uint32_t x = row[j] | src[j];
+      row[j] = x;
+      c += __popc(x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) fcnt[g] = c;
+  }
+}
+// The same from codes (kept value in the high half): iteration 1's delta.
+template <typename K>
+__global__ void k_matrix_codes(MatrixArgs a) {
+  DevState* st = a.st;
+  if ((st->overflow & a.skip_mask) || (a.gate1 > 0 && st->cnt[a.gate1 - 1] == 0)) return;
+  const uint64_t n = st->cnt[a.codes_cnt];
+  const K* codes = static_cast<const K*>(st->buf[a.codes_buf].ptr);
+  uint32_t* fbm = static_cast<uint32_t*>(st->buf[a.fbm_buf].ptr);
+  uint32_t* fcnt = static_cast<uint32_t*>(st->buf[a.fcnt_buf].ptr);
+  const uint32_t vmask = (1u << a.b) - 1;
+  const uint64_t nwords = a.b >= 5 ? (1ull << (a.b - 5)) : 1;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t g = uint32_t(uint64_t(codes[i]) >> a.b) & vmask, o = uint32_t(codes[i]) & vmask;
+    const uint32_t bit = 1u << (o & 31);
+    if (!(atomicOr(&fbm[uint64_t(g) * nwords + (o >> 5)], bit) & bit)) atomicAdd(&fcnt[g], 1u);
   }
 }
 
@@ -649,6 +708,14 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
       const uint32_t g = uint32_t(uint64_t(outer[gs[gi]]) >> a.b) & vmask;
       atomicAnd(&s_bm[g >> 5], ~(1u << (g & 31)));
     }
+    if (a.fbm_buf >= 0) {   // full as a bit matrix: clear the bits of the group's row
+      const uint64_t g = (uint64_t(outer[gs[gi]]) >> a.b) & vmask;
+      const uint32_t* row = static_cast<const uint32_t*>(st->buf[a.fbm_buf].ptr) + g * uint64_t(nwords);
+      for (int j = tid; j < nwords; j += kDenseThreads) {   // atomic: the filter above may clear a bit too
+        const uint32_t f = row[j];
+        if (s_bm[j] & f) atomicAnd(&s_bm[j], ~f);
+      }
+    }
     if (a.full_buf >= 0) {
       const uint64_t nlv = st->cnt[a.nlv_cnt], nk = (1ull << a.b) + 1;
       const uint64_t* lvidx = static_cast<const uint64_t*>(st->buf[a.lvidx_buf].ptr);
@@ -754,9 +821,11 @@ __global__ void __launch_bounds__(kDenseThreads, kPullCtasPerSm) k_dense_pull(De
       }
     }
     __syncthreads();
+    const uint32_t* frow = a.fbm_buf >= 0 ? static_cast<const uint32_t*>(st->buf[a.fbm_buf].ptr) + g * uint64_t(nwords)
+                                          : V;   // full of the group as bits
     for (int base = warp * 32; base < nwords; base += nwarps * 32) {
       const int wl = base + lane;
-      const uint32_t cm_l = wl < nwords ? (outbm[wl] & ~V[wl]) : 0u;
+      const uint32_t cm_l = wl < nwords ? (outbm[wl] & ~frow[wl]) : 0u;
       uint32_t any = __ballot_sync(0xffffffffu, cm_l != 0u);
       uint32_t r_l = 0, m_l = 0;   // this lane's word: hits, and misses of the first tuple
       // first tuples: a word at a time, a lane per candidate, eight words in flight

@@ -681,6 +681,16 @@ hisa_status Engine::compile() {
       Relation& A = rels[sp.inner_rel];
       if (!A.idb && sp.inner_col == 0) A.need_idx[1] = true;   // an EDB relation builds its (c1, c0) copy
     }
+  // full as a bit matrix (dense.cuh) for the one IDB relation of a program
+  // whose writer is the grouped bitmap join: the join is then the last step
+  // of every iteration's join stage, so the matrix takes its delta after it
+  // without any later overflow of that stage re-running the iteration
+  for (int r : idb) {
+    Relation& R = rels[r];
+    R.mfull = R.append && idb.size() == 1 && b >= 8 && b <= kMatrixMaxBits && !(cfg.flags & HISA_FLAG_LEVELS);
+    if (R.mfull && R.fbm < 0) R.fbm = new_slot(4);
+    if (R.mfull && R.fcnt < 0) R.fcnt = new_slot(4);
+  }
   // pull mode (dense.cuh) for a relation written only by a one-step grouped
   // bitmap join of its delta with an EDB relation (REACH's recursive rule):
   // the inner relation is also sorted and directly indexed by its other column
@@ -705,7 +715,7 @@ hisa_status Engine::compile() {
     if (R.pull_out < 0) {
       R.pull_out = new_slot(4);
       R.pull_bm = new_slot(4);
-      R.fcnt = new_slot(4);
+      if (R.fcnt < 0) R.fcnt = new_slot(4);
       R.pull_first = new_slot(4);
       R.tdeg = new_slot(4);
       R.nout = nslots++;
@@ -977,8 +987,10 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
                       inner_buf >= 0 ? inner_buf : sp.inner_col == 0 ? ir.base : ir.rev,
                       table_buf >= 0 ? table_buf : ir.table[sp.inner_col], b,
                       out, out, sc.total, sc.raw_cnt, sc.dense_bm, sc.dense_status, 4, 1, 0,
-                      inner_buf >= 0 || direct_bits > 0, hr.append ? hr.full : -1, hr.lvidx, hr.nlv, sp.nfilt > 0,
+                      inner_buf >= 0 || direct_bits > 0, hr.append && !hr.mfull ? hr.full : -1, hr.lvidx, hr.nlv,
+                      sp.nfilt > 0,
                       sc.dense_units, sc.dense_done, unit_size, sc.dense_mslot, sc.dense_bmm, units_ready};
+  if (hr.mfull) d.dense.fbm_buf = hr.fbm;
   if (pull) {
     DenseArgs& da = d.dense;
     da.pull_inner_buf = hr.pull_inner;
@@ -995,6 +1007,12 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
     da.pull_k16 = uint32_t(cfg.pull_ratio * 16.f + 0.5f);
   }
   ops.push_back(d);
+  if (hr.mfull) {   // the groups' new tuples into full's bit matrix (skipped if this stage overflowed)
+    Op m{};
+    m.kind = Op::MMERGE;
+    m.matrix = MatrixArgs{dst, sc.groups, sc.group_cnt, sp.outer_slot, sc.dense_bm, -1, -1, b, hr.fbm, hr.fcnt, 1, 0};
+    ops.push_back(m);
+  }
   if (hr.append) {   // no unique pass in the tail; |new| (statistics) = |delta|
     Op f{};
     f.kind = Op::CTL;
@@ -1232,6 +1250,13 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
       a.stage_bit = 1;
       a.gate1 = R.sortf + 1;   // skipped when the dense join wrote delta
       ops.push_back(o);
+      if (R.mfull) {   // a delta from the unique (iteration 1) into full's bit matrix
+        Op m{};
+        m.kind = Op::MCODES;
+        m.matrix = MatrixArgs{dst, -1, -1, -1, -1, R.delta_next, R.delta_next, b, R.fbm, R.fcnt, 3, R.sortf + 1};
+        ops.push_back(m);
+        continue;
+      }
       Op p{};
       p.kind = Op::APPEND;
       p.append = AppendArgs{dst, R.delta_next, R.delta_next, R.full, R.full, R.lvidx, R.nlv, b, b, 3, 1};
@@ -1324,7 +1349,8 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
     c.commit.delta_next[i] = R.delta_next;
     c.commit.history[i] = R.history;
     c.commit.fresh[i] = R.fresh;
-    c.commit.append_nlv1[i] = R.append ? R.nlv + 1 : 0;
+    c.commit.append_nlv1[i] = R.append && !R.mfull ? R.nlv + 1 : 0;
+    c.commit.add_full[i] = R.mfull ? 1 : 0;
   }
   c.commit.max_levels = kMaxLevels;
   c.commit.force = force;
@@ -1351,6 +1377,8 @@ hisa_status Engine::exec_t(const std::vector<Op>& ops) {
       case Op::GROUPS: launch_group_starts<K>(o.groups, grid, stream); break;
       case Op::DENSE: launch_join_dense<K>(o.dense, grid, stream); break;
       case Op::CHAIN: launch_chain<K>(o.chain, grid, stream); break;
+      case Op::MMERGE: launch_matrix_merge<K>(o.matrix, grid, stream); break;
+      case Op::MCODES: launch_matrix_codes<K>(o.matrix, grid, stream); break;
     }
   }
   return check_launch("kernel launch");
@@ -1688,6 +1716,14 @@ hisa_status Engine::init_run_state() {
   inst_hist.assign(idb.size(), {});
   for (int r : idb) {
     Relation& R = rels[r];
+    if (!R.mfull) continue;
+    const uint64_t words = (1ull << (2 * b)) / 32;
+    if ((s = ensure(R.fbm, words)) || (s = ensure(R.fcnt, 1ull << b))) return s;
+    CU(cudaMemsetAsync(hs.buf[R.fbm].ptr, 0, words * 4, stream));
+    CU(cudaMemsetAsync(hs.buf[R.fcnt].ptr, 0, (1ull << b) * 4, stream));
+  }
+  for (int r : idb) {
+    Relation& R = rels[r];
     if (!R.pull) continue;
     const uint64_t nw = b >= 5 ? (1ull << (b - 5)) : 1;
     if ((s = ensure(R.fcnt, 1ull << b)) || (s = ensure(R.pull_bm, nw)) || (s = ensure(R.pull_out, nw)) ||
@@ -1792,7 +1828,9 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
             kstat[kKIndex].bytes += 8.0 * double(1u << b);
             kstat[kKGroups].bytes += 16.0 * double(1u << b) + 8.0 * ng;
             // (+ the full levels' runs read for the set difference)
-            kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + bmb + m * kb;
+            // (+ full: its row of the bit matrix, or the levels' runs of the group)
+            kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + bmb + (R.mfull ? bmb : m * kb);
+            if (R.mfull) kstat[kKMatrix].bytes += 3.0 * bmb;   // group bitmaps read, rows read and written
             // pulled groups: their delta, full's runs and the inner tuples they
             // scanned (the push term above still counts full for every group)
             kstat[kKJoinPull].bytes += double(hs.cnt[sc.pull_raw_cnt]) * kb;
@@ -1805,7 +1843,8 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
             // unique of new into delta, then delta copied behind full with its
             // level index
             if (nn > 0 && !dense) kstat[kKSetop].bytes += (nn + nd) * kb;
-            if (nd > 0) kstat[kKAppend].bytes += 2.0 * nd * kb + 8.0 * double((1u << b) + 1);
+            if (nd > 0 && !R.mfull) kstat[kKAppend].bytes += 2.0 * nd * kb + 8.0 * double((1u << b) + 1);
+            if (nd > 0 && R.mfull && !dense) kstat[kKMatrix].bytes += nd * kb + 8.0 * nd;
           } else if (R.log && hs.cnt[R.bigf]) {
             // small level folded in, then new merged into the large level
             const double lp = double(l_prev[i]);
@@ -2141,17 +2180,23 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
   void *t0 = nullptr, *t1 = nullptr;
   hisa_status s;
   int src = r.idb ? r.full : r.base;
+  // a full kept as a bit matrix: its rows written in order, transposed first
+  // when stored column-swapped (the row matrix is needed then: no fallback)
+  const bool matrix = r.idb && r.mfull;
+  if (matrix && (((s = ensure(sc.read_rows, (1ull << b) + 1))) ||
+                 (r.order == 1 && (s = ensure(sc.read_m, (1ull << (2 * b)) / 32)))))
+    return s;
   // an append-only full stored in declared order: its levels merged by
   // group straight into the columns (k_levels_read), no sort
-  const bool levels = r.idb && r.append && r.order == 0;
+  const bool levels = r.idb && r.append && !matrix && r.order == 0;
   // stored column-swapped: transposed through a bit matrix over the domain
   // (k_levels_transpose; 2^(2b) bits), no sort
-  bool transposed = r.idb && r.append && r.order == 1 && b >= 8 && b <= 16;
+  bool transposed = r.idb && r.append && !matrix && r.order == 1 && b >= 8 && b <= 16;
   if (transposed && (ensure(sc.read_m, (1ull << (2 * b)) / 32) || ensure(sc.read_rows, (1ull << b) + 1))) {
     transposed = false;   // the matrix does not fit (budget): sort instead
     last_error.clear();
   }
-  if (r.idb && (r.order == 1 || r.append) && !levels && !transposed) {
+  if (r.idb && (r.order == 1 || r.append) && !levels && !transposed && !matrix) {
     // stored (c1, c0), or as unmerged levels: (exchange the columns and) sort,
     // so the caller gets the lexicographic order of the declared columns
     const int kt = wide ? radix_tile<uint64_t>() : radix_tile<uint32_t>();
@@ -2200,7 +2245,7 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
       // the row emit of a transposed read writes the host link slower than
       // the copy engine does: stage in device memory (kept for the next
       // read) when it fits
-      if (transposed && ensure(sc.read_s0, size) == HISA_OK && ensure(sc.read_s1, size) == HISA_OK) {
+      if ((transposed || matrix) && ensure(sc.read_s0, size) == HISA_OK && ensure(sc.read_s1, size) == HISA_OK) {
         d0 = static_cast<uint32_t*>(hs.buf[sc.read_s0].ptr);
         d1 = static_cast<uint32_t*>(hs.buf[sc.read_s1].ptr);
       } else {
@@ -2216,7 +2261,14 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
       d1 = static_cast<uint32_t*>(t1);
     }
   }
-  if (transposed) {
+  if (matrix) {
+    uint32_t* fbm = static_cast<uint32_t*>(hs.buf[r.fbm].ptr);
+    uint32_t* m = r.order == 1 ? static_cast<uint32_t*>(hs.buf[sc.read_m].ptr) : fbm;
+    LevelsTransposeArgs ta{dst, -1, -1, -1, b, m, static_cast<uint64_t*>(hs.buf[sc.read_rows].ptr), d0, d1};
+    MatrixTransposeArgs mt{fbm, m, b};
+    if (wide) launch_matrix_read<uint64_t>(mt, ta, r.order == 1, grid, stream);
+    else launch_matrix_read<uint32_t>(mt, ta, r.order == 1, grid, stream);
+  } else if (transposed) {
     LevelsTransposeArgs ta{dst, r.full, r.lvidx, r.nlv, b, static_cast<uint32_t*>(hs.buf[sc.read_m].ptr),
                            static_cast<uint64_t*>(hs.buf[sc.read_rows].ptr), d0, d1};
     if (wide) launch_levels_transpose<uint64_t>(ta, grid, stream);

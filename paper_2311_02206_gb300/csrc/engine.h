@@ -59,6 +59,9 @@ struct Relation {
   int pull_out = -1, nout = -1, pull_bm = -1, fcnt = -1;
   int pull_first = -1, tdeg = -1;   // each o's first k; each k's push-run length
   int push_index = -1;              // the push-ordered inner's direct index by k
+  // full kept as a bit matrix (HISA_FLAG_LEVELS off): row g, bit o for (g, o)
+  bool mfull = false;
+  int fbm = -1;
 };
 
 // One binary join (or a one-atom projection) of a compiled rule variant.
@@ -78,7 +81,8 @@ struct StepPlan {
 };
 
 struct Op {
-  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT, APPEND, GROUPS, CHAIN } kind;
+  enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT, APPEND, GROUPS, CHAIN,
+              MMERGE, MCODES } kind;
   CtlArgs ctl;
   JoinArgs join;
   RadixPassArgs pass;
@@ -94,6 +98,7 @@ struct Op {
   AppendArgs append;
   DenseArgs dense;
   ChainArgs chain;
+  MatrixArgs matrix;
 };
 
 struct Scratch {

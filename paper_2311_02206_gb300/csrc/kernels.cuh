@@ -55,6 +55,8 @@ struct CommitArgs {
   // (0: not append-only); the commit adds delta's size to full's count and
   // one level, and asks the host to compact past max_levels
   int append_nlv1[8];
+  // full kept as a bit matrix: the commit only adds delta's size to full's count
+  int add_full[8];
   int max_levels;
   int force;   // commit even when no delta is non-empty (first iteration)
 };
@@ -131,7 +133,7 @@ struct SwapArgs {
 
 enum KernelKind : int {
   kKEncode, kKDecode, kKRuns, kKHist, kKRadixPass, kKSetopPartition, kKSetop, kKIndex,
-  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKAppend, kKChainLen, kKChainScan, kKChainGather, kKJoinPull, kKindCount
+  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKAppend, kKChainLen, kKChainScan, kKChainGather, kKJoinPull, kKMatrix, kKindCount
 };
 extern const char* const kKernelNames[kKindCount];
 
@@ -190,6 +192,12 @@ template <typename K> void launch_join_dense(const DenseArgs& a, const Grid& g, 
 template <typename K> void launch_chain(const ChainArgs& a, const Grid& g, cudaStream_t s);   // len + scan + gather
 template <typename K> void launch_levels_read(const LevelsReadArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_levels_transpose(const LevelsTransposeArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_matrix_merge(const MatrixArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_matrix_codes(const MatrixArgs& a, const Grid& g, cudaStream_t s);
+// a full kept as a bit matrix read in the declared order: transposed (order 1)
+// or read as it is (order 0), then its rows counted, scanned and written
+template <typename K> void launch_matrix_read(const MatrixTransposeArgs& t, const LevelsTransposeArgs& a, bool transpose,
+                                              const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_hist(const InstArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_inst_bounds(const InstArgs& a, const Grid& g, cudaStream_t s);
 void launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, const Grid& g, cudaStream_t s);

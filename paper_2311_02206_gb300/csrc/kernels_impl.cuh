@@ -192,6 +192,22 @@ void launch_levels_transpose(const LevelsTransposeArgs& a, const Grid& g, cudaSt
   HISA_LAUNCH(kKDecode, s, (k_rows_emit<K><<<g.sms * 8, kDenseThreads, 0, s>>>(a)));
 }
 template <typename K>
+void launch_matrix_merge(const MatrixArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKMatrix, s, (k_matrix_merge<K><<<g.sms * 8, 256, 0, s>>>(a)));
+}
+template <typename K>
+void launch_matrix_codes(const MatrixArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKMatrix, s, (k_matrix_codes<K><<<g.small, 256, 0, s>>>(a)));
+}
+template <typename K>
+void launch_matrix_read(const MatrixTransposeArgs& t, const LevelsTransposeArgs& a, bool transpose, const Grid& g,
+                        cudaStream_t s) {
+  if (transpose) HISA_LAUNCH(kKDecode, s, (k_matrix_transpose<<<g.sms * 8, 256, 0, s>>>(t)));
+  HISA_LAUNCH(kKDecode, s, (k_rows_count<K><<<g.small, 256, 0, s>>>(a)));
+  HISA_LAUNCH(kKDecode, s, (k_rows_scan<K><<<1, 1024, 0, s>>>(a)));
+  HISA_LAUNCH(kKDecode, s, (k_rows_emit<K><<<g.sms * 8, kDenseThreads, 0, s>>>(a)));
+}
+template <typename K>
 void launch_append(const AppendArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKAppend, s, (k_append<K><<<g.small * 2, 256, 0, s>>>(a)));
 }
@@ -326,6 +342,10 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_chain<K>(const ChainArgs&, const Grid&, cudaStream_t);            \
   template void launch_levels_read<K>(const LevelsReadArgs&, const Grid&, cudaStream_t);  \
   template void launch_levels_transpose<K>(const LevelsTransposeArgs&, const Grid&, cudaStream_t); \
+  template void launch_matrix_merge<K>(const MatrixArgs&, const Grid&, cudaStream_t);    \
+  template void launch_matrix_codes<K>(const MatrixArgs&, const Grid&, cudaStream_t);    \
+  template void launch_matrix_read<K>(const MatrixTransposeArgs&, const LevelsTransposeArgs&, bool, const Grid&, \
+                                      cudaStream_t);                                     \
   template void launch_radix_hist<K>(const RadixHistArgs&, const Grid&, cudaStream_t);   \
   template void launch_radix_pass<K>(const RadixPassArgs&, const Grid&, cudaStream_t);   \
   template void launch_setop<K>(const SetopArgs&, const Grid&, cudaStream_t);            \

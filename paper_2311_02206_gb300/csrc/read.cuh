@@ -80,6 +80,51 @@ __global__ void __launch_bounds__(1024) k_levels_transpose(LevelsTransposeArgs a
   }
 }
 
+// Transpose of a full kept as a bit matrix (row = stored first column) into
+// M (row = declared first column): a CTA per tile of 256 x 256 bits; each
+// warp loads 32 rows x 8 words (32 contiguous bytes per row), transposes its
+// eight 32 x 32-bit blocks with five shuffle-and-mask stages, and the tile is
+// written back through shared memory as 256 rows x 8 words.
+struct MatrixTransposeArgs {
+  const uint32_t* src;   // 2^(2b) bits, row-major
+  uint32_t* dst;         // 2^(2b) bits, row-major, dst[c][r] = src[r][c]
+  int b;
+};
+__device__ __forceinline__ uint32_t transpose32_lane(uint32_t x) {
+  // lane r holds row r of a 32 x 32 bit block (bit c = column c); returns
+  // row r of the transposed block
+  const int lane = threadIdx.x & 31;
+  const uint32_t lo[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~lo[s]) | ((y & ~lo[s]) >> j)) : ((x & lo[s]) | ((y & lo[s]) << j));
+  }
+  return x;
+}
+static __global__ void __launch_bounds__(256) k_matrix_transpose(MatrixTransposeArgs a) {
+  __shared__ uint32_t s_t[256][9];   // [transposed row][word], padded
+  const uint64_t n = 1ull << a.b, nw = n / 32, tiles = n / 256;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (uint64_t t = blockIdx.x; t < tiles * tiles; t += gridDim.x) {
+    const uint64_t tr = t / tiles, tc = t % tiles;   // source rows [256 tr, +256), columns [256 tc, +256)
+    const uint32_t* srow = a.src + (tr * 256 + warp * 32 + lane) * nw + tc * 8;
+    uint32_t w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) w[u] = srow[u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s_t[u * 32 + lane][warp] = transpose32_lane(w[u]);
+    __syncthreads();
+    // transposed row R = 256 tc + r holds, in words 8 tr .. 8 tr + 7, the bits of source rows 256 tr ..
+    const int r = threadIdx.x;
+    uint32_t* drow = a.dst + (tc * 256 + r) * nw + tr * 8;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) drow[u] = s_t[r][u];
+    __syncthreads();
+  }
+}
+
 template <typename K>
 __global__ void k_rows_count(LevelsTransposeArgs a) {
   const uint64_t ng = 1ull << a.b, nw = ng / 32;

@@ -25,6 +25,7 @@ FLAG_NO_DENSE = 8
 FLAG_HASH_INDEX = 16
 FLAG_NO_CHAIN = 32
 FLAG_NO_PULL = 64
+FLAG_LEVELS = 128
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
