@@ -246,6 +246,8 @@ KERNEL_SOURCES = {   # the sources a kernel's counters depend on
     "join_write": ["join.cuh", "common.cuh"],
     "join_count": ["join.cuh", "common.cuh"],
     "join_dense_mark": ["dense.cuh", "join.cuh", "common.cuh"],
+    "join_dense_pull": ["dense.cuh", "join.cuh", "common.cuh"],
+    "join_dense_emit": ["dense.cuh", "join.cuh", "common.cuh"],
     "setop_diff_probe": ["setops.cuh", "common.cuh"],
 }
 

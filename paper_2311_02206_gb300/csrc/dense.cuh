@@ -186,7 +186,7 @@ struct DenseArgs {
   int pull_inner_buf = -1, pull_index_buf = -1;   // inner codes (o, k) sorted; direct index by o
   int pull_out_buf = -1;                // u32 [2^b / 32]: values o with inner tuples
   int pull_bm_buf = -1;                 // u32 [2^b / 32]: bit g = group g pulls (this and next iteration)
-  int fcnt_buf = -1;                    // u32 [2^b]: |full_g| (kept by the append of each level)
+  int fcnt_buf = -1;                    // u32 [2^b]: |full_g| (kept by the append of each level, or by the emit)
   int nout_cnt = -1;                    // cnt slot: number of values o with inner tuples
   int pull_first_buf = -1;              // u32 [2^b]: each o's first k (PullOutArgs)
   int tdeg_buf = -1;                    // u32 [2^b]: each k's run length in the push-ordered inner
@@ -196,6 +196,11 @@ struct DenseArgs {
   // bit o for every (g, o) in full, 2^b bits per row.  The difference against
   // full is then one AND-NOT of the group's row; full_buf is -1.
   int fbm_buf = -1;
+  // the previous iteration's group bitmaps (the bitmap slots are swapped after
+  // every committed iteration) and, per kept value, its group index there
+  // (written by the emit): from iteration 3 on the pull kernel copies a
+  // group's frontier from there instead of reading its delta codes
+  int prev_bm_buf = -1, prev_gi_buf = -1;
   uint32_t pull_k16 = 64;
 };
 
@@ -334,10 +339,11 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_starts(GroupArgs a) {
   }
 }
 
-// A full kept as a bit matrix takes a committed iteration's delta: each
-// group's bitmap (the grouped join's output, indexed by group) ORed into the
-// row of its kept value, and |full_g| recounted from the row.  Idempotent, so
-// a tail re-run after a buffer grew repeats it safely.  A warp per group.
+// A full kept as a bit matrix takes the new tuples of iterations >= 2 in the
+// grouped join's emit (k_dense_emit: each group's bitmap ORed into the row of
+// its kept value, |full_g| recounted from the row); a delta of iteration 1
+// (from the sort + unique) goes in by codes here, idempotently, so a tail
+// re-run after a buffer grew repeats it safely.
 struct MatrixArgs {
   DevState* st;
   int groups_buf, groups_cnt;   // group starts into the outer relation
@@ -349,35 +355,6 @@ struct MatrixArgs {
   int skip_mask;
   int gate1;                    // k_matrix_codes runs only when cnt[gate1 - 1] != 0 (0: always)
 };
-template <typename K>
-__global__ void k_matrix_merge(MatrixArgs a) {
-  DevState* st = a.st;
-  if (st->overflow & a.skip_mask) return;
-  const uint64_t ngroups = st->cnt[a.groups_cnt];
-  const int nwords = a.b >= 5 ? (1 << (a.b - 5)) : 1;
-  const uint32_t vmask = (1u << a.b) - 1;
-  const K* outer = static_cast<const K*>(st->buf[a.outer_buf].ptr);
-  const uint64_t* gs = static_cast<const uint64_t*>(st->buf[a.groups_buf].ptr);
-  const uint32_t* bm = static_cast<const uint32_t*>(st->buf[a.bm_buf].ptr);
-  uint32_t* fbm = static_cast<uint32_t*>(st->buf[a.fbm_buf].ptr);
-  uint32_t* fcnt = static_cast<uint32_t*>(st->buf[a.fcnt_buf].ptr);
-  const int lane = threadIdx.x & 31;
-  for (uint64_t gi = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5; gi < ngroups;
-       gi += (uint64_t(gridDim.x) * blockDim.x) >> 5) {
-    const uint32_t g = uint32_t(uint64_t(outer[gs[gi]]) >> a.b) & vmask;
-    const uint32_t* src = bm + gi * uint64_t(nwords);
-    uint32_t* row = fbm + uint64_t(g) * nwords;
-    uint32_t c = 0;
-    for (int j = lane; j < nwords; j += 32) {
-      const uint32_t x = row[j] | src[j];
-      row[j] = x;
-      c += __popc(x);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) fcnt[g] = c;
-  }
-}
 // The same from codes (kept value in the high half): iteration 1's delta.
 template <typename K>
 __global__ void k_matrix_codes(MatrixArgs a) {
@@ -809,7 +786,13 @@ __global__ void __launch_bounds__(kDenseThreads, kPullCtasPerSm) k_dense_pull(De
     const uint64_t o0 = gs[gi], o1 = gs[gi + 1];
     const uint32_t g = uint32_t(uint64_t(outer[o0]) >> a.b) & vmask;
     if (tid == 0) raw += o1 - o0;
-    sorted_run_to_bitmap<K>(F, outer, o0, o1, vmask, warp, nwarps);
+    if (a.prev_bm_buf >= 0 && st->iter >= 2) {   // the delta as last iteration's bitmap of the group
+      const uint32_t pgi = static_cast<const uint32_t*>(st->buf[a.prev_gi_buf].ptr)[g];
+      const uint32_t* src = static_cast<const uint32_t*>(st->buf[a.prev_bm_buf].ptr) + uint64_t(pgi) * nwords;
+      for (int j = tid; j < nwords; j += kDenseThreads) F[j] = src[j];
+    } else {
+      sorted_run_to_bitmap<K>(F, outer, o0, o1, vmask, warp, nwarps);
+    }
     if (a.full_buf >= 0) {
       const uint64_t nlv = st->cnt[a.nlv_cnt], nk = (1ull << a.b) + 1;
       const uint64_t* lvidx = static_cast<const uint64_t*>(st->buf[a.lvidx_buf].ptr);
@@ -925,17 +908,36 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_emit(DenseArgs a) {
   const uint32_t* bm = static_cast<const uint32_t*>(st->buf[a.bm_buf].ptr);
   const uint64_t* offs = static_cast<const uint64_t*>(st->buf[a.offs_buf].ptr);
   K* out = static_cast<K*>(st->buf[a.out_buf].ptr) + st->cnt[a.out_cnt];
+  // a full kept as a bit matrix takes the group's new tuples here, and |full_g|
+  // grows by their count: this launch runs once per committed iteration (only
+  // when the join stage did not overflow, and nothing after it in that stage
+  // can: the matrix is kept for single-relation programs only)
+  uint32_t* fbm = a.fbm_buf >= 0 ? static_cast<uint32_t*>(st->buf[a.fbm_buf].ptr) : nullptr;
+  uint32_t* fcnt = fbm ? static_cast<uint32_t*>(st->buf[a.fcnt_buf].ptr) : nullptr;
+  const uint32_t vmask = a.b >= 32 ? 0xFFFFFFFFu : ((1u << a.b) - 1);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (uint64_t gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
     const uint64_t gcode = uint64_t(outer[gs[gi]]) >> a.b;   // (inst, g): the result's high part
     const uint32_t* gbm = bm + gi * uint64_t(nwords);
+    uint32_t* row = fbm ? fbm + uint64_t(uint32_t(gcode) & vmask) * nwords : nullptr;
     const int w0 = warp * wrange, w1 = min(nwords, w0 + wrange);
     uint32_t cnt = 0;
-    for (int j = w0 + lane; j < w1; j += 32) cnt += __popc(gbm[j]);
+    for (int j = w0 + lane; j < w1; j += 32) {
+      const uint32_t x = gbm[j];
+      cnt += __popc(x);
+      if (row && x) row[j] |= x;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if (lane == 0) s_wtot[warp] = cnt;
     __syncthreads();
+    if (row && tid == 0) {
+      uint32_t t = 0;
+      for (int w = 0; w < nwarps; ++w) t += s_wtot[w];
+      fcnt[uint32_t(gcode) & vmask] += t;
+    }
+    if (a.prev_gi_buf >= 0 && tid == 0)
+      static_cast<uint32_t*>(st->buf[a.prev_gi_buf].ptr)[uint32_t(gcode) & vmask] = uint32_t(gi);
     uint64_t base = offs[gi];
     for (int w = 0; w < warp; ++w) base += s_wtot[w];
     for (int j0 = w0; j0 < w1; j0 += 32) {

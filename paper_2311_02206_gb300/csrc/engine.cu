@@ -192,6 +192,8 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.dense_plist = new_slot(4);
   sc.pull_cnt = nslots++;
   sc.pull_raw_cnt = nslots++;
+  sc.dense_bm_prev = new_slot(4);
+  sc.prev_gi = new_slot(4);
   sc.read_m = new_slot(4);
   sc.read_rows = new_slot(8);
   sc.read_s0 = new_slot(4);
@@ -990,7 +992,10 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
                       inner_buf >= 0 || direct_bits > 0, hr.append && !hr.mfull ? hr.full : -1, hr.lvidx, hr.nlv,
                       sp.nfilt > 0,
                       sc.dense_units, sc.dense_done, unit_size, sc.dense_mslot, sc.dense_bmm, units_ready};
-  if (hr.mfull) d.dense.fbm_buf = hr.fbm;
+  if (hr.mfull) {   // the emit ORs the groups' new tuples into full's bit matrix
+    d.dense.fbm_buf = hr.fbm;
+    d.dense.fcnt_buf = hr.fcnt;
+  }
   if (pull) {
     DenseArgs& da = d.dense;
     da.pull_inner_buf = hr.pull_inner;
@@ -1004,15 +1009,11 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
     da.plist_buf = sc.dense_plist;
     da.pull_cnt = sc.pull_cnt;
     da.pull_raw_cnt = sc.pull_raw_cnt;
+    da.prev_bm_buf = sc.dense_bm_prev;
+    da.prev_gi_buf = sc.prev_gi;
     da.pull_k16 = uint32_t(cfg.pull_ratio * 16.f + 0.5f);
   }
   ops.push_back(d);
-  if (hr.mfull) {   // the groups' new tuples into full's bit matrix (skipped if this stage overflowed)
-    Op m{};
-    m.kind = Op::MMERGE;
-    m.matrix = MatrixArgs{dst, sc.groups, sc.group_cnt, sp.outer_slot, sc.dense_bm, -1, -1, b, hr.fbm, hr.fcnt, 1, 0};
-    ops.push_back(m);
-  }
   if (hr.append) {   // no unique pass in the tail; |new| (statistics) = |delta|
     Op f{};
     f.kind = Op::CTL;
@@ -1334,6 +1335,16 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
     a.stage_bit = 1;
     ops.push_back(o);
   }
+  bool any_pull = false;
+  for (int r : idb) any_pull = any_pull || rels[r].pull;
+  if (any_pull) {   // this iteration's group bitmaps become the previous ones (after a clean stage only)
+    Op w{};
+    w.kind = Op::CTL;
+    w.ctl.st = dst;
+    w.ctl.skip_mask = 3;
+    w.ctl.cmd[w.ctl.n++] = {kCtlSwap, sc.dense_bm, sc.dense_bm_prev, 0};
+    ops.push_back(w);
+  }
   Op c{};
   c.kind = Op::COMMIT;
   c.commit.st = dst;
@@ -1377,7 +1388,6 @@ hisa_status Engine::exec_t(const std::vector<Op>& ops) {
       case Op::GROUPS: launch_group_starts<K>(o.groups, grid, stream); break;
       case Op::DENSE: launch_join_dense<K>(o.dense, grid, stream); break;
       case Op::CHAIN: launch_chain<K>(o.chain, grid, stream); break;
-      case Op::MMERGE: launch_matrix_merge<K>(o.matrix, grid, stream); break;
       case Op::MCODES: launch_matrix_codes<K>(o.matrix, grid, stream); break;
     }
   }
@@ -1693,7 +1703,13 @@ hisa_status Engine::init_run_state() {
     return s;
   bool any_pull = false;
   for (int r : idb) any_pull = any_pull || rels[r].pull;
-  if (any_pull && (s = ensure(sc.dense_plist, std::min<uint64_t>(4 * nedb, 1ull << b) + 2))) return s;
+  if (any_pull && ((s = ensure(sc.dense_plist, std::min<uint64_t>(4 * nedb, 1ull << b) + 2)) ||
+                   (s = ensure(sc.prev_gi, 1ull << b))))
+    return s;
+  if (any_pull) {   // the two group-bitmap slots swap every iteration: the same capacity for both
+    const uint64_t cap = std::max(hs.buf[sc.dense_bm].cap, hs.buf[sc.dense_bm_prev].cap);
+    if (cap && ((s = ensure(sc.dense_bm, cap)) || (s = ensure(sc.dense_bm_prev, cap)))) return s;
+  }
   if ((s = ensure(sc.radix_status, (4 * nedb / kt + 2) * 256)) || (s = ensure(sc.offs, 4 * nedb + 1)) ||
       (s = ensure(sc.join_status, 4 * nedb / kJoinTile + 2)) || (s = ensure(sc.starts, 4 * nedb / kJoinChunk + 2)) ||
       (s = ensure(sc.split, 8 * nedb / 2048 + 2)) || (s = ensure(sc.setop_status, 8 * nedb / 2048 + 2)) ||
@@ -1830,7 +1846,6 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
             // (+ the full levels' runs read for the set difference)
             // (+ full: its row of the bit matrix, or the levels' runs of the group)
             kstat[kKJoinDense].bytes += dp * (kb + 16.0) + raw * kb + bmb + (R.mfull ? bmb : m * kb);
-            if (R.mfull) kstat[kKMatrix].bytes += 3.0 * bmb;   // group bitmaps read, rows read and written
             // pulled groups: their delta, full's runs and the inner tuples they
             // scanned (the push term above still counts full for every group)
             kstat[kKJoinPull].bytes += double(hs.cnt[sc.pull_raw_cnt]) * kb;

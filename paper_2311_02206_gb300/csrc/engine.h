@@ -82,7 +82,7 @@ struct StepPlan {
 
 struct Op {
   enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT, APPEND, GROUPS, CHAIN,
-              MMERGE, MCODES } kind;
+              MCODES } kind;
   CtlArgs ctl;
   JoinArgs join;
   RadixPassArgs pass;
@@ -115,6 +115,7 @@ struct Scratch {
   int chain_tfirst;             // a gathered Tmp's direct index by its kept column
   int dense_plist = -1, pull_cnt = -1;   // pulled groups of the grouped bitmap join, and their count
   int pull_raw_cnt = -1;                 // codes read by the pull kernel
+  int dense_bm_prev = -1, prev_gi = -1;   // the previous iteration's group bitmaps; group index per value
   int read_m = -1, read_rows = -1;  // reading a column-swapped append-only full: its bit matrix, row offsets
   int read_s0 = -1, read_s1 = -1;   // and its device staging columns (kept across reads)
 

@@ -192,7 +192,6 @@ template <typename K> void launch_join_dense(const DenseArgs& a, const Grid& g, 
 template <typename K> void launch_chain(const ChainArgs& a, const Grid& g, cudaStream_t s);   // len + scan + gather
 template <typename K> void launch_levels_read(const LevelsReadArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_levels_transpose(const LevelsTransposeArgs& a, const Grid& g, cudaStream_t s);
-template <typename K> void launch_matrix_merge(const MatrixArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_matrix_codes(const MatrixArgs& a, const Grid& g, cudaStream_t s);
 // a full kept as a bit matrix read in the declared order: transposed (order 1)
 // or read as it is (order 0), then its rows counted, scanned and written

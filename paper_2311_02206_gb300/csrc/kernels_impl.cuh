@@ -192,10 +192,6 @@ void launch_levels_transpose(const LevelsTransposeArgs& a, const Grid& g, cudaSt
   HISA_LAUNCH(kKDecode, s, (k_rows_emit<K><<<g.sms * 8, kDenseThreads, 0, s>>>(a)));
 }
 template <typename K>
-void launch_matrix_merge(const MatrixArgs& a, const Grid& g, cudaStream_t s) {
-  HISA_LAUNCH(kKMatrix, s, (k_matrix_merge<K><<<g.sms * 8, 256, 0, s>>>(a)));
-}
-template <typename K>
 void launch_matrix_codes(const MatrixArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKMatrix, s, (k_matrix_codes<K><<<g.small, 256, 0, s>>>(a)));
 }
@@ -342,7 +338,6 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_chain<K>(const ChainArgs&, const Grid&, cudaStream_t);            \
   template void launch_levels_read<K>(const LevelsReadArgs&, const Grid&, cudaStream_t);  \
   template void launch_levels_transpose<K>(const LevelsTransposeArgs&, const Grid&, cudaStream_t); \
-  template void launch_matrix_merge<K>(const MatrixArgs&, const Grid&, cudaStream_t);    \
   template void launch_matrix_codes<K>(const MatrixArgs&, const Grid&, cudaStream_t);    \
   template void launch_matrix_read<K>(const MatrixTransposeArgs&, const LevelsTransposeArgs&, bool, const Grid&, \
                                       cudaStream_t);                                     \

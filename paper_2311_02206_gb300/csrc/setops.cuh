@@ -131,8 +131,20 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
     const uint64_t a0 = split[tile], a1 = split[tile + 1];
     const uint64_t b0 = d0 - a0, b1 = d1 - a1;
     const int nA = int(a1 - a0), nB = int(b1 - b0), nT = nA + nB;
-    for (int i = tid; i < nA; i += kSetopThreads) s_in[i] = A[a0 + i];
-    for (int i = tid; i < nB; i += kSetopThreads) s_in[nA + i] = B[b0 + i];
+    {   // the tile's A part, then its B part, into shared memory: every load of
+        // a thread is in flight before the first store (coalesced, ITEMS each)
+      K v[ITEMS];
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const int i = tid + k * kSetopThreads;
+        v[k] = i < nA ? A[a0 + i] : (i < nT ? B[b0 + (i - nA)] : K(0));
+      }
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const int i = tid + k * kSetopThreads;
+        if (i < nT) s_in[i] = v[k];
+      }
+    }
     if (tid == 0) {
       s_hasA = a0 > 0;
       if (a0 > 0) s_prevA = A[a0 - 1];

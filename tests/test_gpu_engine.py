@@ -30,7 +30,8 @@ def modes():
     return [0, hisa.FLAG_GRAPH, hisa.FLAG_LOG_FULL, hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL,
             hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE, hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE | hisa.FLAG_HASH_INDEX,
             hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_CHAIN,
-            hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_PULL]
+            hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_PULL,
+            hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_LEVELS]
 
 
 @pytest.mark.parametrize("ratio", [1 / 16, 4.0, 4096.0])
@@ -219,9 +220,10 @@ def test_sg_random_dag(seed):
         assert_same(rels, counts, ref)
 
 
-@pytest.mark.parametrize("log_full,no_dense,no_pull", [(False, True, False), (True, True, False), (True, False, False),
-                                                       (True, False, True)])
-def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense, no_pull):
+@pytest.mark.parametrize("log_full,no_dense,no_pull,levels", [(False, True, False, False), (True, True, False, False),
+                                                              (True, False, False, False), (True, False, True, False),
+                                                              (True, False, False, True)])
+def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense, no_pull, levels):
     """REACH on R-MAT scale 16 / 2**19 edges, in the launch configuration the
     benchmark times: total size, delta counts and fingerprint against the
     oracle's stored values, and 16 sampled target columns element by element."""
@@ -232,7 +234,7 @@ def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense, no_pull):
     from paper_2311_02206_gb300 import hisa
     s, d = workloads.config_reach_rmat()
     flags = hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0) | (hisa.FLAG_NO_DENSE if no_dense else 0) | \
-        (hisa.FLAG_NO_PULL if no_pull else 0)
+        (hisa.FLAG_NO_PULL if no_pull else 0) | (hisa.FLAG_LEVELS if levels else 0)
     with hisa.Context(flags=flags) as ctx:
         ctx.program(*oracle.REACH)
         ctx.load_tuples("Edge", s, d)
@@ -268,9 +270,10 @@ def _sg_induced(literal, nodes):
     return _SG_SUB[key]
 
 
-@pytest.mark.parametrize("literal,log_full,no_chain",
-                         [(False, False, False), (True, False, False), (False, True, False), (False, True, True)])
-def test_sg_dag_full_size_golden(literal, log_full, no_chain):
+@pytest.mark.parametrize("literal,log_full,no_chain,levels",
+                         [(False, False, False, False), (True, False, False, False), (False, True, False, False),
+                          (False, True, True, False), (False, True, False, True)])
+def test_sg_dag_full_size_golden(literal, log_full, no_chain, levels):
     """SG on the 20,000-node DAG (x != y on both rules, or on rule 1 only as
     the workload description prints it): size, every delta count and the
     fingerprint of the whole relation against the oracle's stored values; the
@@ -283,7 +286,8 @@ def test_sg_dag_full_size_golden(literal, log_full, no_chain):
     g = json.load(open(path))
     from paper_2311_02206_gb300 import hisa
     s, d = workloads.config_sg_dag()
-    flags = hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0) | (hisa.FLAG_NO_CHAIN if no_chain else 0)
+    flags = hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0) | (hisa.FLAG_NO_CHAIN if no_chain else 0) | \
+        (hisa.FLAG_LEVELS if levels else 0)
     with hisa.Context(flags=flags) as ctx:
         ctx.program(*(oracle.SG_LITERAL if literal else oracle.SG))
         ctx.load_tuples("Edge", s, d)
