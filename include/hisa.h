@@ -132,6 +132,10 @@ typedef struct {
   float pull_ratio;         /* pull mode switch point (HISA_FLAG_NO_PULL): a group pulls when the
                                inner runs its next delta would mark exceed pull_ratio times the
                                values it could still derive (plus the delta's size); 0 = 4 */
+  uint32_t radix_items;     /* keys per thread of a radix-sort tile: 0 = 24 (32-bit codes) / 12 (64-bit);
+                               16 / 8 take a smaller tile; other values = 0 */
+  uint32_t dense_unit;      /* outer tuples per work unit of the grouped bitmap join (the join's work
+                               split): 0 = 16 x the bitmap's words, within 256 .. 32768; 64 .. 2^20 */
 } hisa_config;
 
 typedef struct hisa_ctx hisa_ctx;

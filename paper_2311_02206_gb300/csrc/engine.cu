@@ -136,6 +136,12 @@ hisa_status Engine::init(const hisa_config& c) {
   if (cfg.ebm_k <= 0.f) cfg.ebm_k = 2.f;
   if (cfg.max_iters == 0) cfg.max_iters = 1000000;
   if (!(cfg.pull_ratio > 0.f) || cfg.pull_ratio > 4096.f) cfg.pull_ratio = float(kPullK16) / 16.f;
+  // tuning knobs outside their ranges fall back to the defaults
+  if (cfg.radix_items != 0 && cfg.radix_items != uint32_t(RadixCfg<uint32_t>::items) &&
+      cfg.radix_items != uint32_t(RadixCfg<uint32_t>::items_alt) && cfg.radix_items != uint32_t(RadixCfg<uint64_t>::items) &&
+      cfg.radix_items != uint32_t(RadixCfg<uint64_t>::items_alt))
+    cfg.radix_items = 0;
+  if (cfg.dense_unit != 0 && (cfg.dense_unit < 64 || cfg.dense_unit > (1u << 20))) cfg.dense_unit = 0;
   if (cfg.device >= 0) CU(cudaSetDevice(cfg.device));
   CU(cudaGetDevice(&device));
   stream = static_cast<cudaStream_t>(cfg.cuda_stream);
@@ -966,7 +972,8 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
   // with an append-only full the join writes delta itself, into delta_next
   const int out = hr.append ? hr.delta_next : hr.fresh;
   // a unit holds enough outer tuples to outweigh its bitmap
-  const int unit_size = int(std::max<uint64_t>(256, std::min<uint64_t>(32768, 16ull << (b >= 5 ? b - 5 : 0))));
+  const int unit_size = cfg.dense_unit ? int(cfg.dense_unit)
+                                       : int(std::max<uint64_t>(256, std::min<uint64_t>(32768, 16ull << (b >= 5 ? b - 5 : 0))));
   const bool units_ready = b + inst_bits <= kDirectMaxBits;
   const bool pull = hr.pull && !chain_groups && inner_buf < 0 && units_ready;
   if (units_ready) {
@@ -1167,6 +1174,7 @@ void Engine::emit_sort(std::vector<Op>& ops, int in, int alt, int cnt, int hist,
     a.ctr = 1;
     a.skip_mask = skip_mask;
     a.stage_bit = stage_bit;
+    a.items = int(cfg.radix_items);
     ops.push_back(o);
   }
 }

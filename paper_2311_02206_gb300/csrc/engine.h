@@ -232,6 +232,7 @@ class Engine {
   bool slot_zero[kMaxBufs] = {};   // zero on allocation (look-back status words)
   bool slot_pow2[kMaxBufs] = {};   // capacity must be a power of two (hash tables)
   std::unordered_map<void*, size_t> allocs;
+  std::vector<uint64_t> submit_seen;   // serve_submit's distinct-value bitmap (kept cleared)
   uint64_t bytes_in_use = 0, peak_bytes = 0;
   uint32_t regrows = 0;
   Scratch sc{};

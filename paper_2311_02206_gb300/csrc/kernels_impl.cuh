@@ -228,6 +228,16 @@ template <typename K>
 void launch_radix_hist(const RadixHistArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKHist, s, (k_radix_hist<K><<<g.small, 256, 0, s>>>(a)));
 }
+template <typename K, int ITEMS>
+void launch_radix_pass_items(const RadixPassArgs& a, const Grid& g, cudaStream_t s) {
+  static bool attr = false;   // the tiles exceed the default 48 KB of dynamic shared memory
+  if (!attr) {
+    cudaFuncSetAttribute(k_radix_pass<K, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         radix_dyn_smem<K, ITEMS>());
+    attr = true;
+  }
+  HISA_LAUNCH(kKRadixPass, s, (k_radix_pass<K, ITEMS><<<g.radix, kRadixThreads, radix_dyn_smem<K, ITEMS>(), s>>>(a)));
+}
 template <typename K>
 void launch_radix_pass(const RadixPassArgs& a, const Grid& g, cudaStream_t s) {
   CtlArgs c{};
@@ -237,12 +247,8 @@ void launch_radix_pass(const RadixPassArgs& a, const Grid& g, cudaStream_t s) {
   c.cmd[0] = {kCtlEpoch, 0, 0};
   c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
   launch_ctl(c, s);
-  static bool attr_set = false;   // opt in to the pass's dynamic shared memory once per process
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_radix_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, radix_dyn_smem<K>());
-    attr_set = true;
-  }
-  HISA_LAUNCH(kKRadixPass, s, (k_radix_pass<K><<<g.radix, kRadixThreads, radix_dyn_smem<K>(), s>>>(a)));
+  if (a.items == RadixCfg<K>::items_alt) launch_radix_pass_items<K, RadixCfg<K>::items_alt>(a, g, s);
+  else launch_radix_pass_items<K, RadixCfg<K>::items>(a, g, s);
 }
 template <typename K>
 void launch_setop(const SetopArgs& a, const Grid& g, cudaStream_t s) {

@@ -20,20 +20,23 @@ constexpr int kRadixDigits = 1 << kRadixBits;
 constexpr int kRadixThreads = 256;   // one thread per digit in the per-tile scans
 constexpr int kRadixWarps = kRadixThreads / 32;
 
+// Keys per thread of a tile: a default and a smaller alternative per code
+// width (the tile is chosen per context, hisa_config.radix_items); status
+// buffers are sized for the smaller tile, so either fits.
 template <typename K>
 struct RadixCfg;
 template <>
-struct RadixCfg<uint32_t> { static constexpr int items = 24; };
+struct RadixCfg<uint32_t> { static constexpr int items = 24, items_alt = 16; };
 template <>
-struct RadixCfg<uint64_t> { static constexpr int items = 12; };
+struct RadixCfg<uint64_t> { static constexpr int items = 12, items_alt = 8; };
 
 template <typename K>
-__host__ __device__ constexpr int radix_tile() { return kRadixThreads * RadixCfg<K>::items; }
+__host__ __device__ constexpr int radix_tile() { return kRadixThreads * RadixCfg<K>::items_alt; }
 
 // Dynamic shared memory of one pass: two tile buffers (the one being ranked,
 // which then holds the tile in digit order, and the next tile's TMA target).
-template <typename K>
-__host__ __device__ constexpr int radix_dyn_smem() { return 2 * radix_tile<K>() * int(sizeof(K)); }
+template <typename K, int ITEMS>
+__host__ __device__ constexpr int radix_dyn_smem() { return 2 * kRadixThreads * ITEMS * int(sizeof(K)); }
 
 struct RadixPassArgs {
   DevState* st;
@@ -46,6 +49,7 @@ struct RadixPassArgs {
   int ctr;               // tile counter index
   int skip_mask;         // st->overflow bits that cancel this launch
   int stage_bit;         // overflow bit raised when a buffer is too small
+  int items = 0;         // keys per thread (0: RadixCfg<K>::items; else items or items_alt)
 };
 
 // Digit histograms of all passes in one read of the keys.
@@ -121,9 +125,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, uint32_t
 // straight to its position in the tile's digit order (written over the
 // consumed input buffer); (5) look-back gives each digit run's global start;
 // (6) the tile is written out digit run by digit run.
-template <typename K>
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_pass(RadixPassArgs a) {
-  constexpr int ITEMS = RadixCfg<K>::items;
   constexpr int TILE = kRadixThreads * ITEMS;
   extern __shared__ __align__(128) unsigned char radix_dyn[];
   K* s_buf[2] = {reinterpret_cast<K*>(radix_dyn), reinterpret_cast<K*>(radix_dyn) + TILE};

@@ -266,31 +266,35 @@ hisa_status Engine::serve_submit(uint32_t rid, const uint32_t* const* cols, uint
   Request q;
   q.ticket = next_ticket++;
   q.rel = rid;
-  q.c0.assign(cols ? cols[0] : nullptr, cols ? cols[0] + n : nullptr);
-  q.c1.assign(cols ? cols[1] : nullptr, cols ? cols[1] + n : nullptr);
-  uint32_t mx = 0;
-  std::vector<uint32_t> nodes(q.c0);
-  nodes.insert(nodes.end(), q.c1.begin(), q.c1.end());
-  for (uint32_t v : nodes) mx = std::max(mx, v);
-  if (n && (uint64_t(mx) >> fixed_b) != 0) return ctx_fail(HISA_ERR_INVALID_ARG, "value above max_value", nullptr);
-  std::sort(nodes.begin(), nodes.end());
-  const uint64_t distinct = uint64_t(std::unique(nodes.begin(), nodes.end()) - nodes.begin());
+  // distinct values, by a bitmap over the session's fixed domain (2^b values)
+  if (submit_seen.size() != (size_t(1) << fixed_b) / 64 + 1) submit_seen.assign((size_t(1) << fixed_b) / 64 + 1, 0);
+  uint64_t distinct = 0;
+  for (int c = 0; c < 2 && n; ++c)
+    for (uint64_t i = 0; i < n; ++i) {
+      const uint32_t v = cols[c][i];
+      if ((uint64_t(v) >> fixed_b) != 0) {
+        std::fill(submit_seen.begin(), submit_seen.end(), 0);
+        return ctx_fail(HISA_ERR_INVALID_ARG, "value above max_value", nullptr);
+      }
+      uint64_t& w = submit_seen[v >> 6];
+      const uint64_t bit = 1ull << (v & 63);
+      distinct += (w & bit) ? 0 : 1;
+      w |= bit;
+    }
+  for (int c = 0; c < 2 && n; ++c)   // clear only the words that were set
+    for (uint64_t i = 0; i < n; ++i) submit_seen[cols[c][i] >> 6] = 0;
   // worst case of a binary IDB relation over these values, in both versions
   q.est_bytes = distinct * distinct * (wide ? 8 : 4) * 2 + n * 64;
   q.n = n;
-  if (n) {   // the request's tuples move to the device once
+  if (n) {   // the request's tuples move to the device once (the caller's arrays may go)
     void* p;
     hisa_status s = dev_alloc(2 * n * 4, &p);
     if (s) return s;
     q.dev_edges = static_cast<uint32_t*>(p);
-    CU(cudaMemcpyAsync(q.dev_edges, q.c0.data(), n * 4, cudaMemcpyHostToDevice, stream));
-    CU(cudaMemcpyAsync(q.dev_edges + n, q.c1.data(), n * 4, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync(q.dev_edges, cols[0], n * 4, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync(q.dev_edges + n, cols[1], n * 4, cudaMemcpyHostToDevice, stream));
     CU(cudaStreamSynchronize(stream));
   }
-  q.c0.clear();
-  q.c0.shrink_to_fit();
-  q.c1.clear();
-  q.c1.shrink_to_fit();
   *ticket = q.ticket;
   pending.push_back(q.ticket);
   reqs.emplace(q.ticket, std::move(q));

@@ -44,6 +44,8 @@ class Config(ctypes.Structure):
         ("flags", ctypes.c_uint32),
         ("device", ctypes.c_int32),
         ("pull_ratio", ctypes.c_float),
+        ("radix_items", ctypes.c_uint32),
+        ("dense_unit", ctypes.c_uint32),
     ]
 
 
@@ -195,7 +197,8 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None, flags: int = FLAG_GRAPH | FLAG_LOG_FULL, max_iters: int = 0,
                  load_factor: float = 0.0, ebm_k: float = 0.0, hbm_budget_bytes: int = 0,
-                 torch_allocator: bool = True, allocator=None, pull_ratio: float = 0.0):
+                 torch_allocator: bool = True, allocator=None, pull_ratio: float = 0.0, radix_items: int = 0,
+                 dense_unit: int = 0):
         """``allocator``: optional pair (alloc, free) of Python callables,
         alloc(nbytes, stream) -> device pointer or None, free(ptr, nbytes,
         stream), used in place of torch's caching allocator."""
@@ -216,6 +219,8 @@ class Context:
         cfg.ebm_k = ebm_k
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.pull_ratio = pull_ratio
+        cfg.radix_items = radix_items
+        cfg.dense_unit = dense_unit
         if allocator is not None:
             user_alloc, user_free = allocator
 

@@ -111,3 +111,28 @@ def test_batch_of_config_shapes():
         for i in range(0, 64, 7):
             c0, c1 = ctx.read_instance("Reach", i)
             check(oracle.reach(*graphs[i]), c0, c1, ctx.instance_delta_counts("Reach", i))
+
+
+@pytest.mark.parametrize("knobs", [dict(radix_items=8), dict(load_factor=0.5), dict(dense_unit=64),
+                                   dict(radix_items=16, dense_unit=1024, load_factor=0.65)])
+def test_served_with_tuning_knobs(knobs):
+    """The autotuner's knobs (sort tile, load factor of the hashed indexes,
+    the grouped join's work split) change no result of a served batch."""
+    from paper_2311_02206_gb300 import hisa
+    inst = instances(24, 5, nmax=300)
+    with hisa.Context(**knobs) as ctx:
+        ctx.program(*oracle.REACH)
+        ctx.serve_open(32, 300, 0)
+        tickets = {ctx.serve_submit("Edge", s, d): i for i, (s, d) in enumerate(inst)}
+        done = {}
+        for _ in range(10000):
+            ctx.serve_step(1)
+            for t, i in list(tickets.items()):
+                if i not in done and ctx.serve_poll(t):
+                    done[i] = ctx.serve_result(t, "Reach")
+                    ctx.serve_release(t)
+            if len(done) == len(inst):
+                break
+        for i, (s, d) in enumerate(inst):
+            c0, c1, dc = done[i]
+            check(oracle.reach(s, d), c0, c1, dc)

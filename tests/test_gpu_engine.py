@@ -347,3 +347,23 @@ def test_cspa_golden(div, window, no_chain):
                 assert np.array_equal(c0.cpu().numpy().view(np.uint32), w0), name
                 assert np.array_equal(c1.cpu().numpy().view(np.uint32), w1), name
     assert arrays is not None, "stored sorted relations missing (tests/golden/make_golden.py cspa)"
+
+
+@pytest.mark.parametrize("knobs", [dict(radix_items=16), dict(radix_items=8), dict(dense_unit=64),
+                                   dict(dense_unit=1024, pull_ratio=2.0), dict(load_factor=0.5)])
+def test_tuning_knobs_keep_results(knobs):
+    """Every value the autotuner may pick (radix tile, join work split, pull
+    switch point, load factor of the hashed index) gives the oracle's
+    relations and delta counts, on the sort path, the grouped join and the
+    hashed indexes."""
+    from paper_2311_02206_gb300 import hisa
+    cases = [(oracle.REACH, {"Edge": workloads.config_reach_er()}),
+             (oracle.SG, {"Edge": workloads.dag_graph(300, 700, 16, 4)}),
+             (oracle.CSPA, workloads.config_cspa(1000, 32))]
+    for prog, edb in cases:
+        ref = oracle.seminaive(*prog, edb)
+        for flags in (hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL, hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE,
+                      hisa.FLAG_GRAPH | hisa.FLAG_HASH_INDEX | hisa.FLAG_LOG_FULL):
+            rels, counts, _ = gpu_eval(*prog, edb, flags=flags, **knobs)
+            assert_same(rels, counts, ref)
+
