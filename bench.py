@@ -193,12 +193,17 @@ class ClockSampler:
         self.proc = None
 
     def __enter__(self):
+        self.started = threading.Event()
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                                           "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
                                          text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi's start-up (driver and NVML initialisation) stalls the
+            # GPU's work for up to seconds: the timed region starts only after
+            # its first sample
+            self.started.wait(timeout=30)
         except OSError:
             self.proc = None
         return self
@@ -208,6 +213,8 @@ class ClockSampler:
             f = [x.strip() for x in line.split(",")]
             if len(f) >= 10 and (not self.uuid or self.uuid in f[1]):
                 self.rows.append(f)
+                self.started.set()
+        self.started.set()
 
     def __exit__(self, *exc):
         if self.proc:
