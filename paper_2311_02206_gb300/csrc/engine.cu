@@ -1597,7 +1597,7 @@ hisa_status Engine::regrow() {
     // radix look-back words for new, the swapped delta and a sorted Tmp; Tmp's
     // sort partner; the join's write chunks
     if ((s = ensure(sc.radix_status, (std::max({new_cap, delta_cap, hs.buf[sc.tmp_a].cap}) / kt + 2) * kRadixDigits)) ||
-        (s = ensure(sc.tmp_b, hs.buf[sc.tmp_a].cap)) || (s = ensure(sc.starts, new_cap / kJoinChunk + 2)))
+        (s = ensure(sc.tmp_b, hs.buf[sc.tmp_a].cap)) || (s = ensure(sc.starts, new_cap / kJoinChunkMin + 2)))
       return s;
   }
   for (int r : idb) {   // new minus the large level holds at most |new|
@@ -1719,7 +1719,7 @@ hisa_status Engine::init_run_state() {
     if (cap && ((s = ensure(sc.dense_bm, cap)) || (s = ensure(sc.dense_bm_prev, cap)))) return s;
   }
   if ((s = ensure(sc.radix_status, (4 * nedb / kt + 2) * 256)) || (s = ensure(sc.offs, 4 * nedb + 1)) ||
-      (s = ensure(sc.join_status, 4 * nedb / kJoinTile + 2)) || (s = ensure(sc.starts, 4 * nedb / kJoinChunk + 2)) ||
+      (s = ensure(sc.join_status, 4 * nedb / kJoinTile + 2)) || (s = ensure(sc.starts, 4 * nedb / kJoinChunkMin + 2)) ||
       (s = ensure(sc.split, 8 * nedb / 2048 + 2)) || (s = ensure(sc.setop_status, 8 * nedb / 2048 + 2)) ||
       (s = ensure(sc.tmp_a, 4 * nedb)))
     return s;

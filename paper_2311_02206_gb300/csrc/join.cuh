@@ -69,7 +69,12 @@ struct JoinArgs {
 constexpr int kJoinThreads = 256;
 constexpr int kJoinItems = 8;
 constexpr int kJoinTile = kJoinThreads * kJoinItems;   // outer tuples per count tile
-constexpr int kJoinChunk = kJoinThreads * 8;           // results per write chunk
+// results per write chunk: 16 per thread for 4-byte codes, 8 for 8-byte ones
+// (the chunk is staged in shared memory); the smaller one sizes the buffers
+// of chunk starts
+template <typename K>
+__host__ __device__ constexpr int join_chunk() { return kJoinThreads * (sizeof(K) == 4 ? 16 : 8); }
+constexpr int kJoinChunkMin = kJoinThreads * 8;
 
 // instance id of a batched code (0 when the two columns fill the code)
 template <typename K>
@@ -372,7 +377,7 @@ __global__ void k_join_partition(JoinArgs a) {
   if (st->overflow & a.skip_mask) return;
   const uint64_t n = st->cnt[a.outer_cnt];
   const uint64_t total = st->cnt[a.total_cnt];
-  const uint64_t nchunks = (total + kJoinChunk - 1) / kJoinChunk;
+  const uint64_t nchunks = (total + join_chunk<K>() - 1) / join_chunk<K>();
   if (st->buf[a.starts_buf].cap < nchunks + 1) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       atomicOr(&st->overflow, 1u << a.stage_bit);
@@ -383,7 +388,7 @@ __global__ void k_join_partition(JoinArgs a) {
   const uint64_t* offs = static_cast<const uint64_t*>(st->buf[a.offs_buf].ptr);
   uint64_t* starts = static_cast<uint64_t*>(st->buf[a.starts_buf].ptr);
   for (uint64_t c = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; c <= nchunks; c += uint64_t(gridDim.x) * blockDim.x) {
-    const uint64_t o = min(c * kJoinChunk, total);
+    const uint64_t o = min(c * join_chunk<K>(), total);
     // largest i in [0, n] with offs[i] <= o  (offs is non-decreasing, offs[0] = 0)
     uint64_t lo = 0, hi = n;
     while (lo < hi) {
@@ -398,7 +403,7 @@ __global__ void k_join_partition(JoinArgs a) {
 template <typename K>
 __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
   constexpr int S = kJoinThreads;          // outer tuples staged per batch
-  constexpr int IPT = kJoinChunk / kJoinThreads;   // consecutive results per thread
+  constexpr int IPT = join_chunk<K>() / kJoinThreads;   // consecutive results per thread
   __shared__ uint64_t s_off[S + 1];        // result offset of each staged outer tuple
   __shared__ uint64_t s_begin[S];          // first inner position of its range
   __shared__ uint32_t s_hole[S];           // see Probe::hole
@@ -406,14 +411,14 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
   __shared__ K s_code[S];
   // the chunk's results, for coalesced stores; one pad word per 32 keeps the
   // per-thread runs of IPT consecutive results on distinct banks
-  __shared__ K s_out[kJoinChunk + kJoinChunk / 32];
-  __shared__ uint32_t s_hist[kJoinThreads / 32][256];   // per-warp digit counts of one pass
+  __shared__ K s_out[join_chunk<K>() + join_chunk<K>() / 32];
+  __shared__ uint32_t s_hist[8][256];   // the CTA's digit counts of up to eight passes
   DevState* st = a.st;
   if (st->overflow & a.skip_mask) return;
   const uint64_t n = st->cnt[a.outer_cnt];
   const uint64_t total = st->cnt[a.total_cnt];
   if (total == 0) return;
-  const uint64_t nchunks = (total + kJoinChunk - 1) / kJoinChunk;
+  const uint64_t nchunks = (total + join_chunk<K>() - 1) / join_chunk<K>();
   const K* outer = static_cast<const K*>(st->buf[a.outer_buf].ptr);
   const K* inner = a.has_inner ? static_cast<const K*>(st->buf[a.inner_buf].ptr) : nullptr;
   const uint64_t n_inner = a.has_inner ? st->cnt[a.inner_cnt] : 0;
@@ -422,13 +427,16 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
   const uint64_t* offs = static_cast<const uint64_t*>(st->buf[a.offs_buf].ptr);
   const uint64_t* starts = static_cast<const uint64_t*>(st->buf[a.starts_buf].ptr);
   K* out = static_cast<K*>(st->buf[a.out_buf].ptr) + st->cnt[a.out_cnt];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int passes = a.hist_buf >= 0 ? a.hist_passes : 0;
-  // the histogram of up to 8 digit passes is accumulated one pass at a time
-  // over the staged results of each chunk; counts are flushed per chunk
+  const int tid = threadIdx.x;
+  const int passes = a.hist_buf >= 0 ? min(a.hist_passes, 8) : 0;
+  // the histogram of up to 8 digit passes: every thread counts the digits of
+  // its own consecutive results, one atomic per run of equal digits (the high
+  // digits of one outer tuple's results rarely change); the CTA's counts are
+  // added to the global histogram once, at the end
   unsigned long long* ghist = passes ? static_cast<unsigned long long*>(st->buf[a.hist_buf].ptr) : nullptr;
+  for (int i = tid; i < passes * 256; i += kJoinThreads) (&s_hist[0][0])[i] = 0;
   for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const uint64_t o0 = ch * kJoinChunk, o1 = min(o0 + kJoinChunk, total);
+    const uint64_t o0 = ch * join_chunk<K>(), o1 = min(o0 + join_chunk<K>(), total);
     uint64_t s = starts[ch];
     const uint64_t last = starts[ch + 1];   // outer holding result o1 (or n)
     while (true) {
@@ -465,28 +473,41 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
           if (s_off[m] <= j) l = m;
           else h = m - 1;
         }
-        uint64_t next = s_off[l + 1];
-        for (; j < jend; ++j) {
-          while (j >= next) {   // skip to the outer tuple owning result j
-            ++l;
-            next = s_off[l + 1];
-          }
-          const uint64_t r = j - s_off[l];
-          K ic = K(0);
+        // the results of one outer tuple differ only in the inner tuple's
+        // other column: the outer's part of the code is formed once per outer
+        const bool in0 = a.proj0 == kSrcOther, in1 = a.proj1 == kSrcOther;
+        const uint64_t vmask = a.b >= 32 ? 0xFFFFFFFFull : ((1ull << a.b) - 1);
+        while (j < jend) {   // one outer tuple's share of this thread's results
+          const uint64_t seg_end = min(jend, s_off[l + 1]);
+          const uint32_t r0 = uint32_t(j - s_off[l]);
+          const uint32_t nres = uint32_t(seg_end - j);
+          const K fixed = project<K>(a, s_code[l], K(0), false);
+          const uint64_t begin = s_begin[l];
+          const uint32_t hole = s_hole[l], mode = s_mode[l];
+          const uint32_t q0 = uint32_t(j - o0);
           if (a.has_inner) {
-            Probe p;
-            p.begin = s_begin[l];
-            p.hole = s_hole[l];
-            p.mode = s_mode[l];
-            const uint64_t ip = result_pos(p, uint32_t(r));
-            if (ip >= n_inner) {   // offsets and probes disagree
+            // inner positions rise with the result index: check the last one
+            const uint32_t rl = r0 + nres - 1;
+            const uint64_t last = mode == 1 ? begin + hole : begin + rl + (rl >= hole ? 1 : 0);
+            if (nres && last >= n_inner) {   // offsets and probes disagree
               atomicExch(&st->error, kDevBadState);
-              continue;
+            } else {
+              for (uint32_t t = 0; t < nres; ++t) {
+                const uint32_t r = r0 + t;
+                const uint64_t ip = mode == 1 ? begin + hole : begin + r + (r >= hole ? 1 : 0);
+                const K oth = K(uint64_t(inner[ip]) & vmask);
+                const uint32_t q = q0 + t;
+                s_out[q + (q >> 5)] = fixed | (in0 ? K(oth << a.b) : K(0)) | (in1 ? oth : K(0));
+              }
             }
-            ic = inner[ip];
+          } else {
+            for (uint32_t t = 0; t < nres; ++t) {
+              const uint32_t q = q0 + t;
+              s_out[q + (q >> 5)] = fixed;
+            }
           }
-          const uint32_t q = uint32_t(j - o0);
-          s_out[q + (q >> 5)] = project<K>(a, s_code[l], ic, a.has_inner);
+          j = seg_end;
+          ++l;
         }
       }
       if (hi_batch >= o1 || s + S > last) break;
@@ -495,16 +516,29 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(JoinArgs a) {
     __syncthreads();
     const uint32_t cn = uint32_t(o1 - o0);
     for (uint32_t t = tid; t < cn; t += kJoinThreads) out[o0 + t] = s_out[t + (t >> 5)];
-    for (int q = 0; q < passes; ++q) {
-      for (int w = 0; w < kJoinThreads / 32; ++w) s_hist[w][tid] = 0;
-      __syncthreads();
-      for (uint32_t t = tid; t < cn; t += kJoinThreads)
-        atomicAdd(&s_hist[warp][uint32_t(uint64_t(s_out[t + (t >> 5)]) >> (8 * q)) & 0xFF], 1u);
-      __syncthreads();
-      uint32_t c = 0;
-      for (int w = 0; w < kJoinThreads / 32; ++w) c += s_hist[w][tid];
-      if (c) atomicAdd(&ghist[q * 256 + tid], (unsigned long long)c);
-      __syncthreads();
+    if (passes) {
+      const uint32_t q0 = uint32_t(tid) * IPT, q1 = min(q0 + IPT, cn);
+      for (int q = 0; q < passes; ++q) {
+        uint32_t run_d = 0xFFFFFFFFu, run_n = 0;
+        for (uint32_t t = q0; t < q1; ++t) {
+          const uint32_t d = uint32_t(uint64_t(s_out[t + (t >> 5)]) >> (8 * q)) & 0xFF;
+          if (d != run_d) {
+            if (run_n) atomicAdd(&s_hist[q][run_d], run_n);
+            run_d = d;
+            run_n = 0;
+          }
+          ++run_n;
+        }
+        if (run_n) atomicAdd(&s_hist[q][run_d], run_n);
+      }
+    }
+    __syncthreads();   // s_out is rewritten by the next chunk
+  }
+  if (passes) {
+    __syncthreads();
+    for (int i = tid; i < passes * 256; i += kJoinThreads) {
+      const uint32_t c = (&s_hist[0][0])[i];
+      if (c) atomicAdd(&ghist[i], (unsigned long long)c);
     }
   }
 }

@@ -238,7 +238,7 @@ hisa_status join_t(const void* outer, uint64_t no, const void* inner, uint64_t n
   const uint64_t tot = P.h.cnt[total];
   *n_out = tot;
   if (P.h.overflow) return HISA_ERR_CAPACITY;
-  j.starts_buf = P.scratch(tot / kJoinChunk + 2, 8);
+  j.starts_buf = P.scratch(tot / kJoinChunkMin + 2, 8);
   if ((s = P.upload())) return s;
   launch_join_write<K>(j, P.g, P.s);
   return P.download();

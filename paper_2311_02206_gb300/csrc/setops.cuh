@@ -24,10 +24,12 @@ namespace hisa {
 
 template <typename K>
 struct SetopCfg;
+// Items per thread: odd, so that the threads' merge positions (about
+// tid * items / 2 into each input) fall on different shared-memory banks.
 template <>
-struct SetopCfg<uint32_t> { static constexpr int items = 16; };
+struct SetopCfg<uint32_t> { static constexpr int items = 15; };
 template <>
-struct SetopCfg<uint64_t> { static constexpr int items = 8; };
+struct SetopCfg<uint64_t> { static constexpr int items = 7; };
 constexpr int kSetopThreads = 256;
 template <typename K>
 __host__ __device__ constexpr int setop_tile() { return kSetopThreads * SetopCfg<K>::items; }
@@ -122,10 +124,10 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
   const uint32_t epoch = st->epoch;
   const int tid = threadIdx.x;
 
+  if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+  __syncthreads();
   while (true) {
-    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
+    const uint64_t tile = s_tile;   // (fetched during the previous tile)
     if (tile >= ntiles) break;
     const uint64_t d0 = tile * C, d1 = min(d0 + C, D);
     const uint64_t a0 = split[tile], a1 = split[tile + 1];
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
       if (b0 > 0) s_prevB = B[b0 - 1];
     }
     __syncthreads();
+    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);   // the next tile, read after this one
     const K* sA = s_in;
     const K* sB = s_in + nA;
     // this thread's slice of the tile's merged sequence
@@ -171,50 +174,46 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
     K val[ITEMS];
     uint32_t kind = 0;   // bit k: item k is a kept B element
     uint32_t isA = 0;    // bit k: item k is an A element
-    int nitems = 0;
-    int kept = 0;
-    // heads of A and B and the last element merged from each, kept in registers
+    const int nmine = max(0, min(ITEMS, nT - dt));
+    const int nitems = nmine;
+    // heads of A and B and the last element merged from each, kept in
+    // registers; a step is branch-free: both heads are compared, the taken one
+    // is replaced by one shared-memory load (A and B are adjacent in s_in)
     bool hasA = ai < nA, hasB = bi < nB;
     K va = hasA ? sA[ai] : K(0), vb = hasB ? sB[bi] : K(0);
     bool hasPrevA = ai > 0 || s_hasA, hasPrevB = bi > 0 || s_hasB;
     K pa = ai > 0 ? sA[ai - 1] : s_prevA;
     K pb = bi > 0 ? sB[bi - 1] : s_prevB;
-    const int nmine = min(ITEMS, nT - dt);
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       if (k >= nmine) break;
       const bool takeA = !hasB || (hasA && va <= vb);
-      if (takeA) {
-        val[k] = va;
-        isA |= 1u << k;
-        pa = va;
-        hasPrevA = true;
-        ++ai;
-        hasA = ai < nA;
-        if (hasA) va = sA[ai];
-      } else {
-        const bool keep = !(hasPrevB && pb == vb) && !(hasPrevA && pa == vb);
-        val[k] = vb;
-        if (keep) {
-          kind |= 1u << k;
-          ++kept;
-        }
-        pb = vb;
-        hasPrevB = true;
-        ++bi;
-        hasB = bi < nB;
-        if (hasB) vb = sB[bi];
-      }
-      ++nitems;
+      const bool keep = !takeA && !(hasPrevB && pb == vb) && !(hasPrevA && pa == vb);
+      val[k] = takeA ? va : vb;
+      isA |= uint32_t(takeA) << k;
+      kind |= uint32_t(keep) << k;
+      pa = takeA ? va : pa;
+      pb = takeA ? pb : vb;
+      hasPrevA = hasPrevA || takeA;
+      hasPrevB = hasPrevB || !takeA;
+      ai += takeA;
+      bi += !takeA;
+      const int nx = takeA ? ai : nA + bi;   // the taken side's next element
+      const K v = s_in[min(nx, C - 1)];
+      va = takeA ? v : va;
+      vb = takeA ? vb : v;
+      hasA = ai < nA;
+      hasB = bi < nB;
     }
+    const int kept = __popc(kind);
     uint64_t tile_kept;
+    // (the scan's barriers also mean every thread has its items in registers:
+    // s_in is free for the staged outputs)
     const uint32_t kexcl = uint32_t(block_exclusive_sum<uint64_t>(kept, s_scan, &tile_kept));
-    if (tid < 32) {
+    if (tid < 32) {   // the tile's delta offset, while the other warps stage
       const uint64_t db = lookback_warp(status, tile, tile_kept, epoch, &st->error);
       if (tid == 0) s_dbase = db;
     }
-    __syncthreads();   // s_in is free: every thread holds its items in registers
-    const uint64_t dbase = s_dbase;
     // stage outputs: full' tile index = A items before + kept before
     int fa = ai0, kk = int(kexcl);
 #pragma unroll
@@ -230,6 +229,7 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
       }
     }
     __syncthreads();
+    const uint64_t dbase = s_dbase;
     const int nF = nA + int(tile_kept);
     if (fout) {
       const uint64_t f0 = a0 + dbase;
