@@ -278,6 +278,14 @@ typedef struct {
   uint32_t active;      /* instances on the device after the call */
   uint32_t pending;     /* submitted, not yet admitted */
   uint32_t iterations;  /* iterations run by this call */
+  /* host wall time of this call's phases, ms: admission (slot choice, EDB
+   * re-staging and indexing), the iterations' kernels, the per-instance delta
+   * sizes read back, retirement (finished instances' tuples copied aside),
+   * compaction (retired instances' tuples removed from full).  With
+   * HISA_FLAG_PHASE_TIMES each phase ends with a stream synchronisation, so
+   * its device work is counted in it; otherwise device work is counted where
+   * the host first waits for it. */
+  double ms_admit, ms_iterate, ms_rows, ms_retire, ms_compact;
 } hisa_serve_stats;
 /* Fixes the session's limits: up to max_instances concurrent instances (a
  * power of two is best), EDB values <= max_value, estimated bytes of admitted

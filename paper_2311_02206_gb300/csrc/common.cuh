@@ -294,17 +294,18 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* smem_warp, T* total) {
   }
   if (lane == 31) smem_warp[warp] = x;
   __syncthreads();
-  // every warp scans the (at most 32) warp totals itself: no second round
-  // trip through shared memory
-  T w = lane < nwarps ? smem_warp[lane] : T(0);
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = __shfl_up_sync(0xffffffffu, w, o);
-    if (lane >= o) w += y;
+  if (warp == 0) {
+    T w = lane < nwarps ? smem_warp[lane] : T(0);
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nwarps) smem_warp[lane] = w;  // inclusive warp prefix
   }
-  const T prev = __shfl_sync(0xffffffffu, w, (warp + 31) & 31);   // inclusive prefix of warp - 1
-  const T warp_excl = warp ? prev : T(0);
-  if (total) *total = __shfl_sync(0xffffffffu, w, nwarps - 1);
-  __syncthreads();   // smem_warp is free for the next call
+  __syncthreads();
+  const T warp_excl = warp ? smem_warp[warp - 1] : T(0);
+  if (total) *total = smem_warp[nwarps - 1];
+  __syncthreads();
   return warp_excl + x - v;
 }
 

@@ -135,13 +135,10 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_pass(RadixPassArgs a
   constexpr int TILE = kRadixThreads * ITEMS;
   extern __shared__ __align__(128) unsigned char radix_dyn[];
   K* s_buf[2] = {reinterpret_cast<K*>(radix_dyn), reinterpret_cast<K*>(radix_dyn) + TILE};
-  // per warp and digit: .x the lanes holding the digit (rank step, zero
-  // between steps), .y the warp's count of the digit, then its running tile
-  // position; one 8-byte word, so a key's rank step reads both at once
-  __shared__ uint2 s_mw[kRadixWarps][kRadixDigits];
+  __shared__ uint32_t s_wh[kRadixWarps][kRadixDigits];     // per-warp counts, then tile positions
+  __shared__ uint32_t s_match[kRadixWarps][kRadixDigits];  // lanes holding each digit (rank step)
   __shared__ int s_bad;
   __shared__ uint64_t s_gdelta[kRadixDigits];           // global position - tile position, per digit
-  __shared__ uint32_t s_gdelta32[kRadixDigits];         // the same modulo 2^32 (key counts below 2^32)
   __shared__ uint64_t s_bucket[kRadixDigits];           // global start of each digit bucket
   __shared__ uint64_t s_scan[32];
   __shared__ uint32_t s_tile[2];
@@ -175,7 +172,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_pass(RadixPassArgs a
     s_bucket[tid] = block_exclusive_sum<uint64_t>(hist[tid], s_scan, &tot);
   }
 #pragma unroll
-  for (int w = 0; w < kRadixWarps; ++w) s_mw[w][tid].x = 0;
+  for (int w = 0; w < kRadixWarps; ++w) s_match[w][tid] = 0;
   if (tid == 0) {
     mbar_init(&s_mbar[0], 1);
     mbar_init(&s_mbar[1], 1);
@@ -216,7 +213,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_pass(RadixPassArgs a
       for (uint32_t i = tid; i < tile_n; i += kRadixThreads) sk[i] = in[t0 + i];
     }
 #pragma unroll
-    for (int w = 0; w < kRadixWarps; ++w) s_mw[w][tid].y = 0;
+    for (int w = 0; w < kRadixWarps; ++w) s_wh[w][tid] = 0;
     __syncthreads();
     // warp-striped arrangement: item k of lane l is tile key warp*32*ITEMS + k*32 + l,
     // so processing items in order keeps the tile's key order (stable ranks)
@@ -226,56 +223,54 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_pass(RadixPassArgs a
     for (int k = 0; k < ITEMS; ++k) {
       const uint32_t i = wofs + k * 32;
       key[k] = i < tile_n ? sk[i] : K(0);
-      if (i < tile_n) atomicAdd(&s_mw[warp][uint32_t(key[k] >> shift) & 0xFF].y, 1u);
+      if (i < tile_n) atomicAdd(&s_wh[warp][uint32_t(key[k] >> shift) & 0xFF], 1u);
     }
     __syncthreads();
     uint32_t cnt = 0;
 #pragma unroll
     for (int w = 0; w < kRadixWarps; ++w) {
-      const uint32_t c = s_mw[w][tid].y;
-      s_mw[w][tid].y = cnt;
+      const uint32_t c = s_wh[w][tid];
+      s_wh[w][tid] = cnt;
       cnt += c;
     }
     lookback_publish(status + tid, tile, kRadixDigits, cnt, epoch);
     uint64_t tot;
     const uint32_t excl = uint32_t(block_exclusive_sum<uint64_t>(cnt, s_scan, &tot));
 #pragma unroll
-    for (int w = 0; w < kRadixWarps; ++w) s_mw[w][tid].y += excl;
+    for (int w = 0; w < kRadixWarps; ++w) s_wh[w][tid] += excl;
     __syncthreads();   // every key is in registers: the buffer takes the ranked tile
-    uint2* mw = s_mw[warp];
+    uint32_t* match = s_match[warp];
+    uint32_t* wh = s_wh[warp];
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       const bool valid = wofs + k * 32 < tile_n;
       const uint32_t d = uint32_t(key[k] >> shift) & 0xFF;
-      if (valid) atomicOr(&mw[d].x, 1u << lane);
+      if (valid) atomicOr(&match[d], 1u << lane);
       __syncwarp();
-      uint2 v = make_uint2(0u, 0u);
-      if (valid) v = mw[d];   // .x: the lanes holding d, .y: d's next position
+      uint32_t peers = 0, base = 0;
+      if (valid) {
+        peers = match[d];
+        base = wh[d];
+      }
       __syncwarp();
-      const uint32_t before = __popc(v.x & lt_mask);
-      if (valid && before == 0) mw[d] = make_uint2(0u, v.y + __popc(v.x));   // lowest lane: advance, clear
+      const uint32_t before = __popc(peers & lt_mask);
+      if (valid && before == 0) {   // the lowest lane of the digit: advance and clear
+        wh[d] = base + __popc(peers);
+        match[d] = 0;
+      }
       __syncwarp();
-      if (valid) sk[v.y + before] = key[k];
+      if (valid) sk[base + before] = key[k];
     }
     // global offset of this tile's run of digit `tid`, checked once per digit
     const uint64_t prev = lookback_resolve(status + tid, tile, kRadixDigits, cnt, epoch, &st->error);
     const uint64_t gstart = s_bucket[tid] + prev;
     s_gdelta[tid] = gstart - excl;
-    s_gdelta32[tid] = uint32_t(gstart - excl);
     if (tid == 0) s_bad = 0;
     __syncthreads();
     if (gstart + cnt > n) s_bad = 1;   // histogram and keys disagree
     __syncthreads();
     if (s_bad) {
       if (tid == 0) atomicExch(&st->error, kDevBadState);
-    } else if (tile_n == TILE && n <= 0xFFFFFFFFull) {
-      // every position fits 32 bits: gstart - excl + i is exact modulo 2^32
-#pragma unroll 4
-      for (int k = 0; k < ITEMS; ++k) {
-        const uint32_t i = uint32_t(tid) + uint32_t(k) * kRadixThreads;
-        const K v = sk[i];
-        out[s_gdelta32[uint32_t(v >> shift) & 0xFF] + i] = v;
-      }
     } else if (tile_n == TILE) {
 #pragma unroll 4
       for (int k = 0; k < ITEMS; ++k) {

@@ -10,6 +10,7 @@
 // instance whose delta becomes empty: its tuples are copied out and its range
 // of the sorted relations is cut out.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 
 #include "engine.h"
@@ -470,6 +471,21 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
   if (!serving) return ctx_fail(HISA_ERR_STATE, "no serving session", nullptr);
   hisa_serve_stats out{};
   hisa_status s;
+  // phase clock: with HISA_FLAG_PHASE_TIMES a phase ends with a synchronisation
+  const bool sync_phases = (cfg.flags & HISA_FLAG_PHASE_TIMES) != 0;
+  auto tick = std::chrono::steady_clock::now();
+  auto phase = [&](double& acc) {
+    if (sync_phases) cudaStreamSynchronize(stream);
+    const auto now = std::chrono::steady_clock::now();
+    acc += std::chrono::duration<double, std::milli>(now - tick).count();
+    tick = now;
+  };
+  auto compact_timed = [&]() {
+    phase(out.ms_admit);   // what came before belongs to the caller's phase
+    const hisa_status r = compact_dead();
+    phase(out.ms_compact);
+    return r;
+  };
   for (uint32_t it = 0; it < std::max(max_iters, 1u); ++it) {
     // admission at the iteration boundary: free slot and budget
     std::vector<uint64_t> admitted;
@@ -489,12 +505,12 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
       auto free_slot = clean_free();
       if (free_slot == slot_owner.end() &&
           std::find(slot_owner.begin(), slot_owner.end(), 0ull) != slot_owner.end()) {
-        if ((s = compact_dead())) return s;   // a retired slot is reused: its tuples go first
+        if ((s = compact_timed())) return s;   // a retired slot is reused: its tuples go first
         free_slot = clean_free();
       }
       if (free_slot == slot_owner.end()) break;
       if (serve_budget && active_bytes + q.est_bytes > serve_budget && dead_bytes > 0) {
-        if ((s = compact_dead())) return s;   // retired instances' memory counts until it is freed
+        if ((s = compact_timed())) return s;   // retired instances' memory counts until it is freed
       }
       if (serve_budget && active_bytes + q.est_bytes > serve_budget && active_bytes > 0) break;
       q.slot = int(free_slot - slot_owner.begin());
@@ -505,13 +521,16 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
     }
     out.admitted += uint32_t(admitted.size());
     if (!admitted.empty() && (s = rebuild_serving_edb(admitted))) return s;
+    phase(out.ms_admit);
     const bool any_active = std::any_of(slot_owner.begin(), slot_owner.end(), [](uint64_t t) { return t != 0; });
     if (!any_active) break;
     // one iteration of the shared fixpoint
     if ((s = iterate_once(admitted.empty() ? opsN : ops_admit))) return s;
     ++out.iterations;
+    phase(out.ms_iterate);
     std::vector<std::vector<uint64_t>> rows;
     if ((s = collect_inst_rows(rows))) return s;
+    phase(out.ms_rows);
     std::vector<uint64_t> finished;
     for (uint32_t slot = 0; slot < serve_slots; ++slot) {
       const uint64_t t = slot_owner[slot];
@@ -531,9 +550,13 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
       }
     if ((s = retire(finished))) return s;
     out.retired += uint32_t(finished.size());
+    phase(out.ms_retire);
     uint64_t live = 0;
     for (int r : idb) live += hs.cnt[rels[r].full] + (rels[r].log ? hs.cnt[rels[r].l1] : 0);
-    if (dead_tuples * 2 > live && (s = compact_dead())) return s;
+    if (dead_tuples * 2 > live) {
+      if ((s = compact_dead())) return s;
+      phase(out.ms_compact);
+    }
   }
   out.pending = uint32_t(pending.size());
   out.active = uint32_t(std::count_if(slot_owner.begin(), slot_owner.end(), [](uint64_t t) { return t != 0; }));

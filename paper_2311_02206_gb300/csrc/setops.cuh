@@ -124,10 +124,10 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
   const uint32_t epoch = st->epoch;
   const int tid = threadIdx.x;
 
-  if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
-  __syncthreads();
   while (true) {
-    const uint64_t tile = s_tile;   // (fetched during the previous tile)
+    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
     if (tile >= ntiles) break;
     const uint64_t d0 = tile * C, d1 = min(d0 + C, D);
     const uint64_t a0 = split[tile], a1 = split[tile + 1];
@@ -154,7 +154,6 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
       if (b0 > 0) s_prevB = B[b0 - 1];
     }
     __syncthreads();
-    if (tid == 0) s_tile = atomicAdd(&st->tile_ctr[a.ctr], 1u);   // the next tile, read after this one
     const K* sA = s_in;
     const K* sB = s_in + nA;
     // this thread's slice of the tile's merged sequence
@@ -207,13 +206,13 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
     }
     const int kept = __popc(kind);
     uint64_t tile_kept;
-    // (the scan's barriers also mean every thread has its items in registers:
-    // s_in is free for the staged outputs)
     const uint32_t kexcl = uint32_t(block_exclusive_sum<uint64_t>(kept, s_scan, &tile_kept));
-    if (tid < 32) {   // the tile's delta offset, while the other warps stage
+    if (tid < 32) {
       const uint64_t db = lookback_warp(status, tile, tile_kept, epoch, &st->error);
       if (tid == 0) s_dbase = db;
     }
+    __syncthreads();   // s_in is free: every thread holds its items in registers
+    const uint64_t dbase = s_dbase;
     // stage outputs: full' tile index = A items before + kept before
     int fa = ai0, kk = int(kexcl);
 #pragma unroll
@@ -229,7 +228,6 @@ __global__ void __launch_bounds__(kSetopThreads, 5) k_setop(SetopArgs a) {
       }
     }
     __syncthreads();
-    const uint64_t dbase = s_dbase;
     const int nF = nA + int(tile_kept);
     if (fout) {
       const uint64_t f0 = a0 + dbase;

@@ -85,7 +85,9 @@ class RunStats(ctypes.Structure):
 
 class ServeStats(ctypes.Structure):
     _fields_ = [("admitted", ctypes.c_uint32), ("retired", ctypes.c_uint32), ("active", ctypes.c_uint32),
-                ("pending", ctypes.c_uint32), ("iterations", ctypes.c_uint32)]
+                ("pending", ctypes.c_uint32), ("iterations", ctypes.c_uint32),
+                ("ms_admit", ctypes.c_double), ("ms_iterate", ctypes.c_double), ("ms_rows", ctypes.c_double),
+                ("ms_retire", ctypes.c_double), ("ms_compact", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
