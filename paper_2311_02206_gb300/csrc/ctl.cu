@@ -343,7 +343,7 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
 
 const char* const kKernelNames[kKindCount] = {
     "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
-    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level", "chain_len", "chain_scan", "chain_gather", "join_dense_pull", "matrix_merge"};
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level", "chain_len", "chain_scan", "chain_gather", "join_dense_pull", "matrix_merge", "matrix_diff"};
 
 thread_local KernelTimer* g_timer = nullptr;
 thread_local uint64_t g_launches = 0;

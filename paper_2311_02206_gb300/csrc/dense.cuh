@@ -196,6 +196,12 @@ struct DenseArgs {
   // bit o for every (g, o) in full, 2^b bits per row.  The difference against
   // full is then one AND-NOT of the group's row; full_buf is -1.
   int fbm_buf = -1;
+  // batched runs: the row of (instance, g) is the code shifted right by b,
+  // masked to row_bits bits (instance bits + b; 0: b).  fbm_or = 0 leaves the
+  // matrix to the tail (k_matrix_codes takes each committed delta), so an
+  // iteration that is run again never finds its own tuples in full.
+  int row_bits = 0;
+  int fbm_or = 1;
   // the previous iteration's group bitmaps (the bitmap slots are swapped after
   // every committed iteration) and, per kept value, its group index there
   // (written by the emit): from iteration 3 on the pull kernel copies a
@@ -354,6 +360,7 @@ struct MatrixArgs {
   int fbm_buf, fcnt_buf;
   int skip_mask;
   int gate1;                    // k_matrix_codes runs only when cnt[gate1 - 1] != 0 (0: always)
+  int row_bits = 0;             // bits of a row index (instance bits + b; 0: b)
 };
 // The same from codes (kept value in the high half): iteration 1's delta.
 template <typename K>
@@ -365,9 +372,11 @@ __global__ void k_matrix_codes(MatrixArgs a) {
   uint32_t* fbm = static_cast<uint32_t*>(st->buf[a.fbm_buf].ptr);
   uint32_t* fcnt = static_cast<uint32_t*>(st->buf[a.fcnt_buf].ptr);
   const uint32_t vmask = (1u << a.b) - 1;
+  const uint64_t rmask = a.row_bits > 0 ? (1ull << a.row_bits) - 1 : uint64_t(vmask);
   const uint64_t nwords = a.b >= 5 ? (1ull << (a.b - 5)) : 1;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
-    const uint32_t g = uint32_t(uint64_t(codes[i]) >> a.b) & vmask, o = uint32_t(codes[i]) & vmask;
+    const uint64_t g = (uint64_t(codes[i]) >> a.b) & rmask;
+    const uint32_t o = uint32_t(codes[i]) & vmask;
     const uint32_t bit = 1u << (o & 31);
     if (!(atomicOr(&fbm[uint64_t(g) * nwords + (o >> 5)], bit) & bit)) atomicAdd(&fcnt[g], 1u);
   }
@@ -686,7 +695,8 @@ __global__ void __launch_bounds__(kDenseThreads, kDenseCtasPerSm) k_dense_mark(D
       atomicAnd(&s_bm[g >> 5], ~(1u << (g & 31)));
     }
     if (a.fbm_buf >= 0) {   // full as a bit matrix: clear the bits of the group's row
-      const uint64_t g = (uint64_t(outer[gs[gi]]) >> a.b) & vmask;
+      const uint64_t rmask = a.row_bits > 0 ? (1ull << a.row_bits) - 1 : uint64_t(vmask);
+      const uint64_t g = (uint64_t(outer[gs[gi]]) >> a.b) & rmask;
       const uint32_t* row = static_cast<const uint32_t*>(st->buf[a.fbm_buf].ptr) + g * uint64_t(nwords);
       for (int j = tid; j < nwords; j += kDenseThreads) {   // atomic: the filter above may clear a bit too
         const uint32_t f = row[j];
@@ -912,14 +922,15 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_emit(DenseArgs a) {
   // grows by their count: this launch runs once per committed iteration (only
   // when the join stage did not overflow, and nothing after it in that stage
   // can: the matrix is kept for single-relation programs only)
-  uint32_t* fbm = a.fbm_buf >= 0 ? static_cast<uint32_t*>(st->buf[a.fbm_buf].ptr) : nullptr;
+  uint32_t* fbm = a.fbm_buf >= 0 && a.fbm_or ? static_cast<uint32_t*>(st->buf[a.fbm_buf].ptr) : nullptr;
   uint32_t* fcnt = fbm ? static_cast<uint32_t*>(st->buf[a.fcnt_buf].ptr) : nullptr;
   const uint32_t vmask = a.b >= 32 ? 0xFFFFFFFFu : ((1u << a.b) - 1);
+  const uint64_t rmask = a.row_bits > 0 ? (1ull << a.row_bits) - 1 : uint64_t(vmask);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (uint64_t gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
     const uint64_t gcode = uint64_t(outer[gs[gi]]) >> a.b;   // (inst, g): the result's high part
     const uint32_t* gbm = bm + gi * uint64_t(nwords);
-    uint32_t* row = fbm ? fbm + uint64_t(uint32_t(gcode) & vmask) * nwords : nullptr;
+    uint32_t* row = fbm ? fbm + (gcode & rmask) * nwords : nullptr;
     const int w0 = warp * wrange, w1 = min(nwords, w0 + wrange);
     uint32_t cnt = 0;
     for (int j = w0 + lane; j < w1; j += 32) {
@@ -934,7 +945,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_emit(DenseArgs a) {
     if (row && tid == 0) {
       uint32_t t = 0;
       for (int w = 0; w < nwarps; ++w) t += s_wtot[w];
-      fcnt[uint32_t(gcode) & vmask] += t;
+      fcnt[gcode & rmask] += t;
     }
     if (a.prev_gi_buf >= 0 && tid == 0)
       static_cast<uint32_t*>(st->buf[a.prev_gi_buf].ptr)[uint32_t(gcode) & vmask] = uint32_t(gi);

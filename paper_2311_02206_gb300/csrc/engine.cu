@@ -187,6 +187,7 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.dense_bm = new_slot(4);
   sc.tmp_hist = new_slot(8);
   sc.gather = new_slot(4);
+  sc.mrows = new_slot(8);
   sc.dense_first = new_slot(8);
   sc.dense_units = new_slot(8);
   sc.dense_done = new_slot(4);
@@ -696,6 +697,12 @@ hisa_status Engine::compile() {
   for (int r : idb) {
     Relation& R = rels[r];
     R.mfull = R.append && idb.size() == 1 && b >= 8 && b <= kMatrixMaxBits && !(cfg.flags & HISA_FLAG_LEVELS);
+    // batched and served runs (matrix.cuh): row (instance, g), when the matrix
+    // of all instance slots fits; the dense join then writes new like any
+    // other writer and the tail takes delta = unique(new) \ full by bit tests
+    if (batched && R.dense_head && idb.size() == 1 && b <= kMatrixMaxBits && !(cfg.flags & HISA_FLAG_LEVELS) &&
+        inst_bits + 2 * b <= 40 && (1ull << (inst_bits + 2 * b)) / 8 <= kBatchMatrixMaxBytes)
+      R.mfull = true;
     if (R.mfull && R.fbm < 0) R.fbm = new_slot(4);
     if (R.mfull && R.fcnt < 0) R.fcnt = new_slot(4);
   }
@@ -733,7 +740,7 @@ hisa_status Engine::compile() {
   // and merged): REACH and SG, not CSPA's inner IDB atoms nor batched runs
   for (int r : idb) {
     Relation& R = rels[r];
-    R.log = (cfg.flags & HISA_FLAG_LOG_FULL) && !R.need_idx[0] && !R.need_idx[1] && !R.append;
+    R.log = (cfg.flags & HISA_FLAG_LOG_FULL) && !R.need_idx[0] && !R.need_idx[1] && !R.append && !R.mfull;
   }
   compiled = true;
   graph_stale = true;
@@ -1002,6 +1009,8 @@ void Engine::emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_gro
   if (hr.mfull) {   // the emit ORs the groups' new tuples into full's bit matrix
     d.dense.fbm_buf = hr.fbm;
     d.dense.fcnt_buf = hr.fcnt;
+    d.dense.row_bits = b + inst_bits;
+    d.dense.fbm_or = batched ? 0 : 1;   // batched: the tail adds the committed delta
   }
   if (pull) {
     DenseArgs& da = d.dense;
@@ -1273,6 +1282,20 @@ void Engine::emit_tail(std::vector<Op>& ops, bool force) {
       ops.push_back(p);
       continue;
     }
+    if (R.mfull) {
+      // batched runs (matrix.cuh): delta = unique(new) \ full by bit tests,
+      // then delta ORed into the rows; full's count grows at the commit
+      Op d{};
+      d.kind = Op::MDIFF;
+      d.mdiff = MatrixDiffArgs{dst, R.fresh, R.fresh, R.delta_next, R.delta_next, sc.setop_status, R.fbm, b,
+                               b + inst_bits, 2, 3, 1};
+      ops.push_back(d);
+      Op m{};
+      m.kind = Op::MCODES;
+      m.matrix = MatrixArgs{dst, -1, -1, -1, -1, R.delta_next, R.delta_next, b, R.fbm, R.fcnt, 3, 0, b + inst_bits};
+      ops.push_back(m);
+      continue;
+    }
     if (R.log) {
       const int sorted_new = R.fresh;
       emit_level_merge(ops, R, false);
@@ -1397,6 +1420,7 @@ hisa_status Engine::exec_t(const std::vector<Op>& ops) {
       case Op::DENSE: launch_join_dense<K>(o.dense, grid, stream); break;
       case Op::CHAIN: launch_chain<K>(o.chain, grid, stream); break;
       case Op::MCODES: launch_matrix_codes<K>(o.matrix, grid, stream); break;
+      case Op::MDIFF: launch_matrix_diff<K>(o.mdiff, grid, stream); break;
     }
   }
   return check_launch("kernel launch");
@@ -1741,10 +1765,12 @@ hisa_status Engine::init_run_state() {
   for (int r : idb) {
     Relation& R = rels[r];
     if (!R.mfull) continue;
-    const uint64_t words = (1ull << (2 * b)) / 32;
-    if ((s = ensure(R.fbm, words)) || (s = ensure(R.fcnt, 1ull << b))) return s;
+    // one row per (instance slot, value): 2^(inst_bits + b) rows of 2^b bits
+    const uint64_t rows = 1ull << (b + (batched ? inst_bits : 0));
+    const uint64_t words = rows * (b >= 5 ? (1ull << (b - 5)) : 1ull);
+    if ((s = ensure(R.fbm, words)) || (s = ensure(R.fcnt, rows))) return s;
     CU(cudaMemsetAsync(hs.buf[R.fbm].ptr, 0, words * 4, stream));
-    CU(cudaMemsetAsync(hs.buf[R.fcnt].ptr, 0, (1ull << b) * 4, stream));
+    CU(cudaMemsetAsync(hs.buf[R.fcnt].ptr, 0, rows * 4, stream));
   }
   for (int r : idb) {
     Relation& R = rels[r];
@@ -1868,6 +1894,10 @@ hisa_status Engine::run_loop(hisa_run_stats* stats, std::chrono::steady_clock::t
             if (nn > 0 && !dense) kstat[kKSetop].bytes += (nn + nd) * kb;
             if (nd > 0 && !R.mfull) kstat[kKAppend].bytes += 2.0 * nd * kb + 8.0 * double((1u << b) + 1);
             if (nd > 0 && R.mfull && !dense) kstat[kKMatrix].bytes += nd * kb + 8.0 * nd;
+          } else if (R.mfull) {
+            // bit tests of new (one matrix word each), delta written; delta ORed in
+            if (nn > 0) kstat[kKMatrixDiff].bytes += nn * (kb + 4.0) + nd * kb;
+            if (nd > 0) kstat[kKMatrix].bytes += nd * (kb + 8.0);
           } else if (R.log && hs.cnt[R.bigf]) {
             // small level folded in, then new merged into the large level
             const double lp = double(l_prev[i]);
@@ -2205,7 +2235,18 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
   int src = r.idb ? r.full : r.base;
   // a full kept as a bit matrix: its rows written in order, transposed first
   // when stored column-swapped (the row matrix is needed then: no fallback)
-  const bool matrix = r.idb && r.mfull;
+  const bool matrix = r.idb && r.mfull && !batched;
+  // a batched run's matrix (rows per instance): its rows read out as codes in
+  // the stored order, then handled like a sorted full
+  const bool bmat = r.idb && r.mfull && batched;
+  int codes = r.full;
+  if (bmat) {
+    if ((s = ensure(sc.gather, size)) ||
+        (s = matrix_rows_out(r, 0, 1ull << (b + inst_bits), sc.gather, 0)))
+      return s;
+    codes = sc.gather;
+    hs.cnt[sc.gather] = size;
+  }
   if (matrix && (((s = ensure(sc.read_rows, (1ull << b) + 1))) ||
                  (r.order == 1 && (s = ensure(sc.read_m, (1ull << (2 * b)) / 32)))))
     return s;
@@ -2219,7 +2260,7 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
     transposed = false;   // the matrix does not fit (budget): sort instead
     last_error.clear();
   }
-  if (r.idb && (r.order == 1 || r.append) && !levels && !transposed && !matrix) {
+  if (r.idb && (r.order == 1 || r.append || bmat) && !levels && !transposed && !matrix) {
     // stored (c1, c0), or as unmerged levels: (exchange the columns and) sort,
     // so the caller gets the lexicographic order of the declared columns
     const int kt = wide ? radix_tile<uint64_t>() : radix_tile<uint32_t>();
@@ -2231,10 +2272,10 @@ hisa_status Engine::read_relation(uint32_t rid, uint32_t* const* cols, uint64_t 
     if (r.order == 1) {
       Op w{};
       w.kind = Op::SWAP;
-      w.swap = SwapArgs{dst, r.full, r.full, sc.tmp_a, sc.tmp_cnt, b, 0, 0};
+      w.swap = SwapArgs{dst, codes, codes, sc.tmp_a, sc.tmp_cnt, b, 0, 0};
       ops.push_back(w);
     } else {
-      CU(cudaMemcpyAsync(hs.buf[sc.tmp_a].ptr, hs.buf[r.full].ptr, size * (wide ? 8 : 4), cudaMemcpyDeviceToDevice,
+      CU(cudaMemcpyAsync(hs.buf[sc.tmp_a].ptr, hs.buf[codes].ptr, size * (wide ? 8 : 4), cudaMemcpyDeviceToDevice,
                          stream));
       Op c{};
       c.kind = Op::CTL;

@@ -82,7 +82,7 @@ struct StepPlan {
 
 struct Op {
   enum Kind { CTL, JOIN, PASS, HIST, SETOP, COMMIT, RUNS, INDEX, ZERO, SWAP, DIFF, DENSE, GCOMPACT, APPEND, GROUPS, CHAIN,
-              MCODES } kind;
+              MCODES, MDIFF } kind;
   CtlArgs ctl;
   JoinArgs join;
   RadixPassArgs pass;
@@ -99,6 +99,7 @@ struct Op {
   DenseArgs dense;
   ChainArgs chain;
   MatrixArgs matrix;
+  MatrixDiffArgs mdiff;
 };
 
 struct Scratch {
@@ -108,6 +109,7 @@ struct Scratch {
   int dense_bm;               // the dense join's per-group bitmaps
   int tmp_hist;               // digit histograms of a Tmp relation sorted before a dense join
   int gather;                 // an instance's codes from both levels of a log-structured full
+  int mrows;                  // u64 row offsets of a bit-matrix read-out (matrix.cuh)
   int dense_first;            // direct index of a delta by its kept column (group starts)
   int dense_units, dense_done;  // the dense join's first unit per group and finished-unit counters
   int dense_mslot, dense_bmm;   // multi-unit groups' bitmap slot and those bitmaps (kept zeroed)
@@ -211,6 +213,10 @@ class Engine {
                            std::vector<uint32_t>& c1);
   hisa_status rebuild_serving_edb(const std::vector<uint64_t>& admitted);
   hisa_status retire(const std::vector<uint64_t>& tickets);
+  // codes of bit-matrix rows [row0, row0 + nrows) of R, stored order, into
+  // `slot` from position `at` (the slot must hold them)
+  hisa_status matrix_rows_out(const Relation& R, uint64_t row0, uint64_t nrows, int slot, uint64_t at);
+  uint64_t inst_total(size_t idb_index, uint32_t inst) const;   // sum of an instance's delta sizes
   hisa_status compact_dead();
   hisa_status compact(int slot, int next, const std::vector<uint64_t>& bnd, const std::vector<bool>& drop);
   hisa_status declared_order(int slot, uint64_t begin, uint64_t count, int* out);

@@ -8,6 +8,7 @@
 #include "setops.cuh"
 #include "dense.cuh"
 #include "read.cuh"
+#include "matrix.cuh"
 #include <vector>
 
 namespace hisa {
@@ -133,7 +134,7 @@ struct SwapArgs {
 
 enum KernelKind : int {
   kKEncode, kKDecode, kKRuns, kKHist, kKRadixPass, kKSetopPartition, kKSetop, kKIndex,
-  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKAppend, kKChainLen, kKChainScan, kKChainGather, kKJoinPull, kKMatrix, kKindCount
+  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKAppend, kKChainLen, kKChainScan, kKChainGather, kKJoinPull, kKMatrix, kKMatrixDiff, kKindCount
 };
 extern const char* const kKernelNames[kKindCount];
 
@@ -193,6 +194,8 @@ template <typename K> void launch_chain(const ChainArgs& a, const Grid& g, cudaS
 template <typename K> void launch_levels_read(const LevelsReadArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_levels_transpose(const LevelsTransposeArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_matrix_codes(const MatrixArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_matrix_diff(const MatrixDiffArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_matrix_extract(const MatrixExtractArgs& a, const Grid& g, cudaStream_t s);
 // a full kept as a bit matrix read in the declared order: transposed (order 1)
 // or read as it is (order 0), then its rows counted, scanned and written
 template <typename K> void launch_matrix_read(const MatrixTransposeArgs& t, const LevelsTransposeArgs& a, bool transpose,

@@ -196,6 +196,23 @@ void launch_matrix_codes(const MatrixArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKMatrix, s, (k_matrix_codes<K><<<g.small, 256, 0, s>>>(a)));
 }
 template <typename K>
+void launch_matrix_diff(const MatrixDiffArgs& a, const Grid& g, cudaStream_t s) {
+  CtlArgs c{};
+  c.st = a.st;
+  c.skip_mask = a.skip_mask;
+  c.n = 2;
+  c.cmd[0] = {kCtlEpoch, 0, 0};
+  c.cmd[1] = {kCtlResetCtr, a.ctr, 0};
+  launch_ctl(c, s);
+  HISA_LAUNCH(kKMatrixDiff, s, (k_matrix_diff<K><<<g.setop, kDiffThreads, 0, s>>>(a)));
+}
+template <typename K>
+void launch_matrix_extract(const MatrixExtractArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKDecode, s, (k_matrix_extract_counts<<<g.small, 256, 0, s>>>(a)));
+  HISA_LAUNCH(kKDecode, s, (k_matrix_extract_scan<<<1, 1024, 0, s>>>(a)));
+  HISA_LAUNCH(kKDecode, s, (k_matrix_extract<K><<<g.sms * 8, kDenseThreads, 0, s>>>(a)));
+}
+template <typename K>
 void launch_matrix_read(const MatrixTransposeArgs& t, const LevelsTransposeArgs& a, bool transpose, const Grid& g,
                         cudaStream_t s) {
   if (transpose) HISA_LAUNCH(kKDecode, s, (k_matrix_transpose<<<g.sms * 8, 256, 0, s>>>(t)));
@@ -345,6 +362,8 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_levels_read<K>(const LevelsReadArgs&, const Grid&, cudaStream_t);  \
   template void launch_levels_transpose<K>(const LevelsTransposeArgs&, const Grid&, cudaStream_t); \
   template void launch_matrix_codes<K>(const MatrixArgs&, const Grid&, cudaStream_t);    \
+  template void launch_matrix_diff<K>(const MatrixDiffArgs&, const Grid&, cudaStream_t); \
+  template void launch_matrix_extract<K>(const MatrixExtractArgs&, const Grid&, cudaStream_t); \
   template void launch_matrix_read<K>(const MatrixTransposeArgs&, const LevelsTransposeArgs&, bool, const Grid&, \
                                       cudaStream_t);                                     \
   template void launch_radix_hist<K>(const RadixHistArgs&, const Grid&, cudaStream_t);   \

@@ -92,6 +92,26 @@ hisa_status Engine::decode_range(int slot, uint64_t begin, uint64_t count, std::
   return HISA_OK;
 }
 
+hisa_status Engine::matrix_rows_out(const Relation& R, uint64_t row0, uint64_t nrows, int slot, uint64_t at) {
+  hisa_status s;
+  if ((s = ensure(sc.mrows, nrows + 1))) return s;
+  const uint64_t kb = wide ? 8 : 4;
+  MatrixExtractArgs a{static_cast<const uint32_t*>(hs.buf[R.fbm].ptr), static_cast<const uint32_t*>(hs.buf[R.fcnt].ptr),
+                      row0, nrows, b, static_cast<uint64_t*>(hs.buf[sc.mrows].ptr),
+                      static_cast<char*>(hs.buf[slot].ptr) + at * kb};
+  if (wide) launch_matrix_extract<uint64_t>(a, grid, stream);
+  else launch_matrix_extract<uint32_t>(a, grid, stream);
+  CU(cudaGetLastError());
+  return HISA_OK;
+}
+
+uint64_t Engine::inst_total(size_t i, uint32_t inst) const {
+  uint64_t t = 0;
+  if (i < inst_hist.size() && inst < inst_hist[i].size())
+    for (uint64_t d : inst_hist[i][inst]) t += d;
+  return t;
+}
+
 static int find_idb(const std::vector<int>& idb, uint32_t rid) {
   for (size_t i = 0; i < idb.size(); ++i)
     if (uint32_t(idb[i]) == rid) return int(i);
@@ -103,6 +123,10 @@ hisa_status Engine::instance_size(uint32_t rid, uint32_t inst, uint64_t* n) {
   if (!batched || inst > max_inst) return ctx_fail(HISA_ERR_INVALID_ARG, "no such instance", nullptr);
   const Relation& r = rels[rid];
   if ((r.idb && !ran) || (!r.idb && edb_dirty)) return ctx_fail(HISA_ERR_STATE, "relation not evaluated yet", nullptr);
+  if (r.idb && r.mfull) {   // full as a bit matrix: the instance's deltas are disjoint
+    *n = inst_total(size_t(find_idb(idb, rid)), inst);
+    return HISA_OK;
+  }
   std::vector<uint64_t> bnd;
   hisa_status s = inst_bounds(r.idb ? r.full : r.base, bnd);
   if (s) return s;
@@ -167,15 +191,26 @@ hisa_status Engine::read_instance(uint32_t rid, uint32_t inst, uint32_t* const* 
   if (!batched || inst > max_inst) return ctx_fail(HISA_ERR_INVALID_ARG, "no such instance", nullptr);
   const Relation& r = rels[rid];
   if ((r.idb && !ran) || (!r.idb && edb_dirty)) return ctx_fail(HISA_ERR_STATE, "relation not evaluated yet", nullptr);
-  const int slot = r.idb ? r.full : r.base;
-  std::vector<uint64_t> bnd;
-  hisa_status s = inst_bounds(slot, bnd);
-  if (s) return s;
-  uint64_t lo = bnd[inst];
-  const uint64_t cnt = bnd[inst + 1] - bnd[inst];
-  *n = cnt;
-  if (cap < cnt) return ctx_fail(HISA_ERR_CAPACITY, "read_instance: buffer too small", nullptr);
-  if (cnt == 0) return HISA_OK;
+  int slot = r.idb ? r.full : r.base;
+  hisa_status s;
+  uint64_t lo = 0, cnt = 0;
+  if (r.idb && r.mfull) {   // the instance's block of matrix rows, read out as codes
+    cnt = inst_total(size_t(find_idb(idb, rid)), inst);
+    *n = cnt;
+    if (cap < cnt) return ctx_fail(HISA_ERR_CAPACITY, "read_instance: buffer too small", nullptr);
+    if (cnt == 0) return HISA_OK;
+    if ((s = ensure(sc.gather, cnt)) || (s = matrix_rows_out(r, uint64_t(inst) << b, 1ull << b, sc.gather, 0)))
+      return s;
+    slot = sc.gather;
+  } else {
+    std::vector<uint64_t> bnd;
+    if ((s = inst_bounds(slot, bnd))) return s;
+    lo = bnd[inst];
+    cnt = bnd[inst + 1] - bnd[inst];
+    *n = cnt;
+    if (cap < cnt) return ctx_fail(HISA_ERR_CAPACITY, "read_instance: buffer too small", nullptr);
+    if (cnt == 0) return HISA_OK;
+  }
   int src = slot;
   if (r.idb && r.order == 1) {   // stored (c1, c0): into the declared order
     if ((s = declared_order(slot, lo, cnt, &src))) return s;
@@ -373,6 +408,17 @@ hisa_status Engine::compact_dead() {
   if (!any) return HISA_OK;
   for (int r : idb) {
     Relation& R = rels[r];
+    if (R.mfull) {   // clear the retired instances' blocks of rows
+      const uint64_t nw = b >= 5 ? (1ull << (b - 5)) : 1ull;
+      for (uint32_t i = 0; i < serve_slots; ++i) {
+        if (!drop[i]) continue;
+        const uint64_t row0 = uint64_t(i) << b;
+        CU(cudaMemsetAsync(static_cast<uint32_t*>(hs.buf[R.fbm].ptr) + row0 * nw, 0, (1ull << b) * nw * 4, stream));
+        CU(cudaMemsetAsync(static_cast<uint32_t*>(hs.buf[R.fcnt].ptr) + row0, 0, (1ull << b) * 4, stream));
+      }
+      hs.cnt[R.full] -= std::min(hs.cnt[R.full], dead_tuples);   // (the only IDB relation)
+      continue;
+    }
     std::vector<uint64_t> bnd;
     if ((s = inst_bounds(R.full, bnd)) || (s = compact(R.full, R.full_next, bnd, drop))) return s;
     if (R.log && ((s = inst_bounds(R.l1, bnd)) || (s = compact(R.l1, R.l1_next, bnd, drop)))) return s;
@@ -392,10 +438,52 @@ hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
   hisa_status s;
   for (int r : idb) {
     Relation& R = rels[r];
+    const uint64_t kb = wide ? 8 : 4;
+    if (R.mfull) {
+      // each finished instance's block of rows read out as codes (its size is
+      // the sum of its delta sizes), sorted into the declared column order,
+      // copied aside; the block is cleared when the slot is compacted
+      uint64_t total = 0;
+      std::vector<uint64_t> cnt(tickets.size(), 0);
+      for (size_t k = 0; k < tickets.size(); ++k) {
+        for (uint64_t d : reqs[tickets[k]].deltas[r]) cnt[k] += d;
+        total += cnt[k];
+      }
+      if (total > 0) {
+        if ((s = ensure(sc.gather, total))) return s;
+        uint64_t w = 0;
+        for (size_t k = 0; k < tickets.size(); ++k) {
+          if (cnt[k] && (s = matrix_rows_out(R, uint64_t(reqs[tickets[k]].slot) << b, 1ull << b, sc.gather, w)))
+            return s;
+          w += cnt[k];
+        }
+        int src = -1;
+        if ((s = resort(sc.gather, 0, total, R.order == 1, &src))) return s;
+        hs.cnt[src] = total;
+        uint64_t at = 0;
+        for (size_t k = 0; k < tickets.size(); ++k) {   // instances stay in slot order
+          Request& q = reqs[tickets[k]];
+          void* p = nullptr;
+          if (cnt[k]) {
+            if ((s = dev_alloc(cnt[k] * kb, &p))) return s;
+            CU(cudaMemcpyAsync(p, static_cast<char*>(hs.buf[src].ptr) + at * kb, cnt[k] * kb,
+                               cudaMemcpyDeviceToDevice, stream));
+          }
+          q.result[r] = {p, cnt[k]};
+          at += cnt[k];
+        }
+      } else {
+        for (uint64_t t : tickets) reqs[t].result[r] = {nullptr, 0};
+      }
+      // the rows stay until the slot's compaction: an admission iteration
+      // derives a retired instance's first tuples again from its staged EDB,
+      // and its full must still remove them
+      dead_tuples += total;
+      continue;
+    }
     std::vector<uint64_t> bnd, bnd1;
     if ((s = inst_bounds(R.full, bnd))) return s;
     if (R.log && (s = inst_bounds(R.l1, bnd1))) return s;
-    const uint64_t kb = wide ? 8 : 4;
     if (!R.log && R.order == 0) {   // one sorted array in the declared order: copy the ranges
       for (uint64_t t : tickets) {
         Request& q = reqs[t];

@@ -37,26 +37,45 @@ def check(ref, c0, c1, counts):
     assert counts == ref.delta_counts["Reach"]
 
 
-def test_static_batch_matches_each_instance_alone():
+def _full_modes():
+    from paper_2311_02206_gb300 import hisa
+    # 0: full as a bit matrix with a block of rows per instance; LEVELS: a
+    # sorted full cut by instance
+    return [0, hisa.FLAG_LEVELS]
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["matrix", "sorted"])
+def test_static_batch_matches_each_instance_alone(mode):
+    """Each instance alone, and the whole relation: relation_size is the sum of
+    the instances' sizes and read_relation their tuples in instance order."""
     from paper_2311_02206_gb300 import hisa
     inst = instances(48, 1)
-    with hisa.Context() as ctx:
+    with hisa.Context(flags=_full_modes()[mode]) as ctx:
         ctx.program(*oracle.REACH)
         for i, (s, d) in enumerate(inst):
             ctx.load_instance("Edge", i, s, d)
         ctx.run()
+        all0, all1 = [], []
         for i, (s, d) in enumerate(inst):
             c0, c1 = ctx.read_instance("Reach", i)
             check(oracle.reach(s, d), c0, c1, ctx.instance_delta_counts("Reach", i))
+            assert ctx.instance_size("Reach", i) == len(c0)
+            all0.append(c0)
+            all1.append(c1)
+        assert ctx.relation_size("Reach") == sum(len(x) for x in all0)
+        r0, r1 = ctx.read_relation("Reach")
+        assert np.array_equal(r0, np.concatenate(all0)) and np.array_equal(r1, np.concatenate(all1))
 
 
-def test_serving_continuous_admission_and_slot_reuse():
+@pytest.mark.parametrize("mode", [0, 1], ids=["matrix", "sorted"])
+def test_serving_continuous_admission_and_slot_reuse(mode):
     """8 slots, 40 requests submitted in three waves while the session runs:
     requests wait for free slots, are admitted at iteration boundaries next to
-    running ones, and slots of finished requests are reused."""
+    running ones, and slots of finished requests are reused (a reused slot's
+    block of matrix rows starts empty)."""
     from paper_2311_02206_gb300 import hisa
     inst = instances(40, 2)
-    with hisa.Context() as ctx:
+    with hisa.Context(flags=_full_modes()[mode]) as ctx:
         ctx.program(*oracle.REACH)
         ctx.serve_open(8, 63)
         tickets = {}
@@ -79,6 +98,32 @@ def test_serving_continuous_admission_and_slot_reuse():
             c0, c1, counts = ctx.serve_result(t, "Reach")
             check(oracle.reach(*inst[i]), c0, c1, counts)
             ctx.serve_release(t)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["matrix", "sorted"])
+def test_serving_trickle_admissions(mode):
+    """Two requests arrive per step into 8 slots: admission iterations run
+    while retired instances still sit in their slots (their staged EDB
+    tuples are derived again by the non-recursive rule and must be removed
+    by their full), and slots are reused many times."""
+    from paper_2311_02206_gb300 import hisa
+    inst = instances(60, 7)
+    with hisa.Context(flags=_full_modes()[mode]) as ctx:
+        ctx.program(*oracle.REACH)
+        ctx.serve_open(8, 63)
+        tickets, nxt = {}, 0
+        for step in range(4000):
+            for _ in range(2):
+                if nxt < len(inst):
+                    tickets[ctx.serve_submit("Edge", *inst[nxt])] = nxt
+                    nxt += 1
+            st = ctx.serve_step(1)
+            if st["active"] == 0 and st["pending"] == 0 and nxt == len(inst):
+                break
+        for t, i in tickets.items():
+            assert ctx.serve_poll(t)
+            c0, c1, counts = ctx.serve_result(t, "Reach")
+            check(oracle.reach(*inst[i]), c0, c1, counts)
 
 
 def test_serving_budget_limits_admission():
