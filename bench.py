@@ -805,11 +805,10 @@ def batch5_record(a, cpu=True):
         tk = {c.serve_submit("Edge", *graphs[i]): i for i in samp_srv}
         while tk:
             if c.serve_step(1)["retired"]:
-                for t in list(tk):
-                    if c.serve_poll(t):
-                        c.serve_result(t, "Reach", device=True)
-                        c.serve_release(t)
-                        del tk[t]
+                for t in c.serve_retired():
+                    c.serve_result(t, "Reach", device=True)
+                    c.serve_release(t)
+                    del tk[t]
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         c.close()
@@ -872,8 +871,9 @@ def batch5_record(a, cpu=True):
             st = sctx.serve_step(1)
             if st["retired"]:
                 tnow = time.perf_counter() - start
-                for t, i in list(tickets.items()):
-                    if i not in done and sctx.serve_poll(t):
+                for t in sctx.serve_retired():
+                    i = tickets[t]
+                    if i not in done:
                         done.add(i)
                         lat[i] = tnow - arrivals[i]
                         c0, c1, dc = sctx.serve_result(t, "Reach", device=True)

@@ -296,6 +296,11 @@ hisa_status hisa_serve_submit(hisa_ctx* ctx, uint32_t rel_id, const uint32_t* co
 hisa_status hisa_serve_step(hisa_ctx* ctx, uint32_t max_iterations, hisa_serve_stats* stats);
 /* *done = 1 once the request's fixpoint is complete. */
 hisa_status hisa_serve_poll(hisa_ctx* ctx, uint64_t ticket, int* done);
+/* The tickets the most recent hisa_serve_step retired, in slot order, into
+ * tickets[cap]; *n receives their number (tickets may be NULL to query it).
+ * Lets a caller collect results without polling every outstanding ticket.
+ * Errors: STATE (no serving session), CAPACITY (*n is still set). */
+hisa_status hisa_serve_retired(hisa_ctx* ctx, uint64_t* tickets, uint32_t cap, uint32_t* n);
 /* A completed request's tuples of IDB relation rel_id, ascending (c0, c1),
  * into cols[0], cols[1] (room for cap tuples; device pointers if
  * cols_on_device, else host; cols may be NULL to query sizes), *n receives

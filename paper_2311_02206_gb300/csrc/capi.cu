@@ -127,6 +127,11 @@ hisa_status hisa_serve_poll(hisa_ctx* ctx, uint64_t ticket, int* done) {
   return ctx->eng.serve_poll(ticket, done);
 }
 
+hisa_status hisa_serve_retired(hisa_ctx* ctx, uint64_t* tickets, uint32_t cap, uint32_t* n) {
+  if (!ctx || !n) return HISA_ERR_INVALID_ARG;
+  return ctx->eng.serve_retired(tickets, cap, n);
+}
+
 hisa_status hisa_serve_result(hisa_ctx* ctx, uint64_t ticket, uint32_t rel_id, uint32_t* const* cols, uint64_t cap,
                               uint64_t* n, uint64_t* deltas, uint32_t dcap, uint32_t* n_iters, int cols_on_device) {
   if (!ctx) return HISA_ERR_INVALID_ARG;

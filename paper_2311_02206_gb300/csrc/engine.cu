@@ -188,6 +188,7 @@ hisa_status Engine::init(const hisa_config& c) {
   sc.tmp_hist = new_slot(8);
   sc.gather = new_slot(4);
   sc.mrows = new_slot(8);
+  sc.mslots = new_slot(4);
   sc.dense_first = new_slot(8);
   sc.dense_units = new_slot(8);
   sc.dense_done = new_slot(4);

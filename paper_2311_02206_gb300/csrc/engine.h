@@ -110,6 +110,7 @@ struct Scratch {
   int tmp_hist;               // digit histograms of a Tmp relation sorted before a dense join
   int gather;                 // an instance's codes from both levels of a log-structured full
   int mrows;                  // u64 row offsets of a bit-matrix read-out (matrix.cuh)
+  int mslots;                 // u32 instance slots whose blocks a read-out takes
   int dense_first;            // direct index of a delta by its kept column (group starts)
   int dense_units, dense_done;  // the dense join's first unit per group and finished-unit counters
   int dense_mslot, dense_bmm;   // multi-unit groups' bitmap slot and those bitmaps (kept zeroed)
@@ -160,6 +161,7 @@ class Engine {
   hisa_status serve_submit(uint32_t rid, const uint32_t* const* cols, uint64_t n, uint64_t* ticket);
   hisa_status serve_step(uint32_t max_iters, hisa_serve_stats* st);
   hisa_status serve_poll(uint64_t ticket, int* done);
+  hisa_status serve_retired(uint64_t* tickets, uint32_t cap, uint32_t* n);
   hisa_status serve_result(uint64_t ticket, uint32_t rid, uint32_t* const* cols, uint64_t cap, uint64_t* n,
                            uint64_t* deltas, uint32_t dcap, uint32_t* n_iters, int on_device);
   hisa_status serve_release(uint64_t ticket);
@@ -215,7 +217,8 @@ class Engine {
   hisa_status retire(const std::vector<uint64_t>& tickets);
   // codes of bit-matrix rows [row0, row0 + nrows) of R, stored order, into
   // `slot` from position `at` (the slot must hold them)
-  hisa_status matrix_rows_out(const Relation& R, uint64_t row0, uint64_t nrows, int slot, uint64_t at);
+  hisa_status matrix_rows_out(const Relation& R, uint64_t row0, uint64_t nrows, int slot, uint64_t at,
+                              const std::vector<uint32_t>* blocks = nullptr);
   uint64_t inst_total(size_t idb_index, uint32_t inst) const;   // sum of an instance's delta sizes
   hisa_status compact_dead();
   hisa_status compact(int slot, int next, const std::vector<uint64_t>& bnd, const std::vector<bool>& drop);
@@ -279,6 +282,7 @@ class Engine {
   bool edb_restage = true;                           // the staged EDB still holds retired instances' tuples
   std::unordered_map<uint64_t, Request> reqs;
   std::deque<uint64_t> pending;
+  std::vector<uint64_t> last_retired;   // tickets retired by the latest serve_step
   std::vector<Op> ops_admit;
   int res_slot = -1;          // slot aliasing a request's result codes while they are decoded
   struct KStat { uint64_t launches; double ms, bytes; };

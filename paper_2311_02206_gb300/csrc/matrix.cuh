@@ -141,12 +141,20 @@ struct MatrixExtractArgs {
   int b;
   uint64_t* offs;   // nrows + 1 entries (scratch); offs[nrows] = total
   void* out;        // K codes
+  // instance slots whose blocks are read, in this order (device array; null:
+  // the rows row0 ..): row i is then row i mod 2^b of block slots[i >> b]
+  const uint32_t* slots = nullptr;
 };
+
+__device__ __forceinline__ uint64_t extract_row(const MatrixExtractArgs& a, uint64_t i) {
+  if (!a.slots) return a.row0 + i;
+  return (uint64_t(a.slots[i >> a.b]) << a.b) | (i & ((1ull << a.b) - 1));
+}
 
 static __global__ void k_matrix_extract_counts(MatrixExtractArgs a) {
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < a.nrows;
        i += uint64_t(gridDim.x) * blockDim.x)
-    a.offs[i] = a.fcnt[a.row0 + i];
+    a.offs[i] = a.fcnt[extract_row(a, i)];
 }
 
 static __global__ void __launch_bounds__(1024) k_matrix_extract_scan(MatrixExtractArgs a) {
@@ -170,7 +178,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_matrix_extract(MatrixExtractA
   K* out = static_cast<K*>(a.out);
   for (uint64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {
     if (a.offs[r + 1] == a.offs[r]) continue;   // uniform across the CTA
-    const uint64_t row = a.row0 + r;
+    const uint64_t row = extract_row(a, r);
     const uint32_t* rw = a.fbm + row * uint64_t(nwords);
     uint32_t c = 0;
     for (int j = w0 + lane; j < w1; j += 32) c += __popc(rw[j]);

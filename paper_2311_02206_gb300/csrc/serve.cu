@@ -92,13 +92,23 @@ hisa_status Engine::decode_range(int slot, uint64_t begin, uint64_t count, std::
   return HISA_OK;
 }
 
-hisa_status Engine::matrix_rows_out(const Relation& R, uint64_t row0, uint64_t nrows, int slot, uint64_t at) {
+// With `blocks`, the rows are those of the listed instance slots' blocks, in
+// list order (nrows = blocks->size() << b); row0 is unused.
+hisa_status Engine::matrix_rows_out(const Relation& R, uint64_t row0, uint64_t nrows, int slot, uint64_t at,
+                                    const std::vector<uint32_t>* blocks) {
   hisa_status s;
+  if (blocks) nrows = uint64_t(blocks->size()) << b;
   if ((s = ensure(sc.mrows, nrows + 1))) return s;
   const uint64_t kb = wide ? 8 : 4;
   MatrixExtractArgs a{static_cast<const uint32_t*>(hs.buf[R.fbm].ptr), static_cast<const uint32_t*>(hs.buf[R.fcnt].ptr),
                       row0, nrows, b, static_cast<uint64_t*>(hs.buf[sc.mrows].ptr),
                       static_cast<char*>(hs.buf[slot].ptr) + at * kb};
+  if (blocks) {
+    if (blocks->empty()) return HISA_OK;
+    if ((s = ensure(sc.mslots, blocks->size()))) return s;
+    CU(cudaMemcpyAsync(hs.buf[sc.mslots].ptr, blocks->data(), blocks->size() * 4, cudaMemcpyHostToDevice, stream));
+    a.slots = static_cast<const uint32_t*>(hs.buf[sc.mslots].ptr);
+  }
   if (wide) launch_matrix_extract<uint64_t>(a, grid, stream);
   else launch_matrix_extract<uint32_t>(a, grid, stream);
   CU(cudaGetLastError());
@@ -451,12 +461,10 @@ hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
       }
       if (total > 0) {
         if ((s = ensure(sc.gather, total))) return s;
-        uint64_t w = 0;
-        for (size_t k = 0; k < tickets.size(); ++k) {
-          if (cnt[k] && (s = matrix_rows_out(R, uint64_t(reqs[tickets[k]].slot) << b, 1ull << b, sc.gather, w)))
-            return s;
-          w += cnt[k];
-        }
+        std::vector<uint32_t> blocks;   // one read-out of all finished blocks, in slot order
+        for (size_t k = 0; k < tickets.size(); ++k)
+          if (cnt[k]) blocks.push_back(uint32_t(reqs[tickets[k]].slot));
+        if ((s = matrix_rows_out(R, 0, 0, sc.gather, 0, &blocks))) return s;
         int src = -1;
         if ((s = resort(sc.gather, 0, total, R.order == 1, &src))) return s;
         hs.cnt[src] = total;
@@ -559,6 +567,7 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
   if (!serving) return ctx_fail(HISA_ERR_STATE, "no serving session", nullptr);
   hisa_serve_stats out{};
   hisa_status s;
+  last_retired.clear();
   // phase clock: with HISA_FLAG_PHASE_TIMES a phase ends with a synchronisation
   const bool sync_phases = (cfg.flags & HISA_FLAG_PHASE_TIMES) != 0;
   auto tick = std::chrono::steady_clock::now();
@@ -638,6 +647,7 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
       }
     if ((s = retire(finished))) return s;
     out.retired += uint32_t(finished.size());
+    last_retired.insert(last_retired.end(), finished.begin(), finished.end());
     phase(out.ms_retire);
     uint64_t live = 0;
     for (int r : idb) live += hs.cnt[rels[r].full] + (rels[r].log ? hs.cnt[rels[r].l1] : 0);
@@ -649,6 +659,14 @@ hisa_status Engine::serve_step(uint32_t max_iters, hisa_serve_stats* st) {
   out.pending = uint32_t(pending.size());
   out.active = uint32_t(std::count_if(slot_owner.begin(), slot_owner.end(), [](uint64_t t) { return t != 0; }));
   if (st) *st = out;
+  return HISA_OK;
+}
+
+hisa_status Engine::serve_retired(uint64_t* tickets, uint32_t cap, uint32_t* n) {
+  if (!serving) return ctx_fail(HISA_ERR_STATE, "no serving session", nullptr);
+  *n = uint32_t(last_retired.size());
+  for (uint32_t i = 0; tickets && i < cap && i < last_retired.size(); ++i) tickets[i] = last_retired[i];
+  if (tickets && cap < last_retired.size()) return ctx_fail(HISA_ERR_CAPACITY, "serve_retired: buffer too small", nullptr);
   return HISA_OK;
 }
 

@@ -128,6 +128,7 @@ SIGNATURES = {
                                            _U64P]),
     "hisa_serve_step": (ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.POINTER(ServeStats)]),
     "hisa_serve_poll": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+    "hisa_serve_retired": (ctypes.c_int32, [_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "hisa_serve_result": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p),
                                            ctypes.c_uint64, _U64P, _U64P, ctypes.c_uint32, _U32P, ctypes.c_int]),
     "hisa_serve_release": (ctypes.c_int32, [_P, ctypes.c_uint64]),
@@ -426,6 +427,15 @@ class Context:
         st = ServeStats()
         _check(self._lib.hisa_serve_step(self._h, max_iterations, ctypes.byref(st)), self._h)
         return st.as_dict()
+
+    def serve_retired(self) -> list:
+        """Tickets retired by the latest serve_step, in slot order."""
+        n = ctypes.c_uint32()
+        _check(self._lib.hisa_serve_retired(self._h, None, 0, ctypes.byref(n)), self._h)
+        buf = (ctypes.c_uint64 * max(n.value, 1))()
+        _check(self._lib.hisa_serve_retired(self._h, ctypes.cast(buf, ctypes.c_void_p), n.value, ctypes.byref(n)),
+               self._h)
+        return [int(buf[i]) for i in range(n.value)]
 
     def serve_poll(self, ticket: int) -> bool:
         d = ctypes.c_int()

@@ -111,15 +111,19 @@ def test_serving_trickle_admissions(mode):
     with hisa.Context(flags=_full_modes()[mode]) as ctx:
         ctx.program(*oracle.REACH)
         ctx.serve_open(8, 63)
-        tickets, nxt = {}, 0
+        tickets, nxt, retired = {}, 0, []
         for step in range(4000):
             for _ in range(2):
                 if nxt < len(inst):
                     tickets[ctx.serve_submit("Edge", *inst[nxt])] = nxt
                     nxt += 1
             st = ctx.serve_step(1)
+            got = ctx.serve_retired()   # what this step retired, no polling
+            assert len(got) == st["retired"] and all(ctx.serve_poll(t) for t in got)
+            retired += got
             if st["active"] == 0 and st["pending"] == 0 and nxt == len(inst):
                 break
+        assert sorted(retired) == sorted(tickets)
         for t, i in tickets.items():
             assert ctx.serve_poll(t)
             c0, c1, counts = ctx.serve_result(t, "Reach")
