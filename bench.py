@@ -256,6 +256,8 @@ KERNEL_SOURCES = {   # the sources a kernel's counters depend on
     "join_dense_pull": ["dense.cuh", "join.cuh", "common.cuh"],
     "join_dense_emit": ["dense.cuh", "join.cuh", "common.cuh"],
     "setop_diff_probe": ["setops.cuh", "common.cuh"],
+    "bit_join": ["bitjoin.cuh", "common.cuh"],
+    "matrix_diff": ["matrix.cuh", "setops.cuh", "common.cuh"],
 }
 
 
@@ -337,6 +339,17 @@ def _profile_lines(kernel, workload):
     except (OSError, IndexError, ValueError):
         return {}
     return out
+
+
+def _path_description(kstats):
+    """Which evaluation the engine chose, from the kernels that ran."""
+    if "bit_join" in kstats:
+        return ("full and delta as bit matrices over (first, second column): per tuple (x, y) of the inner "
+                "relation delta's row y ORed into row x, AND-NOT full, ORed into full (bitjoin.cuh)")
+    if "join_dense_mark" in kstats:
+        full = "a bit matrix" if "matrix_merge" in kstats else "sorted levels"
+        return f"grouped bitmap join (push/pull per group), full as {full}"
+    return "sort of raw join results, set difference and merge of sorted arrays"
 
 
 def _timed_steps(ctx, dev_edb, steps, warmup, flush, kstats=None):
@@ -584,9 +597,7 @@ def run_hisa(a):
                    "tuples_joined_last_step": int(st.tuples_joined),
                    "l2": "flushed by a 512 MiB write between steps (outside the timed events)",
                    "loop": "host-driven, CUDA events around every kernel",
-                   "full": "one sorted array" if a.single_full else "two sorted levels (log-structured)",
-                   "dedup": "sort of raw join results" if a.no_dense else
-                            "grouped bitmap join where it applies, else sort of raw join results",
+                   "path": _path_description(kstats),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "step_ms": [round(x, 3) for x in ms], "wall_s_timed_region": round(wall, 3)},
         "roofline": roofline,

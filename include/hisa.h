@@ -117,6 +117,17 @@ typedef void (*hisa_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
  * are ORed into it, and reads write its rows (transposed first when stored
  * column-swapped) in order.  Same results. */
 #define HISA_FLAG_LEVELS 128u
+/* Keep the grouped bitmap join for a program of REACH's shape.  By default,
+ * when the one IDB relation R is defined by rules R(x, y) <- E(x, y) over
+ * EDB relations and one recursive rule R(x, z) <- B(x, y), R(y, z) with B an
+ * EDB relation, over a domain of at most 2^16 values (not in batched runs,
+ * and none of HISA_FLAG_NO_DENSE, HISA_FLAG_NO_PULL, HISA_FLAG_LEVELS set),
+ * R's full and delta are bit matrices over (first column, second column)
+ * and an iteration ORs, for each tuple (x, y) of B, delta's row y into a new
+ * row x, keeps the bits not in full's row x as delta' and ORs them into full
+ * (Algorithm 3 and Section 5.1's difference and merge on 2^b tuples per
+ * word operation).  Same results. */
+#define HISA_FLAG_NO_BITJOIN 256u
 
 typedef struct {
   hisa_alloc_fn alloc;      /* NULL: cudaMallocAsync from a private pool */

@@ -341,9 +341,13 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKZero, s, (k_zero<<<g.small, 256, 0, s>>>(a)));
 }
 
+void launch_bit_count(const BitCountArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKBitInit, s, (k_bit_count<<<g.small, 256, 0, s>>>(a)));
+}
+
 const char* const kKernelNames[kKindCount] = {
     "encode", "decode", "count_runs", "radix_hist", "radix_pass", "setop_partition", "setop_diff_merge",
-    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level", "chain_len", "chain_scan", "chain_gather", "join_dense_pull", "matrix_merge", "matrix_diff"};
+    "index_build", "join_count", "join_partition", "join_write", "ctl", "commit", "zero", "swap_cols", "setop_diff_probe", "group_compact", "join_dense_mark", "join_dense_scan", "join_dense_emit", "append_level", "chain_len", "chain_scan", "chain_gather", "join_dense_pull", "matrix_merge", "matrix_diff", "bit_join", "bit_init"};
 
 thread_local KernelTimer* g_timer = nullptr;
 thread_local uint64_t g_launches = 0;

@@ -743,9 +743,213 @@ hisa_status Engine::compile() {
     Relation& R = rels[r];
     R.log = (cfg.flags & HISA_FLAG_LOG_FULL) && !R.need_idx[0] && !R.need_idx[1] && !R.append && !R.mfull;
   }
+  bitjoin = detect_bitjoin();
+  if (bitjoin) {   // full is kept as a bit matrix in the declared column order
+    Relation& R = rels[bj_rel];
+    R.order = 0;
+    R.mfull = true;
+    if (R.fbm < 0) R.fbm = new_slot(4);
+    if (bj_first < 0) {
+      bj_first = new_slot(8);
+      bj_d = new_slot(4);
+      bj_d2 = new_slot(4);
+      bj_dm = new_slot(4);
+      bj_dm2 = new_slot(4);
+      bj_tot = new_slot(8);
+      bj_ctr = new_slot(4);
+      bj_items = new_slot(8);
+      bj_hslot = new_slot(4);
+      bj_hacc = new_slot(4);
+      bj_hdone = new_slot(4);
+    }
+  }
   compiled = true;
   graph_stale = true;
   once_stale = true;
+  return HISA_OK;
+}
+
+// A program of REACH's shape (bitjoin.cuh): one binary IDB relation R, rules
+// R(x, y) <- E(x, y) with E an EDB relation, and exactly one recursive rule
+// R(x, z) <- B(x, y), R(y, z) with B an EDB relation (either body order), no
+// filters; a domain of at most 2^16 values; no batching and no flag that asks
+// for another path.
+bool Engine::detect_bitjoin() {
+  bj_base.clear();
+  bj_rel = bj_inner = -1;
+  if (batched || serving || idb.size() != 1 || b > kBitMaxBits) return false;
+  if (cfg.flags & (HISA_FLAG_NO_BITJOIN | HISA_FLAG_NO_DENSE | HISA_FLAG_NO_PULL | HISA_FLAG_LEVELS)) return false;
+  const uint32_t r = uint32_t(idb[0]);
+  int recursive = 0;
+  for (const hisa_rule& q : rules) {
+    if (q.head.rel != r || q.n_neq != 0) return false;
+    if (q.n_body == 1) {
+      const hisa_atom& e = q.body[0];
+      if (e.rel == r || rels[e.rel].idb) return false;
+      if (q.head.var[0] == q.head.var[1] || e.var[0] != q.head.var[0] || e.var[1] != q.head.var[1]) return false;
+      bj_base.push_back(int(e.rel));
+    } else if (q.n_body == 2) {
+      const int ri = q.body[0].rel == r ? 0 : 1;
+      const hisa_atom& ra = q.body[ri];
+      const hisa_atom& ba = q.body[1 - ri];
+      if (ra.rel != r || ba.rel == r || rels[ba.rel].idb) return false;
+      const uint32_t x = ba.var[0], y = ba.var[1], z = ra.var[1];
+      if (x == y || y == z || x == z || ra.var[0] != y || q.head.var[0] != x || q.head.var[1] != z) return false;
+      bj_inner = int(ba.rel);
+      ++recursive;
+    } else {
+      return false;
+    }
+  }
+  if (recursive != 1 || bj_base.empty()) return false;
+  bj_rel = int(r);
+  return true;
+}
+
+// The fixpoint of a program of REACH's shape on bit matrices (bitjoin.cuh):
+// iteration 1 sets delta = full = the union of the E relations; every later
+// iteration ORs, per tuple (x, y) of B, delta's row y into row x, keeps the
+// bits not in full as delta' and ORs them into full, until delta' is empty.
+hisa_status Engine::run_bitjoin(hisa_run_stats* stats, std::chrono::steady_clock::time_point t0) {
+  hisa_status s;
+  Relation& R = rels[bj_rel];
+  const Relation& B = rels[bj_inner];
+  const uint64_t rows = 1ull << b, nw = bit_nwords(b), mw = bit_mwords(b);
+  const bool timing = cfg.flags & HISA_FLAG_PHASE_TIMES;
+  std::memset(kstat, 0, sizeof kstat);
+  timer.reset();
+  struct TimerGuard {
+    explicit TimerGuard(KernelTimer* t) { g_timer = t; }
+    ~TimerGuard() { g_timer = nullptr; }
+  } tg(timing ? &timer : nullptr);
+  const uint64_t launches0 = g_launches;
+  if ((s = ensure(R.fbm, rows * nw)) || (s = ensure(bj_d, rows * nw)) || (s = ensure(bj_d2, rows * nw)) ||
+      (s = ensure(bj_dm, rows * mw)) || (s = ensure(bj_dm2, rows * mw)) || (s = ensure(bj_first, rows + 1)) ||
+      (s = ensure(bj_tot, 2)) || (s = ensure(bj_ctr, 1)))
+    return s;
+  CU(cudaMemsetAsync(hs.buf[R.fbm].ptr, 0, rows * nw * 4, stream));
+  CU(cudaMemsetAsync(hs.buf[bj_d].ptr, 0, rows * nw * 4, stream));
+  CU(cudaMemsetAsync(hs.buf[bj_dm].ptr, 0, rows * mw * 4, stream));
+  if ((s = upload())) return s;
+  // B's run of each first column: a direct index over its sorted codes
+  {
+    std::vector<Op> ops(1);
+    ops[0].kind = Op::INDEX;
+    ops[0].index = IndexArgs{dst, B.base, B.base, bj_first, b, -1, 0, b};
+    if ((s = exec(ops))) return s;
+  }
+  // work items (row, segment of at most kBitSeg B tuples), the heaviest rows
+  // first; a row of several segments gets an accumulator
+  uint64_t nitems = 0;
+  {
+    std::vector<uint64_t> first(rows + 1);
+    CU(cudaMemcpyAsync(first.data(), hs.buf[bj_first].ptr, (rows + 1) * 8, cudaMemcpyDeviceToHost, stream));
+    CU(cudaStreamSynchronize(stream));
+    std::vector<uint32_t> byd;
+    for (uint32_t x = 0; x < rows; ++x)
+      if (first[x + 1] > first[x]) byd.push_back(x);
+    std::stable_sort(byd.begin(), byd.end(), [&](uint32_t p, uint32_t q) {
+      return first[p + 1] - first[p] > first[q + 1] - first[q];
+    });
+    std::vector<uint64_t> items;
+    std::vector<uint32_t> hslot(rows, 0);
+    uint32_t nheavy = 0;
+    for (uint32_t x : byd) {
+      const uint64_t nseg = (first[x + 1] - first[x] + kBitSeg - 1) / kBitSeg;
+      if (nseg > 1) hslot[x] = nheavy++;
+      for (uint64_t g = 0; g < nseg; ++g) items.push_back((uint64_t(x) << 32) | g);
+    }
+    nitems = items.size();
+    if ((s = ensure(bj_items, std::max<uint64_t>(nitems, 1))) || (s = ensure(bj_hslot, rows)) ||
+        (s = ensure(bj_hacc, std::max<uint64_t>(nheavy, 1) * nw)) || (s = ensure(bj_hdone, std::max<uint32_t>(nheavy, 1))))
+      return s;
+    if (nitems)
+      CU(cudaMemcpyAsync(hs.buf[bj_items].ptr, items.data(), nitems * 8, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemcpyAsync(hs.buf[bj_hslot].ptr, hslot.data(), rows * 4, cudaMemcpyHostToDevice, stream));
+    CU(cudaMemsetAsync(hs.buf[bj_hacc].ptr, 0, std::max<uint64_t>(nheavy, 1) * nw * 4, stream));
+    CU(cudaMemsetAsync(hs.buf[bj_hdone].ptr, 0, std::max<uint32_t>(nheavy, 1) * 4, stream));
+    CU(cudaStreamSynchronize(stream));   // the host vectors are copied out before they go
+  }
+  auto* tot = static_cast<unsigned long long*>(hs.buf[bj_tot].ptr);
+  uint32_t* D = static_cast<uint32_t*>(hs.buf[bj_d].ptr);
+  uint32_t* D2 = static_cast<uint32_t*>(hs.buf[bj_d2].ptr);
+  uint32_t* Dm = static_cast<uint32_t*>(hs.buf[bj_dm].ptr);
+  uint32_t* Dm2 = static_cast<uint32_t*>(hs.buf[bj_dm2].ptr);
+  uint32_t* F = static_cast<uint32_t*>(hs.buf[R.fbm].ptr);
+  // iteration 1: the non-recursive rules
+  for (int e : bj_base) {
+    const Relation& E = rels[e];
+    if (!hs.cnt[E.base]) continue;
+    BitInitArgs ia{hs.buf[E.base].ptr, hs.cnt[E.base], b, D, Dm, F};
+    if (wide) launch_bit_init<uint64_t>(ia, grid, stream);
+    else launch_bit_init<uint32_t>(ia, grid, stream);
+    if ((s = check_launch("bit init"))) return s;
+  }
+  CU(cudaMemsetAsync(tot, 0, 16, stream));
+  launch_bit_count(BitCountArgs{D, rows * nw, tot}, grid, stream);
+  if ((s = check_launch("bit count"))) return s;
+  unsigned long long h[2] = {0, 0};
+  CU(cudaMemcpyAsync(h, tot, 16, cudaMemcpyDeviceToHost, stream));
+  CU(cudaStreamSynchronize(stream));
+  std::vector<uint64_t> hist;
+  if (h[0]) hist.push_back(h[0]);
+  const double kb = wide ? 8.0 : 4.0;
+  kstat[kKBitInit].bytes += double(hs.cnt[B.base]) * kb + double(rows * nw) * 4.0;
+  uint32_t iters_run = 1;
+  uint64_t d = h[0];
+  while (d > 0 && iters_run < cfg.max_iters) {
+    CU(cudaMemsetAsync(tot, 0, 16, stream));
+    CU(cudaMemsetAsync(hs.buf[bj_ctr].ptr, 0, 4, stream));
+    CU(cudaMemsetAsync(Dm2, 0, rows * mw * 4, stream));
+    BitJoinArgs ja{static_cast<const uint64_t*>(hs.buf[bj_first].ptr),
+                   hs.buf[B.base].ptr,
+                   static_cast<const uint64_t*>(hs.buf[bj_items].ptr),
+                   nitems,
+                   static_cast<const uint32_t*>(hs.buf[bj_hslot].ptr),
+                   static_cast<uint32_t*>(hs.buf[bj_hacc].ptr),
+                   static_cast<uint32_t*>(hs.buf[bj_hdone].ptr),
+                   D, Dm, D2, Dm2, F, tot, tot + 1, static_cast<uint32_t*>(hs.buf[bj_ctr].ptr), b};
+    if (wide) launch_bitjoin<uint64_t>(ja, grid, stream);
+    else launch_bitjoin<uint32_t>(ja, grid, stream);
+    if ((s = check_launch("bit join"))) return s;
+    CU(cudaMemcpyAsync(h, tot, 16, cudaMemcpyDeviceToHost, stream));
+    CU(cudaStreamSynchronize(stream));
+    ++iters_run;
+    d = h[0];
+    // bytes: B read, the delta chunks selected, full's row read and delta'
+    // written where new bits arrived (at most), the masks
+    kstat[kKBitJoin].bytes += double(hs.cnt[B.base]) * kb + double(h[1]) * 128.0 + double(d) * 1.0 +
+                              double(rows * mw) * 8.0 + double(rows + 1) * 8.0;
+    if (d) hist.push_back(d);
+    std::swap(D, D2);
+    std::swap(Dm, Dm2);
+  }
+  if (d > 0) return ctx_fail(HISA_ERR_NOT_CONVERGED, "max_iters reached", nullptr);
+  uint64_t total = 0;
+  for (uint64_t x : hist) total += x;
+  hs.cnt[R.full] = total;
+  R.delta_counts = hist;
+  if ((s = upload())) return s;
+  if (timing) {
+    CU(cudaStreamSynchronize(stream));
+    for (auto& rc : timer.recs) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, rc.a, rc.b);
+      kstat[rc.kind].ms += ms;
+      kstat[rc.kind].launches += 1;
+    }
+    timer.reset();
+  }
+  last_stats.kernel_launches = g_launches - launches0;
+  last_stats.tuples_joined = total;
+  last_stats.iterations = uint32_t(hist.size());
+  last_stats.iterations_run = iters_run;
+  last_stats.regrows = 0;
+  last_stats.graph_launches = 0;
+  last_stats.peak_bytes = peak_bytes;
+  last_stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = last_stats;
+  ran = true;
   return HISA_OK;
 }
 
@@ -1674,6 +1878,7 @@ hisa_status Engine::run(hisa_run_stats* stats) {
   last_stats = hisa_run_stats{};
   last_stats.ms_edb = ms_edb;
   regrows = 0;
+  if (bitjoin) return run_bitjoin(stats, t0);
   if ((s = init_run_state())) return s;
   return run_loop(stats, t0);
 }

@@ -185,6 +185,14 @@ class Engine {
   hisa_status check_launch(const char* what);
   hisa_status device_max(const uint32_t* a, const uint32_t* b, uint64_t n, uint32_t* mx);
   hisa_status compile();
+  // bit-matrix evaluation of a program of REACH's shape (bitjoin.cuh)
+  bool detect_bitjoin();
+  hisa_status run_bitjoin(hisa_run_stats* stats, std::chrono::steady_clock::time_point t0);
+  bool bitjoin = false;
+  int bj_rel = -1, bj_inner = -1;   // R and B of R(x, z) <- B(x, y), R(y, z)
+  std::vector<int> bj_base;         // E of the rules R(x, y) <- E(x, y)
+  int bj_first = -1, bj_d = -1, bj_d2 = -1, bj_dm = -1, bj_dm2 = -1, bj_tot = -1, bj_ctr = -1;
+  int bj_items = -1, bj_hslot = -1, bj_hacc = -1, bj_hdone = -1;
   hisa_status plan_variant(const hisa_rule& R, int delta_atom, std::vector<StepPlan>& out);
   void emit_join(std::vector<Op>& ops, const StepPlan& sp);
   void emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_groups = false, int inner_buf = -1,

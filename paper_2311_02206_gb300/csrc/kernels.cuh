@@ -9,6 +9,7 @@
 #include "dense.cuh"
 #include "read.cuh"
 #include "matrix.cuh"
+#include "bitjoin.cuh"
 #include <vector>
 
 namespace hisa {
@@ -134,7 +135,7 @@ struct SwapArgs {
 
 enum KernelKind : int {
   kKEncode, kKDecode, kKRuns, kKHist, kKRadixPass, kKSetopPartition, kKSetop, kKIndex,
-  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKAppend, kKChainLen, kKChainScan, kKChainGather, kKJoinPull, kKMatrix, kKMatrixDiff, kKindCount
+  kKJoinCount, kKJoinPartition, kKJoinWrite, kKCtl, kKCommit, kKZero, kKSwap, kKDiffProbe, kKGroups, kKJoinDense, kKDenseScan, kKDenseEmit, kKAppend, kKChainLen, kKChainScan, kKChainGather, kKJoinPull, kKMatrix, kKMatrixDiff, kKBitJoin, kKBitInit, kKindCount
 };
 extern const char* const kKernelNames[kKindCount];
 
@@ -195,6 +196,9 @@ template <typename K> void launch_levels_read(const LevelsReadArgs& a, const Gri
 template <typename K> void launch_levels_transpose(const LevelsTransposeArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_matrix_codes(const MatrixArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_matrix_diff(const MatrixDiffArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_bit_init(const BitInitArgs& a, const Grid& g, cudaStream_t s);
+void launch_bit_count(const BitCountArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_bitjoin(const BitJoinArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_matrix_extract(const MatrixExtractArgs& a, const Grid& g, cudaStream_t s);
 // a full kept as a bit matrix read in the declared order: transposed (order 1)
 // or read as it is (order 0), then its rows counted, scanned and written

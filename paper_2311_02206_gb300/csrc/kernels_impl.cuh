@@ -207,6 +207,14 @@ void launch_matrix_diff(const MatrixDiffArgs& a, const Grid& g, cudaStream_t s) 
   HISA_LAUNCH(kKMatrixDiff, s, (k_matrix_diff<K><<<g.setop, kDiffThreads, 0, s>>>(a)));
 }
 template <typename K>
+void launch_bit_init(const BitInitArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKBitInit, s, (k_bit_init<K><<<g.small, 256, 0, s>>>(a)));
+}
+template <typename K>
+void launch_bitjoin(const BitJoinArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKBitJoin, s, (k_bitjoin<K><<<g.sms * 8, kBitThreads, 0, s>>>(a)));
+}
+template <typename K>
 void launch_matrix_extract(const MatrixExtractArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKDecode, s, (k_matrix_extract_counts<<<g.small, 256, 0, s>>>(a)));
   HISA_LAUNCH(kKDecode, s, (k_matrix_extract_scan<<<1, 1024, 0, s>>>(a)));
@@ -363,6 +371,8 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_levels_transpose<K>(const LevelsTransposeArgs&, const Grid&, cudaStream_t); \
   template void launch_matrix_codes<K>(const MatrixArgs&, const Grid&, cudaStream_t);    \
   template void launch_matrix_diff<K>(const MatrixDiffArgs&, const Grid&, cudaStream_t); \
+  template void launch_bit_init<K>(const BitInitArgs&, const Grid&, cudaStream_t);       \
+  template void launch_bitjoin<K>(const BitJoinArgs&, const Grid&, cudaStream_t);        \
   template void launch_matrix_extract<K>(const MatrixExtractArgs&, const Grid&, cudaStream_t); \
   template void launch_matrix_read<K>(const MatrixTransposeArgs&, const LevelsTransposeArgs&, bool, const Grid&, \
                                       cudaStream_t);                                     \

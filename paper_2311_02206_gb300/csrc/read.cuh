@@ -127,7 +127,7 @@ static __global__ void __launch_bounds__(256) k_matrix_transpose(MatrixTranspose
 
 template <typename K>
 __global__ void k_rows_count(LevelsTransposeArgs a) {
-  const uint64_t ng = 1ull << a.b, nw = ng / 32;
+  const uint64_t ng = 1ull << a.b, nw = ng >= 32 ? ng / 32 : 1;   // (b < 5: one word per row)
   const int lane = threadIdx.x & 31;
   for (uint64_t r = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5; r < ng;
        r += (uint64_t(gridDim.x) * blockDim.x) >> 5) {
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_rows_emit(LevelsTransposeArgs
   __shared__ uint32_t s_stage[nwarps][32 * 32];
   __shared__ uint32_t s_wtot[nwarps];
   const uint64_t ng = 1ull << a.b;
-  const int nwords = int(ng / 32);
+  const int nwords = ng >= 32 ? int(ng / 32) : 1;
   const int wrange = (nwords + nwarps - 1) / nwarps;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int w0 = min(nwords, warp * wrange), w1 = min(nwords, w0 + wrange);

@@ -26,6 +26,7 @@ FLAG_HASH_INDEX = 16
 FLAG_NO_CHAIN = 32
 FLAG_NO_PULL = 64
 FLAG_LEVELS = 128
+FLAG_NO_BITJOIN = 256
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

@@ -25,13 +25,16 @@ def _lib():
 def modes():
     """host-driven, graph-captured, both with the log-structured full,
     graph-captured without the grouped bitmap join, and with hashed indexes,
-    with Tmp joined and sorted instead of gathered, and without pull mode"""
+    with Tmp joined and sorted instead of gathered, without pull mode, with a
+    leveled full, and with the grouped bitmap join instead of the bit-matrix
+    evaluation of REACH's shape"""
     from paper_2311_02206_gb300 import hisa
     return [0, hisa.FLAG_GRAPH, hisa.FLAG_LOG_FULL, hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL,
             hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE, hisa.FLAG_GRAPH | hisa.FLAG_NO_DENSE | hisa.FLAG_HASH_INDEX,
             hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_CHAIN,
             hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_PULL,
-            hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_LEVELS]
+            hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_LEVELS,
+            hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_BITJOIN]
 
 
 @pytest.mark.parametrize("ratio", [1 / 16, 4.0, 4096.0])
@@ -59,8 +62,56 @@ def test_reach_pull_switch_points(ratio, graph):
         s = rng.integers(0, n, m).astype(np.uint32)
         d = rng.integers(0, n, m).astype(np.uint32)
     ref = oracle.reach(s, d)
-    for flags in (hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL, hisa.FLAG_LOG_FULL):
-        rels, counts, _ = gpu_eval(*oracle.REACH, {"Edge": (s, d)}, flags=flags, pull_ratio=ratio)
+    for flags in (hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL, hisa.FLAG_LOG_FULL):   # the grouped join's pull mode
+        rels, counts, _ = gpu_eval(*oracle.REACH, {"Edge": (s, d)}, flags=flags | hisa.FLAG_NO_BITJOIN,
+                                   pull_ratio=ratio)
+        assert_same(rels, counts, ref)
+
+
+@pytest.mark.parametrize("n", [3, 40, 700, 2000, 40000])
+def test_reach_bitjoin_taken_and_exact(n):
+    """A program of REACH's shape runs on bit matrices by default (its kernels
+    are the ones launched) and on the grouped bitmap join with
+    HISA_FLAG_NO_BITJOIN; both give the oracle's relation and delta counts.
+    Domains from 2 to 16 bits: rows of one word, of fewer than one chunk, of
+    one and of 32 chunks of 32 words."""
+    from paper_2311_02206_gb300 import hisa
+    rng = np.random.default_rng(n)
+    m = 3 * n if n < 10000 else n + n // 2
+    s = rng.integers(0, n, m).astype(np.uint32)
+    d = rng.integers(0, n, m).astype(np.uint32)
+    if n >= 10000:   # keep the oracle quick: chains of 20 nodes over the whole domain
+        s = np.arange(0, n - 1, dtype=np.uint32)
+        s = s[(s % 20) != 19]
+        d = s + 1
+    ref = oracle.reach(s, d)
+    for flags, bit in ((hisa.FLAG_PHASE_TIMES, True), (hisa.FLAG_PHASE_TIMES | hisa.FLAG_NO_BITJOIN, False)):
+        with hisa.Context(flags=flags) as ctx:
+            ctx.program(*oracle.REACH)
+            ctx.load_tuples("Edge", s, d)
+            ctx.run()
+            names = {e["name"] for e in ctx.kernel_stats() if e["launches"] > 0}
+            assert ("bit_join" in names or "bit_init" in names) == bit, names
+            rels = {"Reach": ctx.read_relation("Reach")}
+            counts = {"Reach": ctx.delta_counts("Reach")}
+        assert_same(rels, counts, ref)
+
+
+def test_bitjoin_two_base_rules_and_another_inner():
+    """R(x, y) <- A(x, y); R(x, y) <- C(x, y); R(x, z) <- B(x, y), R(y, z):
+    iteration 1 is the union of A and C, the recursion joins B."""
+    from paper_2311_02206_gb300 import hisa
+    rng = np.random.default_rng(11)
+    n = 300
+    edb = {k: (rng.integers(0, n, 400).astype(np.uint32), rng.integers(0, n, 400).astype(np.uint32))
+           for k in ("A", "B", "C")}
+    prog = ({"A": "edb", "B": "edb", "C": "edb", "R": "idb"},
+            [(("R", ("x", "y")), [("A", ("x", "y"))], []),
+             (("R", ("x", "y")), [("C", ("x", "y"))], []),
+             (("R", ("x", "z")), [("R", ("y", "z")), ("B", ("x", "y"))], [])])
+    ref = oracle.seminaive(*prog, edb)
+    for flags in (hisa.FLAG_PHASE_TIMES, hisa.FLAG_GRAPH | hisa.FLAG_LOG_FULL | hisa.FLAG_NO_BITJOIN):
+        rels, counts, _ = gpu_eval(*prog, edb, flags=flags)
         assert_same(rels, counts, ref)
 
 
@@ -220,10 +271,11 @@ def test_sg_random_dag(seed):
         assert_same(rels, counts, ref)
 
 
-@pytest.mark.parametrize("log_full,no_dense,no_pull,levels", [(False, True, False, False), (True, True, False, False),
-                                                              (True, False, False, False), (True, False, True, False),
-                                                              (True, False, False, True)])
-def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense, no_pull, levels):
+@pytest.mark.parametrize("log_full,no_dense,no_pull,levels,no_bitjoin",
+                         [(False, True, False, False, False), (True, True, False, False, False),
+                          (True, False, False, False, False), (True, False, True, False, False),
+                          (True, False, False, True, False), (True, False, False, False, True)])
+def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense, no_pull, levels, no_bitjoin):
     """REACH on R-MAT scale 16 / 2**19 edges, in the launch configuration the
     benchmark times: total size, delta counts and fingerprint against the
     oracle's stored values, and 16 sampled target columns element by element."""
@@ -234,7 +286,8 @@ def test_reach_rmat_full_size_golden_and_sampled(log_full, no_dense, no_pull, le
     from paper_2311_02206_gb300 import hisa
     s, d = workloads.config_reach_rmat()
     flags = hisa.FLAG_GRAPH | (hisa.FLAG_LOG_FULL if log_full else 0) | (hisa.FLAG_NO_DENSE if no_dense else 0) | \
-        (hisa.FLAG_NO_PULL if no_pull else 0) | (hisa.FLAG_LEVELS if levels else 0)
+        (hisa.FLAG_NO_PULL if no_pull else 0) | (hisa.FLAG_LEVELS if levels else 0) | \
+        (hisa.FLAG_NO_BITJOIN if no_bitjoin else 0)
     with hisa.Context(flags=flags) as ctx:
         ctx.program(*oracle.REACH)
         ctx.load_tuples("Edge", s, d)
