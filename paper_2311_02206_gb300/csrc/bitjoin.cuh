@@ -28,6 +28,13 @@ __host__ __device__ constexpr uint64_t bit_nwords(int b) { return b >= 5 ? (1ull
 __host__ __device__ constexpr uint64_t bit_nchunks(int b) { return b >= 10 ? (1ull << (b - 10)) : 1ull; }
 __host__ __device__ constexpr uint64_t bit_mwords(int b) { return b >= 15 ? (1ull << (b - 15)) : 1ull; }
 
+constexpr int kBitSeg = 64;                                                 // B tuples per work item
+constexpr int kBitGroups = 8;                                               // chunk groups of a row
+constexpr int kBitChunksPerWarp = (1 << (kBitMaxBits - 10)) / kBitGroups;   // 8 at b = 16
+__host__ __device__ constexpr uint32_t bit_groups(int b) {
+  return bit_nchunks(b) < kBitGroups ? uint32_t(bit_nchunks(b)) : uint32_t(kBitGroups);
+}
+
 // The tuples of codes (c0 << b) | c1 set in a matrix (rows c0) and in its
 // chunk masks; idempotent.
 struct BitInitArgs {
@@ -71,30 +78,67 @@ static __global__ void k_bit_count(BitCountArgs a) {
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.total, c);
 }
 
-// One iteration, over work items (row x, segment of at most kBitSeg of its
-// B tuples): a hub's thousands of tuples are spread over many CTAs.  Items
-// are handed out by an atomic counter, the heaviest rows' first.  A CTA's
-// warp w owns the chunks w, w + 8, ... of the row (a chunk is 32 words, a
-// word per lane) and ORs the delta rows its segment's tuples select, chunk
-// by chunk where the delta row's chunk is non-empty, four tuples' loads in
-// flight.  A row of one segment is finished by its CTA: the difference with
-// full, full ORed, delta' and the row's chunk mask written, bits counted.  A
-// row of several segments ORs each partial row into its accumulator (one per
-// such row); the CTA that completes the row (an arrival counter) takes the
-// accumulator back, leaving it and the counter zeroed, and finishes the row.
-constexpr int kBitSeg = 64;
+// One iteration, over warp work items (row x, segment of at most kBitSeg of
+// its B tuples, chunk group g): warp items need no CTA barrier, and a hub's
+// thousands of tuples are spread over many warps.  The chunk group g of a row
+// of nch chunks is the chunks g, g + 8, ... (a chunk is 32 words, a word per
+// lane).  Items are handed out by an atomic counter, the heaviest rows'
+// first.  A warp ORs the delta rows its segment's tuples select, two tuples
+// at a time with all of their chunk loads issued before any is used (a
+// chunk is loaded only where the delta row's chunk mask is set).  A row of
+// one segment is finished by the warp: the difference with full, full ORed,
+// delta' and the chunk mask bits written, bits counted.  A row of several
+// segments ORs each partial result into its accumulator; the warp that
+// completes the chunk group (an arrival counter per row and group) takes the
+// accumulator back, leaving it and the counter zeroed, and finishes it.
+// The work items, built on the device: per row its item count (segments x
+// groups) and, for a row of several segments, an accumulator slot; a one-CTA
+// scan; every row's items written at its offset (rows in order: the hubs of
+// an R-MAT graph are its first rows).
+struct BitItemsArgs {
+  const uint64_t* first;
+  uint64_t* offs;          // rows + 1; offs[rows] = the number of items
+  uint64_t* items;
+  uint32_t* hslot;
+  uint32_t* nheavy;        // zeroed before the launch
+  int b;
+};
+static __global__ void k_bit_items_count(BitItemsArgs a) {
+  const uint64_t rows = 1ull << a.b;
+  for (uint64_t x = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; x < rows; x += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t nseg = (a.first[x + 1] - a.first[x] + kBitSeg - 1) / kBitSeg;
+    a.offs[x] = nseg * bit_groups(a.b);
+    if (nseg > 1) a.hslot[x] = atomicAdd(a.nheavy, 1u);
+  }
+}
+static __global__ void __launch_bounds__(1024) k_bit_items_scan(BitItemsArgs a) {
+  __shared__ uint64_t s_scan[33];
+  const uint64_t rows = 1ull << a.b;
+  const uint64_t total = cta_scan_inplace(a.offs, rows, s_scan);
+  if (threadIdx.x == 0) a.offs[rows] = total;
+}
+static __global__ void k_bit_items_write(BitItemsArgs a) {
+  const uint64_t rows = 1ull << a.b;
+  const uint32_t ng = bit_groups(a.b);
+  for (uint64_t x = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; x < rows; x += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t n = a.offs[x + 1] - a.offs[x];
+    for (uint64_t i = 0; i < n; ++i)
+      a.items[a.offs[x] + i] = (x << 32) | ((i / ng) << 8) | (i % ng);
+  }
+}
+
 struct BitJoinArgs {
   const uint64_t* first;   // B's run of first column x: codes [first[x], first[x + 1])
   const void* bcodes;      // B's codes (K), sorted
-  const uint64_t* items;   // (x << 32) | segment
-  uint64_t nitems;
+  const uint64_t* items;   // (x << 32) | (segment << 8) | group
+  const uint64_t* nitems;  // device: the number of items
   const uint32_t* hslot;   // row -> its accumulator (rows of several segments; else unused)
-  uint32_t* hacc;          // accumulators, zero between launches
-  uint32_t* hdone;         // arrival counters, zero between launches
+  uint32_t* hacc;          // accumulators (a row each), zero between launches
+  uint32_t* hdone;         // arrival counters (kBitGroups per accumulator), zero between launches
   const uint32_t* D;       // delta
   const uint32_t* Dmask;
   uint32_t* D2;            // delta' (only the chunks its mask marks are written)
-  uint32_t* D2mask;        // zeroed before the launch; written for the rows with B tuples
+  uint32_t* D2mask;        // zeroed before the launch
   uint32_t* R;             // full
   unsigned long long* total;
   unsigned long long* loads;   // delta chunks read (128 B each), for the byte count
@@ -102,92 +146,77 @@ struct BitJoinArgs {
   int b;
 };
 
-constexpr int kBitChunksPerWarp = (1 << (kBitMaxBits - 10)) / (kBitThreads / 32);   // 8 at b = 16
-
 template <typename K>
 __global__ void __launch_bounds__(kBitThreads) k_bitjoin(BitJoinArgs a) {
-  __shared__ uint32_t s_mask[1 << (kBitMaxBits - 15)];
-  __shared__ uint64_t s_item;
-  __shared__ int s_last;
-  __shared__ unsigned long long s_cnt;
   const K* bc = static_cast<const K*>(a.bcodes);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int nwarps = kBitThreads / 32;
+  const int lane = threadIdx.x & 31;
   const uint64_t nw = bit_nwords(a.b), nch = bit_nchunks(a.b), mw = bit_mwords(a.b);
   const uint32_t vmask = (1u << a.b) - 1;
-  // words of a chunk that exist (rows of fewer than 32 words: b < 10)
-  const uint32_t cw = nw < 32 ? uint32_t(nw) : 32u;
-  if (threadIdx.x == 0) s_cnt = 0;
-  uint32_t nloads = 0;
+  const uint32_t cw = nw < 32 ? uint32_t(nw) : 32u;   // words of a chunk (b < 10: fewer than 32)
+  unsigned long long cnt = 0, nloads = 0;
   while (true) {
-    if (threadIdx.x == 0) {
+    uint64_t item = 0;
+    if (lane == 0) {
       const uint32_t i = atomicAdd(a.ctr, 1u);
-      s_item = i < a.nitems ? a.items[i] : ~0ull;
+      item = i < *a.nitems ? a.items[i] : ~0ull;
     }
-    if (threadIdx.x < mw) s_mask[threadIdx.x] = 0;
-    __syncthreads();
-    const uint64_t item = s_item;
+    item = __shfl_sync(0xffffffffu, item, 0);
     if (item == ~0ull) break;
-    const uint32_t x = uint32_t(item >> 32), seg = uint32_t(item);
+    const uint32_t x = uint32_t(item >> 32), seg = uint32_t(item >> 8) & 0xFFFFFFu, g = uint32_t(item) & 0xFFu;
     const uint64_t f0 = a.first[x], f1 = a.first[x + 1];
     const uint64_t e0 = f0 + uint64_t(seg) * kBitSeg, e1 = min(f1, e0 + kBitSeg);
     const uint32_t nseg = uint32_t((f1 - f0 + kBitSeg - 1) / kBitSeg);
     uint32_t acc[kBitChunksPerWarp];
 #pragma unroll
     for (int k = 0; k < kBitChunksPerWarp; ++k) acc[k] = 0;
-    for (uint64_t e = e0; e < e1; e += 4) {
-      uint64_t y[4];
-      uint32_t m0[4], m1[4];
+    for (uint64_t e = e0; e < e1; e += 2) {
+      const bool ok1 = e + 1 < e1;
+      const uint64_t y0 = uint64_t(bc[e]) & vmask;
+      const uint64_t y1 = ok1 ? uint64_t(bc[e + 1]) & vmask : 0;
+      const uint32_t ma0 = a.Dmask[y0 * mw], mb0 = mw > 1 ? a.Dmask[y0 * mw + 1] : 0u;
+      const uint32_t ma1 = ok1 ? a.Dmask[y1 * mw] : 0u, mb1 = ok1 && mw > 1 ? a.Dmask[y1 * mw + 1] : 0u;
+      uint32_t v0[kBitChunksPerWarp], v1[kBitChunksPerWarp];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) y[u] = e + u < e1 ? uint64_t(bc[e + u]) & vmask : ~0ull;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        m0[u] = y[u] != ~0ull ? a.Dmask[y[u] * mw] : 0u;
-        m1[u] = y[u] != ~0ull && mw > 1 ? a.Dmask[y[u] * mw + 1] : 0u;
+      for (int k = 0; k < kBitChunksPerWarp; ++k) {   // every load issued before any is used
+        const uint64_t c = uint64_t(g) + uint64_t(k) * kBitGroups;
+        const bool in = c < nch && lane < cw;
+        const bool p0 = in && (((c < 32 ? ma0 : mb0) >> (c & 31)) & 1u);
+        const bool p1 = in && (((c < 32 ? ma1 : mb1) >> (c & 31)) & 1u);
+        v0[k] = p0 ? a.D[y0 * nw + c * 32 + lane] : 0u;
+        v1[k] = p1 ? a.D[y1 * nw + c * 32 + lane] : 0u;
+        if (lane == 0) nloads += uint32_t(p0) + uint32_t(p1);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-#pragma unroll
-        for (int k = 0; k < kBitChunksPerWarp; ++k) {
-          const uint64_t c = uint64_t(warp) + uint64_t(k) * nwarps;
-          if (c >= nch) break;
-          const uint32_t mword = c < 32 ? m0[u] : m1[u];
-          if ((mword >> (c & 31)) & 1u) {
-            if (lane < cw) acc[k] |= a.D[y[u] * nw + c * 32 + lane];
-            ++nloads;
-          }
-        }
-      }
+      for (int k = 0; k < kBitChunksPerWarp; ++k) acc[k] |= v0[k] | v1[k];
     }
-    if (nseg > 1) {   // a partial row: into the row's accumulator; the last arrival finishes it
-      uint32_t* h = a.hacc + uint64_t(a.hslot[x]) * nw;
+    if (nseg > 1) {   // a partial row: into the row's accumulator; the last arrival finishes the group
+      const uint32_t hs = a.hslot[x];
+      uint32_t* h = a.hacc + uint64_t(hs) * nw;
 #pragma unroll
       for (int k = 0; k < kBitChunksPerWarp; ++k) {
-        const uint64_t c = uint64_t(warp) + uint64_t(k) * nwarps;
-        if (c >= nch) break;
-        if (lane < cw && acc[k]) atomicOr(&h[c * 32 + lane], acc[k]);
+        const uint64_t c = uint64_t(g) + uint64_t(k) * kBitGroups;
+        if (c < nch && lane < cw && acc[k]) atomicOr(&h[c * 32 + lane], acc[k]);
       }
       __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) s_last = atomicAdd(&a.hdone[a.hslot[x]], 1u) == nseg - 1;
-      __syncthreads();
-      if (!s_last) continue;
+      __syncwarp();
+      uint32_t last = 0;
+      if (lane == 0) last = atomicAdd(&a.hdone[uint64_t(hs) * kBitGroups + g], 1u) == nseg - 1;
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (!last) continue;
       __threadfence();
 #pragma unroll
       for (int k = 0; k < kBitChunksPerWarp; ++k) {
-        const uint64_t c = uint64_t(warp) + uint64_t(k) * nwarps;
-        if (c >= nch) break;
-        if (lane < cw) {
+        const uint64_t c = uint64_t(g) + uint64_t(k) * kBitGroups;
+        if (c < nch && lane < cw) {
           acc[k] = __ldcg(&h[c * 32 + lane]);
           h[c * 32 + lane] = 0;
         }
       }
-      if (threadIdx.x == 0) a.hdone[a.hslot[x]] = 0;
+      if (lane == 0) a.hdone[uint64_t(hs) * kBitGroups + g] = 0;
     }
-    uint32_t cnt = 0;
 #pragma unroll
     for (int k = 0; k < kBitChunksPerWarp; ++k) {
-      const uint64_t c = uint64_t(warp) + uint64_t(k) * nwarps;
+      const uint64_t c = uint64_t(g) + uint64_t(k) * kBitGroups;
       if (c >= nch) break;
       uint32_t d = 0;
       if (acc[k]) {   // new bits of this word: not yet in full
@@ -197,19 +226,15 @@ __global__ void __launch_bounds__(kBitThreads) k_bitjoin(BitJoinArgs a) {
       }
       if (__ballot_sync(0xffffffffu, d != 0u)) {
         if (lane < cw) a.D2[uint64_t(x) * nw + c * 32 + lane] = d;
-        if (lane == 0) atomicOr(&s_mask[c >> 5], 1u << (c & 31));
+        if (lane == 0) atomicOr(&a.D2mask[uint64_t(x) * mw + (c >> 5)], 1u << (c & 31));
       }
       cnt += __popc(d);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (lane == 0 && cnt) atomicAdd(&s_cnt, (unsigned long long)cnt);
-    __syncthreads();
-    if (threadIdx.x < mw) a.D2mask[uint64_t(x) * mw + threadIdx.x] = s_mask[threadIdx.x];
-    __syncthreads();   // s_mask and s_item are rewritten for the next item
   }
-  if (threadIdx.x == 0 && s_cnt) atomicAdd(a.total, s_cnt);
-  if (lane == 0 && nloads) atomicAdd(a.loads, (unsigned long long)nloads);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0 && cnt) atomicAdd(a.total, cnt);
+  if (lane == 0 && nloads) atomicAdd(a.loads, nloads);
 }
 
 }  // namespace hisa

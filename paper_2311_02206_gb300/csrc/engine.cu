@@ -838,38 +838,25 @@ hisa_status Engine::run_bitjoin(hisa_run_stats* stats, std::chrono::steady_clock
     ops[0].index = IndexArgs{dst, B.base, B.base, bj_first, b, -1, 0, b};
     if ((s = exec(ops))) return s;
   }
-  // work items (row, segment of at most kBitSeg B tuples), the heaviest rows
-  // first; a row of several segments gets an accumulator
-  uint64_t nitems = 0;
-  {
-    std::vector<uint64_t> first(rows + 1);
-    CU(cudaMemcpyAsync(first.data(), hs.buf[bj_first].ptr, (rows + 1) * 8, cudaMemcpyDeviceToHost, stream));
-    CU(cudaStreamSynchronize(stream));
-    std::vector<uint32_t> byd;
-    for (uint32_t x = 0; x < rows; ++x)
-      if (first[x + 1] > first[x]) byd.push_back(x);
-    std::stable_sort(byd.begin(), byd.end(), [&](uint32_t p, uint32_t q) {
-      return first[p + 1] - first[p] > first[q + 1] - first[q];
-    });
-    std::vector<uint64_t> items;
-    std::vector<uint32_t> hslot(rows, 0);
-    uint32_t nheavy = 0;
-    for (uint32_t x : byd) {
-      const uint64_t nseg = (first[x + 1] - first[x] + kBitSeg - 1) / kBitSeg;
-      if (nseg > 1) hslot[x] = nheavy++;
-      for (uint64_t g = 0; g < nseg; ++g) items.push_back((uint64_t(x) << 32) | g);
-    }
-    nitems = items.size();
-    if ((s = ensure(bj_items, std::max<uint64_t>(nitems, 1))) || (s = ensure(bj_hslot, rows)) ||
-        (s = ensure(bj_hacc, std::max<uint64_t>(nheavy, 1) * nw)) || (s = ensure(bj_hdone, std::max<uint32_t>(nheavy, 1))))
-      return s;
-    if (nitems)
-      CU(cudaMemcpyAsync(hs.buf[bj_items].ptr, items.data(), nitems * 8, cudaMemcpyHostToDevice, stream));
-    CU(cudaMemcpyAsync(hs.buf[bj_hslot].ptr, hslot.data(), rows * 4, cudaMemcpyHostToDevice, stream));
-    CU(cudaMemsetAsync(hs.buf[bj_hacc].ptr, 0, std::max<uint64_t>(nheavy, 1) * nw * 4, stream));
-    CU(cudaMemsetAsync(hs.buf[bj_hdone].ptr, 0, std::max<uint32_t>(nheavy, 1) * 4, stream));
-    CU(cudaStreamSynchronize(stream));   // the host vectors are copied out before they go
-  }
+  // work items (row, segment of at most kBitSeg B tuples, chunk group), built
+  // on the device; a row of several segments gets an accumulator (at most
+  // min(rows, |B| / (kBitSeg + 1) + 1) of them)
+  const uint64_t nb = hs.cnt[B.base];
+  const uint64_t nh = std::min<uint64_t>(rows, nb / (kBitSeg + 1) + 1);
+  const uint64_t max_items = (nb / kBitSeg + rows) * bit_groups(b) + 1;
+  if ((s = ensure(bj_items, max_items)) || (s = ensure(bj_hslot, rows + 1)) || (s = ensure(bj_hacc, nh * nw)) ||
+      (s = ensure(bj_hdone, nh * kBitGroups)) || (s = ensure(sc.mrows, rows + 1)))
+    return s;
+  CU(cudaMemsetAsync(hs.buf[bj_hacc].ptr, 0, nh * nw * 4, stream));
+  CU(cudaMemsetAsync(hs.buf[bj_hdone].ptr, 0, nh * kBitGroups * 4, stream));
+  uint32_t* nheavy = static_cast<uint32_t*>(hs.buf[bj_hslot].ptr) + rows;
+  CU(cudaMemsetAsync(nheavy, 0, 4, stream));
+  uint64_t* item_offs = static_cast<uint64_t*>(hs.buf[sc.mrows].ptr);
+  launch_bit_items(BitItemsArgs{static_cast<const uint64_t*>(hs.buf[bj_first].ptr), item_offs,
+                                static_cast<uint64_t*>(hs.buf[bj_items].ptr),
+                                static_cast<uint32_t*>(hs.buf[bj_hslot].ptr), nheavy, b},
+                   grid, stream);
+  if ((s = check_launch("bit items"))) return s;
   auto* tot = static_cast<unsigned long long*>(hs.buf[bj_tot].ptr);
   uint32_t* D = static_cast<uint32_t*>(hs.buf[bj_d].ptr);
   uint32_t* D2 = static_cast<uint32_t*>(hs.buf[bj_d2].ptr);
@@ -904,7 +891,7 @@ hisa_status Engine::run_bitjoin(hisa_run_stats* stats, std::chrono::steady_clock
     BitJoinArgs ja{static_cast<const uint64_t*>(hs.buf[bj_first].ptr),
                    hs.buf[B.base].ptr,
                    static_cast<const uint64_t*>(hs.buf[bj_items].ptr),
-                   nitems,
+                   item_offs + rows,
                    static_cast<const uint32_t*>(hs.buf[bj_hslot].ptr),
                    static_cast<uint32_t*>(hs.buf[bj_hacc].ptr),
                    static_cast<uint32_t*>(hs.buf[bj_hdone].ptr),
