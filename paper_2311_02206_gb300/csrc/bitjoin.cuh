@@ -29,6 +29,7 @@ __host__ __device__ constexpr uint64_t bit_nchunks(int b) { return b >= 10 ? (1u
 __host__ __device__ constexpr uint64_t bit_mwords(int b) { return b >= 15 ? (1ull << (b - 15)) : 1ull; }
 
 constexpr int kBitSeg = 64;                                                 // B tuples per work item
+constexpr int kBitBatch = 8;                                                // items a warp takes at once
 constexpr int kBitGroups = 8;                                               // chunk groups of a row
 constexpr int kBitChunksPerWarp = (1 << (kBitMaxBits - 10)) / kBitGroups;   // 8 at b = 16
 __host__ __device__ constexpr uint32_t bit_groups(int b) {
@@ -146,6 +147,13 @@ struct BitJoinArgs {
   int b;
 };
 
+// Bits k = 0..7 of the result: mask bit g + 8k of row y (the chunks of group
+// g); rows of one or two mask words.
+__device__ __forceinline__ uint32_t group_bits(const uint32_t* mask, uint64_t y, uint64_t mw, uint32_t g) {
+  const uint64_t m = mw > 1 ? *reinterpret_cast<const unsigned long long*>(mask + y * mw) : uint64_t(mask[y * mw]);
+  return uint32_t((((m >> g) & 0x0101010101010101ull) * 0x0102040810204080ull) >> 56);
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kBitThreads) k_bitjoin(BitJoinArgs a) {
   const K* bc = static_cast<const K*>(a.bcodes);
@@ -154,14 +162,19 @@ __global__ void __launch_bounds__(kBitThreads) k_bitjoin(BitJoinArgs a) {
   const uint32_t vmask = (1u << a.b) - 1;
   const uint32_t cw = nw < 32 ? uint32_t(nw) : 32u;   // words of a chunk (b < 10: fewer than 32)
   unsigned long long cnt = 0, nloads = 0;
+  const uint64_t nitems = *a.nitems;
+  uint32_t next = 0, left = 0;   // this warp's batch of items
   while (true) {
-    uint64_t item = 0;
-    if (lane == 0) {
-      const uint32_t i = atomicAdd(a.ctr, 1u);
-      item = i < *a.nitems ? a.items[i] : ~0ull;
+    if (left == 0) {   // kBitBatch items per atomic: the counter is no bottleneck
+      uint32_t i0 = 0;
+      if (lane == 0) i0 = atomicAdd(a.ctr, uint32_t(kBitBatch));
+      next = __shfl_sync(0xffffffffu, i0, 0);
+      left = kBitBatch;
     }
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item == ~0ull) break;
+    if (next >= nitems) break;
+    const uint64_t item = a.items[next];
+    ++next;
+    --left;
     const uint32_t x = uint32_t(item >> 32), seg = uint32_t(item >> 8) & 0xFFFFFFu, g = uint32_t(item) & 0xFFu;
     const uint64_t f0 = a.first[x], f1 = a.first[x + 1];
     const uint64_t e0 = f0 + uint64_t(seg) * kBitSeg, e1 = min(f1, e0 + kBitSeg);
@@ -169,23 +182,27 @@ __global__ void __launch_bounds__(kBitThreads) k_bitjoin(BitJoinArgs a) {
     uint32_t acc[kBitChunksPerWarp];
 #pragma unroll
     for (int k = 0; k < kBitChunksPerWarp; ++k) acc[k] = 0;
+    // chunks of this group that exist (k with g + 8k < nch) and lanes that hold a word
+    uint32_t live = 0;
+    for (int k = 0; k < kBitChunksPerWarp; ++k)
+      if (uint64_t(g) + uint64_t(k) * kBitGroups < nch) live |= 1u << k;
+    if (lane >= cw) live = 0;
     for (uint64_t e = e0; e < e1; e += 2) {
       const bool ok1 = e + 1 < e1;
       const uint64_t y0 = uint64_t(bc[e]) & vmask;
       const uint64_t y1 = ok1 ? uint64_t(bc[e + 1]) & vmask : 0;
-      const uint32_t ma0 = a.Dmask[y0 * mw], mb0 = mw > 1 ? a.Dmask[y0 * mw + 1] : 0u;
-      const uint32_t ma1 = ok1 ? a.Dmask[y1 * mw] : 0u, mb1 = ok1 && mw > 1 ? a.Dmask[y1 * mw + 1] : 0u;
+      // this group's chunks g, g + 8, ... of each delta row's mask as the
+      // bits of one byte (every eighth mask bit gathered by a multiply)
+      const uint32_t s0 = group_bits(a.Dmask, y0, mw, g) & live;
+      const uint32_t s1 = ok1 ? group_bits(a.Dmask, y1, mw, g) & live : 0u;
       uint32_t v0[kBitChunksPerWarp], v1[kBitChunksPerWarp];
 #pragma unroll
       for (int k = 0; k < kBitChunksPerWarp; ++k) {   // every load issued before any is used
         const uint64_t c = uint64_t(g) + uint64_t(k) * kBitGroups;
-        const bool in = c < nch && lane < cw;
-        const bool p0 = in && (((c < 32 ? ma0 : mb0) >> (c & 31)) & 1u);
-        const bool p1 = in && (((c < 32 ? ma1 : mb1) >> (c & 31)) & 1u);
-        v0[k] = p0 ? a.D[y0 * nw + c * 32 + lane] : 0u;
-        v1[k] = p1 ? a.D[y1 * nw + c * 32 + lane] : 0u;
-        if (lane == 0) nloads += uint32_t(p0) + uint32_t(p1);
+        v0[k] = (s0 >> k) & 1u ? a.D[y0 * nw + c * 32 + lane] : 0u;
+        v1[k] = (s1 >> k) & 1u ? a.D[y1 * nw + c * 32 + lane] : 0u;
       }
+      if (lane == 0) nloads += __popc(s0) + __popc(s1);
 #pragma unroll
       for (int k = 0; k < kBitChunksPerWarp; ++k) acc[k] |= v0[k] | v1[k];
     }
