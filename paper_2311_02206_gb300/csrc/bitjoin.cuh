@@ -45,6 +45,7 @@ struct BitInitArgs {
   uint32_t* M;         // 2^b rows of bit_nwords(b) words
   uint32_t* mask;      // 2^b rows of bit_mwords(b) words
   uint32_t* M2;        // optional second matrix set alike (null: none)
+  unsigned long long* total;   // bits newly set in M (null: not counted)
 };
 
 template <typename K>
@@ -52,46 +53,24 @@ __global__ void k_bit_init(BitInitArgs a) {
   const K* codes = static_cast<const K*>(a.codes);
   const uint64_t nw = bit_nwords(a.b), mw = bit_mwords(a.b);
   const uint32_t vmask = (1u << a.b) - 1;
+  uint32_t fresh = 0;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < a.n; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t c = uint64_t(codes[i]);
     const uint64_t x = (c >> a.b) & vmask;
     const uint32_t z = uint32_t(c) & vmask;
     const uint32_t bit = 1u << (z & 31);
-    atomicOr(&a.M[x * nw + (z >> 5)], bit);
+    fresh += (atomicOr(&a.M[x * nw + (z >> 5)], bit) & bit) ? 0u : 1u;
     if (a.M2) atomicOr(&a.M2[x * nw + (z >> 5)], bit);
     const uint32_t chunk = z >> 10;
     atomicOr(&a.mask[x * mw + (chunk >> 5)], 1u << (chunk & 31));
   }
-}
-
-// Bits set in a matrix, summed into *total.
-struct BitCountArgs {
-  const uint32_t* M;
-  uint64_t words;
-  unsigned long long* total;
-};
-static __global__ void k_bit_count(BitCountArgs a) {
-  unsigned long long c = 0;
-  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < a.words; i += uint64_t(gridDim.x) * blockDim.x)
-    c += __popc(a.M[i]);
+  if (a.total) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.total, c);
+    for (int o = 16; o > 0; o >>= 1) fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
+    if ((threadIdx.x & 31) == 0 && fresh) atomicAdd(a.total, (unsigned long long)fresh);
+  }
 }
 
-// One iteration, over warp work items (row x, segment of at most kBitSeg of
-// its B tuples, chunk group g): warp items need no CTA barrier, and a hub's
-// thousands of tuples are spread over many warps.  The chunk group g of a row
-// of nch chunks is the chunks g, g + 8, ... (a chunk is 32 words, a word per
-// lane).  Items are handed out by an atomic counter, the heaviest rows'
-// first.  A warp ORs the delta rows its segment's tuples select, two tuples
-// at a time with all of their chunk loads issued before any is used (a
-// chunk is loaded only where the delta row's chunk mask is set).  A row of
-// one segment is finished by the warp: the difference with full, full ORed,
-// delta' and the chunk mask bits written, bits counted.  A row of several
-// segments ORs each partial result into its accumulator; the warp that
-// completes the chunk group (an arrival counter per row and group) takes the
-// accumulator back, leaving it and the counter zeroed, and finishes it.
 // The work items, built on the device: per row its item count (segments x
 // groups) and, for a row of several segments, an accumulator slot; a one-CTA
 // scan; every row's items written at its offset (rows in order: the hubs of

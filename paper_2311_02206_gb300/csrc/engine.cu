@@ -863,18 +863,16 @@ hisa_status Engine::run_bitjoin(hisa_run_stats* stats, std::chrono::steady_clock
   uint32_t* Dm = static_cast<uint32_t*>(hs.buf[bj_dm].ptr);
   uint32_t* Dm2 = static_cast<uint32_t*>(hs.buf[bj_dm2].ptr);
   uint32_t* F = static_cast<uint32_t*>(hs.buf[R.fbm].ptr);
-  // iteration 1: the non-recursive rules
+  // iteration 1: the non-recursive rules (|delta_1| counts the bits they set)
+  CU(cudaMemsetAsync(tot, 0, 16, stream));
   for (int e : bj_base) {
     const Relation& E = rels[e];
     if (!hs.cnt[E.base]) continue;
-    BitInitArgs ia{hs.buf[E.base].ptr, hs.cnt[E.base], b, D, Dm, F};
+    BitInitArgs ia{hs.buf[E.base].ptr, hs.cnt[E.base], b, D, Dm, F, tot};
     if (wide) launch_bit_init<uint64_t>(ia, grid, stream);
     else launch_bit_init<uint32_t>(ia, grid, stream);
     if ((s = check_launch("bit init"))) return s;
   }
-  CU(cudaMemsetAsync(tot, 0, 16, stream));
-  launch_bit_count(BitCountArgs{D, rows * nw, tot}, grid, stream);
-  if ((s = check_launch("bit count"))) return s;
   unsigned long long h[2] = {0, 0};
   CU(cudaMemcpyAsync(h, tot, 16, cudaMemcpyDeviceToHost, stream));
   CU(cudaStreamSynchronize(stream));

@@ -197,7 +197,6 @@ template <typename K> void launch_levels_transpose(const LevelsTransposeArgs& a,
 template <typename K> void launch_matrix_codes(const MatrixArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_matrix_diff(const MatrixDiffArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_bit_init(const BitInitArgs& a, const Grid& g, cudaStream_t s);
-void launch_bit_count(const BitCountArgs& a, const Grid& g, cudaStream_t s);
 void launch_bit_items(const BitItemsArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_bitjoin(const BitJoinArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_matrix_extract(const MatrixExtractArgs& a, const Grid& g, cudaStream_t s);
