@@ -341,6 +341,9 @@ void launch_zero(const ZeroArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKZero, s, (k_zero<<<g.small, 256, 0, s>>>(a)));
 }
 
+void launch_matrix_transpose(const MatrixTransposeArgs& t, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKDecode, s, (k_matrix_transpose<<<g.sms * 8, 256, 0, s>>>(t)));
+}
 void launch_bit_items(const BitItemsArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKBitInit, s, (k_bit_items_count<<<g.small, 256, 0, s>>>(a)));
   HISA_LAUNCH(kKBitInit, s, (k_bit_items_scan<<<1, 1024, 0, s>>>(a)));

@@ -200,6 +200,7 @@ template <typename K> void launch_bit_init(const BitInitArgs& a, const Grid& g, 
 void launch_bit_items(const BitItemsArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_bitjoin(const BitJoinArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_matrix_extract(const MatrixExtractArgs& a, const Grid& g, cudaStream_t s);
+void launch_matrix_transpose(const MatrixTransposeArgs& t, const Grid& g, cudaStream_t s);
 // a full kept as a bit matrix read in the declared order: transposed (order 1)
 // or read as it is (order 0), then its rows counted, scanned and written
 template <typename K> void launch_matrix_read(const MatrixTransposeArgs& t, const LevelsTransposeArgs& a, bool transpose,

@@ -144,6 +144,11 @@ struct MatrixExtractArgs {
   // instance slots whose blocks are read, in this order (device array; null:
   // the rows row0 ..): row i is then row i mod 2^b of block slots[i >> b]
   const uint32_t* slots = nullptr;
+  // a standalone block (a transposed copy): rows 0 .. nrows - 1 of fbm are
+  // read, counted by popcount (fcnt unused), and written as the codes of
+  // rows code_row0 + i
+  bool standalone = false;
+  uint64_t code_row0 = 0;
 };
 
 __device__ __forceinline__ uint64_t extract_row(const MatrixExtractArgs& a, uint64_t i) {
@@ -152,9 +157,17 @@ __device__ __forceinline__ uint64_t extract_row(const MatrixExtractArgs& a, uint
 }
 
 static __global__ void k_matrix_extract_counts(MatrixExtractArgs a) {
+  const uint64_t nw = a.b >= 5 ? (1ull << (a.b - 5)) : 1ull;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < a.nrows;
-       i += uint64_t(gridDim.x) * blockDim.x)
-    a.offs[i] = a.fcnt[extract_row(a, i)];
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    if (a.standalone) {
+      uint64_t c = 0;
+      for (uint64_t j = 0; j < nw; ++j) c += __popc(a.fbm[i * nw + j]);
+      a.offs[i] = c;
+    } else {
+      a.offs[i] = a.fcnt[extract_row(a, i)];
+    }
+  }
 }
 
 static __global__ void __launch_bounds__(1024) k_matrix_extract_scan(MatrixExtractArgs a) {
@@ -178,8 +191,8 @@ __global__ void __launch_bounds__(kDenseThreads) k_matrix_extract(MatrixExtractA
   K* out = static_cast<K*>(a.out);
   for (uint64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {
     if (a.offs[r + 1] == a.offs[r]) continue;   // uniform across the CTA
-    const uint64_t row = extract_row(a, r);
-    const uint32_t* rw = a.fbm + row * uint64_t(nwords);
+    const uint64_t row = a.standalone ? a.code_row0 + r : extract_row(a, r);
+    const uint32_t* rw = a.fbm + (a.standalone ? r : row) * uint64_t(nwords);
     uint32_t c = 0;
     for (int j = w0 + lane; j < w1; j += 32) c += __popc(rw[j]);
 #pragma unroll

@@ -461,12 +461,37 @@ hisa_status Engine::retire(const std::vector<uint64_t>& tickets) {
       }
       if (total > 0) {
         if ((s = ensure(sc.gather, total))) return s;
-        std::vector<uint32_t> blocks;   // one read-out of all finished blocks, in slot order
-        for (size_t k = 0; k < tickets.size(); ++k)
-          if (cnt[k]) blocks.push_back(uint32_t(reqs[tickets[k]].slot));
-        if ((s = matrix_rows_out(R, 0, 0, sc.gather, 0, &blocks))) return s;
-        int src = -1;
-        if ((s = resort(sc.gather, 0, total, R.order == 1, &src))) return s;
+        int src = sc.gather;
+        if (R.order == 1 && b >= 8) {
+          // stored column-swapped: each block transposed (256 x 256-bit tiles)
+          // and its rows read out in the declared order, no sort
+          const uint64_t nw = 1ull << (b - 5);
+          if ((s = ensure(sc.read_m, (1ull << b) * nw)) || (s = ensure(sc.mrows, (1ull << b) + 1))) return s;
+          uint64_t w = 0;
+          for (size_t k = 0; k < tickets.size(); ++k) {
+            if (!cnt[k]) continue;
+            const uint64_t slot = uint64_t(reqs[tickets[k]].slot);
+            uint32_t* tm = static_cast<uint32_t*>(hs.buf[sc.read_m].ptr);
+            launch_matrix_transpose(MatrixTransposeArgs{static_cast<const uint32_t*>(hs.buf[R.fbm].ptr) +
+                                                            (slot << b) * nw, tm, b},
+                                    grid, stream);
+            MatrixExtractArgs xa{tm, nullptr, 0, 1ull << b, b, static_cast<uint64_t*>(hs.buf[sc.mrows].ptr),
+                                 static_cast<char*>(hs.buf[sc.gather].ptr) + w * kb};
+            xa.standalone = true;
+            xa.code_row0 = slot << b;
+            if (wide) launch_matrix_extract<uint64_t>(xa, grid, stream);
+            else launch_matrix_extract<uint32_t>(xa, grid, stream);
+            CU(cudaGetLastError());
+            w += cnt[k];
+          }
+        } else {
+          std::vector<uint32_t> blocks;   // one read-out of all finished blocks, in slot order
+          for (size_t k = 0; k < tickets.size(); ++k)
+            if (cnt[k]) blocks.push_back(uint32_t(reqs[tickets[k]].slot));
+          if ((s = matrix_rows_out(R, 0, 0, sc.gather, 0, &blocks))) return s;
+          // (stored in the declared order: the rows are sorted already)
+          if (R.order == 1 && (s = resort(sc.gather, 0, total, true, &src))) return s;
+        }
         hs.cnt[src] = total;
         uint64_t at = 0;
         for (size_t k = 0; k < tickets.size(); ++k) {   // instances stay in slot order
