@@ -82,13 +82,47 @@ struct BitItemsArgs {
   uint32_t* hslot;
   uint32_t* nheavy;        // zeroed before the launch
   int b;
+  // rows to work this iteration (a bit each; null: every row with B tuples,
+  // and the rows of several segments get their accumulators)
+  const uint32_t* todo;
 };
 static __global__ void k_bit_items_count(BitItemsArgs a) {
   const uint64_t rows = 1ull << a.b;
   for (uint64_t x = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; x < rows; x += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t nseg = (a.first[x + 1] - a.first[x] + kBitSeg - 1) / kBitSeg;
-    a.offs[x] = nseg * bit_groups(a.b);
-    if (nseg > 1) a.hslot[x] = atomicAdd(a.nheavy, 1u);
+    if (a.todo) {
+      a.offs[x] = ((a.todo[x >> 5] >> (x & 31)) & 1u) ? nseg * bit_groups(a.b) : 0;
+    } else {
+      a.offs[x] = nseg * bit_groups(a.b);
+      if (nseg > 1) a.hslot[x] = atomicAdd(a.nheavy, 1u);
+    }
+  }
+}
+
+// The rows an iteration must work: every x with a B tuple (x, y) whose delta
+// row y is non-empty (its chunk mask); a thread per B tuple.  Rows whose B
+// tuples all select empty delta rows derive nothing.
+struct BitTodoArgs {
+  const uint32_t* Dmask;
+  const void* bcodes;      // B's codes (K): (x << b) | y
+  uint64_t n;
+  uint32_t* todo;          // zeroed before the launch
+  int b;
+};
+template <typename K>
+__global__ void k_bit_todo(BitTodoArgs a) {
+  const uint64_t mw = bit_mwords(a.b);
+  const uint32_t vmask = (1u << a.b) - 1;
+  const K* bc = static_cast<const K*>(a.bcodes);
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < a.n; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t c = uint64_t(bc[i]);
+    const uint64_t y = c & vmask;
+    uint32_t any = a.Dmask[y * mw];
+    if (mw > 1) any |= a.Dmask[y * mw + 1];
+    if (!any) continue;
+    const uint32_t x = uint32_t(c >> a.b) & vmask;
+    const uint32_t bit = 1u << (x & 31);
+    if (!(a.todo[x >> 5] & bit)) atomicOr(&a.todo[x >> 5], bit);
   }
 }
 static __global__ void __launch_bounds__(1024) k_bit_items_scan(BitItemsArgs a) {

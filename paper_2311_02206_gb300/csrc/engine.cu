@@ -761,6 +761,9 @@ hisa_status Engine::compile() {
       bj_hslot = new_slot(4);
       bj_hacc = new_slot(4);
       bj_hdone = new_slot(4);
+      bj_todo = new_slot(4);
+      bj_items2 = new_slot(8);
+      bj_offs2 = new_slot(8);
     }
   }
   compiled = true;
@@ -832,6 +835,8 @@ hisa_status Engine::run_bitjoin(hisa_run_stats* stats, std::chrono::steady_clock
   CU(cudaMemsetAsync(hs.buf[bj_dm].ptr, 0, rows * mw * 4, stream));
   if ((s = upload())) return s;
   // B's run of each first column: a direct index over its sorted codes
+  if ((s = ensure(bj_todo, (rows + 31) / 32))) return s;
+  if ((s = upload())) return s;
   {
     std::vector<Op> ops(1);
     ops[0].kind = Op::INDEX;
@@ -852,11 +857,21 @@ hisa_status Engine::run_bitjoin(hisa_run_stats* stats, std::chrono::steady_clock
   uint32_t* nheavy = static_cast<uint32_t*>(hs.buf[bj_hslot].ptr) + rows;
   CU(cudaMemsetAsync(nheavy, 0, 4, stream));
   uint64_t* item_offs = static_cast<uint64_t*>(hs.buf[sc.mrows].ptr);
-  launch_bit_items(BitItemsArgs{static_cast<const uint64_t*>(hs.buf[bj_first].ptr), item_offs,
-                                static_cast<uint64_t*>(hs.buf[bj_items].ptr),
-                                static_cast<uint32_t*>(hs.buf[bj_hslot].ptr), nheavy, b},
-                   grid, stream);
+  BitItemsArgs ita{static_cast<const uint64_t*>(hs.buf[bj_first].ptr), item_offs,
+                   static_cast<uint64_t*>(hs.buf[bj_items].ptr), static_cast<uint32_t*>(hs.buf[bj_hslot].ptr),
+                   nheavy, b, nullptr};
+  launch_bit_items(ita, grid, stream);   // every row with B tuples, and the accumulator slots
   if ((s = check_launch("bit items"))) return s;
+  // a sparse delta (below 256 bits per row on average): only the rows with a
+  // B tuple selecting a non-empty delta row are worked, from items made for
+  // the iteration; a dense one takes every row's items
+  if ((s = ensure(bj_items2, max_items)) || (s = ensure(bj_offs2, rows + 1))) return s;
+  uint32_t* todo = static_cast<uint32_t*>(hs.buf[bj_todo].ptr);
+  BitItemsArgs itb = ita;
+  itb.offs = static_cast<uint64_t*>(hs.buf[bj_offs2].ptr);
+  itb.items = static_cast<uint64_t*>(hs.buf[bj_items2].ptr);
+  itb.todo = todo;
+  const uint64_t sparse_below = rows * 256;
   auto* tot = static_cast<unsigned long long*>(hs.buf[bj_tot].ptr);
   uint32_t* D = static_cast<uint32_t*>(hs.buf[bj_d].ptr);
   uint32_t* D2 = static_cast<uint32_t*>(hs.buf[bj_d2].ptr);
@@ -883,13 +898,22 @@ hisa_status Engine::run_bitjoin(hisa_run_stats* stats, std::chrono::steady_clock
   uint32_t iters_run = 1;
   uint64_t d = h[0];
   while (d > 0 && iters_run < cfg.max_iters) {
+    const bool sparse = d < sparse_below;
+    if (sparse) {   // this iteration's rows: those with a B tuple selecting a non-empty delta row
+      CU(cudaMemsetAsync(todo, 0, (rows + 31) / 32 * 4, stream));
+      if (wide) launch_bit_todo<uint64_t>(BitTodoArgs{Dm, hs.buf[B.base].ptr, nb, todo, b}, grid, stream);
+      else launch_bit_todo<uint32_t>(BitTodoArgs{Dm, hs.buf[B.base].ptr, nb, todo, b}, grid, stream);
+      launch_bit_items(itb, grid, stream);
+      if ((s = check_launch("bit items"))) return s;
+    }
+    const BitItemsArgs& it = sparse ? itb : ita;
     CU(cudaMemsetAsync(tot, 0, 16, stream));
     CU(cudaMemsetAsync(hs.buf[bj_ctr].ptr, 0, 4, stream));
     CU(cudaMemsetAsync(Dm2, 0, rows * mw * 4, stream));
     BitJoinArgs ja{static_cast<const uint64_t*>(hs.buf[bj_first].ptr),
                    hs.buf[B.base].ptr,
-                   static_cast<const uint64_t*>(hs.buf[bj_items].ptr),
-                   item_offs + rows,
+                   it.items,
+                   it.offs + rows,
                    static_cast<const uint32_t*>(hs.buf[bj_hslot].ptr),
                    static_cast<uint32_t*>(hs.buf[bj_hacc].ptr),
                    static_cast<uint32_t*>(hs.buf[bj_hdone].ptr),

@@ -192,7 +192,7 @@ class Engine {
   int bj_rel = -1, bj_inner = -1;   // R and B of R(x, z) <- B(x, y), R(y, z)
   std::vector<int> bj_base;         // E of the rules R(x, y) <- E(x, y)
   int bj_first = -1, bj_d = -1, bj_d2 = -1, bj_dm = -1, bj_dm2 = -1, bj_tot = -1, bj_ctr = -1;
-  int bj_items = -1, bj_hslot = -1, bj_hacc = -1, bj_hdone = -1;
+  int bj_items = -1, bj_hslot = -1, bj_hacc = -1, bj_hdone = -1, bj_todo = -1, bj_items2 = -1, bj_offs2 = -1;
   hisa_status plan_variant(const hisa_rule& R, int delta_atom, std::vector<StepPlan>& out);
   void emit_join(std::vector<Op>& ops, const StepPlan& sp);
   void emit_dense(std::vector<Op>& ops, const StepPlan& sp, bool chain_groups = false, int inner_buf = -1,

@@ -199,6 +199,7 @@ template <typename K> void launch_matrix_diff(const MatrixDiffArgs& a, const Gri
 template <typename K> void launch_bit_init(const BitInitArgs& a, const Grid& g, cudaStream_t s);
 void launch_bit_items(const BitItemsArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_bitjoin(const BitJoinArgs& a, const Grid& g, cudaStream_t s);
+template <typename K> void launch_bit_todo(const BitTodoArgs& a, const Grid& g, cudaStream_t s);
 template <typename K> void launch_matrix_extract(const MatrixExtractArgs& a, const Grid& g, cudaStream_t s);
 void launch_matrix_transpose(const MatrixTransposeArgs& t, const Grid& g, cudaStream_t s);
 // a full kept as a bit matrix read in the declared order: transposed (order 1)

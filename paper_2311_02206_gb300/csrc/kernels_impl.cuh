@@ -211,6 +211,10 @@ void launch_bit_init(const BitInitArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKBitInit, s, (k_bit_init<K><<<g.small, 256, 0, s>>>(a)));
 }
 template <typename K>
+void launch_bit_todo(const BitTodoArgs& a, const Grid& g, cudaStream_t s) {
+  HISA_LAUNCH(kKBitInit, s, (k_bit_todo<K><<<g.small, 256, 0, s>>>(a)));
+}
+template <typename K>
 void launch_bitjoin(const BitJoinArgs& a, const Grid& g, cudaStream_t s) {
   HISA_LAUNCH(kKBitJoin, s, (k_bitjoin<K><<<g.sms * 8, kBitThreads, 0, s>>>(a)));
 }
@@ -373,6 +377,7 @@ void launch_join_write(const JoinArgs& a, const Grid& g, cudaStream_t s) {
   template void launch_matrix_diff<K>(const MatrixDiffArgs&, const Grid&, cudaStream_t); \
   template void launch_bit_init<K>(const BitInitArgs&, const Grid&, cudaStream_t);       \
   template void launch_bitjoin<K>(const BitJoinArgs&, const Grid&, cudaStream_t);        \
+  template void launch_bit_todo<K>(const BitTodoArgs&, const Grid&, cudaStream_t);      \
   template void launch_matrix_extract<K>(const MatrixExtractArgs&, const Grid&, cudaStream_t); \
   template void launch_matrix_read<K>(const MatrixTransposeArgs&, const LevelsTransposeArgs&, bool, const Grid&, \
                                       cudaStream_t);                                     \
