@@ -782,9 +782,6 @@ bool Engine::detect_bitjoin() {
   bj_rel = bj_inner = -1;
   if (batched || serving || idb.size() != 1 || b > kBitMaxBits) return false;
   if (cfg.flags & (HISA_FLAG_NO_BITJOIN | HISA_FLAG_NO_DENSE | HISA_FLAG_NO_PULL | HISA_FLAG_LEVELS)) return false;
-  // three matrices (delta, delta', full) and the accumulators of split rows,
-  // at most 4 x 2^(2b) / 8 bytes: not when they alone exceed a memory budget
-  if (cfg.hbm_budget_bytes && 4 * ((1ull << (2 * b)) / 8) > cfg.hbm_budget_bytes) return false;
   const uint32_t r = uint32_t(idb[0]);
   int recursive = 0;
   for (const hisa_rule& q : rules) {
