@@ -65,7 +65,8 @@ def _args():
     ap.add_argument("--no-dense", action="store_true",
                     help="sort raw join results instead of the grouped bitmap join (HISA_FLAG_NO_DENSE)")
     ap.add_argument("--load-factor", type=float, default=0.0, help="hash-index load factor (0: the library default)")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10,
+                    help="end-to-end steps timed (every one is reported)")
     ap.add_argument("--partitioned", action="store_true",
                     help="REACH hash-partitioned over the ranks (one all-to-all per iteration; strong scaling)")
     ap.add_argument("--no-sub", action="store_true",
