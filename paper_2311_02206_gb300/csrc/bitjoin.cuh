@@ -267,4 +267,121 @@ __global__ void __launch_bounds__(kBitThreads) k_bitjoin(BitJoinArgs a) {
   if (lane == 0 && nloads) atomicAdd(a.loads, nloads);
 }
 
+// The same iteration with 16-byte loads, for rows of whole 32-word chunks
+// (b >= 10): lane l holds words 4 (l mod 8) .. + 3 of chunk k = 4p + l / 8 of
+// the group (p = 0, 1), so one warp load covers four chunks and a B tuple's
+// eight chunks take two loads instead of eight.
+__device__ __forceinline__ void or4(uint4& a, const uint4& v) {
+  a.x |= v.x;
+  a.y |= v.y;
+  a.z |= v.z;
+  a.w |= v.w;
+}
+__device__ __forceinline__ bool any4(const uint4& v) { return (v.x | v.y | v.z | v.w) != 0u; }
+
+template <typename K>
+__global__ void __launch_bounds__(kBitThreads) k_bitjoin_vec(BitJoinArgs a) {
+  const K* bc = static_cast<const K*>(a.bcodes);
+  const int lane = threadIdx.x & 31, sub = lane >> 3, w4 = (lane & 7) * 4;
+  const uint64_t nw = bit_nwords(a.b), nch = bit_nchunks(a.b), mw = bit_mwords(a.b);
+  const uint32_t vmask = (1u << a.b) - 1;
+  unsigned long long cnt = 0, nloads = 0;
+  const uint64_t nitems = *a.nitems;
+  uint32_t next = 0, left = 0;   // this warp's batch of items
+  while (true) {
+    if (left == 0) {
+      uint32_t i0 = 0;
+      if (lane == 0) i0 = atomicAdd(a.ctr, uint32_t(kBitBatch));
+      next = __shfl_sync(0xffffffffu, i0, 0);
+      left = kBitBatch;
+    }
+    if (next >= nitems) break;
+    const uint64_t item = a.items[next];
+    ++next;
+    --left;
+    const uint32_t x = uint32_t(item >> 32), seg = uint32_t(item >> 8) & 0xFFFFFFu, g = uint32_t(item) & 0xFFu;
+    const uint64_t f0 = a.first[x], f1 = a.first[x + 1];
+    const uint64_t e0 = f0 + uint64_t(seg) * kBitSeg, e1 = min(f1, e0 + kBitSeg);
+    const uint32_t nseg = uint32_t((f1 - f0 + kBitSeg - 1) / kBitSeg);
+    // this lane's two chunks (k = sub, 4 + sub) and whether they exist
+    const uint64_t c0 = uint64_t(g) + uint64_t(sub) * kBitGroups, c1 = c0 + 4ull * kBitGroups;
+    const uint32_t live = (c0 < nch ? 1u : 0u) | (c1 < nch ? 2u : 0u);
+    uint4 acc0 = make_uint4(0, 0, 0, 0), acc1 = make_uint4(0, 0, 0, 0);
+    for (uint64_t e = e0; e < e1; e += 2) {
+      const bool ok1 = e + 1 < e1;
+      const uint64_t y0 = uint64_t(bc[e]) & vmask;
+      const uint64_t y1 = ok1 ? uint64_t(bc[e + 1]) & vmask : 0;
+      const uint32_t sa = group_bits(a.Dmask, y0, mw, g);
+      const uint32_t sb = ok1 ? group_bits(a.Dmask, y1, mw, g) : 0u;
+      // bits 0, 1: this lane's chunks of the two delta rows
+      const uint32_t m0 = (((sa >> sub) & 1u) | (((sa >> (4 + sub)) & 1u) << 1)) & live;
+      const uint32_t m1 = (((sb >> sub) & 1u) | (((sb >> (4 + sub)) & 1u) << 1)) & live;
+      const uint4 z = make_uint4(0, 0, 0, 0);
+      const uint4 v00 = m0 & 1u ? *reinterpret_cast<const uint4*>(a.D + y0 * nw + c0 * 32 + w4) : z;
+      const uint4 v01 = m0 & 2u ? *reinterpret_cast<const uint4*>(a.D + y0 * nw + c1 * 32 + w4) : z;
+      const uint4 v10 = m1 & 1u ? *reinterpret_cast<const uint4*>(a.D + y1 * nw + c0 * 32 + w4) : z;
+      const uint4 v11 = m1 & 2u ? *reinterpret_cast<const uint4*>(a.D + y1 * nw + c1 * 32 + w4) : z;
+      if (lane == 0) nloads += __popc(sa & 0xFFu) + __popc(sb & 0xFFu);
+      or4(acc0, v00);
+      or4(acc0, v10);
+      or4(acc1, v01);
+      or4(acc1, v11);
+    }
+    if (nseg > 1) {   // a partial row: into the row's accumulator; the last arrival finishes the group
+      const uint32_t hs = a.hslot[x];
+      uint32_t* h = a.hacc + uint64_t(hs) * nw;
+      const uint32_t* p0 = &acc0.x;
+      const uint32_t* p1 = &acc1.x;
+      for (int q = 0; q < 4; ++q) {
+        if ((live & 1u) && p0[q]) atomicOr(&h[c0 * 32 + w4 + q], p0[q]);
+        if ((live & 2u) && p1[q]) atomicOr(&h[c1 * 32 + w4 + q], p1[q]);
+      }
+      __threadfence();
+      __syncwarp();
+      uint32_t last = 0;
+      if (lane == 0) last = atomicAdd(&a.hdone[uint64_t(hs) * kBitGroups + g], 1u) == nseg - 1;
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (!last) continue;
+      __threadfence();
+      uint32_t* q0 = &acc0.x;
+      uint32_t* q1 = &acc1.x;
+      for (int q = 0; q < 4; ++q) {
+        if (live & 1u) {
+          q0[q] = __ldcg(&h[c0 * 32 + w4 + q]);
+          h[c0 * 32 + w4 + q] = 0;
+        }
+        if (live & 2u) {
+          q1[q] = __ldcg(&h[c1 * 32 + w4 + q]);
+          h[c1 * 32 + w4 + q] = 0;
+        }
+      }
+      if (lane == 0) a.hdone[uint64_t(hs) * kBitGroups + g] = 0;
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      if (!__any_sync(0xffffffffu, (live >> p) & 1u)) break;
+      const uint64_t c = p ? c1 : c0;
+      const uint4 ac = p ? acc1 : acc0;
+      uint4 d = make_uint4(0, 0, 0, 0);
+      if (((live >> p) & 1u) && any4(ac)) {   // new bits of these words: not yet in full
+        uint4* rw = reinterpret_cast<uint4*>(a.R + uint64_t(x) * nw + c * 32 + w4);
+        const uint4 r = *rw;
+        d = make_uint4(ac.x & ~r.x, ac.y & ~r.y, ac.z & ~r.z, ac.w & ~r.w);
+        if (any4(d)) *rw = make_uint4(r.x | d.x, r.y | d.y, r.z | d.z, r.w | d.w);
+      }
+      // a chunk is the 8 lanes of one quarter of the warp
+      const uint32_t bal = __ballot_sync(0xffffffffu, any4(d));
+      if ((bal >> (sub * 8)) & 0xFFu) {
+        *reinterpret_cast<uint4*>(a.D2 + uint64_t(x) * nw + c * 32 + w4) = d;
+        if ((lane & 7) == 0) atomicOr(&a.D2mask[uint64_t(x) * mw + (c >> 5)], 1u << (c & 31));
+      }
+      cnt += __popc(d.x) + __popc(d.y) + __popc(d.z) + __popc(d.w);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0 && cnt) atomicAdd(a.total, cnt);
+  if (lane == 0 && nloads) atomicAdd(a.loads, nloads);
+}
+
 }  // namespace hisa

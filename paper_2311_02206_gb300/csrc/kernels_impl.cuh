@@ -216,7 +216,8 @@ void launch_bit_todo(const BitTodoArgs& a, const Grid& g, cudaStream_t s) {
 }
 template <typename K>
 void launch_bitjoin(const BitJoinArgs& a, const Grid& g, cudaStream_t s) {
-  HISA_LAUNCH(kKBitJoin, s, (k_bitjoin<K><<<g.sms * 8, kBitThreads, 0, s>>>(a)));
+  if (a.b >= 10) HISA_LAUNCH(kKBitJoin, s, (k_bitjoin_vec<K><<<g.sms * 8, kBitThreads, 0, s>>>(a)));
+  else HISA_LAUNCH(kKBitJoin, s, (k_bitjoin<K><<<g.sms * 8, kBitThreads, 0, s>>>(a)));
 }
 template <typename K>
 void launch_matrix_extract(const MatrixExtractArgs& a, const Grid& g, cudaStream_t s) {
